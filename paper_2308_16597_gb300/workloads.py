@@ -1,0 +1,152 @@
+"""Seeded synthetic inputs for the sedimentation workloads.
+
+This module only places particles and states the physical parameters of each
+workload; it holds none of the lattice Boltzmann arithmetic, so both the CUDA
+path and the FP64 oracle take their inputs from here.
+
+The workloads follow the paper's sedimentation benchmarks (Sec. 2.6.3: hot
+disks settling in a cold cavity, all four walls no-slip at the cold
+temperature, particles seeded in the upper part).  Particle centres are drawn
+by random sequential addition from a PCG64 stream, with a minimum centre
+distance of 2r + s + 1 so that no two disks start inside each other's
+repulsion range (s = 3 lattice units, Sec. 2.4).  The Rayleigh number
+Ra = Pr * Gr with Gr = g beta dT L^3 / nu^2 (Sec. 2.1) fixes the gravity.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PARTICLE_FIELDS = ("x", "y", "ux", "uy", "theta", "omega", "r", "rho", "T")
+PARTICLE_DTYPE = np.dtype([(n, "f8") for n in PARTICLE_FIELDS])
+
+S_REP = 3.0  # repulsion threshold, lattice units (Sec. 2.4)
+
+
+@dataclass
+class Workload:
+    name: str
+    domain: dict
+    particles: np.ndarray
+    params: dict
+    steps: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def nx(self) -> int:
+        return int(self.domain["nx"])
+
+    @property
+    def ny(self) -> int:
+        return int(self.domain["ny"])
+
+
+def gravity_for_rayleigh(Ra: float, nu: float, alpha: float, H: float, beta: float = 1.0,
+                         dT: float = 1.0) -> float:
+    """g such that Ra = g beta dT H^3 / (nu alpha)."""
+    return Ra * nu * alpha / (beta * dT * H ** 3)
+
+
+def rsa_disks(rng: np.random.Generator, n: int, radii, xlo, xhi, ylo, yhi,
+              min_gap: float, max_tries: int = 2_000_000) -> np.ndarray:
+    """Random sequential addition of n disks with centres in [xlo,xhi]x[ylo,yhi]
+    and centre distance >= r_a + r_b + min_gap.  radii: scalar or length-n."""
+    radii = np.broadcast_to(np.asarray(radii, dtype=np.float64), (n,)).copy()
+    rmax = float(radii.max()) if n else 0.0
+    cell = 2.0 * rmax + min_gap
+    grid: dict = {}
+    xs = np.empty(n)
+    ys = np.empty(n)
+    placed = 0
+    tries = 0
+    while placed < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("random sequential addition could not place %d disks" % n)
+        r = radii[placed]
+        x = rng.uniform(xlo, xhi)
+        y = rng.uniform(ylo, yhi)
+        cx, cy = int(x // cell), int(y // cell)
+        ok = True
+        for gx in (cx - 1, cx, cx + 1):
+            for gy in (cy - 1, cy, cy + 1):
+                for k in grid.get((gx, gy), ()):
+                    if math.hypot(x - xs[k], y - ys[k]) < r + radii[k] + min_gap:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if not ok:
+            continue
+        xs[placed], ys[placed] = x, y
+        grid.setdefault((cx, cy), []).append(placed)
+        placed += 1
+    out = np.zeros(n, PARTICLE_DTYPE)
+    out["x"], out["y"], out["r"] = xs, ys, radii
+    return out
+
+
+def base_params(nu: float, Pr: float, g: float, beta: float = 1.0, **kw) -> dict:
+    p = dict(nu=nu, alpha=nu / Pr, g=g, beta=beta, T0=0.0, rho_f=1.0, T_init=0.0,
+             s_e=0.0, s_eps=0.0, s_q=0.0, q_e=0.0, q_nu=0.0, eps_w=1e-3, s_rep=S_REP,
+             body_fx=0.0, body_fy=0.0, fixed_particles=0)
+    p.update(kw)
+    return p
+
+
+def cavity(nx: int, ny: int, T_wall=(0.0, 0.0, 0.0, 0.0), periodic_x=0, periodic_y=0) -> dict:
+    return dict(nx=nx, ny=ny, periodic_x=periodic_x, periodic_y=periodic_y,
+                T_wall=tuple(float(t) for t in T_wall))
+
+
+def sedimentation(nx, ny, n, radius, rho_ratio, y_frac, seed, nu, Pr, g, T_p=1.0,
+                  name="sedimentation", steps=0) -> Workload:
+    """Hot disks seeded in the upper (1 - y_frac) part of a cold closed cavity."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = float(radius)
+    lo = r + S_REP + 1.0
+    parts = rsa_disks(rng, n, r, lo, nx - 1 - lo, max(y_frac * ny + r + S_REP, lo),
+                      ny - 1 - lo, min_gap=S_REP + 1.0)
+    parts["rho"] = rho_ratio
+    parts["T"] = T_p
+    return Workload(name, cavity(nx, ny), parts, base_params(nu, Pr, g), steps)
+
+
+def parity_256(seed: int = 2308) -> Workload:
+    """256x256 cavity, 8 hot disks r = 10 in the upper half, density ratio 1.5,
+    g = 1e-5, Pr = 0.71, nu = 0.02, beta = 1, 1000 steps."""
+    return sedimentation(256, 256, 8, 10.0, 1.5, 0.5, seed, nu=0.02, Pr=0.71, g=1e-5,
+                         name="cavity256_8disks", steps=1000)
+
+
+def sedimentation_4000(seed: int = 16597) -> Workload:
+    """4000x4000 cavity, 4800 hot disks r = 10 (solid fraction 9.4 %) in the upper
+    60 %, density ratio 1.5, Pr = 0.71, nu = 0.02, Ra = 1e8 on H = 4000."""
+    nu, Pr = 0.02, 0.71
+    g = gravity_for_rayleigh(1e8, nu, nu / Pr, 4000.0)
+    return sedimentation(4000, 4000, 4800, 10.0, 1.5, 0.4, seed, nu=nu, Pr=Pr, g=g,
+                         name="cavity4000_4800disks_r10", steps=10000)
+
+
+def crop_1024(seed: int = 3) -> Workload:
+    """1024x1024 crop with 300 disks r = 10 in the upper half (reduced storage)."""
+    return sedimentation(1024, 1024, 300, 10.0, 1.5, 0.5, seed, nu=0.02, Pr=0.71, g=1e-5,
+                         name="cavity1024_300disks", steps=1000)
+
+
+def random_state(nx: int, ny: int, seed: int, base_f, base_g, amp: float = 1e-3,
+                 T_amp: float = 0.5):
+    """Seeded perturbation of given per-direction base values (e.g. a rest
+    equilibrium): f = base_f (1 + amp N(0,1)), g = base_g T (1 + amp N(0,1)) with
+    T uniform in [0, T_amp).  Returned as f[9][ny][nx], g[5][ny][nx] in FP64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    bf = np.asarray(base_f, dtype=np.float64)
+    bg = np.asarray(base_g, dtype=np.float64)
+    f = bf[:, None, None] * (1.0 + amp * rng.standard_normal((9, ny, nx)))
+    T = T_amp * rng.uniform(0.0, 1.0, (ny, nx))
+    g = bg[:, None, None] * T[None] * (1.0 + amp * rng.standard_normal((5, ny, nx)))
+    return f, g
