@@ -1,0 +1,354 @@
+"""Benchmark: MLUPS and HBM-roofline fraction of the fused FP32 step on the
+4000 x 4000 cavity with 4800 hot disks of radius 10 (the paper's
+sedimentation benchmark shape, Sec. 2.6.3 / Sec. 3).
+
+One bench step = one full time step of the method: link gather + curved
+bounce-back + momentum exchange, particle update, owner map and flags, and the
+fused stream-collide-refill over all 16 M nodes.  MLUPS counts every node,
+solid ones included (the paper's definition, Sec. 3).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the method is
+not sharded here) and rank 0 prints the whole-job MLUPS over the slowest
+rank's time.  ``--impl reference`` times the FP64 CPU oracle on the host cores
+on a bounded 1000 x 1000 crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2308_16597_gb300 import metrics, workloads as W  # noqa: E402
+
+METRIC = "MLUPS"
+UNIT = "MLUPS"
+CROP = 1000
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank scalar over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes_per_rank: int, steps: int, world: int, max_seconds: float) -> float:
+    """Whole-job MLUPS: lattice updates of all ranks over the slowest rank's time."""
+    return metrics.mlups(nodes_per_rank * world, 1, steps, max_seconds)
+
+
+def crop(wl: W.Workload, size: int) -> W.Workload:
+    """A size x size cavity holding the disks of the workload's lower-left
+    window that lies in the seeded band (same density, radius, parameters)."""
+    y0 = wl.ny - size - 1
+    p = wl.particles
+    r = p["r"]
+    keep = (p["x"] - r > 4) & (p["x"] + r < size - 5) & (p["y"] - r > y0 + 4) & \
+           (p["y"] + r < y0 + size - 5)
+    parts = p[keep].copy()
+    parts["y"] -= y0
+    return W.Workload("%s_crop%d" % (wl.name, size), W.cavity(size, size), parts, dict(wl.params))
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel's file; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2308_16597_gb300", "csrc", e["source"])
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if digest != e.get("source_sha256_16"):
+        return None
+    return e["bytes_per_launch_full"]
+
+
+# ------------------------------------------------------------------------------------ oracle
+def cpu_baseline(wl: W.Workload, steps: int, warmup: int = 0):
+    """FP64 oracle on the host cores, on the CROP x CROP sample of the workload."""
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    import oracle.oracle as orc
+    sample = crop(wl, CROP)
+    ref = orc.Oracle(sample.domain, sample.particles, sample.params)
+    if warmup:
+        ref.step(warmup)
+    t0 = time.perf_counter()
+    ref.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": metrics.mlups(sample.nx, sample.ny, steps, dt), "unit": UNIT,
+            "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+            "sample": "%dx%d crop of the %s workload with %d disks, %d FP64 oracle steps"
+                      % (sample.nx, sample.ny, wl.name, len(sample.particles), steps),
+            "seconds": dt}
+
+
+def reference_sample(wl, steps: int, budget_s: float = 90.0) -> W.Workload:
+    """Crop of the workload sized so that `steps` oracle steps take about
+    budget_s on this host (probed with one step of a 256 x 256 crop)."""
+    import oracle.oracle as orc
+    probe = crop(wl, 256)
+    ref = orc.Oracle(probe.domain, probe.particles, probe.params)
+    t0 = time.perf_counter()
+    ref.step(1)
+    per_node = (time.perf_counter() - t0) / (256 * 256)
+    side = int((budget_s / max(steps, 1) / per_node) ** 0.5) // 8 * 8
+    return crop(wl, max(128, min(CROP, side)))
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    import oracle.oracle as orc
+    sample = reference_sample(wl, args.steps + args.warmup)
+    ref = orc.Oracle(sample.domain, sample.particles, sample.params)
+    ref.step(args.warmup)
+    t0 = time.perf_counter()
+    ref.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = metrics.mlups(sample.nx, sample.ny, args.steps, dt)
+    sample_desc = "%dx%d crop of %s (%d disks), one FP64 oracle step per bench step" % (
+        sample.nx, sample.ny, wl.name, len(sample.particles))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(wl, args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": sample_desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(wl, args):
+    p = wl.particles
+    return {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "particles": int(len(p)),
+            "radius": float(p["r"][0]) if len(p) else None, "storage": "fp32",
+            "density_ratio": float(p["rho"][0]) if len(p) else None,
+            "parallelism": "replicas%d" % args.gpus,
+            "l2": "no flush: the 1.8 GB distribution state is 14x the 129 MB L2"}
+
+
+# ------------------------------------------------------------------------------------ ours
+def run_ours(args, wl):
+    import torch
+    from paper_2308_16597_gb300 import build as B, lbm
+
+    rank, world, local = dist_env()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.Stream(device=dev)
+    nodes = wl.nx * wl.ny
+    with torch.cuda.stream(stream):
+        sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream)
+        sim.kernel_timing(True)
+        sim.step(args.warmup)
+        sim.sync()
+        sim.kernel_times()  # reset
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.4)
+        launches0 = sim.launch_count()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        launches = sim.launch_count() - launches0
+        ktimes = sim.kernel_times()
+        sim.sync()
+    max_ms = max_over_ranks(ms, world, dev)
+    value = aggregate_mlups(nodes, args.steps, world, max_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: init from host particles,
+    # every step the particle state read back to pinned host memory, the
+    # fields read back at the end
+    e2e = None
+    if not args.no_e2e:
+        del sim
+        torch.cuda.empty_cache()
+        pinned_p = torch.empty(len(wl.particles) * 72, dtype=torch.uint8, pin_memory=True)
+        pview = pinned_p.numpy().view(lbm.PARTICLE_DTYPE)
+        fields = [torch.empty((wl.ny, wl.nx), dtype=torch.float32, pin_memory=True)
+                  for _ in range(4)]
+        params = lbm.make_params(**wl.params)
+        dom = lbm.make_domain(**wl.domain)
+        parts = lbm.pack_particles(wl.particles)
+        ws_bytes = lbm.lbm_query_footprint(dom, parts, params)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        e2e_steps = max(1, args.steps)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h = lbm.lbm_init(dom, parts, params, ws.data_ptr(), ws_bytes, stream.cuda_stream)
+        for _ in range(e2e_steps):
+            lbm.lbm_step(h, 1)
+            lbm.lbm_get_particles(h, pview)
+        lbm.lbm_get_fields(h, *[f.data_ptr() for f in fields], 0)
+        t1 = time.perf_counter()
+        lbm.lbm_destroy(h)
+        e2e_s = max_over_ranks(t1 - t0, world, dev)
+        pbytes = len(wl.particles) * 72
+        e2e = {"value": aggregate_mlups(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
+               "h2d_bytes_per_step": pbytes / e2e_steps,
+               "d2h_bytes_per_step": pbytes + 4 * 4 * nodes / e2e_steps,
+               "steps": e2e_steps,
+               "includes": "lbm_init from host particles, per step lbm_step(1) + "
+                           "lbm_get_particles to pinned host, final lbm_get_fields to host"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    k_ms, k_n = ktimes["stream_collide"]
+    avg_s = k_ms / 1e3 / max(k_n, 1)
+    B_LU = metrics.bytes_per_update(4)
+    peaks = measured_peaks()
+    achieved = B_LU * nodes / avg_s / 1e9
+    traffic = profiled_traffic("stream_collide")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "k_stream_collide", "algorithmic_bytes_per_launch": B_LU * nodes,
+                "avg_launch_ms": avg_s * 1e3, "peak_source": peaks["source"] + " (hbm_gbs)"}
+    step_ms = max_ms / args.steps
+    per_kernel = {k: {"ms_per_step": v[0] / max(v[1], 1), "launches": v[1],
+                      "share": v[0] / max(sum(x[0] for x in ktimes.values()), 1e-12)}
+                  for k, v in ktimes.items() if v[1]}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(wl, args), "roofline": roofline, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel,
+            "whole_step_hbm_frac": B_LU * nodes / (step_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_steps)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["cavity4000", "cavity256", "cavity1024"],
+                    default="cavity4000")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    wl = {"cavity4000": W.sedimentation_4000, "cavity256": W.parity_256,
+          "cavity1024": W.crop_1024}[args.workload]()
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

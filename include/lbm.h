@@ -1,0 +1,187 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) particle-resolved thermal lattice
+ * Boltzmann library.
+ *
+ * Method: Xu & Li, "Particle-resolved thermal lattice Boltzmann simulation
+ * using OpenACC on multi-GPUs" (arXiv 2308.16597).  One time step is
+ *   - the D2Q9 MRT flow collision with Boussinesq buoyancy (Sec. 2.1, Eq. f)
+ *     and the D2Q5 MRT temperature collision (Sec. 2.1, Eq. g), fused with
+ *     pull streaming;
+ *   - curved bounce-back on every fluid-particle link: Bouzidi quadratic for f
+ *     and the Li et al. Dirichlet rule for g (Sec. 2.3);
+ *   - the Galilean-invariant momentum-exchange force and torque (Sec. 2.4,
+ *     Eq. force, Eq. torque), with the links gathered every step into the
+ *     fixed index array of the indirect-addressing scheme (Sec. 3);
+ *   - the rigid-particle Newton-Euler update with spring repulsion
+ *     (Sec. 2.2, Sec. 2.4);
+ *   - refilling of nodes uncovered by a moving particle (Sec. 2.5).
+ *
+ * Conventions.  Lattice units.  Node (i, j) sits at (i, j), i in [0, nx),
+ * j in [0, ny), y up, gravity along -y.  Cavity walls lie half-way outside
+ * the outermost nodes (at -1/2 and n - 1/2).  D2Q9 directions:
+ * e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1) e5=(1,1) e6=(-1,1)
+ * e7=(-1,-1) e8=(1,-1); D2Q5 uses e0..e4.  Host arrays of fields are
+ * row-major [ny][nx].
+ *
+ * Ownership.  The caller owns the device workspace (sized by
+ * lbm_query_footprint), the CUDA stream and every host buffer; the library
+ * owns only the handle (freed by lbm_destroy).  The library never calls
+ * cudaMalloc.  All device work of a handle runs on its stream.
+ *
+ * Errors.  Every call returns an int: LBM_OK (0) or a negative LBM_E* code.
+ * lbm_step only enqueues work; errors found on the device during a step
+ * (non-finite density, a particle leaving the cavity, a line of the index
+ * array holding two links) are sticky and are returned by the next call that
+ * synchronises (lbm_sync, lbm_get_*).
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* invalid argument, parameter or particle layout */
+#define LBM_ENOSPC (-2)    /* workspace smaller than lbm_query_footprint */
+#define LBM_ENUMERIC (-3)  /* non-finite density or temperature on the device */
+#define LBM_EDOMAIN (-4)   /* a particle crossed a cavity wall */
+#define LBM_EOVERFLOW (-5) /* a line of the fixed index array holds two links */
+#define LBM_ETIMEOUT (-6)  /* a bounded device wait gave up */
+#define LBM_ECUDA (-7)     /* a CUDA runtime call failed */
+
+/* lbm_domain.bc bits: periodic axes (tests); unset = no-slip walls. */
+#define LBM_BC_PERIODIC_X 1u
+#define LBM_BC_PERIODIC_Y 2u
+
+/* lbm_params.storage: how distributions are held in HBM. */
+#define LBM_STORE_FP32 0 /* FP32 deviations from the rest equilibrium */
+#define LBM_STORE_BF16 1 /* BF16 deviations (reserved) */
+#define LBM_STORE_FP16 2 /* FP16 deviations (reserved) */
+
+/* lbm_params.flags */
+#define LBM_FLAG_FIXED_PARTICLES 1u /* particles keep their state (tests) */
+#define LBM_FLAG_NO_GRAPH 2u        /* launch kernels directly, no CUDA graph */
+
+typedef struct {
+    int32_t nx, ny;    /* nodes per axis, >= 4 each */
+    uint32_t bc;       /* LBM_BC_* bits */
+    int32_t reserved;  /* must be 0 */
+    double T_wall[4];  /* wall temperature at x = -1/2, x = nx-1/2, y = -1/2, y = ny-1/2 */
+} lbm_domain;
+
+/* One rigid disk (Sec. 2.2).  72 bytes, 9 doubles. */
+typedef struct {
+    double x, y;    /* centre */
+    double ux, uy;  /* translational velocity */
+    double theta;   /* orientation angle */
+    double omega;   /* angular velocity (z) */
+    double r;       /* radius, >= 1 */
+    double rho;     /* density */
+    double T;       /* surface temperature T_w (Sec. 2.3) */
+} lbm_particle;
+
+typedef struct {
+    double nu;      /* kinematic viscosity, > 0 (s_nu = 1/(3 nu + 1/2)) */
+    double alpha;   /* thermal diffusivity, > 0 (D2Q5 flux rate 1/(5 alpha + 1/2)) */
+    double g;       /* gravitational acceleration (Sec. 2.1) */
+    double beta;    /* thermal expansion coefficient (Sec. 2.1) */
+    double T0;      /* reference temperature of the buoyancy term */
+    double rho_f;   /* fluid density for particle weight and repulsion scale */
+    double T_init;  /* initial fluid temperature */
+    double s_e, s_eps; /* MRT-f energy rates, <= 0 selects 1 */
+    double s_q;     /* MRT-f heat-flux rate, <= 0 selects 8(2 - s_nu)/(8 - s_nu) */
+    double q_e, q_nu; /* MRT-g higher-moment rates, <= 0 selects 1 */
+    double eps_w;   /* repulsion stiffness (Sec. 2.4: 0.001) */
+    double s_rep;   /* repulsion threshold (Sec. 2.4: 3 lattice units) */
+    double body_fx, body_fy; /* uniform body-force density added to buoyancy */
+    int32_t storage;  /* LBM_STORE_* */
+    uint32_t flags;   /* LBM_FLAG_* */
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Device workspace bytes needed for a domain, n particles (host array p, read
+ * for their radii: the index array holds 12N - 12 slots per particle with
+ * N = ceil(2r) + 3, Sec. 3) and parameters.  Pure host computation.
+ * Errors: LBM_EINVAL for invalid arguments. */
+int lbm_query_footprint(const lbm_domain *d, const lbm_particle *p, int32_t n,
+                        const lbm_params *prm, size_t *bytes);
+
+/* Create a simulation.  d, p (host, n entries), prm are copied.  d_workspace
+ * is a device pointer to at least the queried bytes, 256-byte aligned, owned
+ * by the caller and left untouched after lbm_destroy.  stream is a
+ * cudaStream_t (NULL = the legacy default stream).  The initial fluid is at
+ * rest with unit density and temperature T_init; nodes inside disks are
+ * solid.  The first step's pre-collision state is collided here, so the
+ * stored state is always post-collision.  Synchronous.
+ * Errors: LBM_EINVAL (bad sizes or rates, overlapping disks, disks crossing a
+ * wall or, with a periodic axis, the domain edge), LBM_ENOSPC, LBM_ECUDA. */
+int lbm_init(lbm_handle **h, const lbm_domain *d, const lbm_particle *p, int32_t n,
+             const lbm_params *prm, void *d_workspace, size_t ws_bytes, void *stream);
+
+/* Enqueue nsteps time steps on the handle's stream (asynchronous). */
+int lbm_step(lbm_handle *h, int32_t nsteps);
+
+/* Wait for the stream; return the sticky device error, if any. */
+int lbm_sync(lbm_handle *h);
+
+/* Macroscopic fields at the current time: rho = sum f, T = sum g,
+ * u = (sum e f + F/2)/rho (Sec. 2.1), recovered from the stored
+ * post-collision state; NaN at solid nodes.  Each output is [ny][nx] float.
+ * on_device != 0: the four pointers are device memory and the call only
+ * enqueues; otherwise host memory and the call synchronises. */
+int lbm_get_fields(lbm_handle *h, float *rho, float *ux, float *uy, float *T, int32_t on_device);
+
+/* Copy the particle states (host, n entries) after synchronising. */
+int lbm_get_particles(lbm_handle *h, lbm_particle *out, int32_t n);
+
+/* Hydrodynamic force (Fx, Fy) and torque Tz of the last step, 3 doubles per
+ * particle (host), after synchronising. */
+int lbm_get_forces(lbm_handle *h, double *out, int32_t n);
+
+int lbm_destroy(lbm_handle *h);
+const char *lbm_strerror(int code);
+
+/* ---- inspection and checkpoint hooks (tests, serving) ------------------- */
+/* Owner map [ny][nx] int32 (host): particle id whose disk holds the node, or
+ * -1 for fluid.  Synchronises. */
+int lbm_get_owner(lbm_handle *h, int32_t *out);
+/* Fixed index array of the last step (Sec. 3), host copies: per particle
+ * 12N - 12 slots in the order e1..e8, lines within a direction as described
+ * in the design notes; node = j*nx + i of the fluid node or -1; q = wall
+ * fraction (float).  *count receives the total slot count; cap bounds the
+ * copy.  Synchronises. */
+int lbm_get_slots(lbm_handle *h, int32_t *node, float *q, int64_t cap, int64_t *count);
+/* Raw state (distributions, maps, particles) for checkpoint/restore between
+ * handles created with identical arguments.  Synchronises. */
+int lbm_state_bytes(lbm_handle *h, size_t *bytes);
+int lbm_get_state(lbm_handle *h, void *host_buf, size_t bytes);
+int lbm_set_state(lbm_handle *h, const void *host_buf, size_t bytes);
+/* Replace the distributions by pre-collision values f[9][ny][nx] and
+ * g[5][ny][nx] (host FP64) and collide them, as lbm_init does for its
+ * initial state.  Values at solid nodes are ignored.  Synchronises. */
+int lbm_set_distributions(lbm_handle *h, const double *f, const double *g);
+/* Counters of the last step: [0] Bouzidi quadratic->linear fallbacks,
+ * [1] ->simple, [2] thermal ->half-way, [3] refill quadratic->linear,
+ * [4] ->copy, [5] ->equilibrium, [6] newborn nodes, [7] links. */
+int lbm_get_counters(lbm_handle *h, int64_t *out8);
+/* Kernel timing: while enabled, lbm_step launches directly (no graph) and
+ * brackets every kernel with CUDA events on the handle's stream.
+ * lbm_kernel_times synchronises and returns, per kernel kind, the summed
+ * milliseconds and launch counts since the last reset (arrays of nk entries
+ * in the order of lbm_kernel_name), then resets them. */
+int lbm_kernel_timing(lbm_handle *h, int32_t enable);
+int lbm_kernel_times(lbm_handle *h, double *ms, int64_t *launches, int32_t nk);
+int32_t lbm_kernel_count(void);
+const char *lbm_kernel_name(int32_t k);
+/* Kernel launches enqueued by this handle since creation. */
+int64_t lbm_launch_count(lbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,374 @@
+// Fused pull-stream + MRT collision of the flow (D2Q9) and temperature (D2Q5)
+// distributions with Boussinesq buoyancy (Sec. 2.1, Eq. f and Eq. g), with the
+// refilling of newborn nodes (Sec. 2.5) folded into the pull.
+//
+// Layout: 14 planes (9 flow deviations f~ = f - w, 5 temperature populations
+// g) of [ny][pitch] floats, ping-ponged between two buffers.  A plane row is
+// read once and written once per step: 112 algorithmic bytes per node.
+//
+// Each thread owns four consecutive nodes of one row and moves every plane
+// with one aligned 128-bit load and one 128-bit store.  A pull from x - 1 or
+// x + 1 takes the missing edge value from the neighbouring lane by a warp
+// shuffle (one scalar load at the warp edge), so the x-shifted planes cost no
+// extra HBM traffic.  Nodes next to a cavity wall, periodic seam or newborn
+// node take a general (scalar) path.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Post-collision value pulled into node (x, y) for population p, general
+// form: the source x - e is read directly, wrapped across a periodic seam, or
+// replaced across a wall by half-way bounce-back (f) or anti-bounce-back with
+// the wall temperature (g).  In deviation form the half-way rule keeps its
+// shape because w_i = w_ibar.
+__device__ float pull_general(const Dev &D, const float *__restrict__ A, int x, int y, int p)
+{
+    const int d = pdir(p);
+    int xs = x - ex(d), ys = y - ey(d);
+    bool wall = false;
+    if (xs < 0 || xs >= D.nx) {
+        if (D.per_x) xs = xs < 0 ? xs + D.nx : xs - D.nx;
+        else wall = true;
+    }
+    if (ys < 0 || ys >= D.ny) {
+        if (D.per_y) ys = ys < 0 ? ys + D.ny : ys - D.ny;
+        else wall = true;
+    }
+    if (!wall) return A[(long long)p * D.ps + (long long)ys * D.pitch + xs];
+    const long long self = (long long)y * D.pitch + x;
+    if (p < kQ9) return A[(long long)opp(d) * D.ps + self];
+    const int side = d == 1 ? 0 : d == 3 ? 1 : d == 2 ? 2 : 3;
+    return -A[(long long)(kQ9 + opp(d)) * D.ps + self] + 2.f * w5(d) * D.Twall[side];
+}
+
+// Values pulled into a node on the general path; for a newborn node the
+// refilling of Sec. 2.5 instead: e_c maximises n . e_c (FP64, ties to the
+// lowest index, n from the new centre), f is extrapolated from the nodes
+// x + m e_c (m = 1, 2, 3) that are fluid at both times (quadratic, linear,
+// copy, or f_eq(1, u_w)), its momentum is set to rho u_w, and
+// g = g_eq(T_w, u_w).
+// Returns 0 for a general pull, else 1 + the refill class (1 quadratic,
+// 2 linear, 3 copy, 4 equilibrium).
+__device__ __noinline__ int slow_node(const Dev &D, const float *__restrict__ A,
+                                      const int *__restrict__ own_cur, int x, int y, uint8_t fl,
+                                      float *out)
+{
+    if (fl != kNewborn) {
+        for (int p = 0; p < kPop; ++p) out[p] = pull_general(D, A, x, y, p);
+        return 0;
+    }
+    const int pid = own_cur[(long long)y * D.nx + x];
+    const double xc = D.cur.x[pid], yc = D.cur.y[pid];
+    const double dx = __dsub_rn((double)x, xc), dy = __dsub_rn((double)y, yc);
+    int c = 1;
+    double best = __dadd_rn(__dmul_rn((double)ex(1), dx), __dmul_rn((double)ey(1), dy));
+    for (int k = 2; k < kQ9; ++k) {
+        double v = __dadd_rn(__dmul_rn((double)ex(k), dx), __dmul_rn((double)ey(k), dy));
+        if (v > best) {
+            best = v;
+            c = k;
+        }
+    }
+    const float uwx = (float)(D.cur.ux[pid] - D.cur.om[pid] * dy);
+    const float uwy = (float)(D.cur.uy[pid] + D.cur.om[pid] * dx);
+    int nvalid = 0;
+    for (int m = 1; m <= 3; ++m) {
+        int a = x + m * ex(c), b = y + m * ey(c);
+        if (a < 0 || a >= D.nx || b < 0 || b >= D.ny) break;
+        if (D.flags[(long long)b * D.pitch + a] != kFluid) break;
+        nvalid = m;
+    }
+    float fh[kQ9];
+    if (nvalid == 0) {
+        const float uu = uwx * uwx + uwy * uwy;
+        for (int i = 0; i < kQ9; ++i) {
+            float eu = ex(i) * uwx + ey(i) * uwy;
+            fh[i] = w9(i) * (3.f * eu + 4.5f * eu * eu - 1.5f * uu);
+        }
+    } else {
+        float c1 = nvalid == 3 ? 3.f : nvalid == 2 ? 2.f : 1.f;
+        float c2 = nvalid == 3 ? -3.f : nvalid == 2 ? -1.f : 0.f;
+        float c3 = nvalid == 3 ? 1.f : 0.f;
+        const int x1 = x + ex(c), y1 = y + ey(c);
+        for (int i = 0; i < kQ9; ++i) {
+            float v = c1 * pull_general(D, A, x1, y1, i);
+            if (nvalid >= 2) v += c2 * pull_general(D, A, x1 + ex(c), y1 + ey(c), i);
+            if (nvalid >= 3) v += c3 * pull_general(D, A, x1 + 2 * ex(c), y1 + 2 * ey(c), i);
+            fh[i] = v;
+        }
+    }
+    // velocity constraint: j = rho u_w, every other moment kept; the x- and
+    // y-momentum rows of the moment basis have squared norm 6
+    float rho = 1.f, jx = 0.f, jy = 0.f;
+    for (int i = 0; i < kQ9; ++i) {
+        rho += fh[i];
+        jx += ex(i) * fh[i];
+        jy += ey(i) * fh[i];
+    }
+    const float djx = (rho * uwx - jx) * (1.f / 6.f), djy = (rho * uwy - jy) * (1.f / 6.f);
+    for (int i = 0; i < kQ9; ++i) out[i] = fh[i] + ex(i) * djx + ey(i) * djy;
+    const float Tw = (float)D.cur.T[pid];
+    for (int i = 0; i < kQ5; ++i) out[kQ9 + i] = w5(i) * Tw * (1.f + 5.f * (ex(i) * uwx + ey(i) * uwy));
+    return 4 - nvalid;
+}
+
+// MRT collision of one node in deviation form (Eq. f with Guo forcing in
+// moment space, Eq. g), in place on c[14].  Returns false for a non-finite
+// or non-physical density/temperature.
+__device__ __forceinline__ bool collide(const Dev &D, float *c)
+{
+    const float f0 = c[0], f1 = c[1], f2 = c[2], f3 = c[3], f4 = c[4];
+    const float f5 = c[5], f6 = c[6], f7 = c[7], f8 = c[8];
+    const float drho = ((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
+    const float rho = 1.f + drho;
+    const float T = (c[9] + c[10]) + (c[11] + c[12]) + c[13];
+    const float jx = (f1 - f3) + (f5 - f6) + (f8 - f7);
+    const float jy = (f2 - f4) + (f5 + f6) - (f7 + f8);
+    const float Fx = D.bfx;
+    const float Fy = rho * D.gbeta * (T - D.T0) + D.bfy;
+    const float inv = 1.f / rho;
+    const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv;
+    const float sa = (f1 + f2) + (f3 + f4), sd = (f5 + f6) + (f7 + f8);
+    const float m1 = -4.f * f0 - sa + 2.f * sd;
+    const float m2 = 4.f * f0 - 2.f * sa + sd;
+    const float m4 = 2.f * (f3 - f1) + (f5 - f6) + (f8 - f7);
+    const float m6 = 2.f * (f4 - f2) + (f5 + f6) - (f7 + f8);
+    const float m7 = (f1 + f3) - (f2 + f4);
+    const float m8 = (f5 + f7) - (f6 + f8);
+    const float uu = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
+    const float ru = 3.f * rho * uu;
+    const float p1 = m1 - D.s_e * (m1 - (-2.f * drho + ru)) + (1.f - 0.5f * D.s_e) * 6.f * uF;
+    const float p2 = m2 - D.s_eps * (m2 - (drho - ru)) - (1.f - 0.5f * D.s_eps) * 6.f * uF;
+    const float p3 = jx + Fx, p5 = jy + Fy;
+    const float p4 = m4 - D.s_q * (m4 + rho * ux) - (1.f - 0.5f * D.s_q) * Fx;
+    const float p6 = m6 - D.s_q * (m6 + rho * uy) - (1.f - 0.5f * D.s_q) * Fy;
+    const float p7 = m7 - D.s_nu * (m7 - rho * (ux * ux - uy * uy)) +
+                     (1.f - 0.5f * D.s_nu) * 2.f * (ux * Fx - uy * Fy);
+    const float p8 = m8 - D.s_nu * (m8 - rho * ux * uy) + (1.f - 0.5f * D.s_nu) * (ux * Fy + uy * Fx);
+    // f = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m
+    const float a0 = drho * (1.f / 9.f), a1 = p1 * (1.f / 36.f), a2 = p2 * (1.f / 36.f);
+    const float a3 = p3 * (1.f / 6.f), a4 = p4 * (1.f / 12.f), a5 = p5 * (1.f / 6.f);
+    const float a6 = p6 * (1.f / 12.f), a7 = p7 * 0.25f, a8 = p8 * 0.25f;
+    const float base = a0 - a1 - 2.f * a2, dbase = a0 + 2.f * a1 + a2;
+    c[0] = a0 - 4.f * a1 + 4.f * a2;
+    c[1] = base + (a3 - 2.f * a4) + a7;
+    c[2] = base + (a5 - 2.f * a6) - a7;
+    c[3] = base - (a3 - 2.f * a4) + a7;
+    c[4] = base - (a5 - 2.f * a6) - a7;
+    c[5] = dbase + (a3 + a4) + (a5 + a6) + a8;
+    c[6] = dbase - (a3 + a4) + (a5 + a6) - a8;
+    c[7] = dbase - (a3 + a4) - (a5 + a6) + a8;
+    c[8] = dbase + (a3 + a4) - (a5 + a6) - a8;
+    // D2Q5: n = (T, g1-g3, g2-g4, -4g0 + g1+g2+g3+g4, g1-g2+g3-g4),
+    // n_eq = (T, T ux, T uy, -2T, 0); g = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4) n
+    const float g0 = c[9], g1 = c[10], g2 = c[11], g3 = c[12], g4 = c[13];
+    const float n1 = g1 - g3, n2 = g2 - g4;
+    const float n3 = -4.f * g0 + ((g1 + g2) + (g3 + g4));
+    const float n4 = (g1 + g3) - (g2 + g4);
+    const float b0 = T * 0.2f;
+    const float b1 = 0.5f * (n1 - D.q_k * (n1 - T * ux));
+    const float b2 = 0.5f * (n2 - D.q_k * (n2 - T * uy));
+    const float b3 = 0.05f * (n3 - D.q_e * (n3 + 2.f * T));
+    const float b4 = 0.25f * (n4 - D.q_nu * n4);
+    c[9] = b0 - 4.f * b3;
+    c[10] = b0 + b1 + b3 + b4;
+    c[11] = b0 + b2 + b3 - b4;
+    c[12] = b0 - b1 + b3 + b4;
+    c[13] = b0 - b2 + b3 - b4;
+    return (rho > 0.25f) && (rho < 4.f) && (fabsf(T) < 1e30f);
+}
+
+__device__ __forceinline__ float4 ld4(const float *p)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+
+__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+
+// cls: refill classes of up to four nodes, one byte each (see slow_node).
+__device__ __noinline__ void flush_counters(const Dev &D, int parity, unsigned cls)
+{
+    unsigned long long *C = D.status->cnt[parity];
+    for (int n = 0; n < 4; ++n) {
+        const unsigned c = (cls >> (8 * n)) & 0xffu;
+        if (!c) continue;
+        atomicAdd(&C[kCntNewborn], 1ull);
+        if (c == 2) atomicAdd(&C[kCntRfLinear], 1ull);
+        if (c == 3) atomicAdd(&C[kCntRfCopy], 1ull);
+        if (c == 4) atomicAdd(&C[kCntRfEq], 1ull);
+    }
+}
+
+} // namespace
+
+// Thread block: blockDim.x is a multiple of 32 covering quads of one row, so a
+// warp never straddles two rows.
+__global__ void __launch_bounds__(128, 3)
+    k_stream_collide(const Dev D, const float *__restrict__ Ain, float *__restrict__ Aout,
+                     const int *__restrict__ own_cur, int parity)
+{
+    const int lane = threadIdx.x & 31;
+    const int qx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (y >= D.ny) return; // uniform across the warp
+    const int x0 = qx * 4;
+    const bool act = x0 < D.pitch;
+
+    float v[kPop][4];
+#pragma unroll
+    for (int p = 0; p < kPop; ++p) {
+        const int d = pdir(p);
+        const int dx = ex(d), dy = ey(d);
+        int ys = y - dy;
+        bool rowok = ys >= 0 && ys < D.ny;
+        if (!rowok && D.per_y) {
+            ys = ys < 0 ? ys + D.ny : ys - D.ny;
+            rowok = true;
+        }
+        const float *src = Ain + (long long)p * D.ps + (long long)(rowok ? ys : 0) * D.pitch;
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act && rowok) w = ld4(src + x0);
+        if (dx == 0) {
+            v[p][0] = w.x; v[p][1] = w.y; v[p][2] = w.z; v[p][3] = w.w;
+        } else if (dx == 1) {
+            float l = __shfl_up_sync(kFull, w.w, 1);
+            if (lane == 0) l = (act && rowok && x0 >= 1) ? __ldg(src + x0 - 1) : 0.f;
+            v[p][0] = l; v[p][1] = w.x; v[p][2] = w.y; v[p][3] = w.z;
+        } else {
+            float r = __shfl_down_sync(kFull, w.x, 1);
+            if (lane == 31) r = (act && rowok && x0 + 4 < D.pitch) ? __ldg(src + x0 + 4) : 0.f;
+            v[p][0] = w.y; v[p][1] = w.z; v[p][2] = w.w; v[p][3] = r;
+        }
+    }
+
+    uchar4 fl4 = make_uchar4(kSolid, kSolid, kSolid, kSolid);
+    if (act) fl4 = *reinterpret_cast<const uchar4 *>(D.flags + (long long)y * D.pitch + x0);
+    const uint8_t fls[4] = {fl4.x, fl4.y, fl4.z, fl4.w};
+    bool ok = true;
+    unsigned cls = 0;
+    const bool yedge = (y == 0) || (y == D.ny - 1);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        const int x = x0 + n;
+        const bool live = act && x < D.nx && fls[n] != kSolid;
+        float c[kPop];
+#pragma unroll
+        for (int p = 0; p < kPop; ++p) c[p] = v[p][n];
+        if (live) {
+            if (yedge || x == 0 || x == D.nx - 1 || fls[n] == kNewborn) {
+                float tmp[kPop];
+                cls |= (unsigned)slow_node(D, Ain, own_cur, x, y, fls[n], tmp) << (8 * n);
+#pragma unroll
+                for (int p = 0; p < kPop; ++p) c[p] = tmp[p];
+            }
+            ok &= collide(D, c);
+        } else {
+#pragma unroll
+            for (int p = 0; p < kPop; ++p) c[p] = 0.f;
+        }
+#pragma unroll
+        for (int p = 0; p < kPop; ++p) v[p][n] = c[p];
+    }
+    if (act) {
+        float *dst = Aout + (long long)y * D.pitch + x0;
+#pragma unroll
+        for (int p = 0; p < kPop; ++p) st4(dst + (long long)p * D.ps, v[p][0], v[p][1], v[p][2], v[p][3]);
+    }
+    if (__any_sync(kFull, !ok) && lane == 0) atomicOr(&D.status->err, kErrNumeric);
+    if (cls) flush_counters(D, parity, cls);
+}
+
+// Collision without streaming, for the initial state and for distributions
+// supplied by the caller (mode 1 reads pre-collision values from Ain).
+__global__ void k_init_collide(const Dev D, const float *__restrict__ Ain, float *__restrict__ Aout,
+                               float T_init, int mode)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= D.pitch || y >= D.ny) return;
+    const long long n = (long long)y * D.pitch + x;
+    float c[kPop];
+    const bool live = x < D.nx && D.flags[n] != kSolid;
+    for (int p = 0; p < kPop; ++p) {
+        if (mode == 1) c[p] = Ain[(long long)p * D.ps + n];
+        else c[p] = p < kQ9 ? 0.f : w5(p - kQ9) * T_init;
+    }
+    if (live) {
+        if (!collide(D, c)) atomicOr(&D.status->err, kErrNumeric);
+    } else {
+        for (int p = 0; p < kPop; ++p) c[p] = 0.f;
+    }
+    for (int p = 0; p < kPop; ++p) Aout[(long long)p * D.ps + n] = c[p];
+}
+
+// rho, u, T from the post-collision state: the collision keeps rho and T
+// and adds F to the momentum, so u = (sum e f+ - F/2)/rho equals the
+// pre-collision (sum e f + F/2)/rho of Sec. 2.1.
+__global__ void k_fields(const Dev D, const float *__restrict__ A, int row0, float *rho_o,
+                         float *ux_o, float *uy_o, float *T_o)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = row0 + blockIdx.y;
+    if (x >= D.nx || y >= D.ny) return;
+    const long long n = (long long)y * D.pitch + x;
+    const long long o = (long long)blockIdx.y * D.nx + x;
+    if (D.flags[n] == kSolid) {
+        const float nan = __int_as_float(0x7fc00000);
+        rho_o[o] = nan; ux_o[o] = nan; uy_o[o] = nan; T_o[o] = nan;
+        return;
+    }
+    float f[kQ9], T = 0.f, drho = 0.f, jx = 0.f, jy = 0.f;
+    for (int i = 0; i < kQ9; ++i) {
+        f[i] = A[(long long)i * D.ps + n];
+        drho += f[i];
+        jx += ex(i) * f[i];
+        jy += ey(i) * f[i];
+    }
+    for (int i = 0; i < kQ5; ++i) T += A[(long long)(kQ9 + i) * D.ps + n];
+    const float rho = 1.f + drho;
+    const float Fx = D.bfx, Fy = rho * D.gbeta * (T - D.T0) + D.bfy;
+    rho_o[o] = rho;
+    ux_o[o] = (jx - 0.5f * Fx) / rho;
+    uy_o[o] = (jy - 0.5f * Fy) / rho;
+    T_o[o] = T;
+}
+
+cudaError_t launch_stream_collide(const Dev &D, const float *Ain, float *Aout, const int *own_cur,
+                                  int parity, cudaStream_t s)
+{
+    const int quads = (D.pitch + 3) / 4;
+    int bx = ((quads + 31) / 32) * 32;
+    if (bx > 128) bx = 128;
+    const int by = 128 / bx;
+    dim3 block(bx, by);
+    dim3 grid((quads + bx - 1) / bx, (D.ny + by - 1) / by);
+    k_stream_collide<<<grid, block, 0, s>>>(D, Ain, Aout, own_cur, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_collide(const Dev &D, const float *Ain, float *Aout, float T_init, int mode,
+                                cudaStream_t s)
+{
+    dim3 block(128);
+    dim3 grid((D.pitch + 127) / 128, D.ny);
+    k_init_collide<<<grid, block, 0, s>>>(D, Ain, Aout, T_init, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const Dev &D, const float *A, int row0, int rows, float *rho, float *ux,
+                          float *uy, float *T, cudaStream_t s)
+{
+    dim3 block(128);
+    dim3 grid((D.nx + 127) / 128, rows);
+    k_fields<<<grid, block, 0, s>>>(D, A, row0, rho, ux, uy, T);
+    return cudaGetLastError();
+}
+
+} // namespace lbm

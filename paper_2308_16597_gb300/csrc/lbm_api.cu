@@ -1,0 +1,674 @@
+// Host side of the C ABI declared in include/lbm.h: workspace layout,
+// argument validation, initialisation, the per-step launch sequence (direct
+// or replayed from a captured CUDA graph), read-back and checkpoint hooks.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStageBytes = size_t(4) << 20;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int pitch = 0;
+    long long ps = 0;
+    size_t nslots = 0;
+    size_t A[2], own[2], flags, slot_node, slot_q, slot_base, cur, nxt, prev, force, status, pack,
+        stage, total;
+    int stage_rows = 0;
+};
+
+bool finite(double v) { return std::isfinite(v); }
+
+int validate(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_params *prm)
+{
+    if (!d || !prm || n < 0 || (n > 0 && !p)) return LBM_EINVAL;
+    if (d->nx < 4 || d->ny < 4 || d->reserved != 0) return LBM_EINVAL;
+    if ((long long)d->nx * d->ny > (1ll << 31) - 1) return LBM_EINVAL;
+    if (!(prm->nu > 0) || !(prm->alpha > 0) || !finite(prm->nu) || !finite(prm->alpha)) return LBM_EINVAL;
+    if (prm->storage != LBM_STORE_FP32) return LBM_EINVAL;
+    const double rates[] = {prm->s_e, prm->s_eps, prm->s_q, prm->q_e, prm->q_nu};
+    for (double r : rates)
+        if (!finite(r) || r >= 2.0) return LBM_EINVAL;
+    const double vals[] = {prm->g, prm->beta, prm->T0, prm->rho_f, prm->T_init, prm->eps_w,
+                           prm->s_rep, prm->body_fx, prm->body_fy};
+    for (double v : vals)
+        if (!finite(v)) return LBM_EINVAL;
+    if (n > 0 && !(prm->eps_w > 0)) return LBM_EINVAL;
+    for (int i = 0; i < 4; ++i)
+        if (!finite(d->T_wall[i])) return LBM_EINVAL;
+    const bool px = d->bc & LBM_BC_PERIODIC_X, py = d->bc & LBM_BC_PERIODIC_Y;
+    double rmax = 0.0;
+    for (int a = 0; a < n; ++a) {
+        const lbm_particle &P = p[a];
+        const double v[] = {P.x, P.y, P.ux, P.uy, P.theta, P.omega, P.r, P.rho, P.T};
+        for (double x : v)
+            if (!finite(x)) return LBM_EINVAL;
+        if (P.r < 1.0 || P.rho <= 0.0) return LBM_EINVAL;
+        // a disk stays inside the cavity; next to a periodic seam it keeps two
+        // nodes of clearance so that no link or stencil wraps around
+        const double mx = px ? 2.0 : -0.5, my = py ? 2.0 : -0.5;
+        if (P.x - P.r < mx || P.x + P.r > d->nx - 1 - (px ? 2.0 : -0.5)) return LBM_EINVAL;
+        if (P.y - P.r < my || P.y + P.r > d->ny - 1 - (py ? 2.0 : -0.5)) return LBM_EINVAL;
+        rmax = std::max(rmax, P.r);
+    }
+    // overlapping disks (cell hash with cell size 2 rmax)
+    if (n > 1) {
+        const double cs = 2.0 * rmax;
+        std::unordered_map<long long, std::vector<int>> cells;
+        auto key = [](long long cx, long long cy) { return (cx << 32) ^ (cy & 0xffffffffll); };
+        for (int a = 0; a < n; ++a) {
+            long long cx = (long long)std::floor(p[a].x / cs), cy = (long long)std::floor(p[a].y / cs);
+            for (long long gx = cx - 1; gx <= cx + 1; ++gx)
+                for (long long gy = cy - 1; gy <= cy + 1; ++gy) {
+                    auto it = cells.find(key(gx, gy));
+                    if (it == cells.end()) continue;
+                    for (int b : it->second) {
+                        double dx = p[a].x - p[b].x, dy = p[a].y - p[b].y;
+                        if (std::sqrt(dx * dx + dy * dy) < p[a].r + p[b].r) return LBM_EINVAL;
+                    }
+                }
+            cells[key(cx, cy)].push_back(a);
+        }
+    }
+    return LBM_OK;
+}
+
+void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, Layout &L)
+{
+    L.pitch = (int)round_up((size_t)d->nx, 32);
+    L.ps = (long long)round_up((size_t)L.pitch * d->ny, 64);
+    L.nslots = 0;
+    for (int a = 0; a < n; ++a) L.nslots += (size_t)slot_capacity(p[a].r);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = round_up(off + std::max<size_t>(bytes, 1), kAlign);
+        return o;
+    };
+    const size_t nn = (size_t)d->nx * d->ny;
+    for (int b = 0; b < 2; ++b) L.A[b] = take((size_t)kPop * L.ps * sizeof(float));
+    for (int b = 0; b < 2; ++b) L.own[b] = take(nn * sizeof(int));
+    L.flags = take((size_t)L.pitch * d->ny);
+    L.slot_node = take(L.nslots * sizeof(int));
+    L.slot_q = take(L.nslots * sizeof(float));
+    L.slot_base = take((size_t)(n + 1) * sizeof(int));
+    L.cur = take((size_t)9 * n * sizeof(double));
+    L.nxt = take((size_t)9 * n * sizeof(double));
+    L.prev = take((size_t)2 * n * sizeof(double));
+    L.force = take((size_t)3 * n * sizeof(double));
+    L.status = take(sizeof(Status));
+    L.pack = take((size_t)n * sizeof(lbm_particle));
+    L.stage_rows = (int)std::max<size_t>(1, std::min<size_t>(d->ny, kStageBytes / (16 * (size_t)d->nx)));
+    L.stage = take((size_t)4 * L.stage_rows * d->nx * sizeof(float));
+    L.total = off;
+}
+
+PartSoA soa_at(char *base, size_t off, int n)
+{
+    double *b = reinterpret_cast<double *>(base + off);
+    return PartSoA{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n, b + 7 * n, b + 8 * n};
+}
+
+const char *kKernelNames[kNumKernelKinds] = {"link_gather_bb_force", "particle_update",
+                                             "owner_clear",          "owner_raster",
+                                             "node_flags",           "stream_collide",
+                                             "init_collide",         "fields"};
+
+} // namespace
+
+struct lbm_handle {
+    lbm_domain d;
+    lbm_params prm;
+    int np = 0;
+    Layout L;
+    char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    Dev D;
+    float *A[2];
+    int *own[2];
+    int parity = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool timing = false;
+    struct Ev {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Ev> ev;
+    size_t ev_used = 0;
+    double acc_ms[kNumKernelKinds] = {};
+    long long acc_n[kNumKernelKinds] = {};
+    long long launches = 0;
+    int sticky = LBM_OK;
+};
+
+namespace {
+
+int cuda_fail(lbm_handle *h, cudaError_t e)
+{
+    if (e == cudaSuccess) return LBM_OK;
+    if (h) h->sticky = LBM_ECUDA;
+    return LBM_ECUDA;
+}
+
+#define CK(h, call)                                      \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_); \
+    } while (0)
+
+int fold_events(lbm_handle *h)
+{
+    for (size_t i = 0; i < h->ev_used; ++i) {
+        float ms = 0.f;
+        CK(h, cudaEventSynchronize(h->ev[i].b));
+        CK(h, cudaEventElapsedTime(&ms, h->ev[i].a, h->ev[i].b));
+        h->acc_ms[h->ev[i].kind] += ms;
+        h->acc_n[h->ev[i].kind] += 1;
+    }
+    h->ev_used = 0;
+    return LBM_OK;
+}
+
+template <typename F>
+int timed(lbm_handle *h, int kind, cudaStream_t st, F &&launch)
+{
+    const bool t = h->timing && st == h->stream;
+    if (t) {
+        if (h->ev_used >= 32768) {
+            int rc = fold_events(h);
+            if (rc) return rc;
+        }
+        if (h->ev_used == h->ev.size()) {
+            lbm_handle::Ev e{};
+            CK(h, cudaEventCreate(&e.a));
+            CK(h, cudaEventCreate(&e.b));
+            h->ev.push_back(e);
+        }
+        h->ev[h->ev_used].kind = kind;
+        CK(h, cudaEventRecord(h->ev[h->ev_used].a, st));
+    }
+    CK(h, launch());
+    if (t) {
+        CK(h, cudaEventRecord(h->ev[h->ev_used].b, st));
+        ++h->ev_used;
+    }
+    ++h->launches;
+    return LBM_OK;
+}
+
+// One time step, in the order
+//   gather + bounce-back + force (particle state at n, owner map at n)
+//   -> particle update (n -> n+1) -> owner map and flags at n+1
+//   -> fused stream + refill + collide of A_n into A_{n+1}.
+int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
+{
+    const Dev &D = h->D;
+    float *Ain = h->A[par], *Aout = h->A[par ^ 1];
+    int *oc = h->own[par], *on = h->own[par ^ 1];
+    int rc;
+    if (h->np > 0) {
+        if ((rc = timed(h, kKLinks, st, [&] { return launch_links(D, Ain, oc, par, st); }))) return rc;
+    }
+    if ((rc = timed(h, kKParticles, st, [&] { return launch_particles(D, par, st); }))) return rc;
+    if (h->np > 0) {
+        if ((rc = timed(h, kKClear, st, [&] { return launch_clear(D, on, st); }))) return rc;
+        if ((rc = timed(h, kKRaster, st, [&] { return launch_raster(D, on, D.nxt, st); }))) return rc;
+        if ((rc = timed(h, kKFlags, st, [&] { return launch_flags(D, oc, on, 1, st); }))) return rc;
+    }
+    return timed(h, kKStreamCollide, st,
+                 [&] { return launch_stream_collide(D, Ain, Aout, oc, par, st); });
+}
+
+int kernels_per_step(const lbm_handle *h) { return h->np > 0 ? 6 : 2; }
+
+int capture(lbm_handle *h, int par)
+{
+    if (!h->cap) CK(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    const long long before = h->launches;
+    int rc = enqueue_step(h, par, h->cap);
+    h->launches = before;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    CK(h, e);
+    e = cudaGraphInstantiate(&h->gexec[par], g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e);
+    return LBM_OK;
+}
+
+int device_error(lbm_handle *h)
+{
+    unsigned err = 0;
+    CK(h, cudaMemcpy(&err, &h->D.status->err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err & kErrNumeric) return LBM_ENUMERIC;
+    if (err & kErrDomain) return LBM_EDOMAIN;
+    if (err & kErrOverflow) return LBM_EOVERFLOW;
+    return LBM_OK;
+}
+
+int sync_status(lbm_handle *h)
+{
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->sticky) return h->sticky;
+    int rc = device_error(h);
+    if (rc) h->sticky = rc;
+    return rc;
+}
+
+void fill_dev(lbm_handle *h)
+{
+    Dev &D = h->D;
+    const lbm_params &P = h->prm;
+    const Layout &L = h->L;
+    char *ws = h->ws;
+    D.nx = h->d.nx;
+    D.ny = h->d.ny;
+    D.pitch = L.pitch;
+    D.np = h->np;
+    D.ps = L.ps;
+    D.per_x = (h->d.bc & LBM_BC_PERIODIC_X) ? 1 : 0;
+    D.per_y = (h->d.bc & LBM_BC_PERIODIC_Y) ? 1 : 0;
+    const double s_nu = 1.0 / (3.0 * P.nu + 0.5);
+    D.s_nu = (float)s_nu;
+    D.s_e = (float)(P.s_e > 0 ? P.s_e : 1.0);
+    D.s_eps = (float)(P.s_eps > 0 ? P.s_eps : 1.0);
+    D.s_q = (float)(P.s_q > 0 ? P.s_q : 8.0 * (2.0 - s_nu) / (8.0 - s_nu));
+    D.q_k = (float)(1.0 / (P.alpha / 0.2 + 0.5));
+    D.q_e = (float)(P.q_e > 0 ? P.q_e : 1.0);
+    D.q_nu = (float)(P.q_nu > 0 ? P.q_nu : 1.0);
+    D.gbeta = (float)(P.g * P.beta);
+    D.T0 = (float)P.T0;
+    D.bfx = (float)P.body_fx;
+    D.bfy = (float)P.body_fy;
+    for (int i = 0; i < 4; ++i) D.Twall[i] = (float)h->d.T_wall[i];
+    D.g = P.g;
+    D.rho_f = P.rho_f;
+    D.eps_w = P.eps_w;
+    D.s_rep = P.s_rep;
+    D.fixed = (P.flags & LBM_FLAG_FIXED_PARTICLES) ? 1 : 0;
+    D.flags = reinterpret_cast<uint8_t *>(ws + L.flags);
+    D.slot_node = reinterpret_cast<int *>(ws + L.slot_node);
+    D.slot_q = reinterpret_cast<float *>(ws + L.slot_q);
+    D.slot_base = reinterpret_cast<int *>(ws + L.slot_base);
+    D.cur = soa_at(ws, L.cur, h->np);
+    D.nxt = soa_at(ws, L.nxt, h->np);
+    D.px = reinterpret_cast<double *>(ws + L.prev);
+    D.py = D.px + h->np;
+    D.force = reinterpret_cast<double *>(ws + L.force);
+    D.status = reinterpret_cast<Status *>(ws + L.status);
+    for (int b = 0; b < 2; ++b) {
+        h->A[b] = reinterpret_cast<float *>(ws + L.A[b]);
+        h->own[b] = reinterpret_cast<int *>(ws + L.own[b]);
+    }
+}
+
+// Upload a particle array into the current state (and the copies the step
+// keeps), then build the owner map and flags of those positions.
+int upload_particles(lbm_handle *h, const lbm_particle *p)
+{
+    const int n = h->np;
+    if (n == 0) return LBM_OK;
+    std::vector<double> soa((size_t)9 * n);
+    for (int a = 0; a < n; ++a) {
+        const double v[9] = {p[a].x, p[a].y, p[a].ux, p[a].uy, p[a].theta, p[a].omega,
+                             p[a].r, p[a].rho, p[a].T};
+        for (int f = 0; f < 9; ++f) soa[(size_t)f * n + a] = v[f];
+    }
+    const size_t bytes = soa.size() * sizeof(double);
+    CK(h, cudaMemcpyAsync(h->D.cur.x, soa.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->D.nxt.x, h->D.cur.x, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->D.px, h->D.cur.x, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int rebuild_maps(lbm_handle *h)
+{
+    const size_t nn = (size_t)h->d.nx * h->d.ny;
+    CK(h, cudaMemsetAsync(h->own[0], 0xff, nn * sizeof(int), h->stream));
+    CK(h, cudaMemsetAsync(h->own[1], 0xff, nn * sizeof(int), h->stream));
+    CK(h, cudaMemsetAsync(h->D.flags, 0, (size_t)h->L.pitch * h->d.ny, h->stream));
+    int *oc = h->own[h->parity];
+    CK(h, launch_raster(h->D, oc, h->D.cur, h->stream));
+    CK(h, launch_flags(h->D, oc, oc, 0, h->stream));
+    // the owner map one step back, which the first clear expects in the other buffer
+    PartSoA prev = h->D.cur;
+    prev.x = h->D.px;
+    prev.y = h->D.py;
+    CK(h, launch_raster(h->D, h->own[h->parity ^ 1], prev, h->stream));
+    return LBM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *lbm_strerror(int code)
+{
+    switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOSPC: return "workspace too small";
+    case LBM_ENUMERIC: return "non-finite or non-physical density/temperature";
+    case LBM_EDOMAIN: return "a particle crossed a cavity wall";
+    case LBM_EOVERFLOW: return "a fixed index array line holds more than one link";
+    case LBM_ETIMEOUT: return "a bounded device wait gave up";
+    case LBM_ECUDA: return "CUDA runtime error";
+    default: return "unknown error";
+    }
+}
+
+int lbm_query_footprint(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_params *prm,
+                        size_t *bytes)
+{
+    if (!bytes) return LBM_EINVAL;
+    int rc = validate(d, p, n, prm);
+    if (rc) return rc;
+    Layout L;
+    layout(d, p, n, L);
+    *bytes = L.total;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32_t n,
+             const lbm_params *prm, void *d_workspace, size_t ws_bytes, void *stream)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    int rc = validate(d, p, n, prm);
+    if (rc) return rc;
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)) return LBM_EINVAL;
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_EINVAL;
+    h->d = *d;
+    h->prm = *prm;
+    h->np = n;
+    layout(d, p, n, h->L);
+    if (ws_bytes < h->L.total) {
+        delete h;
+        return LBM_ENOSPC;
+    }
+    h->ws = static_cast<char *>(d_workspace);
+    h->stream = static_cast<cudaStream_t>(stream);
+    fill_dev(h);
+    auto fail = [&](int code) {
+        lbm_destroy(h);
+        return code;
+    };
+    if (cudaMemsetAsync(h->D.status, 0, sizeof(Status), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    if (n > 0) {
+        std::vector<int> base(n + 1, 0);
+        for (int a = 0; a < n; ++a) base[a + 1] = base[a] + slot_capacity(p[a].r);
+        if (cudaMemcpyAsync(h->D.slot_base, base.data(), base.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+            return fail(LBM_ECUDA);
+        if (cudaMemsetAsync(h->D.slot_node, 0xff, h->L.nslots * sizeof(int), h->stream) != cudaSuccess)
+            return fail(LBM_ECUDA);
+        if (cudaMemsetAsync(h->D.slot_q, 0, h->L.nslots * sizeof(float), h->stream) != cudaSuccess)
+            return fail(LBM_ECUDA);
+        if (cudaMemsetAsync(h->D.force, 0, 3 * (size_t)n * sizeof(double), h->stream) != cudaSuccess)
+            return fail(LBM_ECUDA);
+        if ((rc = upload_particles(h, p))) return fail(rc);
+    }
+    if ((rc = rebuild_maps(h))) return fail(rc);
+    const size_t abytes = (size_t)kPop * h->L.ps * sizeof(float);
+    if (cudaMemsetAsync(h->A[1], 0, abytes, h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    if (launch_init_collide(h->D, h->A[1], h->A[0], (float)prm->T_init, 0, h->stream) != cudaSuccess)
+        return fail(LBM_ECUDA);
+    if ((rc = sync_status(h))) return fail(rc);
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle *h, int32_t nsteps)
+{
+    if (!h || nsteps < 0) return LBM_EINVAL;
+    if (h->sticky) return h->sticky;
+    const bool graph = !(h->prm.flags & LBM_FLAG_NO_GRAPH) && !h->timing;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        int rc;
+        if (graph) {
+            if (!h->gexec[h->parity] && (rc = capture(h, h->parity))) return rc;
+            CK(h, cudaGraphLaunch(h->gexec[h->parity], h->stream));
+            h->launches += kernels_per_step(h);
+        } else if ((rc = enqueue_step(h, h->parity, h->stream))) {
+            return rc;
+        }
+        h->parity ^= 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle *h)
+{
+    if (!h) return LBM_EINVAL;
+    return sync_status(h);
+}
+
+int lbm_get_fields(lbm_handle *h, float *rho, float *ux, float *uy, float *T, int32_t on_device)
+{
+    if (!h || !rho || !ux || !uy || !T) return LBM_EINVAL;
+    const float *A = h->A[h->parity];
+    const int nx = h->d.nx, ny = h->d.ny;
+    if (on_device) {
+        CK(h, launch_fields(h->D, A, 0, ny, rho, ux, uy, T, h->stream));
+        return h->sticky;
+    }
+    int rc = sync_status(h);
+    if (rc) return rc;
+    float *st = reinterpret_cast<float *>(h->ws + h->L.stage);
+    const int R = h->L.stage_rows;
+    float *outs[4] = {rho, ux, uy, T};
+    for (int r0 = 0; r0 < ny; r0 += R) {
+        const int rows = std::min(R, ny - r0);
+        const size_t cnt = (size_t)rows * nx;
+        CK(h, launch_fields(h->D, A, r0, rows, st, st + cnt, st + 2 * cnt, st + 3 * cnt, h->stream));
+        for (int f = 0; f < 4; ++f)
+            CK(h, cudaMemcpyAsync(outs[f] + (size_t)r0 * nx, st + f * cnt, cnt * sizeof(float),
+                                  cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_get_particles(lbm_handle *h, lbm_particle *out, int32_t n)
+{
+    if (!h || n != h->np || (n > 0 && !out)) return LBM_EINVAL;
+    if (n > 0) {
+        lbm_particle *pk = reinterpret_cast<lbm_particle *>(h->ws + h->L.pack);
+        CK(h, launch_pack_particles(h->D, pk, h->stream));
+        CK(h, cudaMemcpyAsync(out, pk, (size_t)n * sizeof(lbm_particle), cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
+    return sync_status(h);
+}
+
+int lbm_get_forces(lbm_handle *h, double *out, int32_t n)
+{
+    if (!h || n != h->np || (n > 0 && !out)) return LBM_EINVAL;
+    if (n > 0)
+        CK(h, cudaMemcpyAsync(out, h->D.force, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+    return sync_status(h);
+}
+
+int lbm_destroy(lbm_handle *h)
+{
+    if (!h) return LBM_EINVAL;
+    if (h->stream || h->cap) cudaStreamSynchronize(h->stream);
+    for (int b = 0; b < 2; ++b)
+        if (h->gexec[b]) cudaGraphExecDestroy(h->gexec[b]);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    for (auto &e : h->ev) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    delete h;
+    return LBM_OK;
+}
+
+int lbm_get_owner(lbm_handle *h, int32_t *out)
+{
+    if (!h || !out) return LBM_EINVAL;
+    CK(h, cudaMemcpyAsync(out, h->own[h->parity], (size_t)h->d.nx * h->d.ny * sizeof(int),
+                          cudaMemcpyDeviceToHost, h->stream));
+    return sync_status(h);
+}
+
+int lbm_get_slots(lbm_handle *h, int32_t *node, float *q, int64_t cap, int64_t *count)
+{
+    if (!h || !count || cap < 0) return LBM_EINVAL;
+    *count = (int64_t)h->L.nslots;
+    const size_t m = std::min<size_t>((size_t)cap, h->L.nslots);
+    if (m > 0) {
+        if (!node || !q) return LBM_EINVAL;
+        CK(h, cudaMemcpyAsync(node, h->D.slot_node, m * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaMemcpyAsync(q, h->D.slot_q, m * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    }
+    return sync_status(h);
+}
+
+// State image: distributions (current buffer), owner map, flags, particle
+// state and previous positions.
+static size_t state_parts(const lbm_handle *h, size_t sz[5])
+{
+    sz[0] = (size_t)kPop * h->L.ps * sizeof(float);
+    sz[1] = (size_t)h->d.nx * h->d.ny * sizeof(int);
+    sz[2] = (size_t)h->L.pitch * h->d.ny;
+    sz[3] = (size_t)9 * h->np * sizeof(double);
+    sz[4] = (size_t)2 * h->np * sizeof(double);
+    return sz[0] + sz[1] + sz[2] + sz[3] + sz[4];
+}
+
+int lbm_state_bytes(lbm_handle *h, size_t *bytes)
+{
+    if (!h || !bytes) return LBM_EINVAL;
+    size_t sz[5];
+    *bytes = state_parts(h, sz);
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle *h, void *buf, size_t bytes)
+{
+    size_t sz[5];
+    if (!h || !buf || bytes < state_parts(h, sz)) return LBM_EINVAL;
+    int rc = sync_status(h);
+    if (rc) return rc;
+    const void *src[5] = {h->A[h->parity], h->own[h->parity], h->D.flags, h->D.cur.x, h->D.px};
+    char *o = static_cast<char *>(buf);
+    for (int i = 0; i < 5; ++i) {
+        if (sz[i]) CK(h, cudaMemcpyAsync(o, src[i], sz[i], cudaMemcpyDeviceToHost, h->stream));
+        o += sz[i];
+    }
+    return sync_status(h);
+}
+
+int lbm_set_state(lbm_handle *h, const void *buf, size_t bytes)
+{
+    size_t sz[5];
+    if (!h || !buf || bytes < state_parts(h, sz)) return LBM_EINVAL;
+    CK(h, cudaStreamSynchronize(h->stream));
+    void *dst[5] = {h->A[h->parity], h->own[h->parity], h->D.flags, h->D.cur.x, h->D.px};
+    const char *in = static_cast<const char *>(buf);
+    for (int i = 0; i < 5; ++i) {
+        if (sz[i]) CK(h, cudaMemcpyAsync(dst[i], in, sz[i], cudaMemcpyHostToDevice, h->stream));
+        in += sz[i];
+    }
+    if (h->np > 0) {
+        CK(h, cudaMemcpyAsync(h->D.nxt.x, h->D.cur.x, sz[3], cudaMemcpyDeviceToDevice, h->stream));
+        // owner map one step back, expected by the next clear
+        const size_t nn = (size_t)h->d.nx * h->d.ny;
+        CK(h, cudaMemsetAsync(h->own[h->parity ^ 1], 0xff, nn * sizeof(int), h->stream));
+        PartSoA prev = h->D.cur;
+        prev.x = h->D.px;
+        prev.y = h->D.py;
+        CK(h, launch_raster(h->D, h->own[h->parity ^ 1], prev, h->stream));
+    }
+    return sync_status(h);
+}
+
+int lbm_set_distributions(lbm_handle *h, const double *f, const double *g)
+{
+    if (!h || !f || !g) return LBM_EINVAL;
+    int rc = sync_status(h);
+    if (rc) return rc;
+    const int nx = h->d.nx, ny = h->d.ny, pitch = h->L.pitch;
+    const long long ps = h->L.ps;
+    const size_t nn = (size_t)nx * ny;
+    std::vector<float> img((size_t)kPop * ps, 0.f);
+    for (int p = 0; p < kPop; ++p)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const size_t s = (size_t)j * nx + i;
+                const double v = p < kQ9 ? f[(size_t)p * nn + s] - w9d(p) : g[(size_t)(p - kQ9) * nn + s];
+                img[(size_t)p * ps + (size_t)j * pitch + i] = std::isfinite(v) ? (float)v : 0.f;
+            }
+    float *scratch = h->A[h->parity ^ 1];
+    CK(h, cudaMemcpyAsync(scratch, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice,
+                          h->stream));
+    CK(h, launch_init_collide(h->D, scratch, h->A[h->parity], 0.f, 1, h->stream));
+    return sync_status(h);
+}
+
+int lbm_get_counters(lbm_handle *h, int64_t *out8)
+{
+    if (!h || !out8) return LBM_EINVAL;
+    int rc = sync_status(h);
+    if (rc) return rc;
+    unsigned long long c[kNumCounters];
+    CK(h, cudaMemcpy(c, h->D.status->cnt[h->parity ^ 1], sizeof c, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < kNumCounters; ++i) out8[i] = (int64_t)c[i];
+    return LBM_OK;
+}
+
+int lbm_kernel_timing(lbm_handle *h, int32_t enable)
+{
+    if (!h) return LBM_EINVAL;
+    h->timing = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_kernel_times(lbm_handle *h, double *ms, int64_t *launches, int32_t nk)
+{
+    if (!h || !ms || !launches || nk < 0) return LBM_EINVAL;
+    CK(h, cudaStreamSynchronize(h->stream));
+    int rc = fold_events(h);
+    if (rc) return rc;
+    for (int k = 0; k < nk && k < kNumKernelKinds; ++k) {
+        ms[k] = h->acc_ms[k];
+        launches[k] = h->acc_n[k];
+        h->acc_ms[k] = 0.0;
+        h->acc_n[k] = 0;
+    }
+    return LBM_OK;
+}
+
+int32_t lbm_kernel_count(void) { return kNumKernelKinds; }
+
+const char *lbm_kernel_name(int32_t k)
+{
+    return (k >= 0 && k < kNumKernelKinds) ? kKernelNames[k] : "";
+}
+
+int64_t lbm_launch_count(lbm_handle *h) { return h ? h->launches : -1; }
+
+} // extern "C"

@@ -1,0 +1,180 @@
+// Internal declarations of the sm_103a lattice Boltzmann library: lattice
+// constants, the device view of the caller's workspace, exact geometry
+// helpers and the kernel launchers.  Not part of the public ABI (lbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Lattices (Sec. 2.1).  D2Q9 e0..e8 as in lbm.h; D2Q5 uses e0..e4.  The 14
+// stored populations are the 9 flow deviations f~_i = f_i - w_i followed by
+// the 5 raw temperature populations g_i.
+// ---------------------------------------------------------------------------
+constexpr int kQ9 = 9;
+constexpr int kQ5 = 5;
+constexpr int kPop = 14;
+
+__host__ __device__ constexpr int ex(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5;
+}
+// D2Q9 weights (4/9, 1/9, 1/36).
+__host__ __device__ constexpr float w9(int i) { return i == 0 ? 4.f / 9.f : i <= 4 ? 1.f / 9.f : 1.f / 36.f; }
+__host__ __device__ constexpr double w9d(int i) { return i == 0 ? 4.0 / 9.0 : i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0; }
+// D2Q5 weights for an energy-moment equilibrium a T with a = -2:
+// w0 = (1 - a)/5 = 3/5, w1..4 = (4 + a)/20 = 1/10; c_sT^2 = (4 + a)/10 = 1/5.
+__host__ __device__ constexpr float w5(int i) { return i == 0 ? 0.6f : 0.1f; }
+// Population index p in [0, 14) -> lattice direction.
+__host__ __device__ constexpr int pdir(int p) { return p < kQ9 ? p : p - kQ9; }
+
+// Per-node state bytes of the flag map.
+constexpr uint8_t kFluid = 0;   // fluid at the previous and the current time
+constexpr uint8_t kSolid = 1;   // inside a particle at the current time
+constexpr uint8_t kNewborn = 2; // uncovered by a particle during the last step
+
+// Device error bits (sticky, mapped to LBM_E* on the host).
+constexpr unsigned kErrNumeric = 1u;
+constexpr unsigned kErrDomain = 2u;
+constexpr unsigned kErrOverflow = 4u;
+
+// Counter slots (see lbm_get_counters).
+enum { kCntBzLinear = 0, kCntBzSimple, kCntThermHalf, kCntRfLinear, kCntRfCopy, kCntRfEq,
+       kCntNewborn, kCntLinks, kNumCounters };
+
+struct Status {
+    unsigned int err;
+    unsigned int pad;
+    unsigned long long cnt[2][kNumCounters]; // double-buffered by step parity
+};
+
+// Structure-of-arrays particle state on the device (FP64).
+struct PartSoA {
+    double *x, *y, *ux, *uy, *th, *om, *r, *rho, *T;
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+    int nx, ny, pitch, np;
+    long long ps; // plane stride in elements
+    int per_x, per_y;
+    // physics (FP32 for the lattice, FP64 for particles)
+    float s_e, s_eps, s_q, s_nu, q_k, q_e, q_nu;
+    float gbeta, T0, bfx, bfy;
+    float Twall[4];
+    double g, rho_f, eps_w, s_rep;
+    int fixed;
+    // device buffers
+    uint8_t *flags;    // [ny][pitch]
+    int *slot_node;    // [nslots]
+    float *slot_q;     // [nslots]
+    int *slot_base;    // [np + 1]
+    PartSoA cur, nxt;  // state at n (and n+1 after the raster rotation) / new state
+    double *px, *py;   // positions one step back (boxes to clear)
+    double *force;     // [3 np]: hydrodynamic Fx, Fy, Tz of the last step
+    Status *status;
+};
+
+// ---------------------------------------------------------------------------
+// Exact FP64 geometry shared by raster, gather and refill.  Every operation is
+// a correctly rounded IEEE operation with no FMA contraction, so the results
+// agree bit for bit with any other implementation of the same expressions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool in_disk(int i, int j, double xc, double yc, double r)
+{
+    double dx = __dsub_rn((double)i, xc);
+    double dy = __dsub_rn((double)j, yc);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= __dmul_rn(r, r);
+}
+
+// Wall fraction q (Sec. 2.3) of the link (i,j) -> (i,j) + e_k on the circle
+// (xc, yc, r): t = (|d|^2 - r^2) / (-(d.e) + sqrt((d.e)^2 - |e|^2 (|d|^2 - r^2))).
+__device__ __forceinline__ double link_q(int i, int j, int k, double xc, double yc, double r)
+{
+    double dx = __dsub_rn((double)i, xc);
+    double dy = __dsub_rn((double)j, yc);
+    double de = __dadd_rn(__dmul_rn((double)ex(k), dx), __dmul_rn((double)ey(k), dy));
+    double a = (double)(ex(k) * ex(k) + ey(k) * ey(k));
+    double c = __dsub_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(r, r));
+    double disc = __dsub_rn(__dmul_rn(de, de), __dmul_rn(a, c));
+    if (disc < 0.0) disc = 0.0;
+    double t = __ddiv_rn(c, __dadd_rn(-de, __dsqrt_rn(disc)));
+    return t > 1.0 ? 1.0 : t;
+}
+
+// Effective zone of Sec. 3: N = ceil(2r) + 3 nodes per side starting at
+// floor(c - r) - 1 (equal to the paper's INT(c + r) - INT(c - r) + 3 for
+// integer radii); 12N - 12 fixed slots.
+__host__ __device__ inline int zone_size(double r) { return (int)ceil(2.0 * r) + 3; }
+__host__ __device__ inline int slot_capacity(double r) { return 12 * zone_size(r) - 12; }
+
+// Zone point (a, b) of the t-th node on line `line` of direction k; false
+// when it falls outside the N x N zone.  e1/e3: rows (line = b); e2/e4:
+// columns (line = a); e5/e7: constant a - b (line = a - b + N - 2); e6/e8:
+// constant a + b (line = a + b - 1).
+__host__ __device__ inline bool zone_point(int k, int N, int line, int t, int &a, int &b)
+{
+    if (k == 1 || k == 3) {
+        a = t;
+        b = line;
+    } else if (k == 2 || k == 4) {
+        a = line;
+        b = t;
+    } else if (k == 5 || k == 7) {
+        a = t;
+        b = t - (line - (N - 2));
+    } else {
+        a = t;
+        b = (line + 1) - t;
+    }
+    return b >= 0 && b < N;
+}
+
+// Slot s of a zone of size N -> direction k and line.
+__host__ __device__ inline void slot_dir_line(int s, int N, int &k, int &line)
+{
+    if (s < 4 * N) {
+        k = 1 + s / N;
+        line = s % N;
+    } else {
+        int t = s - 4 * N, m = 2 * N - 3;
+        k = 5 + t / m;
+        line = t % m;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in k_fluid.cu and k_particles.cu).
+// ---------------------------------------------------------------------------
+enum KernelKind { kKLinks = 0, kKParticles, kKClear, kKRaster, kKFlags, kKStreamCollide,
+                  kKInit, kKFields, kNumKernelKinds };
+
+cudaError_t launch_stream_collide(const Dev &D, const float *Ain, float *Aout, const int *own_cur,
+                                  int parity, cudaStream_t s);
+// mode 0: fluid at rest (unit density, T_init) then collide; mode 1: collide
+// the pre-collision values read from Ain at each node.
+cudaError_t launch_init_collide(const Dev &D, const float *Ain, float *Aout, float T_init, int mode,
+                                cudaStream_t s);
+cudaError_t launch_fields(const Dev &D, const float *A, int row0, int rows, float *rho, float *ux,
+                          float *uy, float *T, cudaStream_t s);
+cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity, cudaStream_t s);
+cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s);
+cudaError_t launch_clear(const Dev &D, int *own_nxt, cudaStream_t s);
+cudaError_t launch_raster(const Dev &D, int *own, const PartSoA &pos, cudaStream_t s);
+cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate,
+                         cudaStream_t s);
+cudaError_t launch_pack_particles(const Dev &D, lbm_particle *out, cudaStream_t s);
+
+} // namespace lbm

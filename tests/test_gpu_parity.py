@@ -1,0 +1,278 @@
+"""GPU parity: the sm_103a library (through its C ABI) against the FP64 oracle.
+
+Tolerances.  FP32 storage of f - w and g, FP32 collision: a single step from
+a common state agrees to rel-L2 <= 1e-6 per field; the coupled 256^2 run
+agrees to rel-L2 <= 1e-5 per field (rho - 1, ux, uy, T over the fluid nodes
+both runs share) after 100 steps, and the particle centres to 1e-4 lattice
+units.  Owner maps and fixed index arrays built from the same positions are
+bit-exact.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2308_16597_gb300 import lbm, workloads as W  # noqa: E402
+import oracle.oracle as orc  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def compare_fields(sim, ref, tol, min_norm=1e-12):
+    got, exp = sim.fields(), ref.fields()
+    fluid = ~np.isnan(exp[0]) & ~np.isnan(got[0])
+    assert fluid.mean() > 0.5
+    errs = {}
+    for name, a, b in zip(("rho-1", "ux", "uy", "T"), got, exp):
+        a = a[fluid].astype(np.float64)
+        b = b[fluid]
+        if name == "rho-1":
+            a, b = a - 1.0, b - 1.0
+        if np.linalg.norm(b) < min_norm * np.sqrt(b.size):
+            errs[name] = np.abs(a - b).max()
+            assert errs[name] < 1e-7, (name, errs[name])
+            continue
+        errs[name] = rel_l2(a, b)
+        assert errs[name] <= tol, (name, errs[name])
+    return errs
+
+
+def base_f():
+    return orc.feq(1.0, 0.0, 0.0), orc.geq(1.0, 0.0, 0.0)
+
+
+# --------------------------------------------------------------------------- lattice only
+def test_rest_state_stays_exactly_at_rest():
+    dom = W.cavity(133, 70)
+    sim = lbm.Simulation(dom, None, W.base_params(0.05, 0.71, 1e-4))
+    sim.step(100)
+    rho, ux, uy, T = sim.fields()
+    assert np.all(rho == 1.0) and np.all(ux == 0.0) and np.all(uy == 0.0) and np.all(T == 0.0)
+
+
+@pytest.mark.parametrize("shape,periodic", [((300, 37), (0, 0)), ((257, 64), (1, 0)),
+                                            ((129, 131), (1, 1)), ((5, 4), (0, 0)),
+                                            ((520, 9), (0, 1))])
+def test_single_step_from_a_random_state(shape, periodic):
+    nx, ny = shape
+    dom = W.cavity(nx, ny, T_wall=(0.3, 0.8, 1.0, 0.1), periodic_x=periodic[0],
+                   periodic_y=periodic[1])
+    prm = W.base_params(0.03, 0.71, 3e-3, body_fx=1e-5)
+    f, g = W.random_state(nx, ny, 7, *base_f(), amp=2e-2)
+    sim = lbm.Simulation(dom, None, prm)
+    ref = orc.Oracle(dom, None, prm)
+    sim.set_distributions(f, g)
+    ref.set_state(f, g)
+    compare_fields(sim, ref, 1e-6)
+    for steps in (1, 3):
+        sim.step(steps)
+        ref.step(steps)
+        compare_fields(sim, ref, 1e-6)
+
+
+def test_poiseuille_profile_on_the_gpu():
+    H, nu, Fx = 10, 0.1, 1e-6
+    prm = W.base_params(nu, 1.0, 0.0, body_fx=Fx)
+    sim = lbm.Simulation(W.cavity(64, H, periodic_x=1), None, prm)
+    sim.step(20000)
+    rho, ux, uy, T = sim.fields()
+    y = np.arange(H)
+    exact = Fx / (2 * nu) * (y + 0.5) * (H - 0.5 - y)
+    assert np.abs(ux - exact[:, None]).max() / exact.max() < 1e-4
+    assert np.abs(uy).max() < 1e-9
+
+
+def test_linear_conduction_on_the_gpu():
+    H = 8
+    prm = W.base_params(0.1, 0.1 / 0.2, 0.0)
+    sim = lbm.Simulation(W.cavity(40, H, T_wall=(0, 0, 1.0, 0.0), periodic_x=1), None, prm)
+    sim.step(4000)
+    T = sim.fields()[3]
+    y = np.arange(H)
+    assert np.abs(T - (1 - (y + 0.5) / H)[:, None]).max() < 2e-6
+
+
+def test_mass_conservation_fp32_closed_box():
+    prm = W.base_params(0.02, 0.71, 5e-4)
+    sim = lbm.Simulation(W.cavity(96, 80, T_wall=(0, 0, 1.0, 0.0)), None, prm)
+    m0 = np.nansum(sim.fields()[0].astype(np.float64))
+    sim.step(2000)
+    rho = sim.fields()[0].astype(np.float64)
+    assert abs(np.nansum(rho) - m0) / m0 < 1e-6
+
+
+# --------------------------------------------------------------------------- geometry
+def test_owner_map_and_fixed_slots_are_bit_exact():
+    wl = W.parity_256()
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    own0 = orc.raster(wl.nx, wl.ny, wl.particles)
+    assert np.array_equal(sim.owner(), own0)
+    sim.step(1)
+    node, q = sim.slots()
+    onode, oq, over = orc.build_slots(wl.nx, wl.ny, own0, wl.particles)
+    assert over == 0
+    assert np.array_equal(node, onode)
+    assert np.array_equal(q.view(np.uint32), oq.view(np.uint32))
+    # later steps: slots of the last step equal the oracle's slots built from
+    # the positions the GPU had at the start of that step
+    for _ in range(3):
+        sim.step(29)
+        p = sim.particles()
+        sim.step(1)
+        own = orc.raster(wl.nx, wl.ny, p)
+        onode, oq, _ = orc.build_slots(wl.nx, wl.ny, own, p)
+        node, q = sim.slots()
+        assert np.array_equal(node, onode)
+        assert np.array_equal(q.view(np.uint32), oq.view(np.uint32))
+        assert np.array_equal(sim.owner(), orc.raster(wl.nx, wl.ny, sim.particles()))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_slots_match_brute_force_links_for_random_radii(seed):
+    rng = np.random.default_rng(seed)
+    nx, ny = int(rng.integers(60, 140)), int(rng.integers(60, 140))
+    n = int(rng.integers(2, 8))
+    parts = W.rsa_disks(rng, n, rng.uniform(2.5, 12.0, n), 15, nx - 16, 15, ny - 16, 0.5)
+    parts["rho"] = 1.5
+    prm = W.base_params(0.05, 0.71, 0.0, fixed_particles=1)
+    sim = lbm.Simulation(W.cavity(nx, ny), parts, prm)
+    sim.step(1)
+    own = orc.raster(nx, ny, parts)
+    onode, oq, over = orc.build_slots(nx, ny, own, parts)
+    node, q = sim.slots()
+    assert over == 0 and np.array_equal(node, onode)
+    assert np.array_equal(q.view(np.uint32), oq.view(np.uint32))
+    bn, bd, bp, bq = orc.links_bruteforce(nx, ny, own, parts)
+    assert (node >= 0).sum() == len(bn)
+    assert sim.counters()[7] == len(bn)
+
+
+# --------------------------------------------------------------------------- coupled
+def test_first_step_forces_match_the_oracle():
+    wl = W.parity_256()
+    prm = dict(wl.params, fixed_particles=1)
+    sim = lbm.Simulation(wl.domain, wl.particles, prm)
+    ref = orc.Oracle(wl.domain, wl.particles, prm)
+    f, g = W.random_state(wl.nx, wl.ny, 3, *base_f(), amp=1e-2)
+    sim.set_distributions(f, g)
+    ref.set_state(f, g)
+    sim.step(1)
+    ref.step(1)
+    Fg, Fo = sim.forces(), ref.forces()
+    assert np.abs(Fg[:, :2] - Fo[:, :2]).max() <= 1e-6 * np.abs(Fo[:, :2]).max()
+    assert np.abs(Fg[:, 2] - Fo[:, 2]).max() <= 1e-5 * np.abs(Fo[:, 2]).max()
+    cg, co = sim.counters(), ref.counters()
+    assert cg[7] == co[7] and cg[0] == co[0] and cg[1] == co[1] and cg[2] == co[2]
+    compare_fields(sim, ref, 1e-6)
+
+
+def test_cavity_256_eight_disks_100_steps():
+    """256^2 cavity, 8 hot disks: fields rel-L2 <= 1e-5 and centres within
+    1e-4 lattice units of the FP64 oracle after 100 steps."""
+    wl = W.parity_256()
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    ref = orc.Oracle(wl.domain, wl.particles, wl.params)
+    for _ in range(4):
+        sim.step(25)
+        assert ref.step(25) == 0
+        pg, po = sim.particles(), ref.particles()
+        assert np.abs(pg["x"] - po["x"]).max() < 1e-4
+        assert np.abs(pg["y"] - po["y"]).max() < 1e-4
+    errs = compare_fields(sim, ref, 1e-5)
+    print("rel-L2 after 100 steps:", errs)
+
+
+def test_moving_disk_refills_like_the_oracle():
+    parts = np.zeros(2, W.PARTICLE_DTYPE)
+    parts["x"], parts["y"] = [40.3, 90.6], [50.2, 47.7]
+    parts["r"], parts["rho"], parts["T"] = 8.5, 1.5, 1.0
+    parts["ux"], parts["uy"] = [0.04, -0.03], [-0.02, 0.035]
+    dom = W.cavity(140, 100)
+    prm = W.base_params(0.05, 0.71, 1e-4)
+    sim = lbm.Simulation(dom, parts, prm)
+    ref = orc.Oracle(dom, parts, prm)
+    nb_g = nb_o = 0
+    for _ in range(30):
+        sim.step(1)
+        ref.step(1)
+        nb_g += sim.counters()[6]
+        nb_o += ref.counters()[6]
+    assert nb_o > 0 and nb_g == nb_o
+    compare_fields(sim, ref, 1e-5)
+    pg, po = sim.particles(), ref.particles()
+    assert np.abs(pg["x"] - po["x"]).max() < 1e-6
+
+
+# --------------------------------------------------------------------------- runtime
+def test_runs_are_deterministic_and_graphs_match_direct_launches():
+    wl = W.parity_256()
+    a = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    b = lbm.Simulation(wl.domain, wl.particles, wl.params, flags=lbm.LBM_FLAG_NO_GRAPH)
+    a.step(40)
+    b.step(40)
+    assert np.array_equal(a.get_state(), b.get_state())
+
+
+def test_checkpoint_restore_is_bit_exact():
+    wl = W.parity_256()
+    a = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    a.step(30)
+    snap = a.get_state()
+    a.step(30)
+    b = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    b.set_state(snap)
+    b.step(30)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(a.particles(), b.particles())
+
+
+def test_workspace_too_small_is_rejected():
+    wl = W.parity_256()
+    d = lbm.make_domain(**wl.domain)
+    p = lbm.pack_particles(wl.particles)
+    prm = lbm.make_params(**wl.params)
+    need = lbm.lbm_query_footprint(d, p, prm)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_init(d, p, prm, ws.data_ptr(), need - 256, 0)
+    assert e.value.code == lbm.LBM_ENOSPC
+
+
+def test_kernel_timing_counts_launches():
+    wl = W.parity_256()
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    sim.kernel_timing(True)
+    sim.step(5)
+    t = sim.kernel_times()
+    assert t["stream_collide"][1] == 5 and t["link_gather_bb_force"][1] == 5
+    assert t["stream_collide"][0] > 0.0
+
+
+# --------------------------------------------------------------------------- full size
+@pytest.mark.slow
+def test_full_size_4000_cavity_two_steps():
+    """The 4000^2 / 4800-disk workload in the benchmark's launch
+    configuration: owner map bit-exact at init and every field within FP32
+    tolerance of the oracle after two steps."""
+    wl = W.sedimentation_4000()
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    ref = orc.Oracle(wl.domain, wl.particles, wl.params)
+    assert np.array_equal(sim.owner(), ref.owner())
+    sim.step(2)
+    assert ref.step(2) == 0
+    compare_fields(sim, ref, 1e-5)
+    pg, po = sim.particles(), ref.particles()
+    assert np.abs(pg["y"] - po["y"]).max() < 1e-8
