@@ -129,12 +129,14 @@ int lbm_step(lbm_handle *h, int32_t nsteps);
 /* Wait for the stream; return the sticky device error, if any. */
 int lbm_sync(lbm_handle *h);
 
-/* Macroscopic fields at the current time: rho = sum f, T = sum g,
- * u = (sum e f + F/2)/rho (Sec. 2.1), recovered from the stored
- * post-collision state; NaN at solid nodes.  Each output is [ny][nx] float.
- * on_device != 0: the four pointers are device memory and the call only
- * enqueues; otherwise host memory and the call synchronises. */
-int lbm_get_fields(lbm_handle *h, float *rho, float *ux, float *uy, float *T, int32_t on_device);
+/* Macroscopic fields at the current time (Sec. 2.1): drho = rho - 1 with
+ * rho = sum f (the deviation from the reference density keeps full FP32
+ * precision, which rho itself would lose near 1), T = sum g and
+ * u = (sum e f + F/2)/rho, recovered from the stored post-collision state;
+ * NaN at solid nodes.  Each output is [ny][nx] float.  on_device != 0: the
+ * four pointers are device memory and the call only enqueues; otherwise host
+ * memory and the call synchronises. */
+int lbm_get_fields(lbm_handle *h, float *drho, float *ux, float *uy, float *T, int32_t on_device);
 
 /* Copy the particle states (host, n entries) after synchronising. */
 int lbm_get_particles(lbm_handle *h, lbm_particle *out, int32_t n);

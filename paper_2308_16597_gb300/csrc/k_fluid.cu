@@ -308,8 +308,8 @@ __global__ void k_init_collide(const Dev D, const float *__restrict__ Ain, float
     for (int p = 0; p < kPop; ++p) Aout[(long long)p * D.ps + n] = c[p];
 }
 
-// rho, u, T from the post-collision state: the collision keeps rho and T
-// and adds F to the momentum, so u = (sum e f+ - F/2)/rho equals the
+// rho - 1, u, T from the post-collision state: the collision keeps rho and
+// T and adds F to the momentum, so u = (sum e f+ - F/2)/rho equals the
 // pre-collision (sum e f + F/2)/rho of Sec. 2.1.
 __global__ void k_fields(const Dev D, const float *__restrict__ A, int row0, float *rho_o,
                          float *ux_o, float *uy_o, float *T_o)
@@ -334,7 +334,7 @@ __global__ void k_fields(const Dev D, const float *__restrict__ A, int row0, flo
     for (int i = 0; i < kQ5; ++i) T += A[(long long)(kQ9 + i) * D.ps + n];
     const float rho = 1.f + drho;
     const float Fx = D.bfx, Fy = rho * D.gbeta * (T - D.T0) + D.bfy;
-    rho_o[o] = rho;
+    rho_o[o] = drho;
     ux_o[o] = (jx - 0.5f * Fx) / rho;
     uy_o[o] = (jy - 0.5f * Fy) / rho;
     T_o[o] = T;

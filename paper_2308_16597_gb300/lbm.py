@@ -168,8 +168,8 @@ def lbm_destroy(h):
     _check(library().lbm_destroy(h), "lbm_destroy")
 
 
-def lbm_get_fields(h, rho_ptr, ux_ptr, uy_ptr, T_ptr, on_device: int):
-    _check(library().lbm_get_fields(h, rho_ptr, ux_ptr, uy_ptr, T_ptr, int(on_device)),
+def lbm_get_fields(h, drho_ptr, ux_ptr, uy_ptr, T_ptr, on_device: int):
+    _check(library().lbm_get_fields(h, drho_ptr, ux_ptr, uy_ptr, T_ptr, int(on_device)),
            "lbm_get_fields")
 
 
@@ -218,7 +218,8 @@ class Simulation:
         lbm_sync(self.h)
 
     def fields(self):
-        """rho, ux, uy, T as float32 numpy arrays [ny][nx] (NaN at solid nodes)."""
+        """drho = rho - 1, ux, uy, T as float32 numpy arrays [ny][nx] (NaN at
+        solid nodes)."""
         out = [np.empty((self.ny, self.nx), np.float32) for _ in range(4)]
         lbm_get_fields(self.h, *[o.ctypes.data for o in out], 0)
         return tuple(out)

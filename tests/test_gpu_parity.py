@@ -40,7 +40,7 @@ def compare_fields(sim, ref, tol, min_norm=1e-12):
         a = a[fluid].astype(np.float64)
         b = b[fluid]
         if name == "rho-1":
-            a, b = a - 1.0, b - 1.0
+            b = b - 1.0
         if np.linalg.norm(b) < min_norm * np.sqrt(b.size):
             errs[name] = np.abs(a - b).max()
             assert errs[name] < 1e-7, (name, errs[name])
@@ -59,8 +59,8 @@ def test_rest_state_stays_exactly_at_rest():
     dom = W.cavity(133, 70)
     sim = lbm.Simulation(dom, None, W.base_params(0.05, 0.71, 1e-4))
     sim.step(100)
-    rho, ux, uy, T = sim.fields()
-    assert np.all(rho == 1.0) and np.all(ux == 0.0) and np.all(uy == 0.0) and np.all(T == 0.0)
+    drho, ux, uy, T = sim.fields()
+    assert np.all(drho == 0.0) and np.all(ux == 0.0) and np.all(uy == 0.0) and np.all(T == 0.0)
 
 
 @pytest.mark.parametrize("shape,periodic", [((300, 37), (0, 0)), ((257, 64), (1, 0)),
@@ -108,10 +108,11 @@ def test_linear_conduction_on_the_gpu():
 def test_mass_conservation_fp32_closed_box():
     prm = W.base_params(0.02, 0.71, 5e-4)
     sim = lbm.Simulation(W.cavity(96, 80, T_wall=(0, 0, 1.0, 0.0)), None, prm)
-    m0 = np.nansum(sim.fields()[0].astype(np.float64))
+    n = 96 * 80
+    m0 = n + np.nansum(sim.fields()[0].astype(np.float64))
     sim.step(2000)
-    rho = sim.fields()[0].astype(np.float64)
-    assert abs(np.nansum(rho) - m0) / m0 < 1e-6
+    m1 = n + np.nansum(sim.fields()[0].astype(np.float64))
+    assert abs(m1 - m0) / m0 < 1e-7
 
 
 # --------------------------------------------------------------------------- geometry
