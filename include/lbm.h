@@ -158,8 +158,14 @@ int lbm_get_owner(lbm_handle *h, int32_t *out);
  * fraction (float).  *count receives the total slot count; cap bounds the
  * copy.  Synchronises. */
 int lbm_get_slots(lbm_handle *h, int32_t *node, float *q, int64_t cap, int64_t *count);
-/* Raw state (distributions, maps, particles) for checkpoint/restore between
- * handles created with identical arguments.  Synchronises. */
+/* Raw state for checkpoint/restore between handles created with identical
+ * arguments, in this order: the 14 distribution planes (9 flow deviations
+ * f - w, then 5 temperature populations) as FP32 [ny][pitch] planes spaced
+ * plane_stride elements apart, with pitch = nx rounded up to a multiple of 32
+ * and plane_stride = pitch * ny rounded up to a multiple of 64; the owner map
+ * (int32 [ny][nx]); the node flags (uint8 [ny][pitch]); the particle state as
+ * 9 arrays of n doubles (x, y, ux, uy, theta, omega, r, rho, T); the previous
+ * positions (2 arrays of n doubles).  Synchronises. */
 int lbm_state_bytes(lbm_handle *h, size_t *bytes);
 int lbm_get_state(lbm_handle *h, void *host_buf, size_t bytes);
 int lbm_set_state(lbm_handle *h, const void *host_buf, size_t bytes);
@@ -182,6 +188,7 @@ int32_t lbm_kernel_count(void);
 const char *lbm_kernel_name(int32_t k);
 /* Kernel launches enqueued by this handle since creation. */
 int64_t lbm_launch_count(lbm_handle *h);
+
 
 #ifdef __cplusplus
 }
