@@ -189,6 +189,35 @@ const char *lbm_kernel_name(int32_t k);
 /* Kernel launches enqueued by this handle since creation. */
 int64_t lbm_launch_count(lbm_handle *h);
 
+/* ---- allocation-free link forces ---------------------------------------- */
+/* No counterpart in the paper: an entry point for callers that cannot
+ * allocate device memory where they compute particle forces (their device
+ * memory belongs to an allocator or pool they cannot extend, or they run in a
+ * section where cudaMalloc is not allowed), so they cannot provide the
+ * workspace of lbm_init.  It performs the link gather into the fixed index
+ * array, the curved bounce-back and the momentum-exchange reduction of one
+ * step (the same arithmetic as lbm_step's link kernel) for caller-owned
+ * device buffers, and allocates nothing: its index array is a static device
+ * array of the library, holding at most 2,097,152 slots (12N - 12 per
+ * particle, N = ceil(2r) + 3) and 32,768 particles, 16 MiB + 128 KiB held on
+ * every GPU that loads the library until the process exits.
+ *   d_dist        14 FP32 planes in the layout of lbm_get_state (pitch,
+ *                 plane_stride in elements), post-collision; its entries at
+ *                 solid nodes are overwritten with the bounce-back values.
+ *   d_owner       int32 [ny][nx]: particle id per node, -1 for fluid.
+ *   d_particles   n particles (device); every radius must be <= r_max.
+ *   d_forces      output, 3 doubles per particle (Fx, Fy, Tz); NaN for a
+ *                 particle whose radius exceeds r_max or one of whose index
+ *                 lines holds two links.
+ * Asynchronous on stream.  Returns LBM_ENOSPC when n or n * (12N(r_max) - 12)
+ * exceeds the limits above, LBM_EINVAL for bad arguments.  Every call shares
+ * the static array and overwrites it, so calls whose GPU work overlaps race.
+ * The first call on a device looks up the array's address and should come
+ * before any stream capture. */
+int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
+                            const int32_t *d_owner, int32_t nx, int32_t ny,
+                            const lbm_particle *d_particles, int32_t n, double r_max,
+                            double *d_forces, void *stream);
 
 #ifdef __cplusplus
 }

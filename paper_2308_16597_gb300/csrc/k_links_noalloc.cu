@@ -1,0 +1,276 @@
+// Allocation-free variant of the link kernel: gather the fixed index array
+// of fluid-particle links, apply the curved bounce-back on every link and
+// reduce the momentum-exchange force and torque per particle, with the index
+// array held in a file-scope device array instead of a caller workspace.
+//
+// Who needs it: code that may not allocate device memory at the point where
+// it computes particle forces, e.g. a host application whose device memory
+// is owned by another allocator or pool it cannot extend, or a caller inside
+// a section where cudaMalloc is not allowed.  Such a caller still owns and
+// passes the distributions, the owner map, the particles and the force
+// output; the only scratch (the index array) lives here.
+//
+// The array holds 2,097,152 slots (node + wall fraction, 8 bytes each) and
+// the slot offsets of up to 32,768 particles: 16 MiB + 128 KiB held on every
+// GPU that loads the library, for the life of the process.  All calls share
+// it and it keeps the contents of the last call, so calls whose GPU work
+// overlaps (on two streams, or from two threads) race on it.  The first call
+// on a device looks up the array's device address (cudaGetSymbolAddress);
+// make that first call before any stream capture.
+#include <mutex>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr long long kStaticSlots = 1ll << 21;   // 2,097,152 slots
+constexpr int kStaticParticles = 1 << 15;       // 32,768 particles
+constexpr int kThreads = 128;
+constexpr int kMaxDevices = 64;
+
+// [slot nodes: int32 x kStaticSlots][wall fractions: float x kStaticSlots]
+// [slot offsets: int32 x (kStaticParticles + 1)][reject flag: uint32]
+constexpr size_t kScratchBytes =
+    (size_t)kStaticSlots * 8 + ((size_t)kStaticParticles + 1) * 4 + 256;
+
+static __device__ __align__(256) unsigned char g_link_scratch[kScratchBytes];
+
+struct Scratch {
+    int *node;
+    float *q;
+    int *base;
+    unsigned *reject; // set when a radius exceeds r_max for this call
+};
+
+__host__ __device__ inline Scratch carve(unsigned char *p)
+{
+    Scratch s;
+    s.node = reinterpret_cast<int *>(p);
+    s.q = reinterpret_cast<float *>(p + (size_t)kStaticSlots * 4);
+    s.base = reinterpret_cast<int *>(p + (size_t)kStaticSlots * 8);
+    s.reject = reinterpret_cast<unsigned *>(p + (size_t)kStaticSlots * 8 +
+                                            ((size_t)kStaticParticles + 1) * 4);
+    return s;
+}
+
+struct View {
+    float *A;
+    long long ps;
+    int pitch, nx, ny, n;
+    double r_max;
+    const int *own;
+    const lbm_particle *P;
+    double *F;
+};
+
+// Slot offsets: running sum of 12N - 12 over the particles (one thread).
+// The reject flag is rewritten on every call: set when some radius exceeds
+// the r_max the host checked the capacity against.
+__global__ void k_static_bases(View v, unsigned char *scratch)
+{
+    Scratch s = carve(scratch);
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        unsigned bad = 0u;
+        for (int a = 0; a < v.n; ++a) {
+            s.base[a] = acc;
+            const double r = v.P[a].r;
+            if (!(r >= 1.0 && r <= v.r_max)) bad = 1u;
+            else acc += slot_capacity(r);
+        }
+        s.base[v.n] = acc;
+        *s.reject = bad;
+    }
+}
+
+__device__ __forceinline__ bool in_box(const View &v, int i, int j)
+{
+    return i >= 0 && i < v.nx && j >= 0 && j < v.ny;
+}
+
+// Phase 1: one CTA per particle fills its 12N - 12 slots (Sec. 3 mapping).
+// A line holding two links is marked -2 (the particle's force becomes NaN).
+__global__ void __launch_bounds__(kThreads) k_static_gather(View v, unsigned char *scratch)
+{
+    Scratch s = carve(scratch);
+    if (*s.reject) return;
+    const int p = blockIdx.x;
+    const double xc = v.P[p].x, yc = v.P[p].y, r = v.P[p].r;
+    const int N = zone_size(r), cap = 12 * N - 12;
+    const int X0 = (int)floor(xc - r) - 1, Y0 = (int)floor(yc - r) - 1;
+    const int base = s.base[p];
+    for (int t0 = threadIdx.x; t0 < cap; t0 += kThreads) {
+        int k, line;
+        slot_dir_line(t0, N, k, line);
+        int found = 0, fi = 0, fj = 0;
+        for (int t = 0; t < N; ++t) {
+            int a, b;
+            if (!zone_point(k, N, line, t, a, b)) continue;
+            const int i = X0 + a, j = Y0 + b;
+            if (!in_box(v, i, j) || v.own[(long long)j * v.nx + i] != -1) continue;
+            const int si = i + ex(k), sj = j + ey(k);
+            if (!in_box(v, si, sj) || v.own[(long long)sj * v.nx + si] != p) continue;
+            if (++found == 1) {
+                fi = i;
+                fj = j;
+            }
+        }
+        s.node[base + t0] = found > 1 ? -2 : found ? fj * v.nx + fi : -1;
+        s.q[base + t0] = found ? (float)link_q(fi, fj, k, xc, yc, r) : 0.f;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T wsum(T x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Phase 2: bounce-back and momentum exchange on the gathered slots, with the
+// same arithmetic and the same reduction tree as the workspace kernel.
+__global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned char *scratch)
+{
+    Scratch s = carve(scratch);
+    const int p = blockIdx.x;
+    if (*s.reject) {
+        if (threadIdx.x < 3) v.F[3 * p + threadIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const double xc = v.P[p].x, yc = v.P[p].y, r = v.P[p].r;
+    const float Ux = (float)v.P[p].ux, Uy = (float)v.P[p].uy, Om = (float)v.P[p].omega;
+    const float wT = 0.2f * (float)v.P[p].T;
+    const int N = zone_size(r), cap = 12 * N - 12;
+    const int base = s.base[p];
+    double Fx = 0.0, Fy = 0.0, Tz = 0.0;
+    int broken = 0;
+    float *A = v.A;
+    const long long ps = v.ps;
+    for (int t0 = threadIdx.x; t0 < cap; t0 += kThreads) {
+        const int node = s.node[base + t0];
+        broken |= node == -2;
+        if (node < 0) continue;
+        int k, line;
+        slot_dir_line(t0, N, k, line);
+        const float q = s.q[base + t0];
+        const int fi = node % v.nx, fj = node / v.nx;
+        const int kx = ex(k), ky = ey(k), kb = opp(k);
+        const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
+        const bool have1 = in_box(v, i1, j1) && v.own[(long long)j1 * v.nx + i1] == -1;
+        const bool have2 = in_box(v, i2, j2) && v.own[(long long)j2 * v.nx + i2] == -1;
+        const long long n0 = (long long)fj * v.pitch + fi;
+        const long long n1 = have1 ? (long long)j1 * v.pitch + i1 : n0;
+        const long long n2 = have2 ? (long long)j2 * v.pitch + i2 : n0;
+        const float fk0 = A[k * ps + n0], fk1 = A[k * ps + n1], fk2 = A[k * ps + n2];
+        const float fb0 = A[kb * ps + n0], fb1 = A[kb * ps + n1];
+        const double dxi = __dsub_rn((double)fi, xc), dyj = __dsub_rn((double)fj, yc);
+        const float rx = (float)dxi + q * kx, ry = (float)dyj + q * ky;
+        const float uwx = Ux - Om * ry, uwy = Uy + Om * rx;
+        const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy);
+        float fnew;
+        if (q <= 0.5f) {
+            if (have1 && have2)
+                fnew = q * (2.f * q + 1.f) * fk0 + (1.f - 4.f * q * q) * fk1 -
+                       q * (1.f - 2.f * q) * fk2 + wall;
+            else if (have1)
+                fnew = 2.f * q * fk0 + (1.f - 2.f * q) * fk1 + wall;
+            else
+                fnew = fk0 + wall;
+        } else if (have1) {
+            const float cq = 1.f / (q * (2.f * q + 1.f));
+            fnew = cq * fk0 + (2.f * q - 1.f) / q * fb0 - (2.f * q - 1.f) / (2.f * q + 1.f) * fb1 +
+                   cq * wall;
+        } else {
+            const float h = 0.5f / q;
+            fnew = h * fk0 + (2.f * q - 1.f) * h * fb0 + h * wall;
+        }
+        const long long ns = (long long)(fj + ky) * v.pitch + (fi + kx);
+        A[kb * ps + ns] = fnew;
+        if (k <= 4) {
+            const float gk0 = A[(kQ9 + k) * ps + n0];
+            float gnew;
+            if (have1) {
+                const float c23 = (2.f * q - 1.f) / (2.f * q + 1.f), c4 = 2.f / (2.f * q + 1.f);
+                gnew = -gk0 + c23 * (A[(kQ9 + k) * ps + n1] + A[(kQ9 + kb) * ps + n0]) + c4 * wT;
+            } else {
+                gnew = -gk0 + wT;
+            }
+            A[(kQ9 + kb) * ps + ns] = gnew;
+        }
+        const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
+        const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
+        const double cF = 2.0 * w9d(k);
+        Fx += cF * kx + (double)bx;
+        Fy += cF * ky + (double)by;
+        Tz += cF * (dxi * ky - dyj * kx) + (double)(rx * by - ry * bx);
+    }
+    __shared__ double red[3][kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    broken = __syncthreads_or(broken);
+    Fx = wsum(Fx);
+    Fy = wsum(Fy);
+    Tz = wsum(Tz);
+    if (lane == 0) {
+        red[0][warp] = Fx;
+        red[1][warp] = Fy;
+        red[2][warp] = Tz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sx = 0.0, sy = 0.0, st = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            sx += red[0][w];
+            sy += red[1][w];
+            st += red[2][w];
+        }
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        v.F[3 * p + 0] = broken ? nan : sx;
+        v.F[3 * p + 1] = broken ? nan : sy;
+        v.F[3 * p + 2] = broken ? nan : st;
+    }
+}
+
+// Device address of the static array, looked up once per device.
+std::mutex g_mu;
+unsigned char *g_addr[kMaxDevices] = {};
+
+int scratch_address(unsigned char **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ECUDA;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_link_scratch) != cudaSuccess || !ptr) return LBM_ECUDA;
+        g_addr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_addr[dev];
+    return LBM_OK;
+}
+
+} // namespace
+} // namespace lbm
+
+extern "C" int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
+                                       const int32_t *d_owner, int32_t nx, int32_t ny,
+                                       const lbm_particle *d_particles, int32_t n, double r_max,
+                                       double *d_forces, void *stream)
+{
+    using namespace lbm;
+    if (n < 0 || nx < 1 || ny < 1 || pitch < nx || plane_stride < (int64_t)pitch * ny) return LBM_EINVAL;
+    if (n == 0) return LBM_OK;
+    if (!d_dist || !d_owner || !d_particles || !d_forces || !(r_max >= 1.0) || r_max > 1e6)
+        return LBM_EINVAL;
+    if (n > kStaticParticles || (long long)n * slot_capacity(r_max) > kStaticSlots) return LBM_ENOSPC;
+    unsigned char *scratch = nullptr;
+    int rc = scratch_address(&scratch);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    View v{d_dist, (long long)plane_stride, pitch, nx, ny, n, r_max, d_owner, d_particles, d_forces};
+    k_static_bases<<<1, 32, 0, s>>>(v, scratch);
+    k_static_gather<<<n, kThreads, 0, s>>>(v, scratch);
+    k_static_bbforce<<<n, kThreads, 0, s>>>(v, scratch);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+    return LBM_OK;
+}

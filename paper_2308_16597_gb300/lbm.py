@@ -75,6 +75,8 @@ _SIGS = [
     ("lbm_kernel_count", C.c_int32, []),
     ("lbm_kernel_name", C.c_char_p, [C.c_int32]),
     ("lbm_launch_count", C.c_int64, [_P]),
+    ("lbm_link_forces_noalloc", C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, _P,
+                                          C.c_int32, C.c_double, _P, _P]),
 ]
 
 
@@ -292,3 +294,11 @@ class Simulation:
 
     def launch_count(self) -> int:
         return int(library().lbm_launch_count(self.h))
+
+
+def lbm_link_forces_noalloc(dist_ptr, plane_stride, pitch, owner_ptr, nx, ny, particles_ptr, n,
+                            r_max, forces_ptr, stream_ptr):
+    """Allocation-free link forces (see include/lbm.h); device pointers in."""
+    _check(library().lbm_link_forces_noalloc(dist_ptr, plane_stride, pitch, owner_ptr, nx, ny,
+                                             particles_ptr, n, r_max, forces_ptr, stream_ptr),
+           "lbm_link_forces_noalloc")
