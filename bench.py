@@ -149,17 +149,19 @@ def profiled_traffic(kernel: str):
 
 
 # ------------------------------------------------------------------------------------ oracle
-def cpu_baseline(wl: W.Workload, steps: int, warmup: int = 0):
-    """FP64 oracle on the host cores, on the CROP x CROP sample of the workload."""
+def cpu_baseline(wl: W.Workload, seconds: float = 12.0, max_steps: int = 400):
+    """FP64 oracle on the host cores, on the CROP x CROP sample of the workload:
+    oracle steps until about `seconds` of CPU work (at most max_steps)."""
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     import oracle.oracle as orc
     sample = crop(wl, CROP)
     ref = orc.Oracle(sample.domain, sample.particles, sample.params)
-    if warmup:
-        ref.step(warmup)
+    steps = 0
     t0 = time.perf_counter()
-    ref.step(steps)
+    while steps < max_steps and (time.perf_counter() - t0) < seconds:
+        ref.step(1)
+        steps += 1
     dt = time.perf_counter() - t0
     return {"value": metrics.mlups(sample.nx, sample.ny, steps, dt), "unit": UNIT,
             "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
@@ -322,7 +324,7 @@ def run_ours(args, wl):
             "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel,
             "whole_step_hbm_frac": B_LU * nodes / (step_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -335,15 +337,16 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cavity4000", "cavity256", "cavity1024"],
+    ap.add_argument("--workload", choices=["cavity4000", "cavity2000", "cavity256", "cavity1024"],
                     default="cavity4000")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    wl = {"cavity4000": W.sedimentation_4000, "cavity256": W.parity_256,
+    wl = {"cavity4000": W.sedimentation_4000, "cavity2000": W.sedimentation_2000,
+          "cavity256": W.parity_256,
           "cavity1024": W.crop_1024}[args.workload]()
     if args.impl == "reference":
         return run_reference(args, wl)

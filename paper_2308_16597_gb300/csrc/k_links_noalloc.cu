@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kThreads) k_static_gather(View v, unsigned cha
     if (*s.reject) return;
     const int p = blockIdx.x;
     const double xc = v.P[p].x, yc = v.P[p].y, r = v.P[p].r;
+    const DiskDF dk = disk_df(xc, yc, r);
     const int N = zone_size(r), cap = 12 * N - 12;
     const int X0 = (int)floor(xc - r) - 1, Y0 = (int)floor(yc - r) - 1;
     const int base = s.base[p];
@@ -116,8 +117,9 @@ __global__ void __launch_bounds__(kThreads) k_static_gather(View v, unsigned cha
                 fj = j;
             }
         }
+        float dxf, dyf;
         s.node[base + t0] = found > 1 ? -2 : found ? fj * v.nx + fi : -1;
-        s.q[base + t0] = found ? (float)link_q(fi, fj, k, xc, yc, r) : 0.f;
+        s.q[base + t0] = found ? link_q_df(fi, fj, k, dk, dxf, dyf) : 0.f;
     }
 }
 
@@ -128,8 +130,18 @@ __device__ __forceinline__ T wsum(T x)
     return x;
 }
 
+__device__ __forceinline__ void warp_df(float &h, float &l)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, h, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, l, o);
+        df_add(h, l, h2, l2);
+    }
+}
+
 // Phase 2: bounce-back and momentum exchange on the gathered slots, with the
-// same arithmetic and the same reduction tree as the workspace kernel.
+// same device helpers, accumulation, reduction tree and FP64 assembly as the
+// workspace kernels.
 __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned char *scratch)
 {
     Scratch s = carve(scratch);
@@ -139,11 +151,13 @@ __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned ch
         return;
     }
     const double xc = v.P[p].x, yc = v.P[p].y, r = v.P[p].r;
+    const DiskDF dk = disk_df(xc, yc, r);
     const float Ux = (float)v.P[p].ux, Uy = (float)v.P[p].uy, Om = (float)v.P[p].omega;
     const float wT = 0.2f * (float)v.P[p].T;
     const int N = zone_size(r), cap = 12 * N - 12;
     const int base = s.base[p];
-    double Fx = 0.0, Fy = 0.0, Tz = 0.0;
+    float sbx = 0.f, sby = 0.f, stq = 0.f;
+    int ax_x = 0, ax_y = 0, ax_t = 0, dg_x = 0, dg_y = 0, dg_t = 0;
     int broken = 0;
     float *A = v.A;
     const long long ps = v.ps;
@@ -164,70 +178,67 @@ __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned ch
         const long long n2 = have2 ? (long long)j2 * v.pitch + i2 : n0;
         const float fk0 = A[k * ps + n0], fk1 = A[k * ps + n1], fk2 = A[k * ps + n2];
         const float fb0 = A[kb * ps + n0], fb1 = A[kb * ps + n1];
-        const double dxi = __dsub_rn((double)fi, xc), dyj = __dsub_rn((double)fj, yc);
-        const float rx = (float)dxi + q * kx, ry = (float)dyj + q * ky;
+        float dxh, dxl, dyh, dyl;
+        df_offset(fi, dk.xh, dk.xl, dxh, dxl);
+        df_offset(fj, dk.yh, dk.yl, dyh, dyl);
+        const float dxf = dxh + dxl, dyf = dyh + dyl;
+        const float rx = dxf + q * kx, ry = dyf + q * ky;
         const float uwx = Ux - Om * ry, uwy = Uy + Om * rx;
         const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy);
-        float fnew;
-        if (q <= 0.5f) {
-            if (have1 && have2)
-                fnew = q * (2.f * q + 1.f) * fk0 + (1.f - 4.f * q * q) * fk1 -
-                       q * (1.f - 2.f * q) * fk2 + wall;
-            else if (have1)
-                fnew = 2.f * q * fk0 + (1.f - 2.f * q) * fk1 + wall;
-            else
-                fnew = fk0 + wall;
-        } else if (have1) {
-            const float cq = 1.f / (q * (2.f * q + 1.f));
-            fnew = cq * fk0 + (2.f * q - 1.f) / q * fb0 - (2.f * q - 1.f) / (2.f * q + 1.f) * fb1 +
-                   cq * wall;
-        } else {
-            const float h = 0.5f / q;
-            fnew = h * fk0 + (2.f * q - 1.f) * h * fb0 + h * wall;
-        }
+        int lvl;
+        const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
         const long long ns = (long long)(fj + ky) * v.pitch + (fi + kx);
         A[kb * ps + ns] = fnew;
-        if (k <= 4) {
-            const float gk0 = A[(kQ9 + k) * ps + n0];
-            float gnew;
-            if (have1) {
-                const float c23 = (2.f * q - 1.f) / (2.f * q + 1.f), c4 = 2.f / (2.f * q + 1.f);
-                gnew = -gk0 + c23 * (A[(kQ9 + k) * ps + n1] + A[(kQ9 + kb) * ps + n0]) + c4 * wT;
-            } else {
-                gnew = -gk0 + wT;
-            }
-            A[(kQ9 + kb) * ps + ns] = gnew;
-        }
+        if (k <= 4)
+            A[(kQ9 + kb) * ps + ns] = thermal32(q, A[(kQ9 + k) * ps + n0], A[(kQ9 + k) * ps + n1],
+                                                A[(kQ9 + kb) * ps + n0], have1, wT);
         const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
         const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
-        const double cF = 2.0 * w9d(k);
-        Fx += cF * kx + (double)bx;
-        Fy += cF * ky + (double)by;
-        Tz += cF * (dxi * ky - dyj * kx) + (double)(rx * by - ry * bx);
+        sbx += bx;
+        sby += by;
+        stq += rx * by - ry * bx;
+        const int tz = fi * ky - fj * kx;
+        if (k <= 4) { ax_x += kx; ax_y += ky; ax_t += tz; }
+        else { dg_x += kx; dg_y += ky; dg_t += tz; }
     }
-    __shared__ double red[3][kThreads / 32];
+    __shared__ float red[6][kThreads / 32];
+    __shared__ int cnt[6][kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     broken = __syncthreads_or(broken);
-    Fx = wsum(Fx);
-    Fy = wsum(Fy);
-    Tz = wsum(Tz);
+    float fxl = 0.f, fyl = 0.f, tzl = 0.f;
+    warp_df(sbx, fxl);
+    warp_df(sby, fyl);
+    warp_df(stq, tzl);
+    int iv[6] = {ax_x, ax_y, ax_t, dg_x, dg_y, dg_t};
+    for (int c = 0; c < 6; ++c) iv[c] = wsum(iv[c]);
     if (lane == 0) {
-        red[0][warp] = Fx;
-        red[1][warp] = Fy;
-        red[2][warp] = Tz;
+        red[0][warp] = sbx; red[1][warp] = fxl;
+        red[2][warp] = sby; red[3][warp] = fyl;
+        red[4][warp] = stq; red[5][warp] = tzl;
+        for (int c = 0; c < 6; ++c) cnt[c][warp] = iv[c];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sx = 0.0, sy = 0.0, st = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            sx += red[0][w];
-            sy += red[1][w];
-            st += red[2][w];
+        LinkSums S;
+        S.fx_h = red[0][0]; S.fx_l = red[1][0];
+        S.fy_h = red[2][0]; S.fy_l = red[3][0];
+        S.tz_h = red[4][0]; S.tz_l = red[5][0];
+        int a[6];
+        for (int c = 0; c < 6; ++c) a[c] = cnt[c][0];
+        for (int w = 1; w < kThreads / 32; ++w) {
+            df_add(S.fx_h, S.fx_l, red[0][w], red[1][w]);
+            df_add(S.fy_h, S.fy_l, red[2][w], red[3][w]);
+            df_add(S.tz_h, S.tz_l, red[4][w], red[5][w]);
+            for (int c = 0; c < 6; ++c) a[c] += cnt[c][w];
         }
+        S.ax_x = a[0]; S.ax_y = a[1]; S.ax_t = a[2];
+        S.dg_x = a[3]; S.dg_y = a[4]; S.dg_t = a[5];
+        double Fx, Fy, Tz;
+        assemble_force(S, xc, yc, Fx, Fy, Tz);
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
-        v.F[3 * p + 0] = broken ? nan : sx;
-        v.F[3 * p + 1] = broken ? nan : sy;
-        v.F[3 * p + 2] = broken ? nan : st;
+        v.F[3 * p + 0] = broken ? nan : Fx;
+        v.F[3 * p + 1] = broken ? nan : Fy;
+        v.F[3 * p + 2] = broken ? nan : Tz;
     }
 }
 

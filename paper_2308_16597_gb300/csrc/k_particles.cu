@@ -16,7 +16,7 @@ namespace {
 
 constexpr int kLinkThreads = 128;
 constexpr int kBoxThreads = 128;
-constexpr int kPartThreads = 128;
+constexpr int kPartThreads = 1024;
 constexpr double kPi = 3.14159265358979323846;
 
 __device__ __forceinline__ bool inside(const Dev &D, int i, int j)
@@ -37,21 +37,59 @@ __device__ __forceinline__ T warp_sum(T v)
 // One CTA per particle; thread s handles slot s (and s + 128, ...) of the
 // particle's 12N - 12 fixed slots.  The slot of (direction k, line) is fixed
 // by the zone geometry, so the gather needs no atomics and the per-particle
-// reduction is a deterministic tree.  Bounce-back values are written into the
-// solid node x_f + e_k in direction kbar of the post-collision array A, where
-// the next pull stream picks them up: each (solid node, kbar) belongs to one
-// link, and every read is of a fluid node, so the writes never race the reads.
+// reduction is a deterministic tree.  The owner map of the zone (plus a
+// two-node margin for the bounce-back stencil) is first copied to shared
+// memory.  Bounce-back values are written into the solid node x_f + e_k in
+// direction kbar of the post-collision array A, where the next pull stream
+// picks them up: each (solid node, kbar) belongs to one link, and every read
+// is of a fluid node, so the writes never race the reads.
+constexpr int kWinMax = 64; // zone side + 4 held in shared memory (radius <= 28.5)
+
+// Double-float warp sum (lane 0 receives the result).
+__device__ __forceinline__ void warp_df_sum(float &h, float &l)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, h, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, l, o);
+        df_add(h, l, h2, l2);
+    }
+}
+
 __global__ void __launch_bounds__(kLinkThreads)
     k_links(const Dev D, float *A, const int *__restrict__ own, int parity)
 {
+    __shared__ int win[kWinMax * kWinMax];
     const int p = blockIdx.x;
     const double xc = D.cur.x[p], yc = D.cur.y[p], r = D.cur.r[p];
+    const DiskDF dk = disk_df(xc, yc, r);
     const float Ux = (float)D.cur.ux[p], Uy = (float)D.cur.uy[p], Om = (float)D.cur.om[p];
     const float wT = 0.2f * (float)D.cur.T[p]; // 2 w_k T_w for D2Q5
     const int N = zone_size(r), cap = 12 * N - 12;
     const int X0 = (int)floor(xc - r) - 1, Y0 = (int)floor(yc - r) - 1;
     const int base = D.slot_base[p];
-    double Fx = 0.0, Fy = 0.0, Tz = 0.0;
+    if (threadIdx.x == 0) {
+        D.pos4[p] = make_float4(dk.xh, dk.yh, dk.xl, dk.yl);
+        D.prc[p] = make_float2((float)r, (float)(kPi * r * r * (D.cur.rho[p] - D.rho_f) * D.g));
+    }
+
+    // owner window: node (X0 - 2 + a, Y0 - 2 + b) at win[b * W + a], -2 outside
+    const int W = N + 4;
+    const bool use_win = W <= kWinMax;
+    if (use_win) {
+        for (int idx = threadIdx.x; idx < W * W; idx += kLinkThreads) {
+            const int i = X0 - 2 + idx % W, j = Y0 - 2 + idx / W;
+            win[idx] = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
+        }
+        __syncthreads();
+    }
+    auto owner_at = [&](int i, int j) -> int {
+        if (use_win) return win[(j - Y0 + 2) * W + (i - X0 + 2)];
+        return inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
+    };
+
+    float sbx = 0.f, sby = 0.f, stq = 0.f; // link brackets of Eq. force / Eq. torque
+    int ax_x = 0, ax_y = 0, ax_t = 0, dg_x = 0, dg_y = 0, dg_t = 0; // exact constant parts
     unsigned c_lin = 0, c_simple = 0, c_th = 0, c_links = 0, c_over = 0;
 
     for (int s = threadIdx.x; s < cap; s += kLinkThreads) {
@@ -63,124 +101,102 @@ __global__ void __launch_bounds__(kLinkThreads)
             int a, b;
             if (!zone_point(k, N, line, t, a, b)) continue;
             const int i = X0 + a, j = Y0 + b;
-            if (!inside(D, i, j) || own[(long long)j * D.nx + i] != -1) continue;
-            const int si = i + kx, sj = j + ky;
-            if (!inside(D, si, sj) || own[(long long)sj * D.nx + si] != p) continue;
+            if (owner_at(i, j) != -1 || owner_at(i + kx, j + ky) != p) continue;
             if (++found == 1) {
                 fi = i;
                 fj = j;
             }
         }
         c_over += found > 1;
-        int node = -1;
-        float q = 0.f;
-        if (found) {
-            node = fj * D.nx + fi;
-            q = (float)link_q(fi, fj, k, xc, yc, r);
+        if (!found) {
+            D.slot_node[base + s] = -1;
+            D.slot_q[base + s] = 0.f;
+            continue;
         }
-        D.slot_node[base + s] = node;
-        D.slot_q[base + s] = q;
-        if (!found) continue;
         ++c_links;
+        float dxf, dyf;
+        const float q = link_q_df(fi, fj, k, dk, dxf, dyf);
+        D.slot_node[base + s] = fj * D.nx + fi;
+        D.slot_q[base + s] = q;
 
         // ---- curved bounce-back (Sec. 2.3) in deviation form: every rule is
         // an affine combination of populations of equal weight, so it holds
         // for f~ = f - w unchanged.
         const int kb = opp(k);
         const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
-        const bool have1 = inside(D, i1, j1) && own[(long long)j1 * D.nx + i1] == -1;
-        const bool have2 = inside(D, i2, j2) && own[(long long)j2 * D.nx + i2] == -1;
+        const bool have1 = owner_at(i1, j1) == -1;
+        const bool have2 = owner_at(i2, j2) == -1;
         const long long n0 = (long long)fj * D.pitch + fi;
         const long long n1 = have1 ? (long long)j1 * D.pitch + i1 : n0;
         const long long n2 = have2 ? (long long)j2 * D.pitch + i2 : n0;
         const float fk0 = A[k * D.ps + n0], fk1 = A[k * D.ps + n1], fk2 = A[k * D.ps + n2];
         const float fb0 = A[kb * D.ps + n0], fb1 = A[kb * D.ps + n1];
-        const double dxi = __dsub_rn((double)fi, xc), dyj = __dsub_rn((double)fj, yc);
-        const float rx = (float)dxi + q * kx, ry = (float)dyj + q * ky;
+        const float rx = dxf + q * kx, ry = dyf + q * ky;
         const float uwx = Ux - Om * ry, uwy = Uy + Om * rx;
         const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy); // 2 w rho0 e_kbar.u_w / c_s^2
-        float fnew;
-        if (q <= 0.5f) {
-            if (have1 && have2) {
-                fnew = q * (2.f * q + 1.f) * fk0 + (1.f - 4.f * q * q) * fk1 -
-                       q * (1.f - 2.f * q) * fk2 + wall;
-            } else if (have1) {
-                fnew = 2.f * q * fk0 + (1.f - 2.f * q) * fk1 + wall;
-                ++c_lin;
-            } else {
-                fnew = fk0 + wall;
-                ++c_simple;
-            }
-        } else if (have1) {
-            const float cq = 1.f / (q * (2.f * q + 1.f));
-            fnew = cq * fk0 + (2.f * q - 1.f) / q * fb0 - (2.f * q - 1.f) / (2.f * q + 1.f) * fb1 +
-                   cq * wall;
-        } else {
-            const float h = 0.5f / q;
-            fnew = h * fk0 + (2.f * q - 1.f) * h * fb0 + h * wall;
-            ++c_lin;
-        }
+        int lvl;
+        const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
+        c_lin += lvl == 1;
+        c_simple += lvl == 2;
         const long long ns = (long long)(fj + ky) * D.pitch + (fi + kx);
         A[kb * D.ps + ns] = fnew;
         if (k <= 4) {
-            const float gk0 = A[(kQ9 + k) * D.ps + n0];
-            float gnew;
-            if (have1) {
-                const float c23 = (2.f * q - 1.f) / (2.f * q + 1.f), c4 = 2.f / (2.f * q + 1.f);
-                gnew = -gk0 + c23 * (A[(kQ9 + k) * D.ps + n1] + A[(kQ9 + kb) * D.ps + n0]) + c4 * wT;
-            } else {
-                gnew = -gk0 + wT;
-                ++c_th;
-            }
+            const float gnew = thermal32(q, A[(kQ9 + k) * D.ps + n0], A[(kQ9 + k) * D.ps + n1],
+                                         A[(kQ9 + kb) * D.ps + n0], have1, wT);
+            c_th += !have1;
             A[(kQ9 + kb) * D.ps + ns] = gnew;
         }
 
         // ---- momentum exchange.  With f = w + f~ the bracket of Eq. force is
-        // 2 w_k e_k + [f~_k^+ (e_k - u_w) - f~_kbar (e_kbar - u_w)]; the constant
-        // part is added in FP64, and its torque 2 w_k (x_f - x_c) x e_k does not
-        // depend on q.
+        // 2 w_k e_k + [f~_k^+ (e_k - u_w) - f~_kbar (e_kbar - u_w)].  The constant
+        // part and its torque 2 w_k ((i - x_c) e_k,y - (j - y_c) e_k,x) (q drops
+        // out) are kept as exact integer sums, assembled in FP64 by the
+        // particle update.
         const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
         const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
-        const double cF = 2.0 * w9d(k);
-        Fx += cF * kx + (double)bx;
-        Fy += cF * ky + (double)by;
-        Tz += cF * (dxi * ky - dyj * kx) + (double)(rx * by - ry * bx);
+        sbx += bx;
+        sby += by;
+        stq += rx * by - ry * bx;
+        const int tz = fi * ky - fj * kx;
+        if (k <= 4) { ax_x += kx; ax_y += ky; ax_t += tz; }
+        else { dg_x += kx; dg_y += ky; dg_t += tz; }
     }
 
-    __shared__ double red[3][kLinkThreads / 32];
-    __shared__ unsigned cnt[5][kLinkThreads / 32];
+    __shared__ float red[6][kLinkThreads / 32];
+    __shared__ int cnt[11][kLinkThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Fx = warp_sum(Fx);
-    Fy = warp_sum(Fy);
-    Tz = warp_sum(Tz);
-    c_lin = warp_sum(c_lin);
-    c_simple = warp_sum(c_simple);
-    c_th = warp_sum(c_th);
-    c_links = warp_sum(c_links);
-    c_over = warp_sum(c_over);
+    float fxl = 0.f, fyl = 0.f, tzl = 0.f;
+    warp_df_sum(sbx, fxl);
+    warp_df_sum(sby, fyl);
+    warp_df_sum(stq, tzl);
+    int iv[11] = {(int)c_lin, (int)c_simple, (int)c_th, (int)c_links, (int)c_over,
+                  ax_x, ax_y, ax_t, dg_x, dg_y, dg_t};
+#pragma unroll
+    for (int c = 0; c < 11; ++c) iv[c] = warp_sum(iv[c]);
     if (lane == 0) {
-        red[0][warp] = Fx;
-        red[1][warp] = Fy;
-        red[2][warp] = Tz;
-        cnt[0][warp] = c_lin;
-        cnt[1][warp] = c_simple;
-        cnt[2][warp] = c_th;
-        cnt[3][warp] = c_links;
-        cnt[4][warp] = c_over;
+        red[0][warp] = sbx; red[1][warp] = fxl;
+        red[2][warp] = sby; red[3][warp] = fyl;
+        red[4][warp] = stq; red[5][warp] = tzl;
+        for (int c = 0; c < 11; ++c) cnt[c][warp] = iv[c];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sx = 0.0, sy = 0.0, st = 0.0;
-        unsigned a[5] = {0, 0, 0, 0, 0};
-        for (int w = 0; w < kLinkThreads / 32; ++w) {
-            sx += red[0][w];
-            sy += red[1][w];
-            st += red[2][w];
-            for (int c = 0; c < 5; ++c) a[c] += cnt[c][w];
+        LinkSums S;
+        S.fx_h = red[0][0]; S.fx_l = red[1][0];
+        S.fy_h = red[2][0]; S.fy_l = red[3][0];
+        S.tz_h = red[4][0]; S.tz_l = red[5][0];
+        int a[11];
+        for (int c = 0; c < 11; ++c) a[c] = cnt[c][0];
+        for (int w = 1; w < kLinkThreads / 32; ++w) {
+            df_add(S.fx_h, S.fx_l, red[0][w], red[1][w]);
+            df_add(S.fy_h, S.fy_l, red[2][w], red[3][w]);
+            df_add(S.tz_h, S.tz_l, red[4][w], red[5][w]);
+            for (int c = 0; c < 11; ++c) a[c] += cnt[c][w];
         }
-        D.force[3 * p + 0] = sx;
-        D.force[3 * p + 1] = sy;
-        D.force[3 * p + 2] = st;
+        S.ax_x = a[5]; S.ax_y = a[6]; S.ax_t = a[7];
+        S.dg_x = a[8]; S.dg_y = a[9]; S.dg_t = a[10];
+        S.pad[0] = S.pad[1] = S.pad[2] = S.pad[3] = 0;
+        D.lsum[p] = S;
         unsigned long long *C = D.status->cnt[parity];
         if (a[0]) atomicAdd(&C[kCntBzLinear], (unsigned long long)a[0]);
         if (a[1]) atomicAdd(&C[kCntBzSimple], (unsigned long long)a[1]);
@@ -200,67 +216,101 @@ __device__ __forceinline__ double repulsion(double gap, double s, double eps, do
     return C / eps * t * t;
 }
 
-// One thread per particle.  Total force = hydrodynamic + buoyant weight
-// -(rho_p - rho_f) pi r^2 g y-hat + repulsion (walls, then every other disk,
+// Total force = hydrodynamic (assembled from the link sums) + buoyant weight
+// -(rho_p - rho_f) pi r^2 g y-hat + repulsion (walls, and every other disk
 // with C_ab the mean of the two force scales C = pi r^2 (rho_p - rho_f) g).
-// Other disks are screened in FP32 tiles with a one-lattice-unit margin and
-// evaluated in FP64.  Integration: U' = U + F/M, X' = X + (U + U')/2,
-// Omega' = Omega + T/I, theta' = theta + (Omega + Omega')/2 with
-// M = rho_p pi r^2 and I = M r^2 / 2.
+// Each block takes 32 particles: warp w screens particle w against all disks
+// in shared-memory tiles (FP32 centres with a one-lattice-unit margin) and
+// evaluates the pairs in reach from double-float centre differences; lane l
+// of warp 0 then sums, integrates and stores particle l in FP64, so 32
+// particles share every FP64 instruction.  Integration: U' = U + F/M,
+// X' = X + (U + U')/2, Omega' = Omega + T/I, theta' = theta + (Omega + Omega')/2
+// with M = rho_p pi r^2 and I = M r^2 / 2.
+constexpr int kPartTile = 512;
+
+// Pair repulsion on disk a from disk b (FP32 from double-float centres).
+__device__ __noinline__ void pair_force(float4 pa, float2 ca, float4 pb, float2 cb, float s_rep,
+                                        float inv_eps, float &fh_x, float &fl_x, float &fh_y,
+                                        float &fl_y)
+{
+    float hx, ex_, hy, ey_;
+    two_sum(pa.x, -pb.x, hx, ex_);
+    two_sum(pa.y, -pb.y, hy, ey_);
+    const float dx = hx + (ex_ + (pa.z - pb.z));
+    const float dy = hy + (ey_ + (pa.w - pb.w));
+    const float dist = sqrtf(dx * dx + dy * dy);
+    const float gap = dist - ca.x - cb.x;
+    if (gap > s_rep) return;
+    const float t = (gap - s_rep) / s_rep;
+    const float mag = 0.5f * (ca.y + cb.y) * inv_eps * t * t;
+    df_add(fh_x, fl_x, mag * dx / dist, 0.f);
+    df_add(fh_y, fl_y, mag * dy / dist, 0.f);
+}
+
 __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int parity)
 {
-    __shared__ float sx[kPartThreads], sy[kPartThreads], sr[kPartThreads];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float4 sp[kPartTile];
+    __shared__ float2 sc[kPartTile];
+    __shared__ float sred[4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int a = blockIdx.x * 32 + warp;
     if (blockIdx.x == 0 && threadIdx.x < kNumCounters) D.status->cnt[parity ^ 1][threadIdx.x] = 0ull;
     const bool me = a < D.np;
-    double x = 0, y = 0, ux = 0, uy = 0, th = 0, om = 0, r = 1, rho = 1, T = 0;
+    float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 ca = make_float2(1.f, 0.f);
     if (me) {
-        x = D.cur.x[a]; y = D.cur.y[a]; ux = D.cur.ux[a]; uy = D.cur.uy[a];
-        th = D.cur.th[a]; om = D.cur.om[a]; r = D.cur.r[a]; rho = D.cur.rho[a]; T = D.cur.T[a];
+        pa = D.pos4[a];
+        ca = D.prc[a];
     }
-    const double Ca = kPi * r * r * (rho - D.rho_f) * D.g;
-    double Fx = 0.0, Fy = 0.0, Tz = 0.0;
-    if (me) {
-        Fx = D.force[3 * a + 0];
-        Fy = D.force[3 * a + 1] - (rho - D.rho_f) * kPi * r * r * D.g;
-        Tz = D.force[3 * a + 2];
-        if (!D.per_x) {
-            Fx += repulsion((x + 0.5) - r, D.s_rep, D.eps_w, Ca);
-            Fx -= repulsion(((double)D.nx - 0.5 - x) - r, D.s_rep, D.eps_w, Ca);
-        }
-        if (!D.per_y) {
-            Fy += repulsion((y + 0.5) - r, D.s_rep, D.eps_w, Ca);
-            Fy -= repulsion(((double)D.ny - 0.5 - y) - r, D.s_rep, D.eps_w, Ca);
-        }
-    }
-    const float xf = (float)x, yf = (float)y, rf = (float)r, reach = (float)D.s_rep + 1.f;
-    for (int t0 = 0; t0 < D.np; t0 += kPartThreads) {
-        const int b = t0 + threadIdx.x;
+    const float s_rep = (float)D.s_rep, inv_eps = (float)(1.0 / D.eps_w);
+    const float reach = s_rep + 1.f;
+    float fhx = 0.f, flx = 0.f, fhy = 0.f, fly = 0.f;
+    for (int t0 = 0; t0 < D.np; t0 += kPartTile) {
+        const int nb = min(kPartTile, D.np - t0);
         __syncthreads();
-        if (b < D.np) {
-            sx[threadIdx.x] = (float)D.cur.x[b];
-            sy[threadIdx.x] = (float)D.cur.y[b];
-            sr[threadIdx.x] = (float)D.cur.r[b];
+        for (int k = threadIdx.x; k < nb; k += kPartThreads) {
+            sp[k] = D.pos4[t0 + k];
+            sc[k] = D.prc[t0 + k];
         }
         __syncthreads();
-        const int nb = min(kPartThreads, D.np - t0);
         if (!me) continue;
-        for (int u = 0; u < nb; ++u) {
-            const float dxf = xf - sx[u], dyf = yf - sy[u], lim = rf + sr[u] + reach;
+        for (int u = lane; u < nb; u += 32) {
+            const float4 o = sp[u];
+            const float dxf = pa.x - o.x, dyf = pa.y - o.y, lim = ca.x + sc[u].x + reach;
             if (dxf * dxf + dyf * dyf > lim * lim || t0 + u == a) continue;
-            const int bb = t0 + u;
-            const double dx = x - D.cur.x[bb], dy = y - D.cur.y[bb];
-            const double dist = sqrt(dx * dx + dy * dy);
-            const double rb = D.cur.r[bb];
-            const double gap = dist - r - rb;
-            if (gap > D.s_rep) continue;
-            const double Cb = kPi * rb * rb * (D.cur.rho[bb] - D.rho_f) * D.g;
-            const double mag = repulsion(gap, D.s_rep, D.eps_w, 0.5 * (Ca + Cb));
-            Fx += mag * dx / dist;
-            Fy += mag * dy / dist;
+            pair_force(pa, ca, o, sc[u], s_rep, inv_eps, fhx, flx, fhy, fly);
         }
     }
-    if (!me) return;
+    warp_df_sum(fhx, flx);
+    warp_df_sum(fhy, fly);
+    if (lane == 0) {
+        sred[0][warp] = fhx; sred[1][warp] = flx;
+        sred[2][warp] = fhy; sred[3][warp] = fly;
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    const int b = blockIdx.x * 32 + lane;
+    if (b >= D.np) return;
+    double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
+    double th = D.cur.th[b], om = D.cur.om[b];
+    const double r = D.cur.r[b], rho = D.cur.rho[b];
+    double Fx, Fy, Tz;
+    assemble_force(D.lsum[b], x, y, Fx, Fy, Tz);
+    D.force[3 * b + 0] = Fx;
+    D.force[3 * b + 1] = Fy;
+    D.force[3 * b + 2] = Tz;
+    const double Cb = kPi * r * r * (rho - D.rho_f) * D.g;
+    Fy -= (rho - D.rho_f) * kPi * r * r * D.g;
+    if (!D.per_x) {
+        Fx += repulsion((x + 0.5) - r, D.s_rep, D.eps_w, Cb);
+        Fx -= repulsion(((double)D.nx - 0.5 - x) - r, D.s_rep, D.eps_w, Cb);
+    }
+    if (!D.per_y) {
+        Fy += repulsion((y + 0.5) - r, D.s_rep, D.eps_w, Cb);
+        Fy -= repulsion(((double)D.ny - 0.5 - y) - r, D.s_rep, D.eps_w, Cb);
+    }
+    Fx += (double)sred[0][lane] + (double)sred[1][lane];
+    Fy += (double)sred[2][lane] + (double)sred[3][lane];
     if (!D.fixed) {
         const double M = rho * kPi * r * r, I = 0.5 * M * r * r;
         const double ux1 = ux + Fx / M, uy1 = uy + Fy / M, om1 = om + Tz / I;
@@ -273,8 +323,8 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
     }
     if (x - r < -0.5 || x + r > (double)D.nx - 0.5 || y - r < -0.5 || y + r > (double)D.ny - 0.5)
         atomicOr(&D.status->err, kErrDomain);
-    D.nxt.x[a] = x; D.nxt.y[a] = y; D.nxt.ux[a] = ux; D.nxt.uy[a] = uy; D.nxt.th[a] = th;
-    D.nxt.om[a] = om; D.nxt.r[a] = r; D.nxt.rho[a] = rho; D.nxt.T[a] = T;
+    D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
+    D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = D.cur.T[b];
 }
 
 // Zone of a disk at (x, y) with radius r: N x N nodes from
@@ -304,16 +354,38 @@ __global__ void __launch_bounds__(kBoxThreads) k_clear(const Dev D, int *own_nxt
 
 // Owner map: node (i,j) belongs to disk p iff (i - x)^2 + (j - y)^2 <= r^2
 // (exact FP64); where disks overlap the highest index wins (atomicMax, so
-// the result does not depend on the launch order).
+// the result does not depend on the launch order).  One warp per disk, one
+// lane per zone row: the predicate holds on one contiguous run of each row
+// (it is monotone in |i - x|), so the run is found from an FP32 estimate of
+// its ends and settled with the exact predicate at the ends only.
 __global__ void __launch_bounds__(kBoxThreads) k_raster(const Dev D, int *own, const PartSoA pos)
 {
-    const int p = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * (kBoxThreads / 32) + (threadIdx.x >> 5);
+    if (p >= D.np) return;
     const double x = pos.x[p], y = pos.y[p], r = pos.r[p];
     const Box B = box_of(x, y, r);
-    for (int idx = threadIdx.x; idx < B.N * B.N; idx += kBoxThreads) {
-        const int i = B.X0 + idx % B.N, j = B.Y0 + idx / B.N;
-        if (!inside(D, i, j) || !in_disk(i, j, x, y, r)) continue;
-        atomicMax(&own[(long long)j * D.nx + i], p);
+    const DiskDF dk = disk_df(x, y, r);
+    const int ic = (int)floor(x + 0.5); // the node of each row nearest the centre
+    for (int b = lane; b < B.N; b += 32) {
+        const int j = B.Y0 + b;
+        if (j < 0 || j >= D.ny) continue;
+        if (!in_disk_df(ic, j, dk, x, y, r)) continue; // then no node of the row is inside
+        float dyh, dyl;
+        df_offset(j, dk.yh, dk.yl, dyh, dyl);
+        const float h = sqrtf(fmaxf(dk.r2h - dyh * dyh, 0.f));
+        const int xmin = B.X0, xmax = B.X0 + B.N - 1;
+        int lo = min(ic, (int)ceilf(dk.xh - h)), hi = max(ic, (int)floorf(dk.xh + h));
+        lo = max(lo, xmin);
+        hi = min(hi, xmax);
+        while (lo > xmin && in_disk_df(lo - 1, j, dk, x, y, r)) --lo;
+        while (!in_disk_df(lo, j, dk, x, y, r)) ++lo;
+        while (hi < xmax && in_disk_df(hi + 1, j, dk, x, y, r)) ++hi;
+        while (!in_disk_df(hi, j, dk, x, y, r)) --hi;
+        lo = max(lo, 0);
+        hi = min(hi, D.nx - 1);
+        int *row = own + (long long)j * D.nx;
+        for (int i = lo; i <= hi; ++i) atomicMax(row + i, p);
     }
 }
 
@@ -371,7 +443,7 @@ cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity,
 
 cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s)
 {
-    const int blocks = D.np > 0 ? (D.np + kPartThreads - 1) / kPartThreads : 1;
+    const int blocks = D.np > 0 ? (D.np + 31) / 32 : 1;
     k_particles<<<blocks, kPartThreads, 0, s>>>(D, parity);
     return cudaGetLastError();
 }
@@ -386,7 +458,8 @@ cudaError_t launch_clear(const Dev &D, int *own_nxt, cudaStream_t s)
 cudaError_t launch_raster(const Dev &D, int *own, const PartSoA &pos, cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
-    k_raster<<<D.np, kBoxThreads, 0, s>>>(D, own, pos);
+    const int per = kBoxThreads / 32;
+    k_raster<<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own, pos);
     return cudaGetLastError();
 }
 

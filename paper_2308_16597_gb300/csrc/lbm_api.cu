@@ -24,8 +24,8 @@ struct Layout {
     int pitch = 0;
     long long ps = 0;
     size_t nslots = 0;
-    size_t A[2], own[2], flags, slot_node, slot_q, slot_base, cur, nxt, prev, force, status, pack,
-        stage, total;
+    size_t A[2], own[2], flags, slot_node, slot_q, slot_base, cur, nxt, prev, force, pos4, prc, lsum,
+        status, pack, stage, total;
     int stage_rows = 0;
 };
 
@@ -108,6 +108,9 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, Layout &L)
     L.nxt = take((size_t)9 * n * sizeof(double));
     L.prev = take((size_t)2 * n * sizeof(double));
     L.force = take((size_t)3 * n * sizeof(double));
+    L.pos4 = take((size_t)n * sizeof(float4));
+    L.prc = take((size_t)n * sizeof(float2));
+    L.lsum = take((size_t)n * sizeof(LinkSums));
     L.status = take(sizeof(Status));
     L.pack = take((size_t)n * sizeof(lbm_particle));
     L.stage_rows = (int)std::max<size_t>(1, std::min<size_t>(d->ny, kStageBytes / (16 * (size_t)d->nx)));
@@ -261,6 +264,7 @@ int device_error(lbm_handle *h)
     if (err & kErrNumeric) return LBM_ENUMERIC;
     if (err & kErrDomain) return LBM_EDOMAIN;
     if (err & kErrOverflow) return LBM_EOVERFLOW;
+    if (err & kErrTimeout) return LBM_ETIMEOUT;
     return LBM_OK;
 }
 
@@ -313,6 +317,9 @@ void fill_dev(lbm_handle *h)
     D.px = reinterpret_cast<double *>(ws + L.prev);
     D.py = D.px + h->np;
     D.force = reinterpret_cast<double *>(ws + L.force);
+    D.pos4 = reinterpret_cast<float4 *>(ws + L.pos4);
+    D.prc = reinterpret_cast<float2 *>(ws + L.prc);
+    D.lsum = reinterpret_cast<LinkSums *>(ws + L.lsum);
     D.status = reinterpret_cast<Status *>(ws + L.status);
     for (int b = 0; b < 2; ++b) {
         h->A[b] = reinterpret_cast<float *>(ws + L.A[b]);

@@ -49,6 +49,7 @@ constexpr uint8_t kNewborn = 2; // uncovered by a particle during the last step
 constexpr unsigned kErrNumeric = 1u;
 constexpr unsigned kErrDomain = 2u;
 constexpr unsigned kErrOverflow = 4u;
+constexpr unsigned kErrTimeout = 8u;
 
 // Counter slots (see lbm_get_counters).
 enum { kCntBzLinear = 0, kCntBzSimple, kCntThermHalf, kCntRfLinear, kCntRfCopy, kCntRfEq,
@@ -84,6 +85,9 @@ struct Dev {
     PartSoA cur, nxt;  // state at n (and n+1 after the raster rotation) / new state
     double *px, *py;   // positions one step back (boxes to clear)
     double *force;     // [3 np]: hydrodynamic Fx, Fy, Tz of the last step
+    float4 *pos4;      // [np]: centre as double-float (xh, yh, xl, yl) at the start of the step
+    float2 *prc;       // [np]: (r, C = pi r^2 (rho_p - rho_f) g) in FP32 for the pair screening
+    struct LinkSums *lsum; // [np]: link-kernel sums, assembled into force by the particle update
     Status *status;
 };
 
@@ -112,6 +116,169 @@ __device__ __forceinline__ double link_q(int i, int j, int k, double xc, double 
     if (disc < 0.0) disc = 0.0;
     double t = __ddiv_rn(c, __dadd_rn(-de, __dsqrt_rn(disc)));
     return t > 1.0 ? 1.0 : t;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic in FP32 (an unevaluated sum hi + lo).  GB300 runs
+// FP64 at 2 lanes per SM per cycle, so every warp-wide FP64 instruction holds
+// the SM's FP64 pipe for ~16 cycles; geometry and reductions therefore use
+// error-free transformations in FP32: Knuth's TwoSum and the FMA-based
+// TwoProduct (Dekker / Ogita-Rump-Oishi).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+// (h, l) += (h2, l2)
+__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2)
+{
+    float s, e;
+    two_sum(h, h2, s, e);
+    h = s;
+    l = l + l2 + e;
+}
+
+// A disk with its centre split as x = xh + xl, y = yh + yl and r^2 = r2h + r2l
+// (built once per disk in FP64).
+struct DiskDF {
+    float xh, xl, yh, yl, r2h, r2l;
+};
+__device__ __forceinline__ DiskDF disk_df(double x, double y, double r)
+{
+    DiskDF d;
+    d.xh = (float)x;
+    d.xl = (float)(x - (double)d.xh);
+    d.yh = (float)y;
+    d.yl = (float)(y - (double)d.yh);
+    const double r2 = r * r;
+    d.r2h = (float)r2;
+    d.r2l = (float)(r2 - (double)d.r2h);
+    return d;
+}
+// i - xc as (h, l), accurate to ~1e-12 absolute.
+__device__ __forceinline__ void df_offset(int i, float xh, float xl, float &h, float &l)
+{
+    float e;
+    two_sum((float)i, -xh, h, e);
+    l = e - xl;
+}
+// |d|^2 - r^2 for d = (i, j) - centre, with |error| < 1e-9 for |d| < 64.
+// Also returns d as double-float components.
+__device__ __forceinline__ float disk_gap2(int i, int j, const DiskDF &D, float &dxh, float &dxl,
+                                           float &dyh, float &dyl)
+{
+    df_offset(i, D.xh, D.xl, dxh, dxl);
+    df_offset(j, D.yh, D.yl, dyh, dyl);
+    float p1, e1, p2, e2, s, es, t, et;
+    two_prod(dxh, dxh, p1, e1);
+    two_prod(dyh, dyh, p2, e2);
+    two_sum(p1, p2, s, es);
+    two_sum(s, -D.r2h, t, et);
+    const float low = ((e1 + e2) + (es + et)) - D.r2l + 2.f * (dxh * dxl + dyh * dyl) +
+                      (dxl * dxl + dyl * dyl);
+    return t + low;
+}
+// Exact disk predicate (the FP64 one above) decided in FP32 except inside a
+// band of +-1e-6 around the circle, where FP64 rounding could matter.
+__device__ __forceinline__ bool in_disk_df(int i, int j, const DiskDF &D, double xc, double yc,
+                                           double r)
+{
+    float a, b, c, d;
+    const float g = disk_gap2(i, j, D, a, b, c, d);
+    if (g < -1e-6f) return true;
+    if (g > 1e-6f) return false;
+    return in_disk(i, j, xc, yc, r);
+}
+
+// Wall fraction q of the link from (i, j) along e_k to the circle: the
+// cancellation-free closed form, with |d|^2 - r^2 and d.e in double-float
+// and the rest in FP32; within 1e-6 relative of the FP64 value.  Also
+// returns d (FP32) for the wall velocity and torque.
+__device__ __forceinline__ float link_q_df(int i, int j, int k, const DiskDF &D, float &dxf,
+                                           float &dyf)
+{
+    float dxh, dxl, dyh, dyl;
+    const float c = disk_gap2(i, j, D, dxh, dxl, dyh, dyl);
+    float sh, se;
+    two_sum((float)ex(k) * dxh, (float)ey(k) * dyh, sh, se);
+    const float de = sh + (se + ((float)ex(k) * dxl + (float)ey(k) * dyl));
+    const float disc = fmaxf(de * de - (float)(ex(k) * ex(k) + ey(k) * ey(k)) * c, 0.f);
+    dxf = dxh + dxl;
+    dyf = dyh + dyl;
+    return fminf(c / (sqrtf(disc) - de), 1.f);
+}
+
+// Per-particle sums of the link kernel: the variable part of Eq. force /
+// Eq. torque as double-float, and the exact integer sums of the constant part
+// 2 w_k e_k (axis links: 2w = 2/9, diagonal: 1/18) and its torque moment
+// 2 w_k (i e_k,y - j e_k,x).
+struct LinkSums {
+    float fx_h, fx_l, fy_h, fy_l, tz_h, tz_l;
+    int ax_x, ax_y, ax_t, dg_x, dg_y, dg_t;
+    int pad[4];
+};
+// Hydrodynamic force (Fx, Fy) and torque of a particle centred at (xc, yc).
+__device__ __forceinline__ void assemble_force(const LinkSums &S, double xc, double yc, double &Fx,
+                                               double &Fy, double &Tz)
+{
+    const double cax = 2.0 / 9.0, cdg = 1.0 / 18.0;
+    const double Fcx = cax * (double)S.ax_x + cdg * (double)S.dg_x;
+    const double Fcy = cax * (double)S.ax_y + cdg * (double)S.dg_y;
+    const double Tc = cax * (double)S.ax_t + cdg * (double)S.dg_t - xc * Fcy + yc * Fcx;
+    Fx = Fcx + ((double)S.fx_h + (double)S.fx_l);
+    Fy = Fcy + ((double)S.fy_h + (double)S.fy_l);
+    Tz = Tc + ((double)S.tz_h + (double)S.tz_l);
+}
+
+// Bouzidi quadratic bounce-back (Sec. 2.3) in deviation form, with the
+// linear and simple fallbacks when a stencil node is not fluid.  fk0, fk1,
+// fk2 = f~_k^+ at x_f, x_f - e_k, x_f - 2e_k; fb0, fb1 = f~_kbar^+ at x_f,
+// x_f - e_k; wall = 2 w_k rho0 e_kbar.u_w / c_s^2.  *lvl: 0 quadratic,
+// 1 linear, 2 simple.
+__device__ __forceinline__ float bouzidi32(float q, float fk0, float fk1, float fk2, float fb0,
+                                           float fb1, bool have1, bool have2, float wall, int &lvl)
+{
+    if (q <= 0.5f) {
+        if (have1 && have2) {
+            lvl = 0;
+            return q * (2.f * q + 1.f) * fk0 + (1.f - 4.f * q * q) * fk1 - q * (1.f - 2.f * q) * fk2 +
+                   wall;
+        }
+        if (have1) {
+            lvl = 1;
+            return 2.f * q * fk0 + (1.f - 2.f * q) * fk1 + wall;
+        }
+        lvl = 2;
+        return fk0 + wall;
+    }
+    if (have1) {
+        lvl = 0;
+        const float cc = 1.f / (q * (2.f * q + 1.f));
+        return cc * fk0 + (2.f * q - 1.f) / q * fb0 - (2.f * q - 1.f) / (2.f * q + 1.f) * fb1 + cc * wall;
+    }
+    lvl = 1;
+    const float h = 0.5f / q;
+    return h * fk0 + (2.f * q - 1.f) * h * fb0 + h * wall;
+}
+
+// Li et al. curved Dirichlet rule for g (Sec. 2.3), c_d1 = -1,
+// c_d2 = c_d3 = (2q-1)/(2q+1), c_d4 = 2/(2q+1); half-way anti-bounce-back
+// without x_f - e_k.  wT = 2 w_k T_w.
+__device__ __forceinline__ float thermal32(float q, float gk0, float gk1, float gb0, bool have1,
+                                           float wT)
+{
+    if (have1) {
+        const float c23 = (2.f * q - 1.f) / (2.f * q + 1.f), c4 = 2.f / (2.f * q + 1.f);
+        return -gk0 + c23 * (gk1 + gb0) + c4 * wT;
+    }
+    return -gk0 + wT;
 }
 
 // Effective zone of Sec. 3: N = ceil(2r) + 3 nodes per side starting at

@@ -132,6 +132,15 @@ def sedimentation_4000(seed: int = 16597) -> Workload:
                          name="cavity4000_4800disks_r10", steps=10000)
 
 
+def sedimentation_2000(seed: int = 2000) -> Workload:
+    """2000x2000 quarter-area version of sedimentation_4000 (1200 disks, same
+    density, Ra = 1e8 on H = 2000): the profiling case, 0.46 GB of state."""
+    nu, Pr = 0.02, 0.71
+    g = gravity_for_rayleigh(1e8, nu, nu / Pr, 2000.0)
+    return sedimentation(2000, 2000, 1200, 10.0, 1.5, 0.4, seed, nu=nu, Pr=Pr, g=g,
+                         name="cavity2000_1200disks_r10", steps=1000)
+
+
 def crop_1024(seed: int = 3) -> Workload:
     """1024x1024 crop with 300 disks r = 10 in the upper half (reduced storage)."""
     return sedimentation(1024, 1024, 300, 10.0, 1.5, 0.5, seed, nu=0.02, Pr=0.71, g=1e-5,
