@@ -26,7 +26,7 @@ namespace {
 
 constexpr long long kStaticSlots = 1ll << 21;   // 2,097,152 slots
 constexpr int kStaticParticles = 1 << 15;       // 32,768 particles
-constexpr int kThreads = 128;
+constexpr int kThreads = 288; // the slot-to-thread map of the workspace link kernel
 constexpr int kMaxDevices = 64;
 
 // [slot nodes: int32 x kStaticSlots][wall fractions: float x kStaticSlots]

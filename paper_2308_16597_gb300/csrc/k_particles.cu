@@ -14,7 +14,7 @@ namespace lbm {
 
 namespace {
 
-constexpr int kLinkThreads = 128;
+constexpr int kLinkThreads = 288;
 constexpr int kBoxThreads = 128;
 constexpr int kPartThreads = 1024;
 constexpr double kPi = 3.14159265358979323846;
@@ -37,13 +37,18 @@ __device__ __forceinline__ T warp_sum(T v)
 // One CTA per particle; thread s handles slot s (and s + 128, ...) of the
 // particle's 12N - 12 fixed slots.  The slot of (direction k, line) is fixed
 // by the zone geometry, so the gather needs no atomics and the per-particle
-// reduction is a deterministic tree.  The owner map of the zone (plus a
-// two-node margin for the bounce-back stencil) is first copied to shared
-// memory.  Bounce-back values are written into the solid node x_f + e_k in
-// direction kbar of the post-collision array A, where the next pull stream
-// picks them up: each (solid node, kbar) belongs to one link, and every read
-// is of a fluid node, so the writes never race the reads.
-constexpr int kWinMax = 64; // zone side + 4 held in shared memory (radius <= 28.5)
+// reduction is a deterministic tree.
+//
+// The CTA first copies its zone (plus the two-node margin the bounce-back
+// stencil reaches) into shared memory: the owner map and the 12 planes the
+// rules read (f1..f8 and g1..g4), in whole 16-byte chunks with cp.async, so
+// the scattered reads of the links become one coalesced burst per particle.
+// It also issues bulk L2 prefetches of the zone rows of the particle `ahead`
+// places later, so that particle's copies hit L2.  Bounce-back values are
+// written into the solid node x_f + e_k in direction kbar of A in HBM, where
+// the next pull stream picks them up: each (solid node, kbar) belongs to one
+// link, and every read is of a fluid node, so the writes never race the reads.
+constexpr int kTilePlanes = 12;
 
 // Double-float warp sum (lane 0 receives the result).
 __device__ __forceinline__ void warp_df_sum(float &h, float &l)
@@ -56,37 +61,81 @@ __device__ __forceinline__ void warp_df_sum(float &h, float &l)
     }
 }
 
-__global__ void __launch_bounds__(kLinkThreads)
-    k_links(const Dev D, float *A, const int *__restrict__ own, int parity)
+__host__ __device__ inline int link_tile_wy(int N) { return N + 4; }
+__host__ __device__ inline int link_tile_wx(int N) { return ((N + 7) + 3) / 4 * 4; }
+size_t link_smem_bytes(int N)
 {
-    __shared__ int win[kWinMax * kWinMax];
+    const int wy = link_tile_wy(N), wx = link_tile_wx(N), w = N + 4;
+    return (size_t)kTilePlanes * wy * wx * sizeof(float) + (size_t)w * w * sizeof(int);
+}
+
+// Global plane of tile plane t: f1..f8 then g1..g4.
+__device__ __forceinline__ int tile_global_plane(int t) { return t < 8 ? t + 1 : t + 2; }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void prefetch_zone(const Dev &D, const float *A, const GeomRec &G)
+{
+    const int N = G.N, wy = link_tile_wy(N), wx = link_tile_wx(N);
+    const int XA = (G.X0 - 2) & ~3, YA = G.Y0 - 2;
+    const int lo = max(XA, 0), hi = min(XA + wx, D.pitch);
+    if (hi <= lo) return;
+    for (int idx = threadIdx.x; idx < kTilePlanes * wy; idx += kLinkThreads) {
+        const int t = idx / wy, row = YA + idx % wy;
+        if (row < 0 || row >= D.ny) continue;
+        const float *sp = A + (long long)tile_global_plane(t) * D.ps + (long long)row * D.pitch + lo;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sp), "r"((unsigned)(hi - lo) * 4u)
+                     : "memory");
+    }
+}
+
+__global__ void __launch_bounds__(kLinkThreads)
+    k_links(const Dev D, float *A, const int *__restrict__ own, int parity, int ahead)
+{
+    extern __shared__ __align__(16) float ltile[];
     const int p = blockIdx.x;
-    const double xc = D.cur.x[p], yc = D.cur.y[p], r = D.cur.r[p];
-    const DiskDF dk = disk_df(xc, yc, r);
-    const float Ux = (float)D.cur.ux[p], Uy = (float)D.cur.uy[p], Om = (float)D.cur.om[p];
-    const float wT = 0.2f * (float)D.cur.T[p]; // 2 w_k T_w for D2Q5
-    const int N = zone_size(r), cap = 12 * N - 12;
-    const int X0 = (int)floor(xc - r) - 1, Y0 = (int)floor(yc - r) - 1;
+    const GeomRec G = D.geo_cur[p];
+    const DiskDF dk = geom_df(G);
+    const float Ux = G.ux, Uy = G.uy, Om = G.om, wT = G.wT;
+    const int N = G.N, cap = 12 * N - 12;
+    const int X0 = G.X0, Y0 = G.Y0;
     const int base = D.slot_base[p];
     if (threadIdx.x == 0) {
         D.pos4[p] = make_float4(dk.xh, dk.yh, dk.xl, dk.yl);
-        D.prc[p] = make_float2((float)r, (float)(kPi * r * r * (D.cur.rho[p] - D.rho_f) * D.g));
+        D.prc[p] = make_float2(G.r, G.C);
     }
+    if (p + ahead < D.np) prefetch_zone(D, A, D.geo_cur[p + ahead]);
 
-    // owner window: node (X0 - 2 + a, Y0 - 2 + b) at win[b * W + a], -2 outside
+    // tile of the 12 planes: rows YA .. YA + wy - 1, columns XA .. XA + wx - 1
+    // (XA 16-byte aligned); owner window: (X0 - 2 + a, Y0 - 2 + b) at own_w[b * W + a]
+    const int wy = link_tile_wy(D.zone_max), wx = link_tile_wx(D.zone_max);
+    const int XA = (X0 - 2) & ~3, YA = Y0 - 2;
     const int W = N + 4;
-    const bool use_win = W <= kWinMax;
-    if (use_win) {
+    int *own_w = reinterpret_cast<int *>(ltile + kTilePlanes * wy * wx);
+    {
+        const int cpr = wx / 4; // chunks per row
+        for (int idx = threadIdx.x; idx < kTilePlanes * wy * cpr; idx += kLinkThreads) {
+            const int t = idx / (wy * cpr), rem = idx - t * wy * cpr;
+            const int row = rem / cpr, c = rem - row * cpr;
+            const int gy = YA + row, gx = XA + 4 * c;
+            if (gy < 0 || gy >= D.ny || gx < 0 || gx + 4 > D.pitch) continue;
+            cp_async16(ltile + (t * wy + row) * wx + 4 * c,
+                       A + (long long)tile_global_plane(t) * D.ps + (long long)gy * D.pitch + gx);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
         for (int idx = threadIdx.x; idx < W * W; idx += kLinkThreads) {
             const int i = X0 - 2 + idx % W, j = Y0 - 2 + idx / W;
-            win[idx] = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
+            own_w[idx] = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
     }
-    auto owner_at = [&](int i, int j) -> int {
-        if (use_win) return win[(j - Y0 + 2) * W + (i - X0 + 2)];
-        return inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
-    };
+    auto owner_at = [&](int i, int j) -> int { return own_w[(j - Y0 + 2) * W + (i - X0 + 2)]; };
+    auto tv = [&](int t, int i, int j) -> float { return ltile[(t * wy + (j - YA)) * wx + (i - XA)]; };
 
     float sbx = 0.f, sby = 0.f, stq = 0.f; // link brackets of Eq. force / Eq. torque
     int ax_x = 0, ax_y = 0, ax_t = 0, dg_x = 0, dg_y = 0, dg_t = 0; // exact constant parts
@@ -96,17 +145,19 @@ __global__ void __launch_bounds__(kLinkThreads)
         int k, line;
         slot_dir_line(s, N, k, line);
         const int kx = ex(k), ky = ey(k);
-        int found = 0, fi = 0, fj = 0;
-        for (int t = 0; t < N; ++t) {
-            int a, b;
-            if (!zone_point(k, N, line, t, a, b)) continue;
-            const int i = X0 + a, j = Y0 + b;
-            if (owner_at(i, j) != -1 || owner_at(i + kx, j + ky) != p) continue;
-            if (++found == 1) {
-                fi = i;
-                fj = j;
+        // walk the line through the owner window: a link source is a fluid
+        // node whose neighbour along e_k belongs to this particle
+        int a0, b0, da, db, cnt;
+        line_walk(k, N, line, a0, b0, da, db, cnt);
+        int idx = (b0 + 2) * W + (a0 + 2);
+        const int step = db * W + da, nb = ky * W + kx;
+        int found = 0, hit = 0;
+        for (int t = 0; t < cnt; ++t, idx += step) {
+            if (own_w[idx] == -1 && own_w[idx + nb] == p) {
+                if (++found == 1) hit = t;
             }
         }
+        const int fi = X0 + a0 + hit * da, fj = Y0 + b0 + hit * db;
         c_over += found > 1;
         if (!found) {
             D.slot_node[base + s] = -1;
@@ -126,11 +177,10 @@ __global__ void __launch_bounds__(kLinkThreads)
         const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
         const bool have1 = owner_at(i1, j1) == -1;
         const bool have2 = owner_at(i2, j2) == -1;
-        const long long n0 = (long long)fj * D.pitch + fi;
-        const long long n1 = have1 ? (long long)j1 * D.pitch + i1 : n0;
-        const long long n2 = have2 ? (long long)j2 * D.pitch + i2 : n0;
-        const float fk0 = A[k * D.ps + n0], fk1 = A[k * D.ps + n1], fk2 = A[k * D.ps + n2];
-        const float fb0 = A[kb * D.ps + n0], fb1 = A[kb * D.ps + n1];
+        const int ii1 = have1 ? i1 : fi, jj1 = have1 ? j1 : fj;
+        const int ii2 = have2 ? i2 : fi, jj2 = have2 ? j2 : fj;
+        const float fk0 = tv(k - 1, fi, fj), fk1 = tv(k - 1, ii1, jj1), fk2 = tv(k - 1, ii2, jj2);
+        const float fb0 = tv(kb - 1, fi, fj), fb1 = tv(kb - 1, ii1, jj1);
         const float rx = dxf + q * kx, ry = dyf + q * ky;
         const float uwx = Ux - Om * ry, uwy = Uy + Om * rx;
         const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy); // 2 w rho0 e_kbar.u_w / c_s^2
@@ -141,8 +191,8 @@ __global__ void __launch_bounds__(kLinkThreads)
         const long long ns = (long long)(fj + ky) * D.pitch + (fi + kx);
         A[kb * D.ps + ns] = fnew;
         if (k <= 4) {
-            const float gnew = thermal32(q, A[(kQ9 + k) * D.ps + n0], A[(kQ9 + k) * D.ps + n1],
-                                         A[(kQ9 + kb) * D.ps + n0], have1, wT);
+            const float gnew = thermal32(q, tv(8 + k - 1, fi, fj), tv(8 + k - 1, ii1, jj1),
+                                         tv(8 + kb - 1, fi, fj), have1, wT);
             c_th += !have1;
             A[(kQ9 + kb) * D.ps + ns] = gnew;
         }
@@ -161,7 +211,6 @@ __global__ void __launch_bounds__(kLinkThreads)
         if (k <= 4) { ax_x += kx; ax_y += ky; ax_t += tz; }
         else { dg_x += kx; dg_y += ky; dg_t += tz; }
     }
-
     __shared__ float red[6][kLinkThreads / 32];
     __shared__ int cnt[11][kLinkThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -323,8 +372,10 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
     }
     if (x - r < -0.5 || x + r > (double)D.nx - 0.5 || y - r < -0.5 || y + r > (double)D.ny - 0.5)
         atomicOr(&D.status->err, kErrDomain);
+    const double T = D.cur.T[b];
     D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
-    D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = D.cur.T[b];
+    D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T;
+    D.geo_nxt[b] = make_geom(x, y, r, ux, uy, om, T, rho, D.rho_f, D.g);
 }
 
 // Zone of a disk at (x, y) with radius r: N x N nodes from
@@ -333,17 +384,14 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
 struct Box {
     int X0, Y0, N;
 };
-__device__ __forceinline__ Box box_of(double x, double y, double r)
-{
-    return Box{(int)floor(x - r) - 1, (int)floor(y - r) - 1, zone_size(r)};
-}
+__device__ __forceinline__ Box box_of(const GeomRec &G) { return Box{G.X0, G.Y0, G.N}; }
 
 // Reset the zone of each disk's position one step back in the owner map
 // that is about to receive the new positions, and in the flag map.
 __global__ void __launch_bounds__(kBoxThreads) k_clear(const Dev D, int *own_nxt)
 {
     const int p = blockIdx.x;
-    const Box B = box_of(D.px[p], D.py[p], D.cur.r[p]);
+    const Box B = box_of(D.geo_prev[p]);
     for (int idx = threadIdx.x; idx < B.N * B.N; idx += kBoxThreads) {
         const int i = B.X0 + idx % B.N, j = B.Y0 + idx / B.N;
         if (!inside(D, i, j)) continue;
@@ -358,15 +406,17 @@ __global__ void __launch_bounds__(kBoxThreads) k_clear(const Dev D, int *own_nxt
 // lane per zone row: the predicate holds on one contiguous run of each row
 // (it is monotone in |i - x|), so the run is found from an FP32 estimate of
 // its ends and settled with the exact predicate at the ends only.
-__global__ void __launch_bounds__(kBoxThreads) k_raster(const Dev D, int *own, const PartSoA pos)
+__global__ void __launch_bounds__(kBoxThreads)
+    k_raster(const Dev D, int *own, const GeomRec *__restrict__ geo, const PartSoA pos)
 {
     const int lane = threadIdx.x & 31;
     const int p = blockIdx.x * (kBoxThreads / 32) + (threadIdx.x >> 5);
     if (p >= D.np) return;
-    const double x = pos.x[p], y = pos.y[p], r = pos.r[p];
-    const Box B = box_of(x, y, r);
-    const DiskDF dk = disk_df(x, y, r);
-    const int ic = (int)floor(x + 0.5); // the node of each row nearest the centre
+    const GeomRec G = geo[p];
+    const double x = pos.x[p], y = pos.y[p], r = pos.r[p]; // for the FP64 fallback only
+    const Box B = box_of(G);
+    const DiskDF dk = geom_df(G);
+    const int ic = G.ic; // the node of each row nearest the centre
     for (int b = lane; b < B.N; b += 32) {
         const int j = B.Y0 + b;
         if (j < 0 || j >= D.ny) continue;
@@ -397,9 +447,8 @@ __global__ void __launch_bounds__(kBoxThreads)
     k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate)
 {
     const int p = blockIdx.x;
-    const double r = D.cur.r[p];
-    const Box B0 = box_of(D.cur.x[p], D.cur.y[p], r);
-    const Box B1 = box_of(D.nxt.x[p], D.nxt.y[p], r);
+    const Box B0 = box_of(D.geo_cur[p]);
+    const Box B1 = box_of(D.geo_nxt[p]);
     for (int pass = 0; pass < 2; ++pass) {
         const Box B = pass ? B1 : B0;
         for (int idx = threadIdx.x; idx < B.N * B.N; idx += kBoxThreads) {
@@ -419,8 +468,24 @@ __global__ void __launch_bounds__(kBoxThreads)
     case 3: D.cur.uy[p] = D.nxt.uy[p]; break;
     case 4: D.cur.th[p] = D.nxt.th[p]; break;
     case 5: D.cur.om[p] = D.nxt.om[p]; break;
+    case 6: D.geo_prev[p] = D.geo_cur[p]; break;
     default: break;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) D.geo_cur[p] = D.geo_nxt[p];
+}
+
+// Geometry records of the current state and of the previous positions.
+__global__ void k_geom_init(const Dev D)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= D.np) return;
+    const GeomRec G = make_geom(D.cur.x[a], D.cur.y[a], D.cur.r[a], D.cur.ux[a], D.cur.uy[a],
+                                D.cur.om[a], D.cur.T[a], D.cur.rho[a], D.rho_f, D.g);
+    D.geo_cur[a] = G;
+    D.geo_nxt[a] = G;
+    D.geo_prev[a] = make_geom(D.px[a], D.py[a], D.cur.r[a], 0.0, 0.0, 0.0, D.cur.T[a], D.cur.rho[a],
+                              D.rho_f, D.g);
 }
 
 __global__ void k_pack_particles(const Dev D, lbm_particle *out)
@@ -434,10 +499,26 @@ __global__ void k_pack_particles(const Dev D, lbm_particle *out)
     out[a] = P;
 }
 
+cudaError_t prepare_links(Dev &D)
+{
+    D.link_ahead = 1;
+    if (D.np == 0) return cudaSuccess;
+    const size_t smem = link_smem_bytes(D.zone_max);
+    cudaError_t e = cudaFuncSetAttribute(k_links, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0, dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_links, kLinkThreads, smem)) != cudaSuccess)
+        return e;
+    D.link_ahead = max(1, sms * per_sm);
+    return cudaSuccess;
+}
+
 cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity, cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
-    k_links<<<D.np, kLinkThreads, 0, s>>>(D, A, own_cur, parity);
+    k_links<<<D.np, kLinkThreads, link_smem_bytes(D.zone_max), s>>>(D, A, own_cur, parity, D.link_ahead);
     return cudaGetLastError();
 }
 
@@ -455,11 +536,18 @@ cudaError_t launch_clear(const Dev &D, int *own_nxt, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_raster(const Dev &D, int *own, const PartSoA &pos, cudaStream_t s)
+cudaError_t launch_raster(const Dev &D, int *own, const GeomRec *geo, const PartSoA &pos, cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
     const int per = kBoxThreads / 32;
-    k_raster<<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own, pos);
+    k_raster<<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own, geo, pos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geom_init(const Dev &D, cudaStream_t s)
+{
+    if (D.np == 0) return cudaSuccess;
+    k_geom_init<<<(D.np + 127) / 128, 128, 0, s>>>(D);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ struct Layout {
     long long ps = 0;
     size_t nslots = 0;
     size_t A[2], own[2], flags, slot_node, slot_q, slot_base, cur, nxt, prev, force, pos4, prc, lsum,
-        status, pack, stage, total;
+        geo[3], status, pack, stage, total;
     int stage_rows = 0;
 };
 
@@ -56,6 +56,8 @@ int validate(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_pa
         for (double x : v)
             if (!finite(x)) return LBM_EINVAL;
         if (P.r < 1.0 || P.rho <= 0.0) return LBM_EINVAL;
+        // the link kernel holds a particle's zone in shared memory
+        if (link_smem_bytes(zone_size(P.r)) > (size_t)200 * 1024) return LBM_EINVAL;
         // a disk stays inside the cavity; next to a periodic seam it keeps two
         // nodes of clearance so that no link or stencil wraps around
         const double mx = px ? 2.0 : -0.5, my = py ? 2.0 : -0.5;
@@ -111,6 +113,7 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, Layout &L)
     L.pos4 = take((size_t)n * sizeof(float4));
     L.prc = take((size_t)n * sizeof(float2));
     L.lsum = take((size_t)n * sizeof(LinkSums));
+    for (int b = 0; b < 3; ++b) L.geo[b] = take((size_t)n * sizeof(GeomRec));
     L.status = take(sizeof(Status));
     L.pack = take((size_t)n * sizeof(lbm_particle));
     L.stage_rows = (int)std::max<size_t>(1, std::min<size_t>(d->ny, kStageBytes / (16 * (size_t)d->nx)));
@@ -228,7 +231,8 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
     if ((rc = timed(h, kKParticles, st, [&] { return launch_particles(D, par, st); }))) return rc;
     if (h->np > 0) {
         if ((rc = timed(h, kKClear, st, [&] { return launch_clear(D, on, st); }))) return rc;
-        if ((rc = timed(h, kKRaster, st, [&] { return launch_raster(D, on, D.nxt, st); }))) return rc;
+        if ((rc = timed(h, kKRaster, st, [&] { return launch_raster(D, on, D.geo_nxt, D.nxt, st); })))
+            return rc;
         if ((rc = timed(h, kKFlags, st, [&] { return launch_flags(D, oc, on, 1, st); }))) return rc;
     }
     return timed(h, kKStreamCollide, st,
@@ -320,6 +324,9 @@ void fill_dev(lbm_handle *h)
     D.pos4 = reinterpret_cast<float4 *>(ws + L.pos4);
     D.prc = reinterpret_cast<float2 *>(ws + L.prc);
     D.lsum = reinterpret_cast<LinkSums *>(ws + L.lsum);
+    D.geo_prev = reinterpret_cast<GeomRec *>(ws + L.geo[0]);
+    D.geo_cur = reinterpret_cast<GeomRec *>(ws + L.geo[1]);
+    D.geo_nxt = reinterpret_cast<GeomRec *>(ws + L.geo[2]);
     D.status = reinterpret_cast<Status *>(ws + L.status);
     for (int b = 0; b < 2; ++b) {
         h->A[b] = reinterpret_cast<float *>(ws + L.A[b]);
@@ -355,13 +362,14 @@ int rebuild_maps(lbm_handle *h)
     CK(h, cudaMemsetAsync(h->own[1], 0xff, nn * sizeof(int), h->stream));
     CK(h, cudaMemsetAsync(h->D.flags, 0, (size_t)h->L.pitch * h->d.ny, h->stream));
     int *oc = h->own[h->parity];
-    CK(h, launch_raster(h->D, oc, h->D.cur, h->stream));
+    CK(h, launch_geom_init(h->D, h->stream));
+    CK(h, launch_raster(h->D, oc, h->D.geo_cur, h->D.cur, h->stream));
     CK(h, launch_flags(h->D, oc, oc, 0, h->stream));
     // the owner map one step back, which the first clear expects in the other buffer
     PartSoA prev = h->D.cur;
     prev.x = h->D.px;
     prev.y = h->D.py;
-    CK(h, launch_raster(h->D, h->own[h->parity ^ 1], prev, h->stream));
+    CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, h->stream));
     return LBM_OK;
 }
 
@@ -417,11 +425,14 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
     h->ws = static_cast<char *>(d_workspace);
     h->stream = static_cast<cudaStream_t>(stream);
     fill_dev(h);
+    h->D.zone_max = 0;
+    for (int a = 0; a < n; ++a) h->D.zone_max = std::max(h->D.zone_max, zone_size(p[a].r));
     auto fail = [&](int code) {
         lbm_destroy(h);
         return code;
     };
     if (cudaMemsetAsync(h->D.status, 0, sizeof(Status), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    if (prepare_links(h->D) != cudaSuccess) return fail(LBM_ECUDA);
     if (n > 0) {
         std::vector<int> base(n + 1, 0);
         for (int a = 0; a < n; ++a) base[a + 1] = base[a] + slot_capacity(p[a].r);
@@ -608,7 +619,8 @@ int lbm_set_state(lbm_handle *h, const void *buf, size_t bytes)
         PartSoA prev = h->D.cur;
         prev.x = h->D.px;
         prev.y = h->D.py;
-        CK(h, launch_raster(h->D, h->own[h->parity ^ 1], prev, h->stream));
+        CK(h, launch_geom_init(h->D, h->stream));
+        CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, h->stream));
     }
     return sync_status(h);
 }

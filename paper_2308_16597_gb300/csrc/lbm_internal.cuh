@@ -77,6 +77,8 @@ struct Dev {
     float Twall[4];
     double g, rho_f, eps_w, s_rep;
     int fixed;
+    int zone_max;      // largest zone side N over the particles (sizes the link kernel's tile)
+    int link_ahead;    // link-kernel CTAs resident on the GPU (distance of its L2 prefetch)
     // device buffers
     uint8_t *flags;    // [ny][pitch]
     int *slot_node;    // [nslots]
@@ -88,6 +90,7 @@ struct Dev {
     float4 *pos4;      // [np]: centre as double-float (xh, yh, xl, yl) at the start of the step
     float2 *prc;       // [np]: (r, C = pi r^2 (rho_p - rho_f) g) in FP32 for the pair screening
     struct LinkSums *lsum; // [np]: link-kernel sums, assembled into force by the particle update
+    struct GeomRec *geo_prev, *geo_cur, *geo_nxt; // [np] each: FP32/int geometry of the three positions
     Status *status;
 };
 
@@ -117,6 +120,12 @@ __device__ __forceinline__ double link_q(int i, int j, int k, double xc, double 
     double t = __ddiv_rn(c, __dadd_rn(-de, __dsqrt_rn(disc)));
     return t > 1.0 ? 1.0 : t;
 }
+
+// Effective zone of Sec. 3: N = ceil(2r) + 3 nodes per side starting at
+// floor(c - r) - 1 (equal to the paper's INT(c + r) - INT(c - r) + 3 for
+// integer radii); 12N - 12 fixed slots.
+__host__ __device__ inline int zone_size(double r) { return (int)ceil(2.0 * r) + 3; }
+__host__ __device__ inline int slot_capacity(double r) { return 12 * zone_size(r) - 12; }
 
 // ---------------------------------------------------------------------------
 // Double-float arithmetic in FP32 (an unevaluated sum hi + lo).  GB300 runs
@@ -215,6 +224,38 @@ __device__ __forceinline__ float link_q_df(int i, int j, int k, const DiskDF &D,
     return fminf(c / (sqrtf(disc) - de), 1.f);
 }
 
+// Geometry of one disk position in the forms the per-warp kernels use, built
+// once per particle and step in FP64 (one lane per particle) so that no warp
+// repeats FP64 work: the double-float centre and r^2, the zone (origin, side),
+// the row centre index floor(x + 1/2), FP32 velocities and 2 w_k T_w, and the
+// radius and repulsion force scale C = pi r^2 (rho_p - rho_f) g.
+struct GeomRec {
+    float xh, xl, yh, yl, r2h, r2l, r, C;
+    int X0, Y0, N, ic;
+    float ux, uy, om, wT;
+};
+__device__ __forceinline__ GeomRec make_geom(double x, double y, double r, double ux, double uy,
+                                             double om, double T, double rho, double rho_f, double g)
+{
+    GeomRec G;
+    const DiskDF d = disk_df(x, y, r);
+    G.xh = d.xh; G.xl = d.xl; G.yh = d.yh; G.yl = d.yl; G.r2h = d.r2h; G.r2l = d.r2l;
+    G.r = (float)r;
+    G.C = (float)(3.14159265358979323846 * r * r * (rho - rho_f) * g);
+    G.N = zone_size(r);
+    G.X0 = (int)floor(x - r) - 1;
+    G.Y0 = (int)floor(y - r) - 1;
+    G.ic = (int)floor(x + 0.5);
+    G.ux = (float)ux; G.uy = (float)uy; G.om = (float)om; G.wT = (float)(0.2 * T);
+    return G;
+}
+__device__ __forceinline__ DiskDF geom_df(const GeomRec &G)
+{
+    DiskDF d;
+    d.xh = G.xh; d.xl = G.xl; d.yh = G.yh; d.yl = G.yl; d.r2h = G.r2h; d.r2l = G.r2l;
+    return d;
+}
+
 // Per-particle sums of the link kernel: the variable part of Eq. force /
 // Eq. torque as double-float, and the exact integer sums of the constant part
 // 2 w_k e_k (axis links: 2w = 2/9, diagonal: 1/18) and its torque moment
@@ -281,11 +322,7 @@ __device__ __forceinline__ float thermal32(float q, float gk0, float gk1, float 
     return -gk0 + wT;
 }
 
-// Effective zone of Sec. 3: N = ceil(2r) + 3 nodes per side starting at
-// floor(c - r) - 1 (equal to the paper's INT(c + r) - INT(c - r) + 3 for
-// integer radii); 12N - 12 fixed slots.
-__host__ __device__ inline int zone_size(double r) { return (int)ceil(2.0 * r) + 3; }
-__host__ __device__ inline int slot_capacity(double r) { return 12 * zone_size(r) - 12; }
+
 
 // Zone point (a, b) of the t-th node on line `line` of direction k; false
 // when it falls outside the N x N zone.  e1/e3: rows (line = b); e2/e4:
@@ -307,6 +344,27 @@ __host__ __device__ inline bool zone_point(int k, int N, int line, int t, int &a
         b = (line + 1) - t;
     }
     return b >= 0 && b < N;
+}
+
+// Walk of line `line` of direction k in zone coordinates (a = column,
+// b = row): the valid points are (a0 + t da, b0 + t db), t = 0 .. cnt - 1 (the
+// same points as zone_point, in the same order, without per-point tests).
+__host__ __device__ inline void line_walk(int k, int N, int line, int &a0, int &b0, int &da, int &db,
+                                          int &cnt)
+{
+    if (k == 1 || k == 3) {
+        a0 = 0; b0 = line; da = 1; db = 0; cnt = N;
+    } else if (k == 2 || k == 4) {
+        a0 = line; b0 = 0; da = 0; db = 1; cnt = N;
+    } else if (k == 5 || k == 7) {
+        const int m = line - (N - 2); // b = a - m
+        const int t0 = m > 0 ? m : 0, t1 = (N - 1 + m) < (N - 1) ? (N - 1 + m) : (N - 1);
+        a0 = t0; b0 = t0 - m; da = 1; db = 1; cnt = t1 - t0 + 1;
+    } else {
+        const int sm = line + 1; // b = sm - a
+        const int t0 = (sm - N + 1) > 0 ? (sm - N + 1) : 0, t1 = sm < (N - 1) ? sm : (N - 1);
+        a0 = t0; b0 = sm - t0; da = 1; db = -1; cnt = t1 - t0 + 1;
+    }
 }
 
 // Slot s of a zone of size N -> direction k and line.
@@ -337,11 +395,19 @@ cudaError_t launch_init_collide(const Dev &D, const float *Ain, float *Aout, flo
 cudaError_t launch_fields(const Dev &D, const float *A, int row0, int rows, float *rho, float *ux,
                           float *uy, float *T, cudaStream_t s);
 cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity, cudaStream_t s);
+// Shared memory of the link kernel for zones of side N; prepare_links sets the
+// kernel's shared-memory limit and D.link_ahead (call outside stream capture).
+size_t link_smem_bytes(int N);
+cudaError_t prepare_links(Dev &D);
 cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s);
 cudaError_t launch_clear(const Dev &D, int *own_nxt, cudaStream_t s);
-cudaError_t launch_raster(const Dev &D, int *own, const PartSoA &pos, cudaStream_t s);
+cudaError_t launch_raster(const Dev &D, int *own, const struct GeomRec *geo, const PartSoA &pos,
+                          cudaStream_t s);
 cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate,
                          cudaStream_t s);
 cudaError_t launch_pack_particles(const Dev &D, lbm_particle *out, cudaStream_t s);
+// Geometry records of the current state (into cur, nxt and prev) and of the
+// previous positions (into prev), for init and restore.
+cudaError_t launch_geom_init(const Dev &D, cudaStream_t s);
 
 } // namespace lbm
