@@ -61,12 +61,24 @@ __device__ __forceinline__ void warp_df_sum(float &h, float &l)
     }
 }
 
+__host__ __device__ inline int pow2_at_least(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+// Link-kernel shared memory for zones of side N: the 12-plane tile
+// [wy][wx] (wy = N + 4 rows, wx a power of two >= N + 7 columns, 16-byte
+// aligned start), the owner window [N + 4][ws] (ws a power of two >= N + 4),
+// and per-slot counters, link nodes and the compacted list of valid slots.
 __host__ __device__ inline int link_tile_wy(int N) { return N + 4; }
-__host__ __device__ inline int link_tile_wx(int N) { return ((N + 7) + 3) / 4 * 4; }
+__host__ __device__ inline int link_tile_wx(int N) { return pow2_at_least(N + 7); }
+__host__ __device__ inline int link_win_ws(int N) { return pow2_at_least(N + 4); }
 size_t link_smem_bytes(int N)
 {
-    const int wy = link_tile_wy(N), wx = link_tile_wx(N), w = N + 4;
-    return (size_t)kTilePlanes * wy * wx * sizeof(float) + (size_t)w * w * sizeof(int);
+    const int wy = link_tile_wy(N), wx = link_tile_wx(N), ws = link_win_ws(N), cap = 12 * N - 12;
+    return (size_t)kTilePlanes * wy * wx * sizeof(float) + (size_t)(N + 4) * ws * sizeof(int) +
+           (size_t)3 * cap * sizeof(int);
 }
 
 // Global plane of tile plane t: f1..f8 then g1..g4.
@@ -93,86 +105,164 @@ __device__ __forceinline__ void prefetch_zone(const Dev &D, const float *A, cons
     }
 }
 
+// Fixed slot (Sec. 3) of the link from zone node (a, b) along e_k, or -1 for
+// a corner line that cannot carry a link.
+__device__ __forceinline__ int slot_of(int k, int a, int b, int N)
+{
+    const int M = 2 * N - 3;
+    switch (k) {
+    case 1: return b;
+    case 2: return N + a;
+    case 3: return 2 * N + b;
+    case 4: return 3 * N + a;
+    default: {
+        const int line = (k == 5 || k == 7) ? a - b + N - 2 : a + b - 1;
+        if (line < 0 || line >= M) return -1;
+        return 4 * N + (k - 5) * M + line;
+    }
+    }
+}
+
+// One CTA per particle.  Phases:
+//  1. copy the zone (plus the two-node margin of the bounce-back stencil)
+//     into shared memory: the 12 planes the rules read (f1..f8, g1..g4) with
+//     16-byte cp.async, and the owner map; also issue bulk L2 prefetches of
+//     the zone rows of the particle `ahead` places later in launch order;
+//  2. every zone node that is fluid tests its eight neighbours; a neighbour
+//     owned by this particle makes a link, recorded in the link's fixed slot
+//     of the index array (direction k, line through the zone; Sec. 3);
+//  3. the valid slots are compacted in slot order (a block-wide prefix), so
+//     thread i takes the i-th link: the work is balanced and the reduction
+//     order is fixed, hence the forces are bit-reproducible;
+//  4. each link: wall fraction q, curved bounce-back of f and g (Sec. 2.3)
+//     written into the solid node x_f + e_k (direction kbar) of A in HBM,
+//     where the next pull stream picks it up (one link per (solid node, kbar),
+//     and every read is of a fluid node), and the momentum-exchange bracket
+//     of Eq. force / Eq. torque, reduced per particle.
 __global__ void __launch_bounds__(kLinkThreads)
     k_links(const Dev D, float *A, const int *__restrict__ own, int parity, int ahead)
 {
     extern __shared__ __align__(16) float ltile[];
+    __shared__ int s_warp[kLinkThreads / 32 + 1];
+    __shared__ unsigned s_over;
     const int p = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const GeomRec G = D.geo_cur[p];
     const DiskDF dk = geom_df(G);
     const float Ux = G.ux, Uy = G.uy, Om = G.om, wT = G.wT;
     const int N = G.N, cap = 12 * N - 12;
     const int X0 = G.X0, Y0 = G.Y0;
     const int base = D.slot_base[p];
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         D.pos4[p] = make_float4(dk.xh, dk.yh, dk.xl, dk.yl);
         D.prc[p] = make_float2(G.r, G.C);
+        s_over = 0u;
     }
     if (p + ahead < D.np) prefetch_zone(D, A, D.geo_cur[p + ahead]);
 
-    // tile of the 12 planes: rows YA .. YA + wy - 1, columns XA .. XA + wx - 1
-    // (XA 16-byte aligned); owner window: (X0 - 2 + a, Y0 - 2 + b) at own_w[b * W + a]
-    const int wy = link_tile_wy(D.zone_max), wx = link_tile_wx(D.zone_max);
+    const int Nm = D.zone_max;
+    const int wy = link_tile_wy(Nm), wx = link_tile_wx(Nm), ws = link_win_ws(Nm);
     const int XA = (X0 - 2) & ~3, YA = Y0 - 2;
-    const int W = N + 4;
-    int *own_w = reinterpret_cast<int *>(ltile + kTilePlanes * wy * wx);
+    int *win = reinterpret_cast<int *>(ltile + kTilePlanes * wy * wx); // [N + 4][ws]
+    int *cnt = win + (Nm + 4) * ws;                                    // [cap] links per slot
+    int *info = cnt + 12 * Nm - 12;                                    // [cap] (b << 16) | a
+    int *list = info + 12 * Nm - 12;                                   // [cap] valid slots in order
+
+    // ---- 1. tile and owner window
     {
-        const int cpr = wx / 4; // chunks per row
-        for (int idx = threadIdx.x; idx < kTilePlanes * wy * cpr; idx += kLinkThreads) {
-            const int t = idx / (wy * cpr), rem = idx - t * wy * cpr;
-            const int row = rem / cpr, c = rem - row * cpr;
-            const int gy = YA + row, gx = XA + 4 * c;
-            if (gy < 0 || gy >= D.ny || gx < 0 || gx + 4 > D.pitch) continue;
-            cp_async16(ltile + (t * wy + row) * wx + 4 * c,
-                       A + (long long)tile_global_plane(t) * D.ps + (long long)gy * D.pitch + gx);
+        const int cpr = wx >> 2, lcpr = __ffs(cpr) - 1, per_plane = wy * cpr;
+        for (int t = 0; t < kTilePlanes; ++t) {
+            const float *src = A + (long long)tile_global_plane(t) * D.ps;
+            for (int e = tid; e < per_plane; e += kLinkThreads) {
+                const int row = e >> lcpr, c = e & (cpr - 1);
+                const int gy = YA + row, gx = XA + 4 * c;
+                if (gy < 0 || gy >= D.ny || gx < 0 || gx + 4 > D.pitch) continue;
+                cp_async16(ltile + (t * wy + row) * wx + 4 * c, src + (long long)gy * D.pitch + gx);
+            }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        for (int idx = threadIdx.x; idx < W * W; idx += kLinkThreads) {
-            const int i = X0 - 2 + idx % W, j = Y0 - 2 + idx / W;
-            own_w[idx] = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
+        const int lws = __ffs(ws) - 1;
+        for (int e = tid; e < (N + 4) * ws; e += kLinkThreads) {
+            const int row = e >> lws, col = e & (ws - 1);
+            if (col >= N + 4) continue;
+            const int i = X0 - 2 + col, j = Y0 - 2 + row;
+            win[e] = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
         }
+        for (int e = tid; e < cap; e += kLinkThreads) cnt[e] = 0;
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
     }
-    auto owner_at = [&](int i, int j) -> int { return own_w[(j - Y0 + 2) * W + (i - X0 + 2)]; };
+    auto owner_at = [&](int i, int j) -> int { return win[(j - Y0 + 2) * ws + (i - X0 + 2)]; };
     auto tv = [&](int t, int i, int j) -> float { return ltile[(t * wy + (j - YA)) * wx + (i - XA)]; };
 
-    float sbx = 0.f, sby = 0.f, stq = 0.f; // link brackets of Eq. force / Eq. torque
-    int ax_x = 0, ax_y = 0, ax_t = 0, dg_x = 0, dg_y = 0, dg_t = 0; // exact constant parts
-    unsigned c_lin = 0, c_simple = 0, c_th = 0, c_links = 0, c_over = 0;
-
-    for (int s = threadIdx.x; s < cap; s += kLinkThreads) {
-        int k, line;
-        slot_dir_line(s, N, k, line);
-        const int kx = ex(k), ky = ey(k);
-        // walk the line through the owner window: a link source is a fluid
-        // node whose neighbour along e_k belongs to this particle
-        int a0, b0, da, db, cnt;
-        line_walk(k, N, line, a0, b0, da, db, cnt);
-        int idx = (b0 + 2) * W + (a0 + 2);
-        const int step = db * W + da, nb = ky * W + kx;
-        int found = 0, hit = 0;
-        for (int t = 0; t < cnt; ++t, idx += step) {
-            if (own_w[idx] == -1 && own_w[idx + nb] == p) {
-                if (++found == 1) hit = t;
+    // ---- 2. link detection, one zone node per thread
+    {
+        const int lws = __ffs(ws) - 1;
+        for (int e = tid; e < N * ws; e += kLinkThreads) {
+            const int bb = e >> lws, aa = e & (ws - 1);
+            if (aa >= N) continue;
+            const int w0 = (bb + 2) * ws + (aa + 2);
+            if (win[w0] != -1) continue;
+#pragma unroll
+            for (int k = 1; k < kQ9; ++k) {
+                if (win[w0 + ey(k) * ws + ex(k)] != p) continue;
+                const int sl = slot_of(k, aa, bb, N);
+                if (sl < 0) {
+                    s_over = 1u;
+                    continue;
+                }
+                if (atomicAdd(&cnt[sl], 1) == 0) info[sl] = (bb << 16) | aa;
+                else s_over = 1u;
             }
         }
-        const int fi = X0 + a0 + hit * da, fj = Y0 + b0 + hit * db;
-        c_over += found > 1;
-        if (!found) {
-            D.slot_node[base + s] = -1;
-            D.slot_q[base + s] = 0.f;
-            continue;
+        __syncthreads();
+    }
+
+    // ---- 3. compaction of the valid slots in slot order
+    int nvalid = 0;
+    for (int s0 = 0; s0 < cap; s0 += kLinkThreads) {
+        const int sl = s0 + tid;
+        const bool v = sl < cap && cnt[sl] > 0;
+        const unsigned m = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) s_warp[warp] = __popc(m);
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int w = 0; w < kLinkThreads / 32; ++w) {
+                const int c = s_warp[w];
+                s_warp[w] = acc;
+                acc += c;
+            }
+            s_warp[kLinkThreads / 32] = acc;
         }
-        ++c_links;
+        __syncthreads();
+        if (v) list[nvalid + s_warp[warp] + __popc(m & ((1u << lane) - 1u))] = sl;
+        else if (sl < cap) {
+            D.slot_node[base + sl] = -1;
+            D.slot_q[base + sl] = 0.f;
+        }
+        nvalid += s_warp[kLinkThreads / 32];
+        __syncthreads();
+    }
+
+    // ---- 4. bounce-back and momentum exchange, thread i on the i-th link
+    float sbx = 0.f, sby = 0.f, stq = 0.f; // link brackets of Eq. force / Eq. torque
+    int ax_x = 0, ax_y = 0, ax_t = 0, dg_x = 0, dg_y = 0, dg_t = 0; // exact constant parts
+    unsigned c_lin = 0, c_simple = 0, c_th = 0;
+    for (int li = tid; li < nvalid; li += kLinkThreads) {
+        const int sl = list[li];
+        int k, line;
+        slot_dir_line(sl, N, k, line);
+        const int kx = ex(k), ky = ey(k);
+        const int fi = X0 + (info[sl] & 0xffff), fj = Y0 + (info[sl] >> 16);
         float dxf, dyf;
         const float q = link_q_df(fi, fj, k, dk, dxf, dyf);
-        D.slot_node[base + s] = fj * D.nx + fi;
-        D.slot_q[base + s] = q;
+        D.slot_node[base + sl] = fj * D.nx + fi;
+        D.slot_q[base + sl] = q;
 
-        // ---- curved bounce-back (Sec. 2.3) in deviation form: every rule is
-        // an affine combination of populations of equal weight, so it holds
-        // for f~ = f - w unchanged.
+        // curved bounce-back in deviation form: every rule is an affine
+        // combination of populations of equal weight, so it holds for
+        // f~ = f - w unchanged
         const int kb = opp(k);
         const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
         const bool have1 = owner_at(i1, j1) == -1;
@@ -196,12 +286,11 @@ __global__ void __launch_bounds__(kLinkThreads)
             c_th += !have1;
             A[(kQ9 + kb) * D.ps + ns] = gnew;
         }
-
-        // ---- momentum exchange.  With f = w + f~ the bracket of Eq. force is
-        // 2 w_k e_k + [f~_k^+ (e_k - u_w) - f~_kbar (e_kbar - u_w)].  The constant
-        // part and its torque 2 w_k ((i - x_c) e_k,y - (j - y_c) e_k,x) (q drops
-        // out) are kept as exact integer sums, assembled in FP64 by the
-        // particle update.
+        // momentum exchange: with f = w + f~ the bracket of Eq. force is
+        // 2 w_k e_k + [f~_k^+ (e_k - u_w) - f~_kbar (e_kbar - u_w)]; the
+        // constant part and its torque 2 w_k ((i - x_c) e_k,y - (j - y_c) e_k,x)
+        // (q drops out) are kept as exact integer sums, assembled in FP64 by
+        // the particle update
         const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
         const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
         sbx += bx;
@@ -211,47 +300,49 @@ __global__ void __launch_bounds__(kLinkThreads)
         if (k <= 4) { ax_x += kx; ax_y += ky; ax_t += tz; }
         else { dg_x += kx; dg_y += ky; dg_t += tz; }
     }
+
     __shared__ float red[6][kLinkThreads / 32];
-    __shared__ int cnt[11][kLinkThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ int icnt[9][kLinkThreads / 32];
     float fxl = 0.f, fyl = 0.f, tzl = 0.f;
     warp_df_sum(sbx, fxl);
     warp_df_sum(sby, fyl);
     warp_df_sum(stq, tzl);
-    int iv[11] = {(int)c_lin, (int)c_simple, (int)c_th, (int)c_links, (int)c_over,
-                  ax_x, ax_y, ax_t, dg_x, dg_y, dg_t};
-#pragma unroll
-    for (int c = 0; c < 11; ++c) iv[c] = warp_sum(iv[c]);
+    const unsigned F = 0xffffffffu;
+    const int iv[9] = {(int)__reduce_add_sync(F, c_lin), (int)__reduce_add_sync(F, c_simple),
+                       (int)__reduce_add_sync(F, c_th), (int)__reduce_add_sync(F, (unsigned)ax_x),
+                       (int)__reduce_add_sync(F, (unsigned)ax_y), (int)__reduce_add_sync(F, (unsigned)ax_t),
+                       (int)__reduce_add_sync(F, (unsigned)dg_x), (int)__reduce_add_sync(F, (unsigned)dg_y),
+                       (int)__reduce_add_sync(F, (unsigned)dg_t)};
     if (lane == 0) {
         red[0][warp] = sbx; red[1][warp] = fxl;
         red[2][warp] = sby; red[3][warp] = fyl;
         red[4][warp] = stq; red[5][warp] = tzl;
-        for (int c = 0; c < 11; ++c) cnt[c][warp] = iv[c];
+        for (int c = 0; c < 9; ++c) icnt[c][warp] = iv[c];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         LinkSums S;
         S.fx_h = red[0][0]; S.fx_l = red[1][0];
         S.fy_h = red[2][0]; S.fy_l = red[3][0];
         S.tz_h = red[4][0]; S.tz_l = red[5][0];
-        int a[11];
-        for (int c = 0; c < 11; ++c) a[c] = cnt[c][0];
+        int a9[9];
+        for (int c = 0; c < 9; ++c) a9[c] = icnt[c][0];
         for (int w = 1; w < kLinkThreads / 32; ++w) {
             df_add(S.fx_h, S.fx_l, red[0][w], red[1][w]);
             df_add(S.fy_h, S.fy_l, red[2][w], red[3][w]);
             df_add(S.tz_h, S.tz_l, red[4][w], red[5][w]);
-            for (int c = 0; c < 11; ++c) a[c] += cnt[c][w];
+            for (int c = 0; c < 9; ++c) a9[c] += icnt[c][w];
         }
-        S.ax_x = a[5]; S.ax_y = a[6]; S.ax_t = a[7];
-        S.dg_x = a[8]; S.dg_y = a[9]; S.dg_t = a[10];
+        S.ax_x = a9[3]; S.ax_y = a9[4]; S.ax_t = a9[5];
+        S.dg_x = a9[6]; S.dg_y = a9[7]; S.dg_t = a9[8];
         S.pad[0] = S.pad[1] = S.pad[2] = S.pad[3] = 0;
         D.lsum[p] = S;
         unsigned long long *C = D.status->cnt[parity];
-        if (a[0]) atomicAdd(&C[kCntBzLinear], (unsigned long long)a[0]);
-        if (a[1]) atomicAdd(&C[kCntBzSimple], (unsigned long long)a[1]);
-        if (a[2]) atomicAdd(&C[kCntThermHalf], (unsigned long long)a[2]);
-        if (a[3]) atomicAdd(&C[kCntLinks], (unsigned long long)a[3]);
-        if (a[4]) atomicOr(&D.status->err, kErrOverflow);
+        if (a9[0]) atomicAdd(&C[kCntBzLinear], (unsigned long long)a9[0]);
+        if (a9[1]) atomicAdd(&C[kCntBzSimple], (unsigned long long)a9[1]);
+        if (a9[2]) atomicAdd(&C[kCntThermHalf], (unsigned long long)a9[2]);
+        if (nvalid) atomicAdd(&C[kCntLinks], (unsigned long long)nvalid);
+        if (s_over) atomicOr(&D.status->err, kErrOverflow);
     }
 }
 
