@@ -210,7 +210,9 @@ int64_t lbm_launch_count(lbm_handle *h);
  *                 particle whose radius exceeds r_max or one of whose index
  *                 lines holds two links.
  * Asynchronous on stream.  Returns LBM_ENOSPC when n or n * (12N(r_max) - 12)
- * exceeds the limits above, LBM_EINVAL for bad arguments.  Every call shares
+ * exceeds the limits above or when r_max > 354.5 (the per-link results of one
+ * zone, 24 bytes per slot, are held in 200 KB of shared memory), LBM_EINVAL
+ * for bad arguments.  Every call shares
  * the static array and overwrites it, so calls whose GPU work overlaps race.
  * The first call on a device looks up the array's address and should come
  * before any stream capture. */

@@ -6,12 +6,10 @@
 // g) of [ny][pitch] floats, ping-ponged between two buffers.  A plane row is
 // read once and written once per step: 112 algorithmic bytes per node.
 //
-// Each thread owns four consecutive nodes of one row and moves every plane
-// with one aligned 128-bit load and one 128-bit store.  A pull from x - 1 or
-// x + 1 takes the missing edge value from the neighbouring lane by a warp
-// shuffle (one scalar load at the warp edge), so the x-shifted planes cost no
-// extra HBM traffic.  Nodes next to a cavity wall, periodic seam or newborn
-// node take a general (scalar) path.
+// One thread per node.  A pull from x - 1 or x + 1 takes the value from the
+// neighbouring lane by a warp shuffle (one scalar load at the warp edge), so
+// the x-shifted planes cost no extra HBM traffic.  Nodes next to a cavity
+// wall, periodic seam or newborn node take a general (scalar) path.
 #include "lbm_internal.cuh"
 
 namespace lbm {

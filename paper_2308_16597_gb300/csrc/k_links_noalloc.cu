@@ -26,7 +26,7 @@ namespace {
 
 constexpr long long kStaticSlots = 1ll << 21;   // 2,097,152 slots
 constexpr int kStaticParticles = 1 << 15;       // 32,768 particles
-constexpr int kThreads = 288; // the slot-to-thread map of the workspace link kernel
+constexpr int kThreads = 256;
 constexpr int kMaxDevices = 64;
 
 // [slot nodes: int32 x kStaticSlots][wall fractions: float x kStaticSlots]
@@ -123,27 +123,12 @@ __global__ void __launch_bounds__(kThreads) k_static_gather(View v, unsigned cha
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T wsum(T x)
-{
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    return x;
-}
-
-__device__ __forceinline__ void warp_df(float &h, float &l)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_down_sync(0xffffffffu, h, o);
-        const float l2 = __shfl_down_sync(0xffffffffu, l, o);
-        df_add(h, l, h2, l2);
-    }
-}
-
 // Phase 2: bounce-back and momentum exchange on the gathered slots, with the
-// same device helpers, thread-to-link map (the i-th valid slot in slot order
-// to thread i), accumulation, reduction tree and FP64 assembly as the
-// workspace kernels.
-__global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned char *scratch)
+// same device helpers, link order (the valid slots in slot order), per-link
+// arithmetic, one-warp reduction and FP64 assembly as the workspace kernels.
+// Shared memory: the compacted slot list and the per-link results,
+// 24 bytes per slot of the largest zone.
+__global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned char *scratch, int capm)
 {
     Scratch s = carve(scratch);
     const int p = blockIdx.x;
@@ -152,7 +137,12 @@ __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned ch
         return;
     }
     __shared__ int s_warp[kThreads / 32 + 1];
-    extern __shared__ int list[]; // [cap] valid slots in slot order
+    extern __shared__ int list[]; // [capm] valid slots in slot order, then the per-link results
+    float *lbx = reinterpret_cast<float *>(list + capm);
+    float *lby = lbx + capm;
+    float *ltq = lby + capm;
+    int *lcode = reinterpret_cast<int *>(ltq + capm);
+    int *ltz = lcode + capm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double xc = v.P[p].x, yc = v.P[p].y, r = v.P[p].r;
     const DiskDF dk = disk_df(xc, yc, r);
@@ -160,8 +150,6 @@ __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned ch
     const float wT = (float)(0.2 * v.P[p].T);
     const int N = zone_size(r), cap = 12 * N - 12;
     const int base = s.base[p];
-    float sbx = 0.f, sby = 0.f, stq = 0.f;
-    int ax_x = 0, ax_y = 0, ax_t = 0, dg_x = 0, dg_y = 0, dg_t = 0;
     int broken = 0, nvalid = 0;
     float *A = v.A;
     const long long ps = v.ps;
@@ -188,85 +176,56 @@ __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned ch
         __syncthreads();
     }
     for (int li = tid; li < nvalid; li += kThreads) {
-        {
-            const int sl2 = list[li];
-            const int nd = s.node[base + sl2];
-            int k, line;
-            slot_dir_line(sl2, N, k, line);
-            const float q = s.q[base + sl2];
-            const int fi = nd % v.nx, fj = nd / v.nx;
-            const int kx = ex(k), ky = ey(k), kb = opp(k);
-            const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
-            const bool have1 = in_box(v, i1, j1) && v.own[(long long)j1 * v.nx + i1] == -1;
-            const bool have2 = in_box(v, i2, j2) && v.own[(long long)j2 * v.nx + i2] == -1;
-            const long long n0 = (long long)fj * v.pitch + fi;
-            const long long n1 = have1 ? (long long)j1 * v.pitch + i1 : n0;
-            const long long n2 = have2 ? (long long)j2 * v.pitch + i2 : n0;
-            const float fk0 = A[k * ps + n0], fk1 = A[k * ps + n1], fk2 = A[k * ps + n2];
-            const float fb0 = A[kb * ps + n0], fb1 = A[kb * ps + n1];
-            float dxh, dxl, dyh, dyl;
-            df_offset(fi, dk.xh, dk.xl, dxh, dxl);
-            df_offset(fj, dk.yh, dk.yl, dyh, dyl);
-            const float dxf = dxh + dxl, dyf = dyh + dyl;
-            const float rx = dxf + q * kx, ry = dyf + q * ky;
-            const float uwx = Ux - Om * ry, uwy = Uy + Om * rx;
-            const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy);
-            int lvl;
-            const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
-            const long long ns = (long long)(fj + ky) * v.pitch + (fi + kx);
-            A[kb * ps + ns] = fnew;
-            if (k <= 4)
-                A[(kQ9 + kb) * ps + ns] = thermal32(q, A[(kQ9 + k) * ps + n0], A[(kQ9 + k) * ps + n1],
-                                                    A[(kQ9 + kb) * ps + n0], have1, wT);
-            const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
-            const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
-            sbx += bx;
-            sby += by;
-            stq += rx * by - ry * bx;
-            const int tz = fi * ky - fj * kx;
-            if (k <= 4) { ax_x += kx; ax_y += ky; ax_t += tz; }
-            else { dg_x += kx; dg_y += ky; dg_t += tz; }
-        }
+        const int sl2 = list[li];
+        const int nd = s.node[base + sl2];
+        int k, line;
+        slot_dir_line(sl2, N, k, line);
+        const float q = s.q[base + sl2];
+        const int fi = nd % v.nx, fj = nd / v.nx;
+        const int kx = ex(k), ky = ey(k), kb = opp(k);
+        const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
+        const bool have1 = in_box(v, i1, j1) && v.own[(long long)j1 * v.nx + i1] == -1;
+        const bool have2 = in_box(v, i2, j2) && v.own[(long long)j2 * v.nx + i2] == -1;
+        const long long n0 = (long long)fj * v.pitch + fi;
+        const long long n1 = have1 ? (long long)j1 * v.pitch + i1 : n0;
+        const long long n2 = have2 ? (long long)j2 * v.pitch + i2 : n0;
+        const float fk0 = A[k * ps + n0], fk1 = A[k * ps + n1], fk2 = A[k * ps + n2];
+        const float fb0 = A[kb * ps + n0], fb1 = A[kb * ps + n1];
+        float dxh, dxl, dyh, dyl;
+        df_offset(fi, dk.xh, dk.xl, dxh, dxl);
+        df_offset(fj, dk.yh, dk.yl, dyh, dyl);
+        const float dxf = dxh + dxl, dyf = dyh + dyl;
+        const float rx = dxf + q * kx, ry = dyf + q * ky;
+        const float uwx = Ux - Om * ry, uwy = Uy + Om * rx;
+        const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy);
+        int lvl;
+        const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
+        const long long ns = (long long)(fj + ky) * v.pitch + (fi + kx);
+        A[kb * ps + ns] = fnew;
+        if (k <= 4)
+            A[(kQ9 + kb) * ps + ns] = thermal32(q, A[(kQ9 + k) * ps + n0], A[(kQ9 + k) * ps + n1],
+                                                A[(kQ9 + kb) * ps + n0], have1, wT);
+        const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
+        const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
+        lbx[li] = bx;
+        lby[li] = by;
+        ltq[li] = rx * by - ry * bx;
+        lcode[li] = k | (lvl << 4) | ((k <= 4 && !have1) ? 64 : 0);
+        ltz[li] = fi * ky - fj * kx;
     }
-    __shared__ float red[6][kThreads / 32];
-    __shared__ int cnt[6][kThreads / 32];
     broken = __syncthreads_or(broken);
-    float fxl = 0.f, fyl = 0.f, tzl = 0.f;
-    warp_df(sbx, fxl);
-    warp_df(sby, fyl);
-    warp_df(stq, tzl);
-    const unsigned F = 0xffffffffu;
-    const int iv[6] = {(int)__reduce_add_sync(F, (unsigned)ax_x), (int)__reduce_add_sync(F, (unsigned)ax_y),
-                       (int)__reduce_add_sync(F, (unsigned)ax_t), (int)__reduce_add_sync(F, (unsigned)dg_x),
-                       (int)__reduce_add_sync(F, (unsigned)dg_y), (int)__reduce_add_sync(F, (unsigned)dg_t)};
-    if (lane == 0) {
-        red[0][warp] = sbx; red[1][warp] = fxl;
-        red[2][warp] = sby; red[3][warp] = fyl;
-        red[4][warp] = stq; red[5][warp] = tzl;
-        for (int c = 0; c < 6; ++c) cnt[c][warp] = iv[c];
-    }
-    __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
         LinkSums S;
-        S.fx_h = red[0][0]; S.fx_l = red[1][0];
-        S.fy_h = red[2][0]; S.fy_l = red[3][0];
-        S.tz_h = red[4][0]; S.tz_l = red[5][0];
-        int a6[6];
-        for (int c = 0; c < 6; ++c) a6[c] = cnt[c][0];
-        for (int w = 1; w < kThreads / 32; ++w) {
-            df_add(S.fx_h, S.fx_l, red[0][w], red[1][w]);
-            df_add(S.fy_h, S.fy_l, red[2][w], red[3][w]);
-            df_add(S.tz_h, S.tz_l, red[4][w], red[5][w]);
-            for (int c = 0; c < 6; ++c) a6[c] += cnt[c][w];
+        int c3[3];
+        reduce_links(lbx, lby, ltq, lcode, ltz, nvalid, S, c3);
+        if (lane == 0) {
+            double Fx, Fy, Tz;
+            assemble_force(S, xc, yc, Fx, Fy, Tz);
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            v.F[3 * p + 0] = broken ? nan : Fx;
+            v.F[3 * p + 1] = broken ? nan : Fy;
+            v.F[3 * p + 2] = broken ? nan : Tz;
         }
-        S.ax_x = a6[0]; S.ax_y = a6[1]; S.ax_t = a6[2];
-        S.dg_x = a6[3]; S.dg_y = a6[4]; S.dg_t = a6[5];
-        double Fx, Fy, Tz;
-        assemble_force(S, xc, yc, Fx, Fy, Tz);
-        const double nan = __longlong_as_double(0x7ff8000000000000ll);
-        v.F[3 * p + 0] = broken ? nan : Fx;
-        v.F[3 * p + 1] = broken ? nan : Fy;
-        v.F[3 * p + 2] = broken ? nan : Tz;
     }
 }
 
@@ -302,6 +261,11 @@ extern "C" int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int3
     if (!d_dist || !d_owner || !d_particles || !d_forces || !(r_max >= 1.0) || r_max > 1e6)
         return LBM_EINVAL;
     if (n > kStaticParticles || (long long)n * slot_capacity(r_max) > kStaticSlots) return LBM_ENOSPC;
+    // the force kernel holds the slot list and per-link results of the
+    // largest zone in shared memory
+    const int capm = slot_capacity(r_max);
+    const size_t smem = (size_t)capm * 6 * sizeof(int);
+    if (smem > (size_t)200 * 1024) return LBM_ENOSPC;
     unsigned char *scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;
@@ -309,7 +273,11 @@ extern "C" int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int3
     View v{d_dist, (long long)plane_stride, pitch, nx, ny, n, r_max, d_owner, d_particles, d_forces};
     k_static_bases<<<1, 32, 0, s>>>(v, scratch);
     k_static_gather<<<n, kThreads, 0, s>>>(v, scratch);
-    k_static_bbforce<<<n, kThreads, (size_t)slot_capacity(r_max) * sizeof(int), s>>>(v, scratch);
+    if (smem > (size_t)48 * 1024 &&
+        cudaFuncSetAttribute(k_static_bbforce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return LBM_ECUDA;
+    k_static_bbforce<<<n, kThreads, smem, s>>>(v, scratch, capm);
     if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
     return LBM_OK;
 }

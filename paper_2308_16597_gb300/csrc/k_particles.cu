@@ -8,13 +8,17 @@
 //                repulsion (Sec. 2.2, Sec. 2.4);
 //   k_clear, k_raster, k_flags
 //                owner map and node flags at the new positions.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
 namespace {
 
-constexpr int kLinkThreads = 288;
+constexpr int kLinkThreads = 256;
 constexpr int kBoxThreads = 128;
 constexpr int kPartThreads = 1024;
 constexpr double kPi = 3.14159265358979323846;
@@ -34,20 +38,6 @@ __device__ __forceinline__ T warp_sum(T v)
 
 } // namespace
 
-// One CTA per particle; thread s handles slot s (and s + 128, ...) of the
-// particle's 12N - 12 fixed slots.  The slot of (direction k, line) is fixed
-// by the zone geometry, so the gather needs no atomics and the per-particle
-// reduction is a deterministic tree.
-//
-// The CTA first copies its zone (plus the two-node margin the bounce-back
-// stencil reaches) into shared memory: the owner map and the 12 planes the
-// rules read (f1..f8 and g1..g4), in whole 16-byte chunks with cp.async, so
-// the scattered reads of the links become one coalesced burst per particle.
-// It also issues bulk L2 prefetches of the zone rows of the particle `ahead`
-// places later, so that particle's copies hit L2.  Bounce-back values are
-// written into the solid node x_f + e_k in direction kbar of A in HBM, where
-// the next pull stream picks them up: each (solid node, kbar) belongs to one
-// link, and every read is of a fluid node, so the writes never race the reads.
 constexpr int kTilePlanes = 12;
 
 // Double-float warp sum (lane 0 receives the result).
@@ -67,42 +57,78 @@ __host__ __device__ inline int pow2_at_least(int v)
     while (p < v) p <<= 1;
     return p;
 }
-// Link-kernel shared memory for zones of side N: the 12-plane tile
-// [wy][wx] (wy = N + 4 rows, wx a power of two >= N + 7 columns, 16-byte
-// aligned start), the owner window [N + 4][ws] (ws a power of two >= N + 4),
-// and per-slot counters, link nodes and the compacted list of valid slots.
+
+// Link-kernel tile geometry for zones of side N: the tile covers the zone
+// plus the two-node margin of the bounce-back stencil, wy = N + 4 rows of
+// wx columns starting at a multiple of four (16-byte aligned for the tensor
+// copy), wx a power of two >= N + 7 (at most 64: the fluid and owner masks of
+// a row are 64-bit words).  Each of the 12 planes takes tps floats, a
+// multiple of 32 so that every plane starts on a 128-byte boundary.
 __host__ __device__ inline int link_tile_wy(int N) { return N + 4; }
 __host__ __device__ inline int link_tile_wx(int N) { return pow2_at_least(N + 7); }
-__host__ __device__ inline int link_win_ws(int N) { return pow2_at_least(N + 4); }
+__host__ __device__ inline int link_tile_tps(int N)
+{
+    return (link_tile_wy(N) * link_tile_wx(N) + 31) & ~31;
+}
+__host__ __device__ inline int link_occ_words(int N) { return (12 * N - 12 + 31) / 32; }
+
+// Shared memory: 128 bytes of alignment slack, the tile, the fluid and owner
+// row masks [wy] (u64 each), slot occupancy words and their prefix [words],
+// and per slot / per link: the link node, the compacted slot list, three
+// FP32 brackets and two integer words.
 size_t link_smem_bytes(int N)
 {
-    const int wy = link_tile_wy(N), wx = link_tile_wx(N), ws = link_win_ws(N), cap = 12 * N - 12;
-    return (size_t)kTilePlanes * wy * wx * sizeof(float) + (size_t)(N + 4) * ws * sizeof(int) +
-           (size_t)3 * cap * sizeof(int);
+    const size_t cap = (size_t)12 * N - 12;
+    return 128 + (size_t)kTilePlanes * link_tile_tps(N) * sizeof(float) +
+           (size_t)2 * link_tile_wy(N) * sizeof(unsigned long long) +
+           (size_t)2 * link_occ_words(N) * sizeof(unsigned) + cap * 7 * sizeof(int);
 }
+
+bool link_zone_supported(int N) { return link_tile_wx(N) <= 64 && link_smem_bytes(N) <= (size_t)200 * 1024; }
 
 // Global plane of tile plane t: f1..f8 then g1..g4.
 __device__ __forceinline__ int tile_global_plane(int t) { return t < 8 ? t + 1 : t + 2; }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+// ---- tensor-copy and mbarrier primitives (one CTA, no cluster)
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-
-__device__ __forceinline__ void prefetch_zone(const Dev &D, const float *A, const GeomRec &G)
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
 {
-    const int N = G.N, wy = link_tile_wy(N), wx = link_tile_wx(N);
-    const int XA = (G.X0 - 2) & ~3, YA = G.Y0 - 2;
-    const int lo = max(XA, 0), hi = min(XA + wx, D.pitch);
-    if (hi <= lo) return;
-    for (int idx = threadIdx.x; idx < kTilePlanes * wy; idx += kLinkThreads) {
-        const int t = idx / wy, row = YA + idx % wy;
-        if (row < 0 || row >= D.ny) continue;
-        const float *sp = A + (long long)tile_global_plane(t) * D.ps + (long long)row * D.pitch + lo;
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sp), "r"((unsigned)(hi - lo) * 4u)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for phase `parity` of the barrier: false after ~2^31 cycles.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred P;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, P;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
                      : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
     }
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *tm, int x, int y, int z,
+                                            unsigned bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+                 "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *tm, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<unsigned long long>(tm)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
 }
 
 // Fixed slot (Sec. 3) of the link from zone node (a, b) along e_k, or -1 for
@@ -124,131 +150,162 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 }
 
 // One CTA per particle.  Phases:
-//  1. copy the zone (plus the two-node margin of the bounce-back stencil)
-//     into shared memory: the 12 planes the rules read (f1..f8, g1..g4) with
-//     16-byte cp.async, and the owner map; also issue bulk L2 prefetches of
-//     the zone rows of the particle `ahead` places later in launch order;
-//  2. every zone node that is fluid tests its eight neighbours; a neighbour
-//     owned by this particle makes a link, recorded in the link's fixed slot
-//     of the index array (direction k, line through the zone; Sec. 3);
-//  3. the valid slots are compacted in slot order (a block-wide prefix), so
+//  1. thread 0 issues tensor copies of the particle's tile (zone plus the
+//     two-node margin of the bounce-back stencil) of the 12 planes the rules
+//     read (f1..f8, g1..g4) into shared memory, completing on an mbarrier,
+//     and tensor prefetches into L2 of the tile of the particle `ahead`
+//     places later in launch order; meanwhile the warps read the owner map
+//     over the tile and record per row a fluid mask and an owned-by-this-
+//     particle mask (one ballot per 32 nodes);
+//  2. thread (b, k) intersects the fluid mask of zone row b with the owner
+//     mask of row b + e_k,y shifted by e_k,x: each set bit is a link, which
+//     claims its fixed slot of the index array (direction k, line through
+//     the zone; Sec. 3) in an occupancy bitmap;
+//  3. the occupied slots are compacted in slot order (popcount prefix), so
 //     thread i takes the i-th link: the work is balanced and the reduction
 //     order is fixed, hence the forces are bit-reproducible;
 //  4. each link: wall fraction q, curved bounce-back of f and g (Sec. 2.3)
 //     written into the solid node x_f + e_k (direction kbar) of A in HBM,
 //     where the next pull stream picks it up (one link per (solid node, kbar),
-//     and every read is of a fluid node), and the momentum-exchange bracket
-//     of Eq. force / Eq. torque, reduced per particle.
+//     and every read is of a fluid node, so the writes never race the reads),
+//     and the momentum-exchange bracket of Eq. force / Eq. torque, stored per
+//     link and summed by one warp in link order.
 __global__ void __launch_bounds__(kLinkThreads)
-    k_links(const Dev D, float *A, const int *__restrict__ own, int parity, int ahead)
+    k_links(const __grid_constant__ CUtensorMap tmA, const Dev D, float *A, const int *__restrict__ own,
+            int parity, int ahead)
 {
-    extern __shared__ __align__(16) float ltile[];
-    __shared__ int s_warp[kLinkThreads / 32 + 1];
-    __shared__ unsigned s_over;
+    extern __shared__ __align__(128) unsigned char lsm[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ int s_nvalid;
+    __shared__ unsigned s_over, s_fail;
     const int p = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const GeomRec G = D.geo_cur[p];
-    const DiskDF dk = geom_df(G);
-    const float Ux = G.ux, Uy = G.uy, Om = G.om, wT = G.wT;
     const int N = G.N, cap = 12 * N - 12;
     const int X0 = G.X0, Y0 = G.Y0;
     const int base = D.slot_base[p];
-    if (tid == 0) {
-        D.pos4[p] = make_float4(dk.xh, dk.yh, dk.xl, dk.yl);
-        D.prc[p] = make_float2(G.r, G.C);
-        s_over = 0u;
-    }
-    if (p + ahead < D.np) prefetch_zone(D, A, D.geo_cur[p + ahead]);
 
     const int Nm = D.zone_max;
-    const int wy = link_tile_wy(Nm), wx = link_tile_wx(Nm), ws = link_win_ws(Nm);
-    const int XA = (X0 - 2) & ~3, YA = Y0 - 2;
-    int *win = reinterpret_cast<int *>(ltile + kTilePlanes * wy * wx); // [N + 4][ws]
-    int *cnt = win + (Nm + 4) * ws;                                    // [cap] links per slot
-    int *info = cnt + 12 * Nm - 12;                                    // [cap] (b << 16) | a
-    int *list = info + 12 * Nm - 12;                                   // [cap] valid slots in order
+    const int wy = link_tile_wy(Nm), wx = link_tile_wx(Nm), tps = link_tile_tps(Nm);
+    const int XA = (X0 - 2) & ~3, YA = Y0 - 2, off = X0 - XA;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(lsm);
+    const unsigned pad = (128u - (sbase & 127u)) & 127u;
+    float *tile = reinterpret_cast<float *>(lsm + pad);
+    unsigned long long *Fm = reinterpret_cast<unsigned long long *>(tile + kTilePlanes * tps); // [wy]
+    unsigned long long *Om = Fm + wy;                                                       // [wy]
+    const int nw = link_occ_words(Nm), capm = 12 * Nm - 12;
+    unsigned *occ = reinterpret_cast<unsigned *>(Om + wy); // [nw]
+    unsigned *pre = occ + nw;                               // [nw]
+    int *info = reinterpret_cast<int *>(pre + nw);          // [cap] (b << 16) | a of the slot's link
+    int *list = info + capm;                                // [cap] valid slots in order
+    float *lbx = reinterpret_cast<float *>(list + capm);    // [cap] per-link brackets
+    float *lby = lbx + capm;
+    float *ltq = lby + capm;
+    int *lcode = reinterpret_cast<int *>(ltq + capm);
+    int *ltz = lcode + capm;
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar);
 
-    // ---- 1. tile and owner window
-    {
-        const int cpr = wx >> 2, lcpr = __ffs(cpr) - 1, per_plane = wy * cpr;
-        for (int t = 0; t < kTilePlanes; ++t) {
-            const float *src = A + (long long)tile_global_plane(t) * D.ps;
-            for (int e = tid; e < per_plane; e += kLinkThreads) {
-                const int row = e >> lcpr, c = e & (cpr - 1);
-                const int gy = YA + row, gx = XA + 4 * c;
-                if (gy < 0 || gy >= D.ny || gx < 0 || gx + 4 > D.pitch) continue;
-                cp_async16(ltile + (t * wy + row) * wx + 4 * c, src + (long long)gy * D.pitch + gx);
-            }
+    // ---- 1. tensor copies (thread 0) and owner masks (all warps)
+    if (tid == 0) {
+        s_over = 0u;
+        s_fail = 0u;
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, (unsigned)(kTilePlanes * wy * wx * sizeof(float)));
+        const unsigned dst = sbase + pad;
+        for (int t = 0; t < kTilePlanes; ++t)
+            tma_load_3d(dst + (unsigned)(t * tps * sizeof(float)), &tmA, XA, YA, tile_global_plane(t), bar);
+        if (p + ahead < D.np) {
+            const GeomRec Ga = D.geo_cur[p + ahead];
+            for (int t = 0; t < kTilePlanes; ++t)
+                tma_prefetch_3d(&tmA, (Ga.X0 - 2) & ~3, Ga.Y0 - 2, tile_global_plane(t));
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        const int lws = __ffs(ws) - 1;
-        for (int e = tid; e < (N + 4) * ws; e += kLinkThreads) {
-            const int row = e >> lws, col = e & (ws - 1);
-            if (col >= N + 4) continue;
-            const int i = X0 - 2 + col, j = Y0 - 2 + row;
-            win[e] = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
-        }
-        for (int e = tid; e < cap; e += kLinkThreads) cnt[e] = 0;
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
+        const DiskDF d0 = geom_df(G);
+        D.pos4[p] = make_float4(d0.xh, d0.yh, d0.xl, d0.yl);
+        D.prc[p] = make_float2(G.r, G.C);
     }
-    auto owner_at = [&](int i, int j) -> int { return win[(j - Y0 + 2) * ws + (i - X0 + 2)]; };
-    auto tv = [&](int t, int i, int j) -> float { return ltile[(t * wy + (j - YA)) * wx + (i - XA)]; };
+    for (int r = warp; r < wy; r += kLinkThreads / 32) {
+        const int j = YA + r;
+        unsigned lo_f = 0u, lo_o = 0u, hi_f = 0u, hi_o = 0u;
+        {
+            const int i = XA + lane;
+            const int v = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
+            lo_f = __ballot_sync(0xffffffffu, v == -1);
+            lo_o = __ballot_sync(0xffffffffu, v == p);
+        }
+        if (wx > 32) {
+            const int i = XA + 32 + lane;
+            const int v = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
+            hi_f = __ballot_sync(0xffffffffu, v == -1);
+            hi_o = __ballot_sync(0xffffffffu, v == p);
+        }
+        if (lane == 0) {
+            Fm[r] = ((unsigned long long)hi_f << 32) | lo_f;
+            Om[r] = ((unsigned long long)hi_o << 32) | lo_o;
+        }
+    }
+    for (int w = tid; w < nw; w += kLinkThreads) occ[w] = 0u;
+    __syncthreads();
 
-    // ---- 2. link detection, one zone node per thread
+    // ---- 2. link detection: thread (b, k), one mask intersection per row
     {
-        const int lws = __ffs(ws) - 1;
-        for (int e = tid; e < N * ws; e += kLinkThreads) {
-            const int bb = e >> lws, aa = e & (ws - 1);
-            if (aa >= N) continue;
-            const int w0 = (bb + 2) * ws + (aa + 2);
-            if (win[w0] != -1) continue;
-#pragma unroll
-            for (int k = 1; k < kQ9; ++k) {
-                if (win[w0 + ey(k) * ws + ex(k)] != p) continue;
-                const int sl = slot_of(k, aa, bb, N);
+        const unsigned long long Z = ((1ull << N) - 1ull) << off;
+        for (int e = tid; e < 8 * N; e += kLinkThreads) {
+            const int b = e >> 3, k = (e & 7) + 1, kx = ex(k), ky = ey(k);
+            const unsigned long long o = Om[b + 2 + ky];
+            unsigned long long m = Fm[b + 2] & (kx > 0 ? o >> 1 : kx < 0 ? o << 1 : o) & Z;
+            while (m) {
+                const int c = __ffsll((long long)m) - 1;
+                m &= m - 1ull;
+                const int a = c - off;
+                const int sl = slot_of(k, a, b, N);
                 if (sl < 0) {
                     s_over = 1u;
                     continue;
                 }
-                if (atomicAdd(&cnt[sl], 1) == 0) info[sl] = (bb << 16) | aa;
-                else s_over = 1u;
+                const unsigned bit = 1u << (sl & 31);
+                if (atomicOr(&occ[sl >> 5], bit) & bit) s_over = 1u;
+                else info[sl] = (b << 16) | a;
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
 
-    // ---- 3. compaction of the valid slots in slot order
-    int nvalid = 0;
-    for (int s0 = 0; s0 < cap; s0 += kLinkThreads) {
-        const int sl = s0 + tid;
-        const bool v = sl < cap && cnt[sl] > 0;
-        const unsigned m = __ballot_sync(0xffffffffu, v);
-        if (lane == 0) s_warp[warp] = __popc(m);
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int w = 0; w < kLinkThreads / 32; ++w) {
-                const int c = s_warp[w];
-                s_warp[w] = acc;
-                acc += c;
-            }
-            s_warp[kLinkThreads / 32] = acc;
+    // ---- 3. compaction of the occupied slots in slot order
+    const int nwp = (cap + 31) >> 5;
+    if (warp == 0) {
+        const unsigned c = lane < nwp ? (unsigned)__popc(occ[lane]) : 0u;
+        unsigned inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
         }
-        __syncthreads();
-        if (v) list[nvalid + s_warp[warp] + __popc(m & ((1u << lane) - 1u))] = sl;
-        else if (sl < cap) {
+        if (lane < nwp) pre[lane] = inc - c;
+        if (lane == 31) s_nvalid = (int)inc;
+    }
+    __syncthreads();
+    const int nvalid = s_nvalid;
+    for (int sl = tid; sl < cap; sl += kLinkThreads) {
+        const unsigned w = occ[sl >> 5], bit = 1u << (sl & 31);
+        if (w & bit) list[pre[sl >> 5] + __popc(w & (bit - 1u))] = sl;
+        else {
             D.slot_node[base + sl] = -1;
             D.slot_q[base + sl] = 0.f;
         }
-        nvalid += s_warp[kLinkThreads / 32];
-        __syncthreads();
     }
+    if (tid == 0 && !mbar_wait(bar, 0)) {
+        s_fail = 1u;
+        atomicOr(&D.status->err, kErrTimeout);
+        mbar_wait(bar, 0); // copies still in flight write this CTA's shared memory
+    }
+    __syncthreads();
+    if (s_fail) return;
 
     // ---- 4. bounce-back and momentum exchange, thread i on the i-th link
-    float sbx = 0.f, sby = 0.f, stq = 0.f; // link brackets of Eq. force / Eq. torque
-    int ax_x = 0, ax_y = 0, ax_t = 0, dg_x = 0, dg_y = 0, dg_t = 0; // exact constant parts
-    unsigned c_lin = 0, c_simple = 0, c_th = 0;
+    const DiskDF dk = geom_df(G);
+    const float Ux = G.ux, Uy = G.uy, Om_ = G.om, wT = G.wT;
+    auto tv = [&](int t, int i, int j) -> float { return tile[t * tps + (j - YA) * wx + (i - XA)]; };
+    auto fluid = [&](int i, int j) -> bool { return (Fm[j - YA] >> (i - XA)) & 1ull; };
     for (int li = tid; li < nvalid; li += kLinkThreads) {
         const int sl = list[li];
         int k, line;
@@ -265,25 +322,22 @@ __global__ void __launch_bounds__(kLinkThreads)
         // f~ = f - w unchanged
         const int kb = opp(k);
         const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
-        const bool have1 = owner_at(i1, j1) == -1;
-        const bool have2 = owner_at(i2, j2) == -1;
+        const bool have1 = fluid(i1, j1);
+        const bool have2 = fluid(i2, j2);
         const int ii1 = have1 ? i1 : fi, jj1 = have1 ? j1 : fj;
         const int ii2 = have2 ? i2 : fi, jj2 = have2 ? j2 : fj;
         const float fk0 = tv(k - 1, fi, fj), fk1 = tv(k - 1, ii1, jj1), fk2 = tv(k - 1, ii2, jj2);
         const float fb0 = tv(kb - 1, fi, fj), fb1 = tv(kb - 1, ii1, jj1);
         const float rx = dxf + q * kx, ry = dyf + q * ky;
-        const float uwx = Ux - Om * ry, uwy = Uy + Om * rx;
+        const float uwx = Ux - Om_ * ry, uwy = Uy + Om_ * rx;
         const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy); // 2 w rho0 e_kbar.u_w / c_s^2
         int lvl;
         const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
-        c_lin += lvl == 1;
-        c_simple += lvl == 2;
         const long long ns = (long long)(fj + ky) * D.pitch + (fi + kx);
         A[kb * D.ps + ns] = fnew;
         if (k <= 4) {
             const float gnew = thermal32(q, tv(8 + k - 1, fi, fj), tv(8 + k - 1, ii1, jj1),
                                          tv(8 + kb - 1, fi, fj), have1, wT);
-            c_th += !have1;
             A[(kQ9 + kb) * D.ps + ns] = gnew;
         }
         // momentum exchange: with f = w + f~ the bracket of Eq. force is
@@ -293,56 +347,26 @@ __global__ void __launch_bounds__(kLinkThreads)
         // the particle update
         const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
         const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
-        sbx += bx;
-        sby += by;
-        stq += rx * by - ry * bx;
-        const int tz = fi * ky - fj * kx;
-        if (k <= 4) { ax_x += kx; ax_y += ky; ax_t += tz; }
-        else { dg_x += kx; dg_y += ky; dg_t += tz; }
-    }
-
-    __shared__ float red[6][kLinkThreads / 32];
-    __shared__ int icnt[9][kLinkThreads / 32];
-    float fxl = 0.f, fyl = 0.f, tzl = 0.f;
-    warp_df_sum(sbx, fxl);
-    warp_df_sum(sby, fyl);
-    warp_df_sum(stq, tzl);
-    const unsigned F = 0xffffffffu;
-    const int iv[9] = {(int)__reduce_add_sync(F, c_lin), (int)__reduce_add_sync(F, c_simple),
-                       (int)__reduce_add_sync(F, c_th), (int)__reduce_add_sync(F, (unsigned)ax_x),
-                       (int)__reduce_add_sync(F, (unsigned)ax_y), (int)__reduce_add_sync(F, (unsigned)ax_t),
-                       (int)__reduce_add_sync(F, (unsigned)dg_x), (int)__reduce_add_sync(F, (unsigned)dg_y),
-                       (int)__reduce_add_sync(F, (unsigned)dg_t)};
-    if (lane == 0) {
-        red[0][warp] = sbx; red[1][warp] = fxl;
-        red[2][warp] = sby; red[3][warp] = fyl;
-        red[4][warp] = stq; red[5][warp] = tzl;
-        for (int c = 0; c < 9; ++c) icnt[c][warp] = iv[c];
+        lbx[li] = bx;
+        lby[li] = by;
+        ltq[li] = rx * by - ry * bx;
+        lcode[li] = k | (lvl << 4) | ((k <= 4 && !have1) ? 64 : 0);
+        ltz[li] = fi * ky - fj * kx;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
         LinkSums S;
-        S.fx_h = red[0][0]; S.fx_l = red[1][0];
-        S.fy_h = red[2][0]; S.fy_l = red[3][0];
-        S.tz_h = red[4][0]; S.tz_l = red[5][0];
-        int a9[9];
-        for (int c = 0; c < 9; ++c) a9[c] = icnt[c][0];
-        for (int w = 1; w < kLinkThreads / 32; ++w) {
-            df_add(S.fx_h, S.fx_l, red[0][w], red[1][w]);
-            df_add(S.fy_h, S.fy_l, red[2][w], red[3][w]);
-            df_add(S.tz_h, S.tz_l, red[4][w], red[5][w]);
-            for (int c = 0; c < 9; ++c) a9[c] += icnt[c][w];
+        int c3[3];
+        reduce_links(lbx, lby, ltq, lcode, ltz, nvalid, S, c3);
+        if (lane == 0) {
+            D.lsum[p] = S;
+            unsigned long long *C = D.status->cnt[parity];
+            if (c3[0]) atomicAdd(&C[kCntBzLinear], (unsigned long long)c3[0]);
+            if (c3[1]) atomicAdd(&C[kCntBzSimple], (unsigned long long)c3[1]);
+            if (c3[2]) atomicAdd(&C[kCntThermHalf], (unsigned long long)c3[2]);
+            if (nvalid) atomicAdd(&C[kCntLinks], (unsigned long long)nvalid);
+            if (s_over) atomicOr(&D.status->err, kErrOverflow);
         }
-        S.ax_x = a9[3]; S.ax_y = a9[4]; S.ax_t = a9[5];
-        S.dg_x = a9[6]; S.dg_y = a9[7]; S.dg_t = a9[8];
-        S.pad[0] = S.pad[1] = S.pad[2] = S.pad[3] = 0;
-        D.lsum[p] = S;
-        unsigned long long *C = D.status->cnt[parity];
-        if (a9[0]) atomicAdd(&C[kCntBzLinear], (unsigned long long)a9[0]);
-        if (a9[1]) atomicAdd(&C[kCntBzSimple], (unsigned long long)a9[1]);
-        if (a9[2]) atomicAdd(&C[kCntThermHalf], (unsigned long long)a9[2]);
-        if (nvalid) atomicAdd(&C[kCntLinks], (unsigned long long)nvalid);
-        if (s_over) atomicOr(&D.status->err, kErrOverflow);
     }
 }
 
@@ -606,11 +630,45 @@ cudaError_t prepare_links(Dev &D)
     return cudaSuccess;
 }
 
-cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity, cudaStream_t s)
+cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity, const CUtensorMap &tmA,
+                         cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
-    k_links<<<D.np, kLinkThreads, link_smem_bytes(D.zone_max), s>>>(D, A, own_cur, parity, D.link_ahead);
+    k_links<<<D.np, kLinkThreads, link_smem_bytes(D.zone_max), s>>>(tmA, D, A, own_cur, parity, D.link_ahead);
     return cudaGetLastError();
+}
+
+// 3-D tensor map over one distribution buffer: x (pitch columns), y (ny
+// rows), plane (kPop planes), FP32, box wx x wy x 1 of the link tile.  Reads
+// outside the box's range return zeros.
+cudaError_t make_plane_map(const Dev &D, const float *A, CUtensorMap *m)
+{
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!encode) {
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                             cudaEnableDefault, &q);
+            if (e != cudaSuccess) return e;
+            if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+    }
+    const int N = D.zone_max > 0 ? D.zone_max : 4;
+    const cuuint64_t dims[3] = {(cuuint64_t)D.pitch, (cuuint64_t)D.ny, (cuuint64_t)kPop};
+    const cuuint64_t strides[2] = {(cuuint64_t)D.pitch * sizeof(float), (cuuint64_t)D.ps * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)link_tile_wx(N), (cuuint32_t)link_tile_wy(N), 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (box[0] > 256 || box[1] > 256 || (box[0] * sizeof(float)) % 16 != 0 || strides[0] % 16 != 0 ||
+        strides[1] % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
+        return cudaErrorInvalidValue;
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(A), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s)

@@ -57,7 +57,7 @@ int validate(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_pa
             if (!finite(x)) return LBM_EINVAL;
         if (P.r < 1.0 || P.rho <= 0.0) return LBM_EINVAL;
         // the link kernel holds a particle's zone in shared memory
-        if (link_smem_bytes(zone_size(P.r)) > (size_t)200 * 1024) return LBM_EINVAL;
+        if (!link_zone_supported(zone_size(P.r))) return LBM_EINVAL;
         // a disk stays inside the cavity; next to a periodic seam it keeps two
         // nodes of clearance so that no link or stencil wraps around
         const double mx = px ? 2.0 : -0.5, my = py ? 2.0 : -0.5;
@@ -147,6 +147,7 @@ struct lbm_handle {
     int *own[2];
     int parity = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    CUtensorMap tmA[2]; // link-tile tensor maps over A[0] and A[1]
     bool timing = false;
     struct Ev {
         cudaEvent_t a, b;
@@ -226,7 +227,7 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
     int *oc = h->own[par], *on = h->own[par ^ 1];
     int rc;
     if (h->np > 0) {
-        if ((rc = timed(h, kKLinks, st, [&] { return launch_links(D, Ain, oc, par, st); }))) return rc;
+        if ((rc = timed(h, kKLinks, st, [&] { return launch_links(D, Ain, oc, par, h->tmA[par], st); }))) return rc;
     }
     if ((rc = timed(h, kKParticles, st, [&] { return launch_particles(D, par, st); }))) return rc;
     if (h->np > 0) {
@@ -433,6 +434,8 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
     };
     if (cudaMemsetAsync(h->D.status, 0, sizeof(Status), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
     if (prepare_links(h->D) != cudaSuccess) return fail(LBM_ECUDA);
+    for (int b = 0; b < 2 && n > 0; ++b)
+        if (make_plane_map(h->D, h->A[b], &h->tmA[b]) != cudaSuccess) return fail(LBM_ECUDA);
     if (n > 0) {
         std::vector<int> base(n + 1, 0);
         for (int a = 0; a < n; ++a) base[a + 1] = base[a] + slot_capacity(p[a].r);

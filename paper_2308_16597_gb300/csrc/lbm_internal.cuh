@@ -3,6 +3,7 @@
 // helpers and the kernel launchers.  Not part of the public ABI (lbm.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -265,6 +266,54 @@ struct LinkSums {
     int ax_x, ax_y, ax_t, dg_x, dg_y, dg_t;
     int pad[4];
 };
+// Reduction of per-link results by one warp, in link order (lane l takes links
+// l, l + 32, ...), the same in every kernel that sums links so that their
+// results agree bit for bit.  bx, by, tq: the variable part of Eq. force /
+// Eq. torque of each link; code: k | fallback level << 4 | thermal half-way
+// << 6; tz: the torque moment i e_k,y - j e_k,x of the constant part.
+// Returns the sums in S (lane 0) and the fallback counts in cnt3 (lane 0).
+__device__ __forceinline__ void reduce_links(const float *bx, const float *by, const float *tq,
+                                             const int *code, const int *tz, int n, LinkSums &S,
+                                             int *cnt3)
+{
+    const int lane = threadIdx.x & 31;
+    float fxh = 0.f, fxl = 0.f, fyh = 0.f, fyl = 0.f, tqh = 0.f, tql = 0.f;
+    int axx = 0, axy = 0, axt = 0, dgx = 0, dgy = 0, dgt = 0, cl = 0, cs = 0, ct = 0;
+    for (int i = lane; i < n; i += 32) {
+        df_add(fxh, fxl, bx[i], 0.f);
+        df_add(fyh, fyl, by[i], 0.f);
+        df_add(tqh, tql, tq[i], 0.f);
+        const int c = code[i], k = c & 15, lvl = (c >> 4) & 3;
+        cl += lvl == 1;
+        cs += lvl == 2;
+        ct += (c >> 6) & 1;
+        if (k <= 4) { axx += ex(k); axy += ey(k); axt += tz[i]; }
+        else { dgx += ex(k); dgy += ey(k); dgt += tz[i]; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned F = 0xffffffffu;
+        float h2 = __shfl_down_sync(F, fxh, o), l2 = __shfl_down_sync(F, fxl, o);
+        df_add(fxh, fxl, h2, l2);
+        h2 = __shfl_down_sync(F, fyh, o); l2 = __shfl_down_sync(F, fyl, o);
+        df_add(fyh, fyl, h2, l2);
+        h2 = __shfl_down_sync(F, tqh, o); l2 = __shfl_down_sync(F, tql, o);
+        df_add(tqh, tql, h2, l2);
+    }
+    const unsigned F = 0xffffffffu;
+    S.fx_h = fxh; S.fx_l = fxl; S.fy_h = fyh; S.fy_l = fyl; S.tz_h = tqh; S.tz_l = tql;
+    S.ax_x = (int)__reduce_add_sync(F, (unsigned)axx);
+    S.ax_y = (int)__reduce_add_sync(F, (unsigned)axy);
+    S.ax_t = (int)__reduce_add_sync(F, (unsigned)axt);
+    S.dg_x = (int)__reduce_add_sync(F, (unsigned)dgx);
+    S.dg_y = (int)__reduce_add_sync(F, (unsigned)dgy);
+    S.dg_t = (int)__reduce_add_sync(F, (unsigned)dgt);
+    S.pad[0] = S.pad[1] = S.pad[2] = S.pad[3] = 0;
+    cnt3[0] = (int)__reduce_add_sync(F, (unsigned)cl);
+    cnt3[1] = (int)__reduce_add_sync(F, (unsigned)cs);
+    cnt3[2] = (int)__reduce_add_sync(F, (unsigned)ct);
+}
+
 // Hydrodynamic force (Fx, Fy) and torque of a particle centred at (xc, yc).
 __device__ __forceinline__ void assemble_force(const LinkSums &S, double xc, double yc, double &Fx,
                                                double &Fy, double &Tz)
@@ -394,10 +443,17 @@ cudaError_t launch_init_collide(const Dev &D, const float *Ain, float *Aout, flo
                                 cudaStream_t s);
 cudaError_t launch_fields(const Dev &D, const float *A, int row0, int rows, float *rho, float *ux,
                           float *uy, float *T, cudaStream_t s);
-cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity, cudaStream_t s);
+cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity,
+                         const CUtensorMap &tmA, cudaStream_t s);
+// 3-D tensor map (x, y, plane) over one distribution buffer, for the link
+// kernel's TMA tile loads.
+cudaError_t make_plane_map(const Dev &D, const float *A, CUtensorMap *m);
 // Shared memory of the link kernel for zones of side N; prepare_links sets the
 // kernel's shared-memory limit and D.link_ahead (call outside stream capture).
 size_t link_smem_bytes(int N);
+// Whether the link kernel holds a zone of side N (tile rows of at most 64
+// columns, shared memory within 200 KB).
+bool link_zone_supported(int N);
 cudaError_t prepare_links(Dev &D);
 cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s);
 cudaError_t launch_clear(const Dev &D, int *own_nxt, cudaStream_t s);
