@@ -34,6 +34,9 @@ sys.path.insert(0, ROOT)
 from paper_2308_16597_gb300 import metrics, workloads as W  # noqa: E402
 
 METRIC = "MLUPS"
+# plane storage: lbm_params.storage code and bytes per stored population
+STORAGE_CODES = {"fp32": 0, "bf16": 1, "fp16": 2}
+STORAGE_BYTES = {"fp32": 4, "bf16": 2, "fp16": 2}
 UNIT = "MLUPS"
 CROP = 1000
 
@@ -213,7 +216,8 @@ def run_reference(args, wl):
 def config_of(wl, args):
     p = wl.particles
     return {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "particles": int(len(p)),
-            "radius": float(p["r"][0]) if len(p) else None, "storage": "fp32",
+            "radius": float(p["r"][0]) if len(p) else None,
+            "storage": getattr(args, "storage", "fp32"),
             "density_ratio": float(p["rho"][0]) if len(p) else None,
             "parallelism": "replicas%d" % args.gpus,
             "l2": "no flush: the 1.8 GB distribution state is 14x the 129 MB L2"}
@@ -234,7 +238,8 @@ def run_ours(args, wl):
     stream = torch.cuda.Stream(device=dev)
     nodes = wl.nx * wl.ny
     with torch.cuda.stream(stream):
-        sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream)
+        storage = STORAGE_CODES[args.storage]
+        sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream, storage=storage)
         sim.kernel_timing(True)
         sim.step(args.warmup)
         sim.sync()
@@ -272,7 +277,7 @@ def run_ours(args, wl):
         pview = pinned_p.numpy().view(lbm.PARTICLE_DTYPE)
         fields = [torch.empty((wl.ny, wl.nx), dtype=torch.float32, pin_memory=True)
                   for _ in range(4)]
-        params = lbm.make_params(**wl.params)
+        params = lbm.make_params(**dict(wl.params, storage=storage))
         dom = lbm.make_domain(**wl.domain)
         parts = lbm.pack_particles(wl.particles)
         ws_bytes = lbm.lbm_query_footprint(dom, parts, params)
@@ -305,10 +310,11 @@ def run_ours(args, wl):
 
     k_ms, k_n = ktimes["stream_collide"]
     avg_s = k_ms / 1e3 / max(k_n, 1)
-    B_LU = metrics.bytes_per_update(4)
+    B_LU = metrics.bytes_per_update(STORAGE_BYTES[args.storage])
     peaks = measured_peaks()
     achieved = B_LU * nodes / avg_s / 1e9
-    traffic = profiled_traffic("stream_collide")
+    traffic = profiled_traffic("stream_collide" if args.storage == "fp32"
+                               else "stream_collide_" + args.storage)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": "k_stream_collide", "algorithmic_bytes_per_launch": B_LU * nodes,
@@ -342,6 +348,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--storage", choices=sorted(STORAGE_CODES), default="fp32",
+                    help="plane storage: FP32 (the headline), or BF16 / scaled FP16 deviations")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -3,8 +3,9 @@
 // refilling of newborn nodes (Sec. 2.5) folded into the pull.
 //
 // Layout: 14 planes (9 flow deviations f~ = f - w, 5 temperature populations
-// g) of [ny][pitch] floats, ping-ponged between two buffers.  A plane row is
-// read once and written once per step: 112 algorithmic bytes per node.
+// g) of [ny][pitch] elements (FP32, BF16 or scaled FP16; arithmetic in FP32),
+// ping-ponged between two buffers.  A plane row is read once and written once
+// per step: 112 (FP32) or 56 (16-bit) algorithmic bytes per node.
 //
 // One thread per node.  A pull from x - 1 or x + 1 takes the value from the
 // neighbouring lane by a warp shuffle (one scalar load at the warp edge), so
@@ -23,8 +24,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // replaced across a wall by half-way bounce-back (f) or anti-bounce-back with
 // the wall temperature (g).  In deviation form the half-way rule keeps its
 // shape because w_i = w_ibar.
-__device__ float pull_general(const Dev &D, const float *__restrict__ A, int x, int y, int p)
+template <typename T>
+__device__ float pull_general(const Dev &D, const T *__restrict__ A, int x, int y, int p)
 {
+    using E = Elem<T>;
     const int d = pdir(p);
     int xs = x - ex(d), ys = y - ey(d);
     bool wall = false;
@@ -36,11 +39,11 @@ __device__ float pull_general(const Dev &D, const float *__restrict__ A, int x, 
         if (D.per_y) ys = ys < 0 ? ys + D.ny : ys - D.ny;
         else wall = true;
     }
-    if (!wall) return A[(long long)p * D.ps + (long long)ys * D.pitch + xs];
+    if (!wall) return E::ld(A[(long long)p * D.ps + (long long)ys * D.pitch + xs]);
     const long long self = (long long)y * D.pitch + x;
-    if (p < kQ9) return A[(long long)opp(d) * D.ps + self];
+    if (p < kQ9) return E::ld(A[(long long)opp(d) * D.ps + self]);
     const int side = d == 1 ? 0 : d == 3 ? 1 : d == 2 ? 2 : 3;
-    return -A[(long long)(kQ9 + opp(d)) * D.ps + self] + 2.f * w5(d) * D.Twall[side];
+    return -E::ld(A[(long long)(kQ9 + opp(d)) * D.ps + self]) + 2.f * w5(d) * D.Twall[side];
 }
 
 // Values pulled into a node on the general path; for a newborn node the
@@ -51,7 +54,8 @@ __device__ float pull_general(const Dev &D, const float *__restrict__ A, int x, 
 // g = g_eq(T_w, u_w).
 // Returns 0 for a general pull, else 1 + the refill class (1 quadratic,
 // 2 linear, 3 copy, 4 equilibrium).
-__device__ __noinline__ int slow_node(const Dev &D, const float *__restrict__ A,
+template <typename T>
+__device__ __noinline__ int slow_node(const Dev &D, const T *__restrict__ A,
                                       const int *__restrict__ own_cur, int x, int y, uint8_t fl,
                                       float *out)
 {
@@ -211,17 +215,63 @@ __device__ __noinline__ void flush_counters(const Dev &D, int parity, const unsi
 // ---------------------------------------------------------------------------
 constexpr int kSCThreads = 128;
 
-__global__ void __launch_bounds__(kSCThreads, 8)
-    k_stream_collide(const Dev D, const float *__restrict__ Ain, float *__restrict__ Aout,
+// V consecutive stored elements moved as one aligned vector.
+template <typename T, int V>
+struct Vec;
+template <>
+struct Vec<float, 1> {
+    using W = float;
+    __device__ static void unpack(W w, float *v) { v[0] = w; }
+    __device__ static W pack(const float *v) { return v[0]; }
+};
+template <>
+struct Vec<float, 2> {
+    using W = float2;
+    __device__ static void unpack(W w, float *v) { v[0] = w.x; v[1] = w.y; }
+    __device__ static W pack(const float *v) { return make_float2(v[0], v[1]); }
+};
+template <>
+struct Vec<__nv_bfloat16, 2> {
+    using W = __nv_bfloat162;
+    __device__ static void unpack(W w, float *v)
+    {
+        const float2 f = __bfloat1622float2(w);
+        v[0] = f.x;
+        v[1] = f.y;
+    }
+    __device__ static W pack(const float *v) { return __floats2bfloat162_rn(v[0], v[1]); }
+};
+template <>
+struct Vec<__half, 2> {
+    using W = __half2;
+    __device__ static void unpack(W w, float *v)
+    {
+        const float2 f = __half22float2(w);
+        v[0] = f.x * (1.f / kHalfScale);
+        v[1] = f.y * (1.f / kHalfScale);
+    }
+    __device__ static W pack(const float *v) { return __floats2half2_rn(v[0] * kHalfScale, v[1] * kHalfScale); }
+};
+
+// Stream-collide kernel, V consecutive nodes per thread (one vector load and
+// one vector store per plane); FP32 runs V = 1, the 16-bit storages V = 2 so
+// that every load still moves four bytes.
+template <typename T, int V>
+__global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
+    k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout,
                      const int *__restrict__ own_cur, int parity, int ahead)
 {
+    using E = Elem<T>;
+    using VW = typename Vec<T, V>::W;
+    constexpr int kAl = 16 / (int)sizeof(T); // elements per 16 bytes
     const int lane = threadIdx.x & 31;
+    const int span = (int)blockDim.x * V; // nodes of a row per block
     if (threadIdx.x < kPop && threadIdx.y == 0) {
         const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x + ahead;
         const int by = (int)(lin / gridDim.x), bx = (int)(lin % gridDim.x);
         const int yb = by * (int)blockDim.y;
-        const int xs = bx * (int)blockDim.x;
-        const int lo = max(xs - 4, 0), hi = min(xs + (int)blockDim.x + 4, D.pitch);
+        const int xs = bx * span;
+        const int lo = max(xs - kAl, 0), hi = min(xs + span + kAl, D.pitch);
         const int p = threadIdx.x;
         for (int yy = yb; yy < min(yb + (int)blockDim.y, D.ny) && hi > lo; ++yy) {
             int ys = yy - ey(pdir(p));
@@ -229,16 +279,17 @@ __global__ void __launch_bounds__(kSCThreads, 8)
                 if (!D.per_y) continue;
                 ys = ys < 0 ? ys + D.ny : ys - D.ny;
             }
-            const float *sp = Ain + (long long)p * D.ps + (long long)ys * D.pitch + lo;
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sp), "r"((unsigned)(hi - lo) * 4u)
+            const T *sp = Ain + (long long)p * D.ps + (long long)ys * D.pitch + lo;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sp),
+                         "r"((unsigned)((hi - lo) * (int)sizeof(T)))
                          : "memory");
         }
     }
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (y >= D.ny) return; // uniform across the warp: blockDim.x is a multiple of 32
-    const bool act = x < D.pitch;
-    float c[kPop];
+    const bool act = x0 < D.pitch; // the pitch is a multiple of 32, so all V nodes are in the row
+    float c[V][kPop];
 #pragma unroll
     for (int p = 0; p < kPop; ++p) {
         const int d = pdir(p);
@@ -249,50 +300,71 @@ __global__ void __launch_bounds__(kSCThreads, 8)
             ys = ys < 0 ? ys + D.ny : ys - D.ny;
             rowok = true;
         }
-        const float *src = Ain + (long long)p * D.ps + (long long)(rowok ? ys : 0) * D.pitch;
-        const float w = (act && rowok) ? __ldg(src + x) : 0.f;
+        const T *src = Ain + (long long)p * D.ps + (long long)(rowok ? ys : 0) * D.pitch;
+        float v[V];
+        if (act && rowok) Vec<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src + x0)), v);
+        else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[k] = 0.f;
+        }
         if (dx == 0) {
-            c[p] = w;
-        } else if (dx == 1) {
-            float l = __shfl_up_sync(kFull, w, 1);
-            if (lane == 0) l = (act && rowok && x >= 1) ? __ldg(src + x - 1) : 0.f;
-            c[p] = l;
-        } else {
-            float r = __shfl_down_sync(kFull, w, 1);
-            if (lane == 31) r = (act && rowok && x + 1 < D.pitch) ? __ldg(src + x + 1) : 0.f;
-            c[p] = r;
+#pragma unroll
+            for (int k = 0; k < V; ++k) c[k][p] = v[k];
+        } else if (dx == 1) { // pull from x - 1
+            float l = __shfl_up_sync(kFull, v[V - 1], 1);
+            if (lane == 0) l = (act && rowok && x0 >= 1) ? E::ld(__ldg(src + x0 - 1)) : 0.f;
+            c[0][p] = l;
+#pragma unroll
+            for (int k = 1; k < V; ++k) c[k][p] = v[k - 1];
+        } else { // pull from x + 1
+            float r = __shfl_down_sync(kFull, v[0], 1);
+            if (lane == 31) r = (act && rowok && x0 + V < D.pitch) ? E::ld(__ldg(src + x0 + V)) : 0.f;
+#pragma unroll
+            for (int k = 0; k + 1 < V; ++k) c[k][p] = v[k + 1];
+            c[V - 1][p] = r;
         }
     }
     if (!act) return;
-    const uint8_t fl = D.flags[(long long)y * D.pitch + x];
     bool ok = true;
-    if (x < D.nx && fl != kSolid) {
-        if (y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1 || fl == kNewborn) {
-            float tmp[kPop];
-            const int r = slow_node(D, Ain, own_cur, x, y, fl, tmp);
-            if (r) {
-                unsigned n4[4] = {1u, r == 2, r == 3, r == 4};
-                flush_counters(D, parity, n4);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int x = x0 + k;
+        const uint8_t fl = D.flags[(long long)y * D.pitch + x];
+        if (x < D.nx && fl != kSolid) {
+            if (y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1 || fl == kNewborn) {
+                float tmp[kPop];
+                const int r = slow_node(D, Ain, own_cur, x, y, fl, tmp);
+                if (r) {
+                    unsigned n4[4] = {1u, r == 2, r == 3, r == 4};
+                    flush_counters(D, parity, n4);
+                }
+#pragma unroll
+                for (int p = 0; p < kPop; ++p) c[k][p] = tmp[p];
             }
+            ok &= collide(D, c[k]);
+        } else {
 #pragma unroll
-            for (int p = 0; p < kPop; ++p) c[p] = tmp[p];
+            for (int p = 0; p < kPop; ++p) c[k][p] = 0.f;
         }
-        ok = collide(D, c);
-    } else {
-#pragma unroll
-        for (int p = 0; p < kPop; ++p) c[p] = 0.f;
     }
-    float *dst = Aout + (long long)y * D.pitch + x;
+    T *dst = Aout + (long long)y * D.pitch + x0;
 #pragma unroll
-    for (int p = 0; p < kPop; ++p) dst[(long long)p * D.ps] = c[p];
+    for (int p = 0; p < kPop; ++p) {
+        float v[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) v[k] = c[k][p];
+        *reinterpret_cast<VW *>(dst + (long long)p * D.ps) = Vec<T, V>::pack(v);
+    }
     if (!ok) atomicOr(&D.status->err, kErrNumeric);
 }
 
 // Collision without streaming, for the initial state and for distributions
 // supplied by the caller (mode 1 reads pre-collision values from Ain).
-__global__ void k_init_collide(const Dev D, const float *__restrict__ Ain, float *__restrict__ Aout,
-                               float T_init, int mode)
+template <typename T>
+__global__ void k_init_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, float T_init,
+                               int mode)
 {
+    using E = Elem<T>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= D.pitch || y >= D.ny) return;
@@ -300,7 +372,7 @@ __global__ void k_init_collide(const Dev D, const float *__restrict__ Ain, float
     float c[kPop];
     const bool live = x < D.nx && D.flags[n] != kSolid;
     for (int p = 0; p < kPop; ++p) {
-        if (mode == 1) c[p] = Ain[(long long)p * D.ps + n];
+        if (mode == 1) c[p] = E::ld(Ain[(long long)p * D.ps + n]);
         else c[p] = p < kQ9 ? 0.f : w5(p - kQ9) * T_init;
     }
     if (live) {
@@ -308,15 +380,17 @@ __global__ void k_init_collide(const Dev D, const float *__restrict__ Ain, float
     } else {
         for (int p = 0; p < kPop; ++p) c[p] = 0.f;
     }
-    for (int p = 0; p < kPop; ++p) Aout[(long long)p * D.ps + n] = c[p];
+    for (int p = 0; p < kPop; ++p) Aout[(long long)p * D.ps + n] = E::st(c[p]);
 }
 
 // rho - 1, u, T from the post-collision state: the collision keeps rho and
 // T and adds F to the momentum, so u = (sum e f+ - F/2)/rho equals the
 // pre-collision (sum e f + F/2)/rho of Sec. 2.1.
-__global__ void k_fields(const Dev D, const float *__restrict__ A, int row0, float *rho_o,
-                         float *ux_o, float *uy_o, float *T_o)
+template <typename S>
+__global__ void k_fields(const Dev D, const S *__restrict__ A, int row0, float *rho_o, float *ux_o,
+                         float *uy_o, float *T_o)
 {
+    using E = Elem<S>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = row0 + blockIdx.y;
     if (x >= D.nx || y >= D.ny) return;
@@ -329,12 +403,12 @@ __global__ void k_fields(const Dev D, const float *__restrict__ A, int row0, flo
     }
     float f[kQ9], T = 0.f, drho = 0.f, jx = 0.f, jy = 0.f;
     for (int i = 0; i < kQ9; ++i) {
-        f[i] = A[(long long)i * D.ps + n];
+        f[i] = E::ld(A[(long long)i * D.ps + n]);
         drho += f[i];
         jx += ex(i) * f[i];
         jy += ey(i) * f[i];
     }
-    for (int i = 0; i < kQ5; ++i) T += A[(long long)(kQ9 + i) * D.ps + n];
+    for (int i = 0; i < kQ5; ++i) T += E::ld(A[(long long)(kQ9 + i) * D.ps + n]);
     const float rho = 1.f + drho;
     const float Fx = D.bfx, Fy = rho * D.gbeta * (T - D.T0) + D.bfy;
     rho_o[o] = drho;
@@ -343,42 +417,84 @@ __global__ void k_fields(const Dev D, const float *__restrict__ A, int row0, flo
     T_o[o] = T;
 }
 
-cudaError_t launch_stream_collide(const Dev &D, const float *Ain, float *Aout, const int *own_cur,
-                                  int parity, cudaStream_t s)
+namespace {
+
+template <typename T, int V>
+cudaError_t stream_collide_t(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
+                             cudaStream_t s)
 {
     static int resident = 0;
     if (!resident) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide, kSCThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide<T, V>, kSCThreads, 0);
         resident = max(1, sms * per_sm);
     }
-    int bx = ((D.pitch + 31) / 32) * 32;
+    const int tx = D.pitch / V; // threads per row (the pitch is a multiple of 32)
+    int bx = ((tx + 31) / 32) * 32;
     if (bx > kSCThreads) bx = kSCThreads;
     const int by = kSCThreads / bx;
     dim3 block(bx, by);
-    dim3 grid((D.pitch + bx - 1) / bx, (D.ny + by - 1) / by);
-    k_stream_collide<<<grid, block, 0, s>>>(D, Ain, Aout, own_cur, parity, resident);
+    dim3 grid((tx + bx - 1) / bx, (D.ny + by - 1) / by);
+    k_stream_collide<T, V><<<grid, block, 0, s>>>(D, static_cast<const T *>(Ain), static_cast<T *>(Aout),
+                                                  own_cur, parity, resident);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_collide(const Dev &D, const float *Ain, float *Aout, float T_init, int mode,
-                                cudaStream_t s)
+template <typename T>
+cudaError_t init_collide_t(const Dev &D, const void *Ain, void *Aout, float T_init, int mode, cudaStream_t s)
 {
     dim3 block(128);
     dim3 grid((D.pitch + 127) / 128, D.ny);
-    k_init_collide<<<grid, block, 0, s>>>(D, Ain, Aout, T_init, mode);
+    k_init_collide<T><<<grid, block, 0, s>>>(D, static_cast<const T *>(Ain), static_cast<T *>(Aout), T_init,
+                                             mode);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fields(const Dev &D, const float *A, int row0, int rows, float *rho, float *ux,
-                          float *uy, float *T, cudaStream_t s)
+template <typename T>
+cudaError_t fields_t(const Dev &D, const void *A, int row0, int rows, float *rho, float *ux, float *uy,
+                     float *Tf, cudaStream_t s)
 {
     dim3 block(128);
     dim3 grid((D.nx + 127) / 128, rows);
-    k_fields<<<grid, block, 0, s>>>(D, A, row0, rho, ux, uy, T);
+    k_fields<T><<<grid, block, 0, s>>>(D, static_cast<const T *>(A), row0, rho, ux, uy, Tf);
     return cudaGetLastError();
+}
+
+} // namespace
+
+cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
+                                  cudaStream_t s)
+{
+    switch (D.storage) {
+    case LBM_STORE_FP32: return stream_collide_t<float, 1>(D, Ain, Aout, own_cur, parity, s);
+    case LBM_STORE_BF16: return stream_collide_t<__nv_bfloat16, 2>(D, Ain, Aout, own_cur, parity, s);
+    case LBM_STORE_FP16: return stream_collide_t<__half, 2>(D, Ain, Aout, own_cur, parity, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_init_collide(const Dev &D, const void *Ain, void *Aout, float T_init, int mode,
+                                cudaStream_t s)
+{
+    switch (D.storage) {
+    case LBM_STORE_FP32: return init_collide_t<float>(D, Ain, Aout, T_init, mode, s);
+    case LBM_STORE_BF16: return init_collide_t<__nv_bfloat16>(D, Ain, Aout, T_init, mode, s);
+    case LBM_STORE_FP16: return init_collide_t<__half>(D, Ain, Aout, T_init, mode, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fields(const Dev &D, const void *A, int row0, int rows, float *rho, float *ux, float *uy,
+                          float *T, cudaStream_t s)
+{
+    switch (D.storage) {
+    case LBM_STORE_FP32: return fields_t<float>(D, A, row0, rows, rho, ux, uy, T, s);
+    case LBM_STORE_BF16: return fields_t<__nv_bfloat16>(D, A, row0, rows, rho, ux, uy, T, s);
+    case LBM_STORE_FP16: return fields_t<__half>(D, A, row0, rows, rho, ux, uy, T, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 } // namespace lbm

@@ -18,7 +18,7 @@ namespace lbm {
 
 namespace {
 
-constexpr int kLinkThreads = 256;
+constexpr int kLinkThreads = 128;
 constexpr int kBoxThreads = 128;
 constexpr int kPartThreads = 1024;
 constexpr double kPi = 3.14159265358979323846;
@@ -38,7 +38,7 @@ __device__ __forceinline__ T warp_sum(T v)
 
 } // namespace
 
-constexpr int kTilePlanes = 12;
+constexpr int kTilePlanes = 12; // planes the rules read: f1..f8, g1..g4
 
 // Double-float warp sum (lane 0 receives the result).
 __device__ __forceinline__ void warp_df_sum(float &h, float &l)
@@ -51,78 +51,42 @@ __device__ __forceinline__ void warp_df_sum(float &h, float &l)
     }
 }
 
-__host__ __device__ inline int pow2_at_least(int v)
-{
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
-
-// Link-kernel tile geometry for zones of side N: the tile covers the zone
-// plus the two-node margin of the bounce-back stencil, wy = N + 4 rows of
-// wx columns starting at a multiple of four (16-byte aligned for the tensor
-// copy), wx a power of two >= N + 7 (at most 64: the fluid and owner masks of
-// a row are 64-bit words).  Each of the 12 planes takes tps floats, a
-// multiple of 32 so that every plane starts on a 128-byte boundary.
+// The link kernel's window for zones of side N and es-byte elements: the
+// zone plus the two-node margin of the bounce-back stencil, wy = N + 4 rows
+// of wx columns.  Its first column is the zone's first column minus two,
+// rounded down to a multiple of al = 16 / es elements (a tensor prefetch box
+// starts on a 16-byte boundary), so wx = N + 3 + al rounded up to a multiple
+// of al; wx is at most 64 (the fluid and owner masks of a row are 64-bit
+// words).
+__host__ __device__ inline int link_tile_al(int es) { return 16 / es; }
 __host__ __device__ inline int link_tile_wy(int N) { return N + 4; }
-__host__ __device__ inline int link_tile_wx(int N) { return pow2_at_least(N + 7); }
-__host__ __device__ inline int link_tile_tps(int N)
+__host__ __device__ inline int link_tile_wx(int N, int es)
 {
-    return (link_tile_wy(N) * link_tile_wx(N) + 31) & ~31;
+    const int al = link_tile_al(es);
+    return (N + 3 + al + al - 1) / al * al;
 }
 __host__ __device__ inline int link_occ_words(int N) { return (12 * N - 12 + 31) / 32; }
 
-// Shared memory: 128 bytes of alignment slack, the tile, the fluid and owner
-// row masks [wy] (u64 each), slot occupancy words and their prefix [words],
-// and per slot / per link: the link node, the compacted slot list, three
-// FP32 brackets and two integer words.
-size_t link_smem_bytes(int N)
+// Shared memory: the fluid and owner row masks [wy] (u64 each), slot occupancy words and their prefix [words], and per
+// slot / per link: the link node, the compacted slot list, three FP32
+// brackets and two integer words.
+size_t link_smem_bytes(int N, int storage)
 {
+    (void)storage;
     const size_t cap = (size_t)12 * N - 12;
-    return 128 + (size_t)kTilePlanes * link_tile_tps(N) * sizeof(float) +
-           (size_t)2 * link_tile_wy(N) * sizeof(unsigned long long) +
+    return (size_t)2 * link_tile_wy(N) * sizeof(unsigned long long) +
            (size_t)2 * link_occ_words(N) * sizeof(unsigned) + cap * 7 * sizeof(int);
 }
 
-bool link_zone_supported(int N) { return link_tile_wx(N) <= 64 && link_smem_bytes(N) <= (size_t)200 * 1024; }
+bool link_zone_supported(int N, int storage)
+{
+    return link_tile_wx(N, storage_bytes(storage)) <= 64 && link_smem_bytes(N, storage) <= (size_t)200 * 1024;
+}
 
-// Global plane of tile plane t: f1..f8 then g1..g4.
+// Global plane of window plane t: f1..f8 then g1..g4.
 __device__ __forceinline__ int tile_global_plane(int t) { return t < 8 ? t + 1 : t + 2; }
 
-// ---- tensor-copy and mbarrier primitives (one CTA, no cluster)
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-// Bounded wait for phase `parity` of the barrier: false after ~2^31 cycles.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
-{
-    const long long t0 = clock64();
-    for (;;) {
-        unsigned done;
-        asm volatile("{\n\t.reg .pred P;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, P;\n\t}"
-                     : "=r"(done)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
-        if (done) return true;
-        if (clock64() - t0 > (1ll << 31)) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *tm, int x, int y, int z,
-                                            unsigned bar)
-{
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-                 "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
-                 : "memory");
-}
+// Tensor prefetch of one box into L2 (no completion to wait for).
 __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *tm, int x, int y, int z)
 {
     asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];" ::"l"(
@@ -150,13 +114,14 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 }
 
 // One CTA per particle.  Phases:
-//  1. thread 0 issues tensor copies of the particle's tile (zone plus the
-//     two-node margin of the bounce-back stencil) of the 12 planes the rules
-//     read (f1..f8, g1..g4) into shared memory, completing on an mbarrier,
-//     and tensor prefetches into L2 of the tile of the particle `ahead`
-//     places later in launch order; meanwhile the warps read the owner map
-//     over the tile and record per row a fluid mask and an owned-by-this-
-//     particle mask (one ballot per 32 nodes);
+//  1. the warps read the owner map over the particle's window (zone plus
+//     the two-node margin of the bounce-back stencil) and record per row a
+//     fluid mask and an owned-by-this-particle mask (one ballot per 32
+//     nodes); thread 0 issues tensor prefetches into L2 of the window of
+//     the 12 planes the rules read (f1..f8, g1..g4) for the particle `ahead`
+//     places later in launch order (about one residency wave ahead), and a
+//     warp prefetches that particle's owner rows, so that the scattered
+//     reads of phases 1 and 4 hit L2;
 //  2. thread (b, k) intersects the fluid mask of zone row b with the owner
 //     mask of row b + e_k,y shifted by e_k,x: each set bit is a link, which
 //     claims its fixed slot of the index array (direction k, line through
@@ -165,19 +130,22 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 //     thread i takes the i-th link: the work is balanced and the reduction
 //     order is fixed, hence the forces are bit-reproducible;
 //  4. each link: wall fraction q, curved bounce-back of f and g (Sec. 2.3)
+//     from the populations read at x_f, x_f - e_k and x_f - 2 e_k,
 //     written into the solid node x_f + e_k (direction kbar) of A in HBM,
 //     where the next pull stream picks it up (one link per (solid node, kbar),
 //     and every read is of a fluid node, so the writes never race the reads),
 //     and the momentum-exchange bracket of Eq. force / Eq. torque, stored per
 //     link and summed by one warp in link order.
+template <typename T>
 __global__ void __launch_bounds__(kLinkThreads)
-    k_links(const __grid_constant__ CUtensorMap tmA, const Dev D, float *A, const int *__restrict__ own,
+    k_links(const __grid_constant__ CUtensorMap tmA, const Dev D, T *A, const int *__restrict__ own,
             int parity, int ahead)
 {
-    extern __shared__ __align__(128) unsigned char lsm[];
-    __shared__ __align__(8) unsigned long long s_bar;
+    using E = Elem<T>;
+    constexpr int es = (int)sizeof(T), al = 16 / es;
+    extern __shared__ __align__(16) unsigned char lsm[];
     __shared__ int s_nvalid;
-    __shared__ unsigned s_over, s_fail;
+    __shared__ unsigned s_over;
     const int p = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const GeomRec G = D.geo_cur[p];
@@ -186,13 +154,10 @@ __global__ void __launch_bounds__(kLinkThreads)
     const int base = D.slot_base[p];
 
     const int Nm = D.zone_max;
-    const int wy = link_tile_wy(Nm), wx = link_tile_wx(Nm), tps = link_tile_tps(Nm);
-    const int XA = (X0 - 2) & ~3, YA = Y0 - 2, off = X0 - XA;
-    const unsigned sbase = (unsigned)__cvta_generic_to_shared(lsm);
-    const unsigned pad = (128u - (sbase & 127u)) & 127u;
-    float *tile = reinterpret_cast<float *>(lsm + pad);
-    unsigned long long *Fm = reinterpret_cast<unsigned long long *>(tile + kTilePlanes * tps); // [wy]
-    unsigned long long *Om = Fm + wy;                                                       // [wy]
+    const int wy = link_tile_wy(Nm), wx = link_tile_wx(Nm, es);
+    const int XA = (X0 - 2) & ~(al - 1), YA = Y0 - 2, off = X0 - XA;
+    unsigned long long *Fm = reinterpret_cast<unsigned long long *>(lsm); // [wy]
+    unsigned long long *Om = Fm + wy;                                       // [wy]
     const int nw = link_occ_words(Nm), capm = 12 * Nm - 12;
     unsigned *occ = reinterpret_cast<unsigned *>(Om + wy); // [nw]
     unsigned *pre = occ + nw;                               // [nw]
@@ -203,44 +168,57 @@ __global__ void __launch_bounds__(kLinkThreads)
     float *ltq = lby + capm;
     int *lcode = reinterpret_cast<int *>(ltq + capm);
     int *ltz = lcode + capm;
-    const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar);
 
-    // ---- 1. tensor copies (thread 0) and owner masks (all warps)
+    // ---- 1. owner masks (all warps) and look-ahead prefetches
     if (tid == 0) {
         s_over = 0u;
-        s_fail = 0u;
-        mbar_init(bar, 1);
-        mbar_expect_tx(bar, (unsigned)(kTilePlanes * wy * wx * sizeof(float)));
-        const unsigned dst = sbase + pad;
-        for (int t = 0; t < kTilePlanes; ++t)
-            tma_load_3d(dst + (unsigned)(t * tps * sizeof(float)), &tmA, XA, YA, tile_global_plane(t), bar);
         if (p + ahead < D.np) {
             const GeomRec Ga = D.geo_cur[p + ahead];
             for (int t = 0; t < kTilePlanes; ++t)
-                tma_prefetch_3d(&tmA, (Ga.X0 - 2) & ~3, Ga.Y0 - 2, tile_global_plane(t));
+                tma_prefetch_3d(&tmA, (Ga.X0 - 2) & ~(al - 1), Ga.Y0 - 2, tile_global_plane(t));
         }
         const DiskDF d0 = geom_df(G);
         D.pos4[p] = make_float4(d0.xh, d0.yh, d0.xl, d0.yl);
         D.prc[p] = make_float2(G.r, G.C);
     }
-    for (int r = warp; r < wy; r += kLinkThreads / 32) {
-        const int j = YA + r;
-        unsigned lo_f = 0u, lo_o = 0u, hi_f = 0u, hi_o = 0u;
-        {
-            const int i = XA + lane;
-            const int v = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
-            lo_f = __ballot_sync(0xffffffffu, v == -1);
-            lo_o = __ballot_sync(0xffffffffu, v == p);
+    {
+        // owner rows in chunks of four per warp, all four loads issued before
+        // the first ballot, so a chunk costs one memory latency
+        constexpr int kW = kLinkThreads / 32;
+        for (int r0 = 0; r0 < wy; r0 += 4 * kW) {
+            int vlo[4], vhi[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int r = r0 + warp + t * kW, j = YA + r, i = XA + lane;
+                vlo[t] = (r < wy && inside(D, i, j)) ? own[(long long)j * D.nx + i] : -2;
+                vhi[t] = (wx > 32 && r < wy && inside(D, i + 32, j)) ? own[(long long)j * D.nx + i + 32] : -2;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (r0 + t * kW >= wy) break; // no warp has a row left
+                const int r = r0 + warp + t * kW;
+                const unsigned lo_f = __ballot_sync(0xffffffffu, vlo[t] == -1);
+                const unsigned lo_o = __ballot_sync(0xffffffffu, vlo[t] == p);
+                unsigned hi_f = 0u, hi_o = 0u;
+                if (wx > 32) {
+                    hi_f = __ballot_sync(0xffffffffu, vhi[t] == -1);
+                    hi_o = __ballot_sync(0xffffffffu, vhi[t] == p);
+                }
+                if (lane == 0 && r < wy) {
+                    Fm[r] = ((unsigned long long)hi_f << 32) | lo_f;
+                    Om[r] = ((unsigned long long)hi_o << 32) | lo_o;
+                }
+            }
         }
-        if (wx > 32) {
-            const int i = XA + 32 + lane;
-            const int v = inside(D, i, j) ? own[(long long)j * D.nx + i] : -2;
-            hi_f = __ballot_sync(0xffffffffu, v == -1);
-            hi_o = __ballot_sync(0xffffffffu, v == p);
-        }
-        if (lane == 0) {
-            Fm[r] = ((unsigned long long)hi_f << 32) | lo_f;
-            Om[r] = ((unsigned long long)hi_o << 32) | lo_o;
+    }
+    // L2 prefetch of the owner rows of the particle `ahead` places later
+    if (warp == 1 && p + ahead < D.np) {
+        const GeomRec Ga = D.geo_cur[p + ahead];
+        const int xa = (Ga.X0 - 2) & ~(al - 1), ya = Ga.Y0 - 2;
+        for (int r = lane; r < 2 * wy; r += 32) {
+            const int j = ya + (r >> 1), i = min(max(xa + (r & 1) * (wx - 1), 0), D.nx - 1);
+            if (j >= 0 && j < D.ny)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(own + (long long)j * D.nx + i) : "memory");
         }
     }
     for (int w = tid; w < nw; w += kLinkThreads) occ[w] = 0u;
@@ -293,18 +271,16 @@ __global__ void __launch_bounds__(kLinkThreads)
             D.slot_q[base + sl] = 0.f;
         }
     }
-    if (tid == 0 && !mbar_wait(bar, 0)) {
-        s_fail = 1u;
-        atomicOr(&D.status->err, kErrTimeout);
-        mbar_wait(bar, 0); // copies still in flight write this CTA's shared memory
-    }
     __syncthreads();
-    if (s_fail) return;
 
     // ---- 4. bounce-back and momentum exchange, thread i on the i-th link
     const DiskDF dk = geom_df(G);
     const float Ux = G.ux, Uy = G.uy, Om_ = G.om, wT = G.wT;
-    auto tv = [&](int t, int i, int j) -> float { return tile[t * tps + (j - YA) * wx + (i - XA)]; };
+    // populations of fluid nodes: no CTA writes them during this kernel
+    const T *Ar = A;
+    auto tv = [&](int t, int i, int j) -> float {
+        return E::ld(__ldg(Ar + (long long)tile_global_plane(t) * D.ps + (long long)j * D.pitch + i));
+    };
     auto fluid = [&](int i, int j) -> bool { return (Fm[j - YA] >> (i - XA)) & 1ull; };
     for (int li = tid; li < nvalid; li += kLinkThreads) {
         const int sl = list[li];
@@ -334,11 +310,11 @@ __global__ void __launch_bounds__(kLinkThreads)
         int lvl;
         const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
         const long long ns = (long long)(fj + ky) * D.pitch + (fi + kx);
-        A[kb * D.ps + ns] = fnew;
+        A[kb * D.ps + ns] = E::st(fnew);
         if (k <= 4) {
             const float gnew = thermal32(q, tv(8 + k - 1, fi, fj), tv(8 + k - 1, ii1, jj1),
                                          tv(8 + kb - 1, fi, fj), have1, wT);
-            A[(kQ9 + kb) * D.ps + ns] = gnew;
+            A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
         }
         // momentum exchange: with f = w + f~ the bracket of Eq. force is
         // 2 w_k e_k + [f~_k^+ (e_k - u_w) - f~_kbar (e_kbar - u_w)]; the
@@ -614,34 +590,69 @@ __global__ void k_pack_particles(const Dev D, lbm_particle *out)
     out[a] = P;
 }
 
+namespace {
+
+template <typename T>
+void *link_kernel()
+{
+    return reinterpret_cast<void *>(&k_links<T>);
+}
+
+void *link_kernel_for(int storage)
+{
+    switch (storage) {
+    case LBM_STORE_BF16: return link_kernel<__nv_bfloat16>();
+    case LBM_STORE_FP16: return link_kernel<__half>();
+    default: return link_kernel<float>();
+    }
+}
+
+} // namespace
+
 cudaError_t prepare_links(Dev &D)
 {
     D.link_ahead = 1;
     if (D.np == 0) return cudaSuccess;
-    const size_t smem = link_smem_bytes(D.zone_max);
-    cudaError_t e = cudaFuncSetAttribute(k_links, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = link_smem_bytes(D.zone_max, D.storage);
+    const void *fn = link_kernel_for(D.storage);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0, dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_links, kLinkThreads, smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLinkThreads, smem)) != cudaSuccess)
         return e;
     D.link_ahead = max(1, sms * per_sm);
     return cudaSuccess;
 }
 
-cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity, const CUtensorMap &tmA,
+cudaError_t launch_links(const Dev &D, void *A, const int *own_cur, int parity, const CUtensorMap &tmA,
                          cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
-    k_links<<<D.np, kLinkThreads, link_smem_bytes(D.zone_max), s>>>(tmA, D, A, own_cur, parity, D.link_ahead);
+    const size_t smem = link_smem_bytes(D.zone_max, D.storage);
+    switch (D.storage) {
+    case LBM_STORE_FP32:
+        k_links<float><<<D.np, kLinkThreads, smem, s>>>(tmA, D, static_cast<float *>(A), own_cur, parity,
+                                                        D.link_ahead);
+        break;
+    case LBM_STORE_BF16:
+        k_links<__nv_bfloat16><<<D.np, kLinkThreads, smem, s>>>(tmA, D, static_cast<__nv_bfloat16 *>(A), own_cur,
+                                                                parity, D.link_ahead);
+        break;
+    case LBM_STORE_FP16:
+        k_links<__half><<<D.np, kLinkThreads, smem, s>>>(tmA, D, static_cast<__half *>(A), own_cur, parity,
+                                                         D.link_ahead);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 // 3-D tensor map over one distribution buffer: x (pitch columns), y (ny
-// rows), plane (kPop planes), FP32, box wx x wy x 1 of the link tile.  Reads
-// outside the box's range return zeros.
-cudaError_t make_plane_map(const Dev &D, const float *A, CUtensorMap *m)
+// rows), plane (kPop planes), in the storage element type, box wx x wy x 1
+// of the link tile.  Reads outside the tensor return zeros.
+cudaError_t make_plane_map(const Dev &D, const void *A, CUtensorMap *m)
 {
     static std::mutex mu;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -657,17 +668,21 @@ cudaError_t make_plane_map(const Dev &D, const float *A, CUtensorMap *m)
             encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
         }
     }
+    const int es = storage_bytes(D.storage);
     const int N = D.zone_max > 0 ? D.zone_max : 4;
     const cuuint64_t dims[3] = {(cuuint64_t)D.pitch, (cuuint64_t)D.ny, (cuuint64_t)kPop};
-    const cuuint64_t strides[2] = {(cuuint64_t)D.pitch * sizeof(float), (cuuint64_t)D.ps * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)link_tile_wx(N), (cuuint32_t)link_tile_wy(N), 1u};
+    const cuuint64_t strides[2] = {(cuuint64_t)D.pitch * es, (cuuint64_t)D.ps * es};
+    const cuuint32_t box[3] = {(cuuint32_t)link_tile_wx(N, es), (cuuint32_t)link_tile_wy(N), 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
-    if (box[0] > 256 || box[1] > 256 || (box[0] * sizeof(float)) % 16 != 0 || strides[0] % 16 != 0 ||
-        strides[1] % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
+    if (box[0] > 256 || box[1] > 256 || (box[0] * es) % 16 != 0 || strides[0] % 16 != 0 || strides[1] % 16 != 0 ||
+        (reinterpret_cast<uintptr_t>(A) & 15) != 0)
         return cudaErrorInvalidValue;
-    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(A), dims, strides, box,
-                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUtensorMapDataType dt = D.storage == LBM_STORE_BF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                   : D.storage == LBM_STORE_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUresult r = encode(m, dt, 3, const_cast<void *>(A), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 

@@ -37,7 +37,8 @@ int validate(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_pa
     if (d->nx < 4 || d->ny < 4 || d->reserved != 0) return LBM_EINVAL;
     if ((long long)d->nx * d->ny > (1ll << 31) - 1) return LBM_EINVAL;
     if (!(prm->nu > 0) || !(prm->alpha > 0) || !finite(prm->nu) || !finite(prm->alpha)) return LBM_EINVAL;
-    if (prm->storage != LBM_STORE_FP32) return LBM_EINVAL;
+    if (prm->storage != LBM_STORE_FP32 && prm->storage != LBM_STORE_BF16 && prm->storage != LBM_STORE_FP16)
+        return LBM_EINVAL;
     const double rates[] = {prm->s_e, prm->s_eps, prm->s_q, prm->q_e, prm->q_nu};
     for (double r : rates)
         if (!finite(r) || r >= 2.0) return LBM_EINVAL;
@@ -57,7 +58,7 @@ int validate(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_pa
             if (!finite(x)) return LBM_EINVAL;
         if (P.r < 1.0 || P.rho <= 0.0) return LBM_EINVAL;
         // the link kernel holds a particle's zone in shared memory
-        if (!link_zone_supported(zone_size(P.r))) return LBM_EINVAL;
+        if (!link_zone_supported(zone_size(P.r), prm->storage)) return LBM_EINVAL;
         // a disk stays inside the cavity; next to a periodic seam it keeps two
         // nodes of clearance so that no link or stencil wraps around
         const double mx = px ? 2.0 : -0.5, my = py ? 2.0 : -0.5;
@@ -87,7 +88,7 @@ int validate(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_pa
     return LBM_OK;
 }
 
-void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, Layout &L)
+void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, Layout &L)
 {
     L.pitch = (int)round_up((size_t)d->nx, 32);
     L.ps = (long long)round_up((size_t)L.pitch * d->ny, 64);
@@ -100,7 +101,7 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, Layout &L)
         return o;
     };
     const size_t nn = (size_t)d->nx * d->ny;
-    for (int b = 0; b < 2; ++b) L.A[b] = take((size_t)kPop * L.ps * sizeof(float));
+    for (int b = 0; b < 2; ++b) L.A[b] = take((size_t)kPop * L.ps * storage_bytes(storage));
     for (int b = 0; b < 2; ++b) L.own[b] = take(nn * sizeof(int));
     L.flags = take((size_t)L.pitch * d->ny);
     L.slot_node = take(L.nslots * sizeof(int));
@@ -143,7 +144,7 @@ struct lbm_handle {
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
     Dev D;
-    float *A[2];
+    void *A[2]; // planes of D.storage elements
     int *own[2];
     int parity = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -223,7 +224,7 @@ int timed(lbm_handle *h, int kind, cudaStream_t st, F &&launch)
 int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
 {
     const Dev &D = h->D;
-    float *Ain = h->A[par], *Aout = h->A[par ^ 1];
+    void *Ain = h->A[par], *Aout = h->A[par ^ 1];
     int *oc = h->own[par], *on = h->own[par ^ 1];
     int rc;
     if (h->np > 0) {
@@ -293,6 +294,7 @@ void fill_dev(lbm_handle *h)
     D.pitch = L.pitch;
     D.np = h->np;
     D.ps = L.ps;
+    D.storage = P.storage;
     D.per_x = (h->d.bc & LBM_BC_PERIODIC_X) ? 1 : 0;
     D.per_y = (h->d.bc & LBM_BC_PERIODIC_Y) ? 1 : 0;
     const double s_nu = 1.0 / (3.0 * P.nu + 0.5);
@@ -330,7 +332,7 @@ void fill_dev(lbm_handle *h)
     D.geo_nxt = reinterpret_cast<GeomRec *>(ws + L.geo[2]);
     D.status = reinterpret_cast<Status *>(ws + L.status);
     for (int b = 0; b < 2; ++b) {
-        h->A[b] = reinterpret_cast<float *>(ws + L.A[b]);
+        h->A[b] = ws + L.A[b];
         h->own[b] = reinterpret_cast<int *>(ws + L.own[b]);
     }
 }
@@ -400,7 +402,7 @@ int lbm_query_footprint(const lbm_domain *d, const lbm_particle *p, int32_t n, c
     int rc = validate(d, p, n, prm);
     if (rc) return rc;
     Layout L;
-    layout(d, p, n, L);
+    layout(d, p, n, prm->storage, L);
     *bytes = L.total;
     return LBM_OK;
 }
@@ -418,7 +420,7 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
     h->d = *d;
     h->prm = *prm;
     h->np = n;
-    layout(d, p, n, h->L);
+    layout(d, p, n, prm->storage, h->L);
     if (ws_bytes < h->L.total) {
         delete h;
         return LBM_ENOSPC;
@@ -451,7 +453,7 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
         if ((rc = upload_particles(h, p))) return fail(rc);
     }
     if ((rc = rebuild_maps(h))) return fail(rc);
-    const size_t abytes = (size_t)kPop * h->L.ps * sizeof(float);
+    const size_t abytes = (size_t)kPop * h->L.ps * storage_bytes(h->D.storage);
     if (cudaMemsetAsync(h->A[1], 0, abytes, h->stream) != cudaSuccess) return fail(LBM_ECUDA);
     if (launch_init_collide(h->D, h->A[1], h->A[0], (float)prm->T_init, 0, h->stream) != cudaSuccess)
         return fail(LBM_ECUDA);
@@ -488,7 +490,7 @@ int lbm_sync(lbm_handle *h)
 int lbm_get_fields(lbm_handle *h, float *rho, float *ux, float *uy, float *T, int32_t on_device)
 {
     if (!h || !rho || !ux || !uy || !T) return LBM_EINVAL;
-    const float *A = h->A[h->parity];
+    const void *A = h->A[h->parity];
     const int nx = h->d.nx, ny = h->d.ny;
     if (on_device) {
         CK(h, launch_fields(h->D, A, 0, ny, rho, ux, uy, T, h->stream));
@@ -572,7 +574,7 @@ int lbm_get_slots(lbm_handle *h, int32_t *node, float *q, int64_t cap, int64_t *
 // state and previous positions.
 static size_t state_parts(const lbm_handle *h, size_t sz[5])
 {
-    sz[0] = (size_t)kPop * h->L.ps * sizeof(float);
+    sz[0] = (size_t)kPop * h->L.ps * storage_bytes(h->D.storage);
     sz[1] = (size_t)h->d.nx * h->d.ny * sizeof(int);
     sz[2] = (size_t)h->L.pitch * h->d.ny;
     sz[3] = (size_t)9 * h->np * sizeof(double);
@@ -636,17 +638,22 @@ int lbm_set_distributions(lbm_handle *h, const double *f, const double *g)
     const int nx = h->d.nx, ny = h->d.ny, pitch = h->L.pitch;
     const long long ps = h->L.ps;
     const size_t nn = (size_t)nx * ny;
-    std::vector<float> img((size_t)kPop * ps, 0.f);
+    // pre-collision image in the storage type, collided on the device
+    const int es = storage_bytes(h->D.storage);
+    std::vector<unsigned char> img((size_t)kPop * ps * es, 0);
     for (int p = 0; p < kPop; ++p)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 const size_t s = (size_t)j * nx + i;
                 const double v = p < kQ9 ? f[(size_t)p * nn + s] - w9d(p) : g[(size_t)(p - kQ9) * nn + s];
-                img[(size_t)p * ps + (size_t)j * pitch + i] = std::isfinite(v) ? (float)v : 0.f;
+                const float x = std::isfinite(v) ? (float)v : 0.f;
+                const size_t at = (size_t)p * ps + (size_t)j * pitch + i;
+                if (h->D.storage == LBM_STORE_BF16) reinterpret_cast<__nv_bfloat16 *>(img.data())[at] = Elem<__nv_bfloat16>::st(x);
+                else if (h->D.storage == LBM_STORE_FP16) reinterpret_cast<__half *>(img.data())[at] = Elem<__half>::st(x);
+                else reinterpret_cast<float *>(img.data())[at] = x;
             }
-    float *scratch = h->A[h->parity ^ 1];
-    CK(h, cudaMemcpyAsync(scratch, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice,
-                          h->stream));
+    void *scratch = h->A[h->parity ^ 1];
+    CK(h, cudaMemcpyAsync(scratch, img.data(), img.size(), cudaMemcpyHostToDevice, h->stream));
     CK(h, launch_init_collide(h->D, scratch, h->A[h->parity], 0.f, 1, h->stream));
     return sync_status(h);
 }

@@ -4,6 +4,8 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,6 +43,35 @@ __host__ __device__ constexpr float w5(int i) { return i == 0 ? 0.6f : 0.1f; }
 // Population index p in [0, 14) -> lattice direction.
 __host__ __device__ constexpr int pdir(int p) { return p < kQ9 ? p : p - kQ9; }
 
+// ---------------------------------------------------------------------------
+// Storage of the 14 planes (lbm_params.storage).  Every kernel computes in
+// FP32: a load widens, a store rounds to nearest even.  FP16 holds the values
+// scaled by 2^12, so that deviations down to 1.5e-8 stay in its normal range
+// (stored magnitudes up to 16; larger ones overflow to infinity and raise
+// LBM_ENUMERIC); the power-of-two scale is exact both ways.  BF16 has FP32's
+// exponent range and needs no scale.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Elem;
+template <>
+struct Elem<float> {
+    __host__ __device__ static float ld(float v) { return v; }
+    __host__ __device__ static float st(float v) { return v; }
+};
+template <>
+struct Elem<__nv_bfloat16> {
+    __host__ __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __host__ __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+constexpr float kHalfScale = 4096.f;
+template <>
+struct Elem<__half> {
+    __host__ __device__ static float ld(__half v) { return __half2float(v) * (1.f / kHalfScale); }
+    __host__ __device__ static __half st(float v) { return __float2half_rn(v * kHalfScale); }
+};
+// Bytes per stored population.
+__host__ __device__ constexpr int storage_bytes(int storage) { return storage == LBM_STORE_FP32 ? 4 : 2; }
+
 // Per-node state bytes of the flag map.
 constexpr uint8_t kFluid = 0;   // fluid at the previous and the current time
 constexpr uint8_t kSolid = 1;   // inside a particle at the current time
@@ -71,6 +102,7 @@ struct PartSoA {
 struct Dev {
     int nx, ny, pitch, np;
     long long ps; // plane stride in elements
+    int storage;  // LBM_STORE_*: element type of the planes
     int per_x, per_y;
     // physics (FP32 for the lattice, FP64 for particles)
     float s_e, s_eps, s_q, s_nu, q_k, q_e, q_nu;
@@ -435,25 +467,26 @@ __host__ __device__ inline void slot_dir_line(int s, int N, int &k, int &line)
 enum KernelKind { kKLinks = 0, kKParticles, kKClear, kKRaster, kKFlags, kKStreamCollide,
                   kKInit, kKFields, kNumKernelKinds };
 
-cudaError_t launch_stream_collide(const Dev &D, const float *Ain, float *Aout, const int *own_cur,
+// Planes are passed untyped: their element type is D.storage.
+cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, const int *own_cur,
                                   int parity, cudaStream_t s);
 // mode 0: fluid at rest (unit density, T_init) then collide; mode 1: collide
 // the pre-collision values read from Ain at each node.
-cudaError_t launch_init_collide(const Dev &D, const float *Ain, float *Aout, float T_init, int mode,
+cudaError_t launch_init_collide(const Dev &D, const void *Ain, void *Aout, float T_init, int mode,
                                 cudaStream_t s);
-cudaError_t launch_fields(const Dev &D, const float *A, int row0, int rows, float *rho, float *ux,
+cudaError_t launch_fields(const Dev &D, const void *A, int row0, int rows, float *rho, float *ux,
                           float *uy, float *T, cudaStream_t s);
-cudaError_t launch_links(const Dev &D, float *A, const int *own_cur, int parity,
+cudaError_t launch_links(const Dev &D, void *A, const int *own_cur, int parity,
                          const CUtensorMap &tmA, cudaStream_t s);
 // 3-D tensor map (x, y, plane) over one distribution buffer, for the link
 // kernel's TMA tile loads.
-cudaError_t make_plane_map(const Dev &D, const float *A, CUtensorMap *m);
+cudaError_t make_plane_map(const Dev &D, const void *A, CUtensorMap *m);
 // Shared memory of the link kernel for zones of side N; prepare_links sets the
 // kernel's shared-memory limit and D.link_ahead (call outside stream capture).
-size_t link_smem_bytes(int N);
+size_t link_smem_bytes(int N, int storage);
 // Whether the link kernel holds a zone of side N (tile rows of at most 64
 // columns, shared memory within 200 KB).
-bool link_zone_supported(int N);
+bool link_zone_supported(int N, int storage);
 cudaError_t prepare_links(Dev &D);
 cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s);
 cudaError_t launch_clear(const Dev &D, int *own_nxt, cudaStream_t s);
