@@ -290,38 +290,70 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
     if (y >= D.ny) return; // uniform across the warp: blockDim.x is a multiple of 32
     const bool act = x0 < D.pitch; // the pitch is a multiple of 32, so all V nodes are in the row
     float c[V][kPop];
+    // A warp whose nodes and their neighbours all lie strictly inside the
+    // cavity (the common case) pulls without any wall, seam or range test.
+    const int xw = x0 - lane * V; // first node of the warp (a warp spans one row)
+    const bool interior = y >= 1 && y + 1 < D.ny && xw >= 1 && xw + 32 * V + 1 <= D.nx;
+    if (interior) {
+        const T *b0 = Ain + (long long)y * D.pitch + x0;
 #pragma unroll
-    for (int p = 0; p < kPop; ++p) {
-        const int d = pdir(p);
-        const int dx = ex(d), dy = ey(d);
-        int ys = y - dy;
-        bool rowok = ys >= 0 && ys < D.ny;
-        if (!rowok && D.per_y) {
-            ys = ys < 0 ? ys + D.ny : ys - D.ny;
-            rowok = true;
+        for (int p = 0; p < kPop; ++p) {
+            const int d = pdir(p);
+            const int dx = ex(d), dy = ey(d);
+            const T *src = b0 + (long long)p * D.ps - (long long)dy * D.pitch;
+            float v[V];
+            Vec<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src)), v);
+            if (dx == 0) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) c[k][p] = v[k];
+            } else if (dx == 1) { // pull from x - 1
+                float l = __shfl_up_sync(kFull, v[V - 1], 1);
+                if (lane == 0) l = E::ld(__ldg(src - 1));
+                c[0][p] = l;
+#pragma unroll
+                for (int k = 1; k < V; ++k) c[k][p] = v[k - 1];
+            } else { // pull from x + 1
+                float r = __shfl_down_sync(kFull, v[0], 1);
+                if (lane == 31) r = E::ld(__ldg(src + V));
+#pragma unroll
+                for (int k = 0; k + 1 < V; ++k) c[k][p] = v[k + 1];
+                c[V - 1][p] = r;
+            }
         }
-        const T *src = Ain + (long long)p * D.ps + (long long)(rowok ? ys : 0) * D.pitch;
-        float v[V];
-        if (act && rowok) Vec<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src + x0)), v);
-        else {
+    } else {
 #pragma unroll
-            for (int k = 0; k < V; ++k) v[k] = 0.f;
-        }
-        if (dx == 0) {
+        for (int p = 0; p < kPop; ++p) {
+            const int d = pdir(p);
+            const int dx = ex(d), dy = ey(d);
+            int ys = y - dy;
+            bool rowok = ys >= 0 && ys < D.ny;
+            if (!rowok && D.per_y) {
+                ys = ys < 0 ? ys + D.ny : ys - D.ny;
+                rowok = true;
+            }
+            const T *src = Ain + (long long)p * D.ps + (long long)(rowok ? ys : 0) * D.pitch;
+            float v[V];
+            if (act && rowok) Vec<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src + x0)), v);
+            else {
 #pragma unroll
-            for (int k = 0; k < V; ++k) c[k][p] = v[k];
-        } else if (dx == 1) { // pull from x - 1
-            float l = __shfl_up_sync(kFull, v[V - 1], 1);
-            if (lane == 0) l = (act && rowok && x0 >= 1) ? E::ld(__ldg(src + x0 - 1)) : 0.f;
-            c[0][p] = l;
+                for (int k = 0; k < V; ++k) v[k] = 0.f;
+            }
+            if (dx == 0) {
 #pragma unroll
-            for (int k = 1; k < V; ++k) c[k][p] = v[k - 1];
-        } else { // pull from x + 1
-            float r = __shfl_down_sync(kFull, v[0], 1);
-            if (lane == 31) r = (act && rowok && x0 + V < D.pitch) ? E::ld(__ldg(src + x0 + V)) : 0.f;
+                for (int k = 0; k < V; ++k) c[k][p] = v[k];
+            } else if (dx == 1) { // pull from x - 1
+                float l = __shfl_up_sync(kFull, v[V - 1], 1);
+                if (lane == 0) l = (act && rowok && x0 >= 1) ? E::ld(__ldg(src + x0 - 1)) : 0.f;
+                c[0][p] = l;
 #pragma unroll
-            for (int k = 0; k + 1 < V; ++k) c[k][p] = v[k + 1];
-            c[V - 1][p] = r;
+                for (int k = 1; k < V; ++k) c[k][p] = v[k - 1];
+            } else { // pull from x + 1
+                float r = __shfl_down_sync(kFull, v[0], 1);
+                if (lane == 31) r = (act && rowok && x0 + V < D.pitch) ? E::ld(__ldg(src + x0 + V)) : 0.f;
+#pragma unroll
+                for (int k = 0; k + 1 < V; ++k) c[k][p] = v[k + 1];
+                c[V - 1][p] = r;
+            }
         }
     }
     if (!act) return;
@@ -331,7 +363,7 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
         const int x = x0 + k;
         const uint8_t fl = D.flags[(long long)y * D.pitch + x];
         if (x < D.nx && fl != kSolid) {
-            if (y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1 || fl == kNewborn) {
+            if (fl == kNewborn || (!interior && (y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1))) {
                 float tmp[kPop];
                 const int r = slow_node(D, Ain, own_cur, x, y, fl, tmp);
                 if (r) {
