@@ -9,8 +9,10 @@
 //
 // One thread per node.  A pull from x - 1 or x + 1 takes the value from the
 // neighbouring lane by a warp shuffle (one scalar load at the warp edge), so
-// the x-shifted planes cost no extra HBM traffic.  Nodes next to a cavity
-// wall, periodic seam or newborn node take a general (scalar) path.
+// the x-shifted planes cost no extra HBM traffic.  The nodes of the cavity
+// frame (walls, periodic seams) and newborn nodes take a general (scalar)
+// path in a second, small kernel (k_boundary) that runs concurrently with
+// the streaming kernel and keeps that code and its registers out of it.
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -55,11 +57,12 @@ __device__ float pull_general(const Dev &D, const T *__restrict__ A, int x, int 
 // Returns 0 for a general pull, else 1 + the refill class (1 quadratic,
 // 2 linear, 3 copy, 4 equilibrium).
 template <typename T>
-__device__ __noinline__ int slow_node(const Dev &D, const T *__restrict__ A,
+__device__ __forceinline__ int slow_node(const Dev &D, const T *__restrict__ A,
                                       const int *__restrict__ own_cur, int x, int y, uint8_t fl,
                                       float *out)
 {
     if (fl != kNewborn) {
+#pragma unroll
         for (int p = 0; p < kPop; ++p) out[p] = pull_general(D, A, x, y, p);
         return 0;
     }
@@ -96,6 +99,7 @@ __device__ __noinline__ int slow_node(const Dev &D, const T *__restrict__ A,
         float c2 = nvalid == 3 ? -3.f : nvalid == 2 ? -1.f : 0.f;
         float c3 = nvalid == 3 ? 1.f : 0.f;
         const int x1 = x + ex(c), y1 = y + ey(c);
+#pragma unroll
         for (int i = 0; i < kQ9; ++i) {
             float v = c1 * pull_general(D, A, x1, y1, i);
             if (nvalid >= 2) v += c2 * pull_general(D, A, x1 + ex(c), y1 + ey(c), i);
@@ -132,7 +136,7 @@ __device__ __forceinline__ bool collide(const Dev &D, float *c)
     const float jy = (f2 - f4) + (f5 + f6) - (f7 + f8);
     const float Fx = D.bfx;
     const float Fy = rho * D.gbeta * (T - D.T0) + D.bfy;
-    const float inv = 1.f / rho;
+    const float inv = __frcp_rn(rho); // correctly rounded, as 1 / rho
     const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv;
     const float sa = (f1 + f2) + (f3 + f4), sd = (f5 + f6) + (f7 + f8);
     const float m1 = -4.f * f0 - sa + 2.f * sd;
@@ -259,7 +263,7 @@ struct Vec<__half, 2> {
 template <typename T, int V>
 __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
     k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout,
-                     const int *__restrict__ own_cur, int parity, int ahead)
+                     const int *__restrict__ own_cur, int parity, int ahead_y, int ahead_x)
 {
     using E = Elem<T>;
     using VW = typename Vec<T, V>::W;
@@ -267,8 +271,13 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
     const int lane = threadIdx.x & 31;
     const int span = (int)blockDim.x * V; // nodes of a row per block
     if (threadIdx.x < kPop && threadIdx.y == 0) {
-        const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x + ahead;
-        const int by = (int)(lin / gridDim.x), bx = (int)(lin % gridDim.x);
+        // the block `ahead` places later in launch order: ahead = ahead_y
+        // grid rows + ahead_x blocks (ahead_x < gridDim.x)
+        int bx = (int)blockIdx.x + ahead_x, by = (int)blockIdx.y + ahead_y;
+        if (bx >= (int)gridDim.x) {
+            bx -= (int)gridDim.x;
+            ++by;
+        }
         const int yb = by * (int)blockDim.y;
         const int xs = bx * span;
         const int lo = max(xs - kAl, 0), hi = min(xs + span + kAl, D.pitch);
@@ -357,36 +366,86 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
         }
     }
     if (!act) return;
-    bool ok = true;
+    bool ok = true, gen[V], anygen = false;
 #pragma unroll
     for (int k = 0; k < V; ++k) {
         const int x = x0 + k;
         const uint8_t fl = D.flags[(long long)y * D.pitch + x];
+        gen[k] = false;
         if (x < D.nx && fl != kSolid) {
-            if (fl == kNewborn || (!interior && (y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1))) {
-                float tmp[kPop];
-                const int r = slow_node(D, Ain, own_cur, x, y, fl, tmp);
-                if (r) {
-                    unsigned n4[4] = {1u, r == 2, r == 3, r == 4};
-                    flush_counters(D, parity, n4);
-                }
-#pragma unroll
-                for (int p = 0; p < kPop; ++p) c[k][p] = tmp[p];
-            }
-            ok &= collide(D, c[k]);
+            // frame and newborn nodes belong to k_boundary, which writes them
+            gen[k] = fl == kNewborn || (!interior && (y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1));
+            if (!gen[k]) ok &= collide(D, c[k]);
         } else {
 #pragma unroll
             for (int p = 0; p < kPop; ++p) c[k][p] = 0.f;
         }
+        anygen |= gen[k];
     }
     T *dst = Aout + (long long)y * D.pitch + x0;
+    if (!anygen) {
 #pragma unroll
-    for (int p = 0; p < kPop; ++p) {
-        float v[V];
+        for (int p = 0; p < kPop; ++p) {
+            float v[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) v[k] = c[k][p];
-        *reinterpret_cast<VW *>(dst + (long long)p * D.ps) = Vec<T, V>::pack(v);
+            for (int k = 0; k < V; ++k) v[k] = c[k][p];
+            *reinterpret_cast<VW *>(dst + (long long)p * D.ps) = Vec<T, V>::pack(v);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (!gen[k]) {
+#pragma unroll
+                for (int p = 0; p < kPop; ++p) dst[(long long)p * D.ps + k] = E::st(c[k][p]);
+            }
     }
+    if (!ok) atomicOr(&D.status->err, kErrNumeric);
+}
+
+// General path, beside the stream-collide kernel (it reads only the previous
+// state and writes only nodes that kernel leaves alone): the fluid nodes of
+// the cavity frame (walls, periodic seams) and the newborn nodes listed by
+// k_flags, each pulled (or refilled, Sec. 2.5) by slow_node and collided.
+// A fixed grid strides over the 2 nx + 2 (ny - 2) frame nodes and then the
+// list, whose length the device holds.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_boundary(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, const int *__restrict__ own_cur,
+               int parity)
+{
+    using E = Elem<T>;
+    const int nx = D.nx, ny = D.ny;
+    const int nframe = 2 * nx + 2 * (ny - 2);
+    const int nlist = min((int)D.status->nb, D.newborn_cap);
+    unsigned n4[4] = {0u, 0u, 0u, 0u};
+    bool ok = true;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nframe + nlist; idx += gridDim.x * blockDim.x) {
+        int x, y;
+        if (idx < nx) { x = idx; y = 0; }
+        else if (idx < 2 * nx) { x = idx - nx; y = ny - 1; }
+        else if (idx < 2 * nx + (ny - 2)) { x = 0; y = 1 + idx - 2 * nx; }
+        else if (idx < nframe) { x = nx - 1; y = 1 + idx - 2 * nx - (ny - 2); }
+        else {
+            const int n = D.newborn[idx - nframe];
+            y = n / nx;
+            x = n - y * nx;
+        }
+        const long long o = (long long)y * D.pitch + x;
+        const uint8_t fl = D.flags[o];
+        if (fl == kSolid) continue;
+        float c[kPop];
+        const int r = slow_node(D, Ain, own_cur, x, y, fl, c);
+        if (r) {
+            n4[0] += 1u;
+            n4[1] += r == 2;
+            n4[2] += r == 3;
+            n4[3] += r == 4;
+        }
+        ok &= collide(D, c);
+#pragma unroll
+        for (int p = 0; p < kPop; ++p) Aout[(long long)p * D.ps + o] = E::st(c[p]);
+    }
+    flush_counters(D, parity, n4);
     if (!ok) atomicOr(&D.status->err, kErrNumeric);
 }
 
@@ -470,7 +529,22 @@ cudaError_t stream_collide_t(const Dev &D, const void *Ain, void *Aout, const in
     dim3 block(bx, by);
     dim3 grid((tx + bx - 1) / bx, (D.ny + by - 1) / by);
     k_stream_collide<T, V><<<grid, block, 0, s>>>(D, static_cast<const T *>(Ain), static_cast<T *>(Aout),
-                                                  own_cur, parity, resident);
+                                                  own_cur, parity, resident / (int)grid.x,
+                                                  resident % (int)grid.x);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t boundary_t(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity, cudaStream_t s)
+{
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks = max(1, 2 * sms);
+    }
+    k_boundary<T><<<blocks, 128, 0, s>>>(D, static_cast<const T *>(Ain), static_cast<T *>(Aout), own_cur, parity);
     return cudaGetLastError();
 }
 
@@ -503,6 +577,17 @@ cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, con
     case LBM_STORE_FP32: return stream_collide_t<float, 1>(D, Ain, Aout, own_cur, parity, s);
     case LBM_STORE_BF16: return stream_collide_t<__nv_bfloat16, 2>(D, Ain, Aout, own_cur, parity, s);
     case LBM_STORE_FP16: return stream_collide_t<__half, 2>(D, Ain, Aout, own_cur, parity, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_boundary(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
+                            cudaStream_t s)
+{
+    switch (D.storage) {
+    case LBM_STORE_FP32: return boundary_t<float>(D, Ain, Aout, own_cur, parity, s);
+    case LBM_STORE_BF16: return boundary_t<__nv_bfloat16>(D, Ain, Aout, own_cur, parity, s);
+    case LBM_STORE_FP16: return boundary_t<__half>(D, Ain, Aout, own_cur, parity, s);
     default: return cudaErrorInvalidValue;
     }
 }

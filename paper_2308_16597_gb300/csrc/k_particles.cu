@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kLinkThreads)
     const int nw = link_occ_words(Nm), capm = 12 * Nm - 12;
     unsigned *occ = reinterpret_cast<unsigned *>(Om + wy); // [nw]
     unsigned *pre = occ + nw;                               // [nw]
-    int *info = reinterpret_cast<int *>(pre + nw);          // [cap] (b << 16) | a of the slot's link
+    int *info = reinterpret_cast<int *>(pre + nw);          // [cap] k | a << 4 | b << 12 of the slot's link
     int *list = info + capm;                                // [cap] valid slots in order
     float *lbx = reinterpret_cast<float *>(list + capm);    // [cap] per-link brackets
     float *lby = lbx + capm;
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kLinkThreads)
                 }
                 const unsigned bit = 1u << (sl & 31);
                 if (atomicOr(&occ[sl >> 5], bit) & bit) s_over = 1u;
-                else info[sl] = (b << 16) | a;
+                else info[sl] = k | (a << 4) | (b << 12);
             }
         }
     }
@@ -284,10 +284,9 @@ __global__ void __launch_bounds__(kLinkThreads)
     auto fluid = [&](int i, int j) -> bool { return (Fm[j - YA] >> (i - XA)) & 1ull; };
     for (int li = tid; li < nvalid; li += kLinkThreads) {
         const int sl = list[li];
-        int k, line;
-        slot_dir_line(sl, N, k, line);
+        const int inf = info[sl], k = inf & 15;
         const int kx = ex(k), ky = ey(k);
-        const int fi = X0 + (info[sl] & 0xffff), fj = Y0 + (info[sl] >> 16);
+        const int fi = X0 + ((inf >> 4) & 255), fj = Y0 + (inf >> 12);
         float dxf, dyf;
         const float q = link_q_df(fi, fj, k, dk, dxf, dyf);
         D.slot_node[base + sl] = fj * D.nx + fi;
@@ -395,6 +394,7 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int a = blockIdx.x * 32 + warp;
     if (blockIdx.x == 0 && threadIdx.x < kNumCounters) D.status->cnt[parity ^ 1][threadIdx.x] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) D.status->nb = 0u;
     const bool me = a < D.np;
     float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 ca = make_float2(1.f, 0.f);
@@ -538,6 +538,7 @@ __global__ void __launch_bounds__(kBoxThreads)
     k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate)
 {
     const int p = blockIdx.x;
+    const bool list = rotate != 0; // a step (not the initial flags): list the newborn nodes
     const Box B0 = box_of(D.geo_cur[p]);
     const Box B1 = box_of(D.geo_nxt[p]);
     for (int pass = 0; pass < 2; ++pass) {
@@ -548,6 +549,14 @@ __global__ void __launch_bounds__(kBoxThreads)
             const long long n = (long long)j * D.nx + i;
             const uint8_t f = own_nxt[n] >= 0 ? kSolid : own_cur[n] >= 0 ? kNewborn : kFluid;
             D.flags[(long long)j * D.pitch + i] = f;
+            // each newborn node once: by the particle that owned it, from
+            // its old box; frame nodes are always on the general path
+            if (list && pass == 0 && f == kNewborn && own_cur[n] == p && i > 0 && i < D.nx - 1 && j > 0 &&
+                j < D.ny - 1) {
+                const unsigned at = atomicAdd(&D.status->nb, 1u);
+                if (at < (unsigned)D.newborn_cap) D.newborn[at] = (int)n;
+                else atomicOr(&D.status->err, kErrOverflow);
+            }
         }
     }
     if (!rotate) return;

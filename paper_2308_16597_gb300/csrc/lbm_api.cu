@@ -25,7 +25,8 @@ struct Layout {
     long long ps = 0;
     size_t nslots = 0;
     size_t A[2], own[2], flags, slot_node, slot_q, slot_base, cur, nxt, prev, force, pos4, prc, lsum,
-        geo[3], status, pack, stage, total;
+        geo[3], status, pack, stage, newborn, total;
+    int newborn_cap = 0;
     int stage_rows = 0;
 };
 
@@ -119,6 +120,12 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
     L.pack = take((size_t)n * sizeof(lbm_particle));
     L.stage_rows = (int)std::max<size_t>(1, std::min<size_t>(d->ny, kStageBytes / (16 * (size_t)d->nx)));
     L.stage = take((size_t)4 * L.stage_rows * d->nx * sizeof(float));
+    // newborn nodes of one step: a disk moving less than one node per step
+    // uncovers fewer than 2N nodes; room for 4N per particle
+    int zmax = 0;
+    for (int a = 0; a < n; ++a) zmax = std::max(zmax, zone_size(p[a].r));
+    L.newborn_cap = std::max(1024, 4 * n * zmax);
+    L.newborn = take((size_t)L.newborn_cap * sizeof(int));
     L.total = off;
 }
 
@@ -131,6 +138,7 @@ PartSoA soa_at(char *base, size_t off, int n)
 const char *kKernelNames[kNumKernelKinds] = {"link_gather_bb_force", "particle_update",
                                              "owner_clear",          "owner_raster",
                                              "node_flags",           "stream_collide",
+                                             "boundary_refill",
                                              "init_collide",         "fields"};
 
 } // namespace
@@ -143,6 +151,8 @@ struct lbm_handle {
     char *ws = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t side = nullptr;           // branch for k_boundary beside k_stream_collide
+    cudaEvent_t fork = nullptr, join = nullptr;
     Dev D;
     void *A[2]; // planes of D.storage elements
     int *own[2];
@@ -237,11 +247,25 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
             return rc;
         if ((rc = timed(h, kKFlags, st, [&] { return launch_flags(D, oc, on, 1, st); }))) return rc;
     }
-    return timed(h, kKStreamCollide, st,
-                 [&] { return launch_stream_collide(D, Ain, Aout, oc, par, st); });
+    if (h->timing && st == h->stream) { // per-kernel timing: one stream, one kernel at a time
+        if ((rc = timed(h, kKStreamCollide, st, [&] { return launch_stream_collide(D, Ain, Aout, oc, par, st); })))
+            return rc;
+        return timed(h, kKBoundary, st, [&] { return launch_boundary(D, Ain, Aout, oc, par, st); });
+    }
+    // k_boundary and k_stream_collide write disjoint nodes of Aout and read
+    // only inputs complete at this point: run them side by side
+    CK(h, cudaEventRecord(h->fork, st));
+    CK(h, cudaStreamWaitEvent(h->side, h->fork, 0));
+    if ((rc = timed(h, kKBoundary, h->side, [&] { return launch_boundary(D, Ain, Aout, oc, par, h->side); })))
+        return rc;
+    CK(h, cudaEventRecord(h->join, h->side));
+    if ((rc = timed(h, kKStreamCollide, st, [&] { return launch_stream_collide(D, Ain, Aout, oc, par, st); })))
+        return rc;
+    CK(h, cudaStreamWaitEvent(st, h->join, 0));
+    return LBM_OK;
 }
 
-int kernels_per_step(const lbm_handle *h) { return h->np > 0 ? 6 : 2; }
+int kernels_per_step(const lbm_handle *h) { return h->np > 0 ? 7 : 3; }
 
 int capture(lbm_handle *h, int par)
 {
@@ -316,6 +340,8 @@ void fill_dev(lbm_handle *h)
     D.s_rep = P.s_rep;
     D.fixed = (P.flags & LBM_FLAG_FIXED_PARTICLES) ? 1 : 0;
     D.flags = reinterpret_cast<uint8_t *>(ws + L.flags);
+    D.newborn = reinterpret_cast<int *>(ws + L.newborn);
+    D.newborn_cap = L.newborn_cap;
     D.slot_node = reinterpret_cast<int *>(ws + L.slot_node);
     D.slot_q = reinterpret_cast<float *>(ws + L.slot_q);
     D.slot_base = reinterpret_cast<int *>(ws + L.slot_base);
@@ -435,6 +461,10 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
         return code;
     };
     if (cudaMemsetAsync(h->D.status, 0, sizeof(Status), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(LBM_ECUDA);
     if (prepare_links(h->D) != cudaSuccess) return fail(LBM_ECUDA);
     for (int b = 0; b < 2 && n > 0; ++b)
         if (make_plane_map(h->D, h->A[b], &h->tmA[b]) != cudaSuccess) return fail(LBM_ECUDA);
@@ -541,6 +571,12 @@ int lbm_destroy(lbm_handle *h)
     for (int b = 0; b < 2; ++b)
         if (h->gexec[b]) cudaGraphExecDestroy(h->gexec[b]);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     for (auto &e : h->ev) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);

@@ -91,6 +91,8 @@ struct Status {
     unsigned int err;
     unsigned int pad;
     unsigned long long cnt[2][kNumCounters]; // double-buffered by step parity
+    unsigned int nb;     // newborn nodes listed this step (reset by the particle update)
+    unsigned int nb_pad;
 };
 
 // Structure-of-arrays particle state on the device (FP64).
@@ -114,6 +116,8 @@ struct Dev {
     int link_ahead;    // link-kernel CTAs resident on the GPU (distance of its L2 prefetch)
     // device buffers
     uint8_t *flags;    // [ny][pitch]
+    int *newborn;      // [newborn_cap]: j * nx + i of this step's newborn nodes off the cavity frame
+    int newborn_cap;
     int *slot_node;    // [nslots]
     float *slot_q;     // [nslots]
     int *slot_base;    // [np + 1]
@@ -380,13 +384,16 @@ __device__ __forceinline__ float bouzidi32(float q, float fk0, float fk1, float 
         lvl = 2;
         return fk0 + wall;
     }
+    // q > 1/2: coefficients from the two reciprocals 1/q and 1/(2q + 1)
+    const float rq = __frcp_rn(q);
     if (have1) {
         lvl = 0;
-        const float cc = 1.f / (q * (2.f * q + 1.f));
-        return cc * fk0 + (2.f * q - 1.f) / q * fb0 - (2.f * q - 1.f) / (2.f * q + 1.f) * fb1 + cc * wall;
+        const float r1 = __frcp_rn(2.f * q + 1.f);
+        const float cc = rq * r1, t = 2.f * q - 1.f;
+        return cc * fk0 + t * rq * fb0 - t * r1 * fb1 + cc * wall;
     }
     lvl = 1;
-    const float h = 0.5f / q;
+    const float h = 0.5f * rq;
     return h * fk0 + (2.f * q - 1.f) * h * fb0 + h * wall;
 }
 
@@ -397,13 +404,11 @@ __device__ __forceinline__ float thermal32(float q, float gk0, float gk1, float 
                                            float wT)
 {
     if (have1) {
-        const float c23 = (2.f * q - 1.f) / (2.f * q + 1.f), c4 = 2.f / (2.f * q + 1.f);
-        return -gk0 + c23 * (gk1 + gb0) + c4 * wT;
+        const float r1 = __frcp_rn(2.f * q + 1.f);
+        return -gk0 + (2.f * q - 1.f) * r1 * (gk1 + gb0) + 2.f * r1 * wT;
     }
     return -gk0 + wT;
 }
-
-
 
 // Zone point (a, b) of the t-th node on line `line` of direction k; false
 // when it falls outside the N x N zone.  e1/e3: rows (line = b); e2/e4:
@@ -465,11 +470,15 @@ __host__ __device__ inline void slot_dir_line(int s, int N, int &k, int &line)
 // Kernel launchers (defined in k_fluid.cu and k_particles.cu).
 // ---------------------------------------------------------------------------
 enum KernelKind { kKLinks = 0, kKParticles, kKClear, kKRaster, kKFlags, kKStreamCollide,
-                  kKInit, kKFields, kNumKernelKinds };
+                  kKBoundary, kKInit, kKFields, kNumKernelKinds };
 
 // Planes are passed untyped: their element type is D.storage.
 cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, const int *own_cur,
                                   int parity, cudaStream_t s);
+// Nodes the stream-collide kernel leaves to the general path: the cavity
+// frame (x = 0, nx - 1, y = 0, ny - 1) and the listed newborn nodes.
+cudaError_t launch_boundary(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
+                            cudaStream_t s);
 // mode 0: fluid at rest (unit density, T_init) then collide; mode 1: collide
 // the pre-collision values read from Ain at each node.
 cudaError_t launch_init_collide(const Dev &D, const void *Ain, void *Aout, float T_init, int mode,
