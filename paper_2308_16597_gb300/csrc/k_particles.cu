@@ -6,8 +6,9 @@
 //                particle in FP64;
 //   k_particles  Newton-Euler update with gravity, buoyancy and spring
 //                repulsion (Sec. 2.2, Sec. 2.4);
-//   k_clear, k_raster, k_flags
-//                owner map and node flags at the new positions.
+//   k_raster, k_flags
+//                owner map and node flags at the new positions (the
+//                owner map is cleared over the old zones by k_links).
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -20,7 +21,7 @@ namespace {
 
 constexpr int kLinkThreads = 128;
 constexpr int kBoxThreads = 128;
-constexpr int kPartThreads = 1024;
+constexpr int kPartThreads = 256;
 constexpr double kPi = 3.14159265358979323846;
 
 __device__ __forceinline__ bool inside(const Dev &D, int i, int j)
@@ -114,6 +115,8 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 }
 
 // One CTA per particle.  Phases:
+//  0. clear the particle's zone one step back in the owner map that the
+//     raster fills next;
 //  1. the warps read the owner map over the particle's window (zone plus
 //     the two-node margin of the bounce-back stencil) and record per row a
 //     fluid mask and an owned-by-this-particle mask (one ballot per 32
@@ -139,7 +142,7 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 template <typename T>
 __global__ void __launch_bounds__(kLinkThreads)
     k_links(const __grid_constant__ CUtensorMap tmA, const Dev D, T *A, const int *__restrict__ own,
-            int parity, int ahead)
+            int *__restrict__ own_nxt, int parity, int ahead)
 {
     using E = Elem<T>;
     constexpr int es = (int)sizeof(T), al = 16 / es;
@@ -168,6 +171,20 @@ __global__ void __launch_bounds__(kLinkThreads)
     float *ltq = lby + capm;
     int *lcode = reinterpret_cast<int *>(ltq + capm);
     int *ltz = lcode + capm;
+
+    // ---- 0. the owner map the raster fills next (positions n + 1) still
+    // holds positions n - 1: clear this particle's zone of that time
+    {
+        const GeomRec Gp = D.geo_prev[p];
+        for (int r = warp; r < Gp.N; r += kLinkThreads / 32) {
+            const int j = Gp.Y0 + r;
+            if (j < 0 || j >= D.ny) continue;
+            for (int c = lane; c < Gp.N; c += 32) {
+                const int i = Gp.X0 + c;
+                if (i >= 0 && i < D.nx) own_nxt[(long long)j * D.nx + i] = -1;
+            }
+        }
+    }
 
     // ---- 1. owner masks (all warps) and look-ahead prefetches
     if (tid == 0) {
@@ -358,14 +375,17 @@ __device__ __forceinline__ double repulsion(double gap, double s, double eps, do
 // Total force = hydrodynamic (assembled from the link sums) + buoyant weight
 // -(rho_p - rho_f) pi r^2 g y-hat + repulsion (walls, and every other disk
 // with C_ab the mean of the two force scales C = pi r^2 (rho_p - rho_f) g).
-// Each block takes 32 particles: warp w screens particle w against all disks
-// in shared-memory tiles (FP32 centres with a one-lattice-unit margin) and
+// Each block takes 8 particles: warp w screens particle w against all disks
+// in shared-memory tiles of 1600 (FP32 centres with a one-lattice-unit
+// margin; a tile is loaded with all its loads in flight at once) and
 // evaluates the pairs in reach from double-float centre differences; lane l
-// of warp 0 then sums, integrates and stores particle l in FP64, so 32
-// particles share every FP64 instruction.  Integration: U' = U + F/M,
-// X' = X + (U + U')/2, Omega' = Omega + T/I, theta' = theta + (Omega + Omega')/2
-// with M = rho_p pi r^2 and I = M r^2 / 2.
-constexpr int kPartTile = 512;
+// of warp 0 then sums, integrates and stores particle l in FP64.  Small
+// blocks let four of them share an SM, so that the latency of one block's
+// tile loads and FP64 tail overlaps the others' work.  Integration:
+// U' = U + F/M, X' = X + (U + U')/2, Omega' = Omega + T/I,
+// theta' = theta + (Omega + Omega')/2 with M = rho_p pi r^2 and I = M r^2 / 2.
+constexpr int kPartTile = 1600;
+constexpr int kPartPerBlock = kPartThreads / 32;
 
 // Pair repulsion on disk a from disk b (FP32 from double-float centres).
 __device__ __noinline__ void pair_force(float4 pa, float2 ca, float4 pb, float2 cb, float s_rep,
@@ -390,9 +410,9 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
 {
     __shared__ float4 sp[kPartTile];
     __shared__ float2 sc[kPartTile];
-    __shared__ float sred[4][32];
+    __shared__ float sred[4][kPartPerBlock];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int a = blockIdx.x * 32 + warp;
+    const int a = blockIdx.x * kPartPerBlock + warp;
     if (blockIdx.x == 0 && threadIdx.x < kNumCounters) D.status->cnt[parity ^ 1][threadIdx.x] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) D.status->nb = 0u;
     const bool me = a < D.np;
@@ -408,6 +428,7 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
     for (int t0 = 0; t0 < D.np; t0 += kPartTile) {
         const int nb = min(kPartTile, D.np - t0);
         __syncthreads();
+#pragma unroll 8
         for (int k = threadIdx.x; k < nb; k += kPartThreads) {
             sp[k] = D.pos4[t0 + k];
             sc[k] = D.prc[t0 + k];
@@ -428,8 +449,8 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
         sred[2][warp] = fhy; sred[3][warp] = fly;
     }
     __syncthreads();
-    if (warp != 0) return;
-    const int b = blockIdx.x * 32 + lane;
+    if (warp != 0 || lane >= kPartPerBlock) return;
+    const int b = blockIdx.x * kPartPerBlock + lane;
     if (b >= D.np) return;
     double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
     double th = D.cur.th[b], om = D.cur.om[b];
@@ -477,20 +498,6 @@ struct Box {
 };
 __device__ __forceinline__ Box box_of(const GeomRec &G) { return Box{G.X0, G.Y0, G.N}; }
 
-// Reset the zone of each disk's position one step back in the owner map
-// that is about to receive the new positions, and in the flag map.
-__global__ void __launch_bounds__(kBoxThreads) k_clear(const Dev D, int *own_nxt)
-{
-    const int p = blockIdx.x;
-    const Box B = box_of(D.geo_prev[p]);
-    for (int idx = threadIdx.x; idx < B.N * B.N; idx += kBoxThreads) {
-        const int i = B.X0 + idx % B.N, j = B.Y0 + idx / B.N;
-        if (!inside(D, i, j)) continue;
-        own_nxt[(long long)j * D.nx + i] = -1;
-        D.flags[(long long)j * D.pitch + i] = kFluid;
-    }
-}
-
 // Owner map: node (i,j) belongs to disk p iff (i - x)^2 + (j - y)^2 <= r^2
 // (exact FP64); where disks overlap the highest index wins (atomicMax, so
 // the result does not depend on the launch order).  One warp per disk, one
@@ -530,49 +537,70 @@ __global__ void __launch_bounds__(kBoxThreads)
     }
 }
 
-// Flags over the zones of the old and the new position: solid at the new
-// time, newborn (solid before, fluid now) or fluid.  Then each block moves
-// its particle's new state into the current slot and keeps the old position
-// for the next clear.
+// Flags over the rectangle that holds the particle's zones one step back, now
+// and next (so every node whose flag may have changed since the last step):
+// solid at the new time, newborn (solid before, fluid now) or fluid, from
+// the two owner maps.  Warp w takes rows w, w + 4, ... of the rectangle (four
+// at a time, all loads issued first), lane l columns l and l + 32.  During a
+// step each block also moves its particle's new state into the current slot
+// and keeps the old position for the next clear.
 __global__ void __launch_bounds__(kBoxThreads)
     k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate)
 {
     const int p = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kW = kBoxThreads / 32, kU = 4;
     const bool list = rotate != 0; // a step (not the initial flags): list the newborn nodes
-    const Box B0 = box_of(D.geo_cur[p]);
-    const Box B1 = box_of(D.geo_nxt[p]);
-    for (int pass = 0; pass < 2; ++pass) {
-        const Box B = pass ? B1 : B0;
-        for (int idx = threadIdx.x; idx < B.N * B.N; idx += kBoxThreads) {
-            const int i = B.X0 + idx % B.N, j = B.Y0 + idx / B.N;
-            if (!inside(D, i, j)) continue;
-            const long long n = (long long)j * D.nx + i;
-            const uint8_t f = own_nxt[n] >= 0 ? kSolid : own_cur[n] >= 0 ? kNewborn : kFluid;
-            D.flags[(long long)j * D.pitch + i] = f;
-            // each newborn node once: by the particle that owned it, from
-            // its old box; frame nodes are always on the general path
-            if (list && pass == 0 && f == kNewborn && own_cur[n] == p && i > 0 && i < D.nx - 1 && j > 0 &&
-                j < D.ny - 1) {
-                const unsigned at = atomicAdd(&D.status->nb, 1u);
-                if (at < (unsigned)D.newborn_cap) D.newborn[at] = (int)n;
-                else atomicOr(&D.status->err, kErrOverflow);
-            }
+    const Box Ba = box_of(D.geo_prev[p]), Bb = box_of(D.geo_cur[p]), Bc = box_of(D.geo_nxt[p]);
+    if (rotate) {
+        // the new state moves into the current slot (and the current position
+        // into the previous one) while the other threads work on the flags;
+        // every thread has read the three boxes before
+        __syncthreads();
+        switch (threadIdx.x) {
+        case 0: D.px[p] = D.cur.x[p]; D.cur.x[p] = D.nxt.x[p]; break;
+        case 1: D.py[p] = D.cur.y[p]; D.cur.y[p] = D.nxt.y[p]; break;
+        case 2: D.cur.ux[p] = D.nxt.ux[p]; break;
+        case 3: D.cur.uy[p] = D.nxt.uy[p]; break;
+        case 4: D.cur.th[p] = D.nxt.th[p]; break;
+        case 5: D.cur.om[p] = D.nxt.om[p]; break;
+        case 6: D.geo_prev[p] = D.geo_cur[p]; D.geo_cur[p] = D.geo_nxt[p]; break;
+        default: break;
         }
     }
-    if (!rotate) return;
-    __syncthreads();
-    switch (threadIdx.x) {
-    case 0: D.px[p] = D.cur.x[p]; D.cur.x[p] = D.nxt.x[p]; break;
-    case 1: D.py[p] = D.cur.y[p]; D.cur.y[p] = D.nxt.y[p]; break;
-    case 2: D.cur.ux[p] = D.nxt.ux[p]; break;
-    case 3: D.cur.uy[p] = D.nxt.uy[p]; break;
-    case 4: D.cur.th[p] = D.nxt.th[p]; break;
-    case 5: D.cur.om[p] = D.nxt.om[p]; break;
-    case 6: D.geo_prev[p] = D.geo_cur[p]; break;
-    default: break;
+    const int X0 = max(min(min(Ba.X0, Bb.X0), Bc.X0), 0);
+    const int Y0 = max(min(min(Ba.Y0, Bb.Y0), Bc.Y0), 0);
+    const int X1 = min(max(max(Ba.X0 + Ba.N, Bb.X0 + Bb.N), Bc.X0 + Bc.N), D.nx); // exclusive
+    const int Y1 = min(max(max(Ba.Y0 + Ba.N, Bb.Y0 + Bb.N), Bc.Y0 + Bc.N), D.ny);
+    for (int r0 = Y0 + warp; r0 < Y1; r0 += kW * kU) {
+        int oc[kU][2], on[kU][2];
+#pragma unroll
+        for (int t = 0; t < kU; ++t)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = r0 + t * kW, i = X0 + lane + 32 * h;
+                const bool v = j < Y1 && i < X1;
+                const long long n = (long long)j * D.nx + i;
+                oc[t][h] = v ? own_cur[n] : -3;
+                on[t][h] = v ? own_nxt[n] : -3;
+            }
+#pragma unroll
+        for (int t = 0; t < kU; ++t)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (oc[t][h] == -3) continue;
+                const int j = r0 + t * kW, i = X0 + lane + 32 * h;
+                const uint8_t f = on[t][h] >= 0 ? kSolid : oc[t][h] >= 0 ? kNewborn : kFluid;
+                D.flags[(long long)j * D.pitch + i] = f;
+                // each newborn node once: by the particle that owned it; frame
+                // nodes are always on the general path
+                if (list && f == kNewborn && oc[t][h] == p && i > 0 && i < D.nx - 1 && j > 0 && j < D.ny - 1) {
+                    const unsigned at = atomicAdd(&D.status->nb, 1u);
+                    if (at < (unsigned)D.newborn_cap) D.newborn[at] = j * D.nx + i;
+                    else atomicOr(&D.status->err, kErrOverflow);
+                }
+            }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) D.geo_cur[p] = D.geo_nxt[p];
 }
 
 // Geometry records of the current state and of the previous positions.
@@ -631,26 +659,27 @@ cudaError_t prepare_links(Dev &D)
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLinkThreads, smem)) != cudaSuccess)
         return e;
-    D.link_ahead = max(1, sms * per_sm);
+    D.link_ahead = max(1, sms * per_sm); // particles (CTAs) resident at once
     return cudaSuccess;
 }
 
-cudaError_t launch_links(const Dev &D, void *A, const int *own_cur, int parity, const CUtensorMap &tmA,
-                         cudaStream_t s)
+cudaError_t launch_links(const Dev &D, void *A, const int *own_cur, int *own_nxt, int parity,
+                         const CUtensorMap &tmA, cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
     const size_t smem = link_smem_bytes(D.zone_max, D.storage);
+    const int grid = D.np;
     switch (D.storage) {
     case LBM_STORE_FP32:
-        k_links<float><<<D.np, kLinkThreads, smem, s>>>(tmA, D, static_cast<float *>(A), own_cur, parity,
+        k_links<float><<<grid, kLinkThreads, smem, s>>>(tmA, D, static_cast<float *>(A), own_cur, own_nxt, parity,
                                                         D.link_ahead);
         break;
     case LBM_STORE_BF16:
-        k_links<__nv_bfloat16><<<D.np, kLinkThreads, smem, s>>>(tmA, D, static_cast<__nv_bfloat16 *>(A), own_cur,
-                                                                parity, D.link_ahead);
+        k_links<__nv_bfloat16><<<grid, kLinkThreads, smem, s>>>(tmA, D, static_cast<__nv_bfloat16 *>(A), own_cur,
+                                                                own_nxt, parity, D.link_ahead);
         break;
     case LBM_STORE_FP16:
-        k_links<__half><<<D.np, kLinkThreads, smem, s>>>(tmA, D, static_cast<__half *>(A), own_cur, parity,
+        k_links<__half><<<grid, kLinkThreads, smem, s>>>(tmA, D, static_cast<__half *>(A), own_cur, own_nxt, parity,
                                                          D.link_ahead);
         break;
     default: return cudaErrorInvalidValue;
@@ -697,15 +726,8 @@ cudaError_t make_plane_map(const Dev &D, const void *A, CUtensorMap *m)
 
 cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s)
 {
-    const int blocks = D.np > 0 ? (D.np + 31) / 32 : 1;
+    const int blocks = D.np > 0 ? (D.np + kPartPerBlock - 1) / kPartPerBlock : 1;
     k_particles<<<blocks, kPartThreads, 0, s>>>(D, parity);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_clear(const Dev &D, int *own_nxt, cudaStream_t s)
-{
-    if (D.np == 0) return cudaSuccess;
-    k_clear<<<D.np, kBoxThreads, 0, s>>>(D, own_nxt);
     return cudaGetLastError();
 }
 

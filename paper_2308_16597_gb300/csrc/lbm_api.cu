@@ -136,7 +136,7 @@ PartSoA soa_at(char *base, size_t off, int n)
 }
 
 const char *kKernelNames[kNumKernelKinds] = {"link_gather_bb_force", "particle_update",
-                                             "owner_clear",          "owner_raster",
+                                             "owner_raster",
                                              "node_flags",           "stream_collide",
                                              "boundary_refill",
                                              "init_collide",         "fields"};
@@ -228,9 +228,11 @@ int timed(lbm_handle *h, int kind, cudaStream_t st, F &&launch)
 }
 
 // One time step, in the order
-//   gather + bounce-back + force (particle state at n, owner map at n)
+//   gather + bounce-back + force (particle state at n, owner map at n; also
+//   clears the other owner map over the zones at n - 1)
 //   -> particle update (n -> n+1) -> owner map and flags at n+1
-//   -> fused stream + refill + collide of A_n into A_{n+1}.
+//   -> fused stream + collide of A_n into A_{n+1}, beside the general path
+//      (frame and newborn nodes, refill).
 int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
 {
     const Dev &D = h->D;
@@ -238,11 +240,10 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
     int *oc = h->own[par], *on = h->own[par ^ 1];
     int rc;
     if (h->np > 0) {
-        if ((rc = timed(h, kKLinks, st, [&] { return launch_links(D, Ain, oc, par, h->tmA[par], st); }))) return rc;
+        if ((rc = timed(h, kKLinks, st, [&] { return launch_links(D, Ain, oc, on, par, h->tmA[par], st); }))) return rc;
     }
     if ((rc = timed(h, kKParticles, st, [&] { return launch_particles(D, par, st); }))) return rc;
     if (h->np > 0) {
-        if ((rc = timed(h, kKClear, st, [&] { return launch_clear(D, on, st); }))) return rc;
         if ((rc = timed(h, kKRaster, st, [&] { return launch_raster(D, on, D.geo_nxt, D.nxt, st); })))
             return rc;
         if ((rc = timed(h, kKFlags, st, [&] { return launch_flags(D, oc, on, 1, st); }))) return rc;
@@ -265,7 +266,7 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
     return LBM_OK;
 }
 
-int kernels_per_step(const lbm_handle *h) { return h->np > 0 ? 7 : 3; }
+int kernels_per_step(const lbm_handle *h) { return h->np > 0 ? 6 : 3; }
 
 int capture(lbm_handle *h, int par)
 {

@@ -302,52 +302,71 @@ struct LinkSums {
     int ax_x, ax_y, ax_t, dg_x, dg_y, dg_t;
     int pad[4];
 };
-// Reduction of per-link results by one warp, in link order (lane l takes links
-// l, l + 32, ...), the same in every kernel that sums links so that their
-// results agree bit for bit.  bx, by, tq: the variable part of Eq. force /
-// Eq. torque of each link; code: k | fallback level << 4 | thermal half-way
-// << 6; tz: the torque moment i e_k,y - j e_k,x of the constant part.
-// Returns the sums in S (lane 0) and the fallback counts in cnt3 (lane 0).
+// Per-link momentum-exchange sums of one warp.  Lane l accumulates links
+// l, l + 32, l + 64, ... in that order (add), then finish() combines the
+// lanes by a fixed shuffle tree; every kernel that sums links does exactly
+// this, so their results agree bit for bit.  bx, by, tq: the variable part
+// of Eq. force / Eq. torque of a link; k its direction; lvl its Bouzidi
+// fallback level; half whether its thermal rule fell back to half-way; tz
+// the torque moment i e_k,y - j e_k,x of its constant part.
+struct LinkAcc {
+    float fxh = 0.f, fxl = 0.f, fyh = 0.f, fyl = 0.f, tqh = 0.f, tql = 0.f;
+    int axx = 0, axy = 0, axt = 0, dgx = 0, dgy = 0, dgt = 0, cl = 0, cs = 0, ct = 0;
+
+    __device__ __forceinline__ void add(float bx, float by, float tq, int k, int lvl, bool half, int tz)
+    {
+        df_add(fxh, fxl, bx, 0.f);
+        df_add(fyh, fyl, by, 0.f);
+        df_add(tqh, tql, tq, 0.f);
+        cl += lvl == 1;
+        cs += lvl == 2;
+        ct += half;
+        if (k <= 4) { axx += ex(k); axy += ey(k); axt += tz; }
+        else { dgx += ex(k); dgy += ey(k); dgt += tz; }
+    }
+    // Whole warp; the sums land in S and cnt3 (fallback counts: linear,
+    // simple, thermal half-way) on every lane.
+    __device__ __forceinline__ void finish(LinkSums &S, int *cnt3)
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned F = 0xffffffffu;
+            float h2 = __shfl_down_sync(F, fxh, o), l2 = __shfl_down_sync(F, fxl, o);
+            df_add(fxh, fxl, h2, l2);
+            h2 = __shfl_down_sync(F, fyh, o); l2 = __shfl_down_sync(F, fyl, o);
+            df_add(fyh, fyl, h2, l2);
+            h2 = __shfl_down_sync(F, tqh, o); l2 = __shfl_down_sync(F, tql, o);
+            df_add(tqh, tql, h2, l2);
+        }
+        const unsigned F = 0xffffffffu;
+        S.fx_h = __shfl_sync(F, fxh, 0); S.fx_l = __shfl_sync(F, fxl, 0);
+        S.fy_h = __shfl_sync(F, fyh, 0); S.fy_l = __shfl_sync(F, fyl, 0);
+        S.tz_h = __shfl_sync(F, tqh, 0); S.tz_l = __shfl_sync(F, tql, 0);
+        S.ax_x = (int)__reduce_add_sync(F, (unsigned)axx);
+        S.ax_y = (int)__reduce_add_sync(F, (unsigned)axy);
+        S.ax_t = (int)__reduce_add_sync(F, (unsigned)axt);
+        S.dg_x = (int)__reduce_add_sync(F, (unsigned)dgx);
+        S.dg_y = (int)__reduce_add_sync(F, (unsigned)dgy);
+        S.dg_t = (int)__reduce_add_sync(F, (unsigned)dgt);
+        S.pad[0] = S.pad[1] = S.pad[2] = S.pad[3] = 0;
+        cnt3[0] = (int)__reduce_add_sync(F, (unsigned)cl);
+        cnt3[1] = (int)__reduce_add_sync(F, (unsigned)cs);
+        cnt3[2] = (int)__reduce_add_sync(F, (unsigned)ct);
+    }
+};
+
+// Reduction of per-link results stored in shared memory, by one warp, in
+// link order.  code: k | fallback level << 4 | thermal half-way << 6.
 __device__ __forceinline__ void reduce_links(const float *bx, const float *by, const float *tq,
                                              const int *code, const int *tz, int n, LinkSums &S,
                                              int *cnt3)
 {
-    const int lane = threadIdx.x & 31;
-    float fxh = 0.f, fxl = 0.f, fyh = 0.f, fyl = 0.f, tqh = 0.f, tql = 0.f;
-    int axx = 0, axy = 0, axt = 0, dgx = 0, dgy = 0, dgt = 0, cl = 0, cs = 0, ct = 0;
-    for (int i = lane; i < n; i += 32) {
-        df_add(fxh, fxl, bx[i], 0.f);
-        df_add(fyh, fyl, by[i], 0.f);
-        df_add(tqh, tql, tq[i], 0.f);
-        const int c = code[i], k = c & 15, lvl = (c >> 4) & 3;
-        cl += lvl == 1;
-        cs += lvl == 2;
-        ct += (c >> 6) & 1;
-        if (k <= 4) { axx += ex(k); axy += ey(k); axt += tz[i]; }
-        else { dgx += ex(k); dgy += ey(k); dgt += tz[i]; }
+    LinkAcc acc;
+    for (int i = (int)(threadIdx.x & 31); i < n; i += 32) {
+        const int c = code[i];
+        acc.add(bx[i], by[i], tq[i], c & 15, (c >> 4) & 3, (c >> 6) & 1, tz[i]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned F = 0xffffffffu;
-        float h2 = __shfl_down_sync(F, fxh, o), l2 = __shfl_down_sync(F, fxl, o);
-        df_add(fxh, fxl, h2, l2);
-        h2 = __shfl_down_sync(F, fyh, o); l2 = __shfl_down_sync(F, fyl, o);
-        df_add(fyh, fyl, h2, l2);
-        h2 = __shfl_down_sync(F, tqh, o); l2 = __shfl_down_sync(F, tql, o);
-        df_add(tqh, tql, h2, l2);
-    }
-    const unsigned F = 0xffffffffu;
-    S.fx_h = fxh; S.fx_l = fxl; S.fy_h = fyh; S.fy_l = fyl; S.tz_h = tqh; S.tz_l = tql;
-    S.ax_x = (int)__reduce_add_sync(F, (unsigned)axx);
-    S.ax_y = (int)__reduce_add_sync(F, (unsigned)axy);
-    S.ax_t = (int)__reduce_add_sync(F, (unsigned)axt);
-    S.dg_x = (int)__reduce_add_sync(F, (unsigned)dgx);
-    S.dg_y = (int)__reduce_add_sync(F, (unsigned)dgy);
-    S.dg_t = (int)__reduce_add_sync(F, (unsigned)dgt);
-    S.pad[0] = S.pad[1] = S.pad[2] = S.pad[3] = 0;
-    cnt3[0] = (int)__reduce_add_sync(F, (unsigned)cl);
-    cnt3[1] = (int)__reduce_add_sync(F, (unsigned)cs);
-    cnt3[2] = (int)__reduce_add_sync(F, (unsigned)ct);
+    acc.finish(S, cnt3);
 }
 
 // Hydrodynamic force (Fx, Fy) and torque of a particle centred at (xc, yc).
@@ -469,7 +488,7 @@ __host__ __device__ inline void slot_dir_line(int s, int N, int &k, int &line)
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in k_fluid.cu and k_particles.cu).
 // ---------------------------------------------------------------------------
-enum KernelKind { kKLinks = 0, kKParticles, kKClear, kKRaster, kKFlags, kKStreamCollide,
+enum KernelKind { kKLinks = 0, kKParticles, kKRaster, kKFlags, kKStreamCollide,
                   kKBoundary, kKInit, kKFields, kNumKernelKinds };
 
 // Planes are passed untyped: their element type is D.storage.
@@ -485,7 +504,7 @@ cudaError_t launch_init_collide(const Dev &D, const void *Ain, void *Aout, float
                                 cudaStream_t s);
 cudaError_t launch_fields(const Dev &D, const void *A, int row0, int rows, float *rho, float *ux,
                           float *uy, float *T, cudaStream_t s);
-cudaError_t launch_links(const Dev &D, void *A, const int *own_cur, int parity,
+cudaError_t launch_links(const Dev &D, void *A, const int *own_cur, int *own_nxt, int parity,
                          const CUtensorMap &tmA, cudaStream_t s);
 // 3-D tensor map (x, y, plane) over one distribution buffer, for the link
 // kernel's TMA tile loads.
@@ -498,7 +517,6 @@ size_t link_smem_bytes(int N, int storage);
 bool link_zone_supported(int N, int storage);
 cudaError_t prepare_links(Dev &D);
 cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s);
-cudaError_t launch_clear(const Dev &D, int *own_nxt, cudaStream_t s);
 cudaError_t launch_raster(const Dev &D, int *own, const struct GeomRec *geo, const PartSoA &pos,
                           cudaStream_t s);
 cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate,
