@@ -32,7 +32,10 @@
  * lbm_step only enqueues work; errors found on the device during a step
  * (non-finite density, a particle leaving the cavity, a line of the index
  * array holding two links) are sticky and are returned by the next call that
- * synchronises (lbm_sync, lbm_get_*).
+ * synchronises (lbm_sync, lbm_get_*).  After such an error the state is not
+ * meaningful; a disk that would have left the cavity (or whose state is no
+ * longer finite) is held at its last position, so that later steps stay
+ * within the caller's buffers.
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
@@ -58,9 +61,9 @@ extern "C" {
 #define LBM_BC_PERIODIC_Y 2u
 
 /* lbm_params.storage: how distributions are held in HBM. */
-#define LBM_STORE_FP32 0 /* FP32 deviations from the rest equilibrium */
-#define LBM_STORE_BF16 1 /* BF16 deviations (reserved) */
-#define LBM_STORE_FP16 2 /* FP16 deviations (reserved) */
+#define LBM_STORE_FP32 0 /* FP32 deviations f - w from the rest equilibrium, raw g */
+#define LBM_STORE_BF16 1 /* the same values in BF16 (56 instead of 112 bytes per node and step) */
+#define LBM_STORE_FP16 2 /* the same values times 2^12 in FP16; stored magnitudes must stay below 16 */
 
 /* lbm_params.flags */
 #define LBM_FLAG_FIXED_PARTICLES 1u /* particles keep their state (tests) */
@@ -220,6 +223,42 @@ int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
                             const int32_t *d_owner, int32_t nx, int32_t ny,
                             const lbm_particle *d_particles, int32_t n, double r_max,
                             double *d_forces, void *stream);
+
+/* ---- batched instances --------------------------------------------------- */
+/* No counterpart in the paper, whose outlook runs several small tasks on one
+ * GPU concurrently: a batch steps n independent simulations (handles from
+ * lbm_init, same device, same storage, same step parity, i.e. created
+ * together or stepped equally often) with one launch per step kernel over
+ * all of them, replayed from a CUDA graph.  Every instance computes exactly
+ * what lbm_step computes for it alone (bit for bit).
+ *   lbm_batch_footprint  device workspace bytes for the batch's tables.
+ *   lbm_batch_create     d_workspace: caller-owned device memory of at least
+ *                        that size, 256-byte aligned; stream: the batch's
+ *                        stream (the handles' own streams are not used by
+ *                        batch calls).  The handles stay owned by the
+ *                        caller and must outlive the batch; while a batch
+ *                        call runs, no other call may use them.
+ *   lbm_batch_autotune   times the stream-collide tile shapes (128x1, 64x2,
+ *                        32x4 threads) on the batch, `reps` launches each,
+ *                        without changing any state, and keeps the fastest;
+ *                        *choice receives its index (may be NULL).
+ *   lbm_batch_step       enqueues nsteps steps of every instance on the
+ *                        batch's stream; call lbm_batch_sync before using a
+ *                        handle on its own again.
+ *   lbm_batch_sync       waits for the batch's stream and returns the first
+ *                        sticky device error of any instance (its index in
+ *                        *which, may be NULL), else LBM_OK.
+ * Errors: LBM_EINVAL (mismatched handles, n < 1 or n > 4096), LBM_ENOSPC
+ * (workspace too small), LBM_ECUDA. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_footprint(lbm_handle *const *hs, int32_t n, size_t *bytes);
+int lbm_batch_create(lbm_batch **b, lbm_handle *const *hs, int32_t n, void *d_workspace, size_t ws_bytes,
+                     void *stream);
+int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *choice);
+int lbm_batch_step(lbm_batch *b, int32_t nsteps);
+int lbm_batch_sync(lbm_batch *b, int32_t *which);
+int64_t lbm_batch_launch_count(lbm_batch *b); /* kernel launches enqueued by lbm_batch_step */
+int lbm_batch_destroy(lbm_batch *b);
 
 #ifdef __cplusplus
 }

@@ -261,9 +261,8 @@ struct Vec<__half, 2> {
 // one vector store per plane); FP32 runs V = 1, the 16-bit storages V = 2 so
 // that every load still moves four bytes.
 template <typename T, int V>
-__global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
-    k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout,
-                     const int *__restrict__ own_cur, int parity, int ahead_y, int ahead_x)
+__device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
+                                        int ahead_y, int ahead_x, const Blk blk)
 {
     using E = Elem<T>;
     using VW = typename Vec<T, V>::W;
@@ -272,10 +271,10 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
     const int span = (int)blockDim.x * V; // nodes of a row per block
     if (threadIdx.x < kPop && threadIdx.y == 0) {
         // the block `ahead` places later in launch order: ahead = ahead_y
-        // grid rows + ahead_x blocks (ahead_x < gridDim.x)
-        int bx = (int)blockIdx.x + ahead_x, by = (int)blockIdx.y + ahead_y;
-        if (bx >= (int)gridDim.x) {
-            bx -= (int)gridDim.x;
+        // grid rows + ahead_x blocks (ahead_x < blk.gx)
+        int bx = blk.x + ahead_x, by = blk.y + ahead_y;
+        if (bx >= blk.gx) {
+            bx -= blk.gx;
             ++by;
         }
         const int yb = by * (int)blockDim.y;
@@ -294,8 +293,8 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
                          : "memory");
         }
     }
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x0 = (blk.x * (int)blockDim.x + (int)threadIdx.x) * V;
+    const int y = blk.y * (int)blockDim.y + (int)threadIdx.y;
     if (y >= D.ny) return; // uniform across the warp: blockDim.x is a multiple of 32
     const bool act = x0 < D.pitch; // the pitch is a multiple of 32, so all V nodes are in the row
     float c[V][kPop];
@@ -409,9 +408,8 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
 // A fixed grid strides over the 2 nx + 2 (ny - 2) frame nodes and then the
 // list, whose length the device holds.
 template <typename T>
-__global__ void __launch_bounds__(128)
-    k_boundary(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, const int *__restrict__ own_cur,
-               int parity)
+__device__ __forceinline__ void boundary_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
+                                              const int *__restrict__ own_cur, int parity, const Blk blk)
 {
     using E = Elem<T>;
     const int nx = D.nx, ny = D.ny;
@@ -419,7 +417,7 @@ __global__ void __launch_bounds__(128)
     const int nlist = min((int)D.status->nb, D.newborn_cap);
     unsigned n4[4] = {0u, 0u, 0u, 0u};
     bool ok = true;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nframe + nlist; idx += gridDim.x * blockDim.x) {
+    for (int idx = blk.x * (int)blockDim.x + (int)threadIdx.x; idx < nframe + nlist; idx += blk.gx * (int)blockDim.x) {
         int x, y;
         if (idx < nx) { x = idx; y = 0; }
         else if (idx < 2 * nx) { x = idx - nx; y = ny - 1; }
@@ -447,6 +445,52 @@ __global__ void __launch_bounds__(128)
     }
     flush_counters(D, parity, n4);
     if (!ok) atomicOr(&D.status->err, kErrNumeric);
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
+    k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ahead_y, int ahead_x)
+{
+    sc_body<T, V>(D, Ain, Aout, ahead_y, ahead_x, this_blk());
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_boundary(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, const int *__restrict__ own_cur,
+               int parity)
+{
+    boundary_body<T>(D, Ain, Aout, own_cur, parity, this_blk());
+}
+
+// Batched forms: one grid over all instances.  Stream-collide blocks are
+// laid out per instance as gx x gy tiles of the instance's lattice (gx from
+// its pitch), and each block prefetches the block `resident` places later
+// within its own instance.
+template <typename T, int V>
+__global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
+    k_stream_collide_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity,
+                           int resident)
+{
+    const int i = batch_find(start, n, (int)blockIdx.x);
+    const InstArgs &a = I[i];
+    const int local = (int)blockIdx.x - __ldg(start + i);
+    const int gx = (a.D.pitch / V + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int gy = (a.D.ny + (int)blockDim.y - 1) / (int)blockDim.y;
+    const Blk blk{local % gx, local / gx, gx, gy};
+    sc_body<T, V>(a.D, static_cast<const T *>(a.A[parity]), static_cast<T *>(a.A[parity ^ 1]), resident / gx,
+                  resident % gx, blk);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_boundary_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
+{
+    const int i = batch_find(start, n, (int)blockIdx.x);
+    const InstArgs &a = I[i];
+    const int s0 = __ldg(start + i);
+    const Blk blk{(int)blockIdx.x - s0, 0, __ldg(start + i + 1) - s0, 1};
+    boundary_body<T>(a.D, static_cast<const T *>(a.A[parity]), static_cast<T *>(a.A[parity ^ 1]),
+                     a.own[parity], parity, blk);
 }
 
 // Collision without streaming, for the initial state and for distributions
@@ -529,8 +573,7 @@ cudaError_t stream_collide_t(const Dev &D, const void *Ain, void *Aout, const in
     dim3 block(bx, by);
     dim3 grid((tx + bx - 1) / bx, (D.ny + by - 1) / by);
     k_stream_collide<T, V><<<grid, block, 0, s>>>(D, static_cast<const T *>(Ain), static_cast<T *>(Aout),
-                                                  own_cur, parity, resident / (int)grid.x,
-                                                  resident % (int)grid.x);
+                                                  resident / (int)grid.x, resident % (int)grid.x);
     return cudaGetLastError();
 }
 
@@ -590,6 +633,56 @@ cudaError_t launch_boundary(const Dev &D, const void *Ain, void *Aout, const int
     case LBM_STORE_FP16: return boundary_t<__half>(D, Ain, Aout, own_cur, parity, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_stream_collide_batch(const InstArgs *I, const int *start, int n, int total, int storage,
+                                        int parity, dim3 block, int resident, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    switch (storage) {
+    case LBM_STORE_FP32:
+        k_stream_collide_batch<float, 1><<<total, block, 0, s>>>(I, start, n, parity, resident);
+        break;
+    case LBM_STORE_BF16:
+        k_stream_collide_batch<__nv_bfloat16, 2><<<total, block, 0, s>>>(I, start, n, parity, resident);
+        break;
+    case LBM_STORE_FP16:
+        k_stream_collide_batch<__half, 2><<<total, block, 0, s>>>(I, start, n, parity, resident);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boundary_batch(const InstArgs *I, const int *start, int n, int total, int storage, int parity,
+                                  cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    switch (storage) {
+    case LBM_STORE_FP32: k_boundary_batch<float><<<total, 128, 0, s>>>(I, start, n, parity); break;
+    case LBM_STORE_BF16: k_boundary_batch<__nv_bfloat16><<<total, 128, 0, s>>>(I, start, n, parity); break;
+    case LBM_STORE_FP16: k_boundary_batch<__half><<<total, 128, 0, s>>>(I, start, n, parity); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int stream_collide_batch_resident(int storage, dim3 block)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nt = (int)(block.x * block.y);
+    switch (storage) {
+    case LBM_STORE_BF16:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_batch<__nv_bfloat16, 2>, nt, 0);
+        break;
+    case LBM_STORE_FP16:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_batch<__half, 2>, nt, 0);
+        break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_batch<float, 1>, nt, 0);
+    }
+    return max(1, sms * per_sm);
 }
 
 cudaError_t launch_init_collide(const Dev &D, const void *Ain, void *Aout, float T_init, int mode,

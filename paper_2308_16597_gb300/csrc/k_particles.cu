@@ -140,16 +140,14 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 //     and the momentum-exchange bracket of Eq. force / Eq. torque, stored per
 //     link and summed by one warp in link order.
 template <typename T>
-__global__ void __launch_bounds__(kLinkThreads)
-    k_links(const __grid_constant__ CUtensorMap tmA, const Dev D, T *A, const int *__restrict__ own,
-            int *__restrict__ own_nxt, int parity, int ahead)
+__device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D, T *A, const int *__restrict__ own,
+                                           int *__restrict__ own_nxt, int parity, int ahead, const int p)
 {
     using E = Elem<T>;
     constexpr int es = (int)sizeof(T), al = 16 / es;
     extern __shared__ __align__(16) unsigned char lsm[];
     __shared__ int s_nvalid;
     __shared__ unsigned s_over;
-    const int p = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const GeomRec G = D.geo_cur[p];
     const int N = G.N, cap = 12 * N - 12;
@@ -189,10 +187,10 @@ __global__ void __launch_bounds__(kLinkThreads)
     // ---- 1. owner masks (all warps) and look-ahead prefetches
     if (tid == 0) {
         s_over = 0u;
-        if (p + ahead < D.np) {
+        if (p + ahead < D.np && tmA) {
             const GeomRec Ga = D.geo_cur[p + ahead];
             for (int t = 0; t < kTilePlanes; ++t)
-                tma_prefetch_3d(&tmA, (Ga.X0 - 2) & ~(al - 1), Ga.Y0 - 2, tile_global_plane(t));
+                tma_prefetch_3d(tmA, (Ga.X0 - 2) & ~(al - 1), Ga.Y0 - 2, tile_global_plane(t));
         }
         const DiskDF d0 = geom_df(G);
         D.pos4[p] = make_float4(d0.xh, d0.yh, d0.xl, d0.yl);
@@ -236,6 +234,20 @@ __global__ void __launch_bounds__(kLinkThreads)
             const int j = ya + (r >> 1), i = min(max(xa + (r & 1) * (wx - 1), 0), D.nx - 1);
             if (j >= 0 && j < D.ny)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(own + (long long)j * D.nx + i) : "memory");
+        }
+    }
+    // without a tensor map (batched form): the window rows of the 12 planes,
+    // one L2 prefetch per row end
+    if (!tmA && warp >= 2 && p + ahead < D.np) {
+        const GeomRec Ga = D.geo_cur[p + ahead];
+        const int xa = (Ga.X0 - 2) & ~(al - 1), ya = Ga.Y0 - 2;
+        for (int r = tid - 64; r < 2 * kTilePlanes * wy; r += kLinkThreads - 64) {
+            const int row = r >> 1, t = row / wy, j = ya + row % wy;
+            const int i = min(max(xa + (r & 1) * (wx - 1), 0), D.pitch - 1);
+            if (j >= 0 && j < D.ny)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (long long)tile_global_plane(t) * D.ps +
+                                                            (long long)j * D.pitch + i)
+                             : "memory");
         }
     }
     for (int w = tid; w < nw; w += kLinkThreads) occ[w] = 0u;
@@ -406,15 +418,15 @@ __device__ __noinline__ void pair_force(float4 pa, float2 ca, float4 pb, float2 
     df_add(fh_y, fl_y, mag * dy / dist, 0.f);
 }
 
-__global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int parity)
+__device__ __forceinline__ void particles_body(const Dev &D, int parity, const int blk)
 {
     __shared__ float4 sp[kPartTile];
     __shared__ float2 sc[kPartTile];
     __shared__ float sred[4][kPartPerBlock];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int a = blockIdx.x * kPartPerBlock + warp;
-    if (blockIdx.x == 0 && threadIdx.x < kNumCounters) D.status->cnt[parity ^ 1][threadIdx.x] = 0ull;
-    if (blockIdx.x == 0 && threadIdx.x == 0) D.status->nb = 0u;
+    const int a = blk * kPartPerBlock + warp;
+    if (blk == 0 && threadIdx.x < kNumCounters) D.status->cnt[parity ^ 1][threadIdx.x] = 0ull;
+    if (blk == 0 && threadIdx.x == 0) D.status->nb = 0u;
     const bool me = a < D.np;
     float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 ca = make_float2(1.f, 0.f);
@@ -450,7 +462,7 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
     }
     __syncthreads();
     if (warp != 0 || lane >= kPartPerBlock) return;
-    const int b = blockIdx.x * kPartPerBlock + lane;
+    const int b = blk * kPartPerBlock + lane;
     if (b >= D.np) return;
     double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
     double th = D.cur.th[b], om = D.cur.om[b];
@@ -482,8 +494,14 @@ __global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int par
         uy = uy1;
         om = om1;
     }
-    if (x - r < -0.5 || x + r > (double)D.nx - 0.5 || y - r < -0.5 || y + r > (double)D.ny - 0.5)
+    // a disk that would leave the cavity, or whose state is no longer finite,
+    // raises the (sticky) domain error and stays where it was, so that its
+    // zone stays inside the arrays every later kernel indexes
+    if (!(x - r >= -0.5 && x + r <= (double)D.nx - 0.5 && y - r >= -0.5 && y + r <= (double)D.ny - 0.5)) {
         atomicOr(&D.status->err, kErrDomain);
+        x = D.cur.x[b];
+        y = D.cur.y[b];
+    }
     const double T = D.cur.T[b];
     D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
     D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T;
@@ -504,11 +522,11 @@ __device__ __forceinline__ Box box_of(const GeomRec &G) { return Box{G.X0, G.Y0,
 // lane per zone row: the predicate holds on one contiguous run of each row
 // (it is monotone in |i - x|), so the run is found from an FP32 estimate of
 // its ends and settled with the exact predicate at the ends only.
-__global__ void __launch_bounds__(kBoxThreads)
-    k_raster(const Dev D, int *own, const GeomRec *__restrict__ geo, const PartSoA pos)
+__device__ __forceinline__ void raster_body(const Dev &D, int *own, const GeomRec *__restrict__ geo,
+                                            const PartSoA &pos, const int blk)
 {
     const int lane = threadIdx.x & 31;
-    const int p = blockIdx.x * (kBoxThreads / 32) + (threadIdx.x >> 5);
+    const int p = blk * (kBoxThreads / 32) + (threadIdx.x >> 5);
     if (p >= D.np) return;
     const GeomRec G = geo[p];
     const double x = pos.x[p], y = pos.y[p], r = pos.r[p]; // for the FP64 fallback only
@@ -544,10 +562,9 @@ __global__ void __launch_bounds__(kBoxThreads)
 // at a time, all loads issued first), lane l columns l and l + 32.  During a
 // step each block also moves its particle's new state into the current slot
 // and keeps the old position for the next clear.
-__global__ void __launch_bounds__(kBoxThreads)
-    k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate)
+__device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__ own_cur,
+                                           const int *__restrict__ own_nxt, int rotate, const int p)
 {
-    const int p = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kW = kBoxThreads / 32, kU = 4;
     const bool list = rotate != 0; // a step (not the initial flags): list the newborn nodes
@@ -601,6 +618,62 @@ __global__ void __launch_bounds__(kBoxThreads)
                 }
             }
     }
+}
+
+// ---- single-instance kernels
+template <typename T>
+__global__ void __launch_bounds__(kLinkThreads)
+    k_links(const __grid_constant__ CUtensorMap tmA, const Dev D, T *A, const int *__restrict__ own,
+            int *__restrict__ own_nxt, int parity, int ahead)
+{
+    links_body<T>(&tmA, D, A, own, own_nxt, parity, ahead, (int)blockIdx.x);
+}
+__global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int parity)
+{
+    particles_body(D, parity, (int)blockIdx.x);
+}
+__global__ void __launch_bounds__(kBoxThreads)
+    k_raster(const Dev D, int *own, const GeomRec *__restrict__ geo, const PartSoA pos)
+{
+    raster_body(D, own, geo, pos, (int)blockIdx.x);
+}
+__global__ void __launch_bounds__(kBoxThreads)
+    k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate)
+{
+    flags_body(D, own_cur, own_nxt, rotate, (int)blockIdx.x);
+}
+
+// ---- batched kernels: one grid over all instances (InstArgs table, block
+// offsets `start`).  The link kernel's look-ahead prefetch stays within the
+// instance and uses per-row L2 prefetches instead of a tensor map.
+template <typename T>
+__global__ void __launch_bounds__(kLinkThreads)
+    k_links_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity, int ahead)
+{
+    const int i = batch_find(start, n, (int)blockIdx.x);
+    const InstArgs &a = I[i];
+    links_body<T>(nullptr, a.D, static_cast<T *>(a.A[parity]), a.own[parity], a.own[parity ^ 1], parity, ahead,
+                  (int)blockIdx.x - __ldg(start + i));
+}
+__global__ void __launch_bounds__(kPartThreads)
+    k_particles_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
+{
+    const int i = batch_find(start, n, (int)blockIdx.x);
+    particles_body(I[i].D, parity, (int)blockIdx.x - __ldg(start + i));
+}
+__global__ void __launch_bounds__(kBoxThreads)
+    k_raster_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
+{
+    const int i = batch_find(start, n, (int)blockIdx.x);
+    const InstArgs &a = I[i];
+    raster_body(a.D, a.own[parity ^ 1], a.D.geo_nxt, a.D.nxt, (int)blockIdx.x - __ldg(start + i));
+}
+__global__ void __launch_bounds__(kBoxThreads)
+    k_flags_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
+{
+    const int i = batch_find(start, n, (int)blockIdx.x);
+    const InstArgs &a = I[i];
+    flags_body(a.D, a.own[parity], a.own[parity ^ 1], 1, (int)blockIdx.x - __ldg(start + i));
 }
 
 // Geometry records of the current state and of the previous positions.
@@ -722,6 +795,74 @@ cudaError_t make_plane_map(const Dev &D, const void *A, CUtensorMap *m)
                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// ---- batched launches (one grid over all instances)
+cudaError_t prepare_links_batch(int zone_max, int storage, size_t *smem, int *ahead)
+{
+    *smem = link_smem_bytes(zone_max, storage);
+    const void *fn = storage == LBM_STORE_BF16   ? reinterpret_cast<const void *>(&k_links_batch<__nv_bfloat16>)
+                     : storage == LBM_STORE_FP16 ? reinterpret_cast<const void *>(&k_links_batch<__half>)
+                                                 : reinterpret_cast<const void *>(&k_links_batch<float>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0, dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLinkThreads, *smem)) != cudaSuccess)
+        return e;
+    *ahead = max(1, sms * per_sm);
+    return cudaSuccess;
+}
+
+cudaError_t launch_links_batch(const InstArgs *I, const int *start, int n, int total, int storage, int parity,
+                               int ahead, size_t smem, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    switch (storage) {
+    case LBM_STORE_FP32: k_links_batch<float><<<total, kLinkThreads, smem, s>>>(I, start, n, parity, ahead); break;
+    case LBM_STORE_BF16:
+        k_links_batch<__nv_bfloat16><<<total, kLinkThreads, smem, s>>>(I, start, n, parity, ahead);
+        break;
+    case LBM_STORE_FP16: k_links_batch<__half><<<total, kLinkThreads, smem, s>>>(I, start, n, parity, ahead); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particles_batch(const InstArgs *I, const int *start, int n, int total, int parity,
+                                   cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    k_particles_batch<<<total, kPartThreads, 0, s>>>(I, start, n, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raster_batch(const InstArgs *I, const int *start, int n, int total, int parity, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    k_raster_batch<<<total, kBoxThreads, 0, s>>>(I, start, n, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flags_batch(const InstArgs *I, const int *start, int n, int total, int parity, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    k_flags_batch<<<total, kBoxThreads, 0, s>>>(I, start, n, parity);
+    return cudaGetLastError();
+}
+
+// Blocks of each batched step kernel for one instance.
+void batch_blocks(const Dev &D, dim3 sc_block, int out[kBatchPhases])
+{
+    const int V = D.storage == LBM_STORE_FP32 ? 1 : 2;
+    out[kBLinks] = D.np;
+    out[kBParticles] = D.np > 0 ? (D.np + kPartPerBlock - 1) / kPartPerBlock : 1;
+    out[kBRaster] = (D.np + kBoxThreads / 32 - 1) / (kBoxThreads / 32);
+    out[kBFlags] = D.np;
+    out[kBStream] = ((D.pitch / V + (int)sc_block.x - 1) / (int)sc_block.x) *
+                    ((D.ny + (int)sc_block.y - 1) / (int)sc_block.y);
+    out[kBBoundary] = kBoundaryBlocksPerInstance;
 }
 
 cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s)

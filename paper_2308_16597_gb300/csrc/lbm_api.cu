@@ -9,7 +9,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "lbm_internal.cuh"
+#include "lbm_handle.cuh"
 
 using namespace lbm;
 
@@ -20,15 +20,6 @@ constexpr size_t kStageBytes = size_t(4) << 20;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-struct Layout {
-    int pitch = 0;
-    long long ps = 0;
-    size_t nslots = 0;
-    size_t A[2], own[2], flags, slot_node, slot_q, slot_base, cur, nxt, prev, force, pos4, prc, lsum,
-        geo[3], status, pack, stage, newborn, total;
-    int newborn_cap = 0;
-    int stage_rows = 0;
-};
 
 bool finite(double v) { return std::isfinite(v); }
 
@@ -143,34 +134,6 @@ const char *kKernelNames[kNumKernelKinds] = {"link_gather_bb_force", "particle_u
 
 } // namespace
 
-struct lbm_handle {
-    lbm_domain d;
-    lbm_params prm;
-    int np = 0;
-    Layout L;
-    char *ws = nullptr;
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap = nullptr;
-    cudaStream_t side = nullptr;           // branch for k_boundary beside k_stream_collide
-    cudaEvent_t fork = nullptr, join = nullptr;
-    Dev D;
-    void *A[2]; // planes of D.storage elements
-    int *own[2];
-    int parity = 0;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    CUtensorMap tmA[2]; // link-tile tensor maps over A[0] and A[1]
-    bool timing = false;
-    struct Ev {
-        cudaEvent_t a, b;
-        int kind;
-    };
-    std::vector<Ev> ev;
-    size_t ev_used = 0;
-    double acc_ms[kNumKernelKinds] = {};
-    long long acc_n[kNumKernelKinds] = {};
-    long long launches = 0;
-    int sticky = LBM_OK;
-};
 
 namespace {
 

@@ -486,6 +486,39 @@ __host__ __device__ inline void slot_dir_line(int s, int N, int &k, int &line)
 }
 
 // ---------------------------------------------------------------------------
+// Batched instances.  Every step kernel is a device body that takes the
+// position of its block within one instance's launch (Blk): the
+// single-instance kernels fill it from the built-in indices, the batched
+// kernels from the block's slice of one grid over all instances, whose
+// per-instance block offsets are `start` (start[i] <= block < start[i + 1]).
+// ---------------------------------------------------------------------------
+struct Blk {
+    int x, y, gx, gy;
+};
+__device__ __forceinline__ Blk this_blk()
+{
+    return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
+}
+// Instance whose slice holds batched block g (binary search over n + 1
+// offsets; instances with no blocks in this launch are skipped).
+__device__ __forceinline__ int batch_find(const int *__restrict__ start, int n, int g)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(start + mid) <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+// Per-instance arguments of the batched kernels (device table).
+struct InstArgs {
+    Dev D;
+    void *A[2];   // distribution buffers by step parity
+    int *own[2];  // owner maps by step parity
+};
+
+// ---------------------------------------------------------------------------
 // Kernel launchers (defined in k_fluid.cu and k_particles.cu).
 // ---------------------------------------------------------------------------
 enum KernelKind { kKLinks = 0, kKParticles, kKRaster, kKFlags, kKStreamCollide,
@@ -525,5 +558,23 @@ cudaError_t launch_pack_particles(const Dev &D, lbm_particle *out, cudaStream_t 
 // Geometry records of the current state (into cur, nxt and prev) and of the
 // previous positions (into prev), for init and restore.
 cudaError_t launch_geom_init(const Dev &D, cudaStream_t s);
+
+// Batched step kernels over an InstArgs table (one grid over all instances;
+// `start` holds the n + 1 block offsets of the launch, `total` its blocks).
+enum BatchPhase { kBLinks = 0, kBParticles, kBRaster, kBFlags, kBStream, kBBoundary, kBatchPhases };
+constexpr int kBoundaryBlocksPerInstance = 8;
+void batch_blocks(const Dev &D, dim3 sc_block, int out[kBatchPhases]);
+cudaError_t prepare_links_batch(int zone_max, int storage, size_t *smem, int *ahead);
+cudaError_t launch_links_batch(const InstArgs *I, const int *start, int n, int total, int storage, int parity,
+                               int ahead, size_t smem, cudaStream_t s);
+cudaError_t launch_particles_batch(const InstArgs *I, const int *start, int n, int total, int parity,
+                                   cudaStream_t s);
+cudaError_t launch_raster_batch(const InstArgs *I, const int *start, int n, int total, int parity, cudaStream_t s);
+cudaError_t launch_flags_batch(const InstArgs *I, const int *start, int n, int total, int parity, cudaStream_t s);
+cudaError_t launch_stream_collide_batch(const InstArgs *I, const int *start, int n, int total, int storage,
+                                        int parity, dim3 block, int resident, cudaStream_t s);
+cudaError_t launch_boundary_batch(const InstArgs *I, const int *start, int n, int total, int storage, int parity,
+                                  cudaStream_t s);
+int stream_collide_batch_resident(int storage, dim3 block);
 
 } // namespace lbm

@@ -77,6 +77,13 @@ _SIGS = [
     ("lbm_launch_count", C.c_int64, [_P]),
     ("lbm_link_forces_noalloc", C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, _P,
                                           C.c_int32, C.c_double, _P, _P]),
+    ("lbm_batch_footprint", C.c_int, [_P, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("lbm_batch_create", C.c_int, [C.POINTER(_P), _P, C.c_int32, _P, C.c_size_t, _P]),
+    ("lbm_batch_autotune", C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32)]),
+    ("lbm_batch_step", C.c_int, [_P, C.c_int32]),
+    ("lbm_batch_sync", C.c_int, [_P, C.POINTER(C.c_int32)]),
+    ("lbm_batch_launch_count", C.c_int64, [_P]),
+    ("lbm_batch_destroy", C.c_int, [_P]),
 ]
 
 
@@ -302,3 +309,57 @@ def lbm_link_forces_noalloc(dist_ptr, plane_stride, pitch, owner_ptr, nx, ny, pa
     _check(library().lbm_link_forces_noalloc(dist_ptr, plane_stride, pitch, owner_ptr, nx, ny,
                                              particles_ptr, n, r_max, forces_ptr, stream_ptr),
            "lbm_link_forces_noalloc")
+
+
+class Batch:
+    """Independent simulations stepped together: one launch per step kernel
+    over all of them (lbm_batch_* in include/lbm.h).  The simulations stay
+    usable on their own after sync()."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        lib = library()
+        self.sims = list(sims)
+        n = len(self.sims)
+        arr = (_P * n)(*[s.h for s in self.sims])
+        self._arr = arr
+        b = C.c_size_t()
+        _check(lib.lbm_batch_footprint(arr, n, C.byref(b)), "lbm_batch_footprint")
+        dev = self.sims[0].workspace.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.workspace = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=dev)
+        h = _P()
+        _check(lib.lbm_batch_create(C.byref(h), arr, n, self.workspace.data_ptr(), int(b.value),
+                                    self.stream.cuda_stream), "lbm_batch_create")
+        self.h = h
+
+    @property
+    def nodes(self) -> int:
+        return sum(s.nx * s.ny for s in self.sims)
+
+    def autotune(self, reps: int = 3) -> int:
+        c = C.c_int32()
+        _check(library().lbm_batch_autotune(self.h, int(reps), C.byref(c)), "lbm_batch_autotune")
+        return int(c.value)
+
+    def step(self, n: int = 1):
+        _check(library().lbm_batch_step(self.h, int(n)), "lbm_batch_step")
+
+    def sync(self):
+        w = C.c_int32()
+        rc = library().lbm_batch_sync(self.h, C.byref(w))
+        _check(rc, "lbm_batch_sync (instance %d)" % w.value)
+
+    def launch_count(self) -> int:
+        return int(library().lbm_batch_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

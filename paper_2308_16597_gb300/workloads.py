@@ -147,6 +147,36 @@ def crop_1024(seed: int = 3) -> Workload:
                          name="cavity1024_300disks", steps=1000)
 
 
+def ensemble(count: int = 64, seed: int = 4, sizes=(256, 512, 768, 1024), n_range=(8, 400),
+             r_range=(6.0, 12.0), ra_range=(1e6, 1e8), nu: float = 0.02, Pr: float = 0.71):
+    """Batched ensemble of independent cavities: nx and ny drawn independently
+    from `sizes`, a disk count from n_range (capped to what random sequential
+    addition fits in the upper half at a 25 % solid fraction), per-disk radii
+    uniform in r_range, Ra log-uniform in ra_range (g from Ra on H = ny)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(count):
+        nx = int(rng.choice(sizes))
+        ny = int(rng.choice(sizes))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        radii = rng.uniform(r_range[0], r_range[1], n)
+        upper = (nx - 2 * (r_range[1] + S_REP + 1)) * (ny / 2 - 2 * (r_range[1] + S_REP))
+        n = max(1, min(n, int(0.25 * upper / (math.pi * np.mean(radii) ** 2))))
+        radii = radii[:n]
+        Ra = float(np.exp(rng.uniform(np.log(ra_range[0]), np.log(ra_range[1]))))
+        alpha = nu / Pr
+        g = gravity_for_rayleigh(Ra, nu, alpha, ny)
+        rmax = float(radii.max())
+        lo = rmax + S_REP + 1.0
+        parts = rsa_disks(rng, n, radii, lo, nx - 1 - lo, max(0.5 * ny + rmax + S_REP, lo), ny - 1 - lo,
+                          min_gap=S_REP + 1.0)
+        parts["rho"] = 1.5
+        parts["T"] = 1.0
+        out.append(Workload("ensemble%d_%dx%d_%ddisks" % (k, nx, ny, n), cavity(nx, ny), parts,
+                            base_params(nu, Pr, g), 0, dict(Ra=Ra)))
+    return out
+
+
 def random_state(nx: int, ny: int, seed: int, base_f, base_g, amp: float = 1e-3,
                  T_amp: float = 0.5):
     """Seeded perturbation of given per-direction base values (e.g. a rest
