@@ -241,7 +241,8 @@ int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
  *   lbm_batch_autotune   times the stream-collide tile shapes (128x1, 64x2,
  *                        32x4 threads) on the batch, `reps` launches each,
  *                        without changing any state, and keeps the fastest;
- *                        *choice receives its index (may be NULL).
+ *                        *choice receives its index and *best_ms its mean
+ *                        time per launch (either may be NULL).
  *   lbm_batch_step       enqueues nsteps steps of every instance on the
  *                        batch's stream; call lbm_batch_sync before using a
  *                        handle on its own again.
@@ -254,7 +255,7 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_footprint(lbm_handle *const *hs, int32_t n, size_t *bytes);
 int lbm_batch_create(lbm_batch **b, lbm_handle *const *hs, int32_t n, void *d_workspace, size_t ws_bytes,
                      void *stream);
-int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *choice);
+int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *choice, double *best_ms);
 int lbm_batch_step(lbm_batch *b, int32_t nsteps);
 int lbm_batch_sync(lbm_batch *b, int32_t *which);
 int64_t lbm_batch_launch_count(lbm_batch *b); /* kernel launches enqueued by lbm_batch_step */

@@ -300,6 +300,8 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
     float c[V][kPop];
     // A warp whose nodes and their neighbours all lie strictly inside the
     // cavity (the common case) pulls without any wall, seam or range test.
+    // (Letting the first and last warp of a row in as well, with range-checked
+    // edge loads, measured slower on small cavities.)
     const int xw = x0 - lane * V; // first node of the warp (a warp spans one row)
     const bool interior = y >= 1 && y + 1 < D.ny && xw >= 1 && xw + 32 * V + 1 <= D.nx;
     if (interior) {
@@ -373,7 +375,7 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
         gen[k] = false;
         if (x < D.nx && fl != kSolid) {
             // frame and newborn nodes belong to k_boundary, which writes them
-            gen[k] = fl == kNewborn || (!interior && (y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1));
+            gen[k] = fl == kNewborn || y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1;
             if (!gen[k]) ok &= collide(D, c[k]);
         } else {
 #pragma unroll
@@ -485,11 +487,13 @@ template <typename T>
 __global__ void __launch_bounds__(128)
     k_boundary_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
 {
+    __shared__ Dev sD;
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
+    copy_dev(sD, a.D);
     const int s0 = __ldg(start + i);
     const Blk blk{(int)blockIdx.x - s0, 0, __ldg(start + i + 1) - s0, 1};
-    boundary_body<T>(a.D, static_cast<const T *>(a.A[parity]), static_cast<T *>(a.A[parity ^ 1]),
+    boundary_body<T>(sD, static_cast<const T *>(a.A[parity]), static_cast<T *>(a.A[parity ^ 1]),
                      a.own[parity], parity, blk);
 }
 

@@ -650,30 +650,38 @@ template <typename T>
 __global__ void __launch_bounds__(kLinkThreads)
     k_links_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity, int ahead)
 {
+    __shared__ Dev sD;
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
-    links_body<T>(nullptr, a.D, static_cast<T *>(a.A[parity]), a.own[parity], a.own[parity ^ 1], parity, ahead,
+    copy_dev(sD, a.D);
+    links_body<T>(nullptr, sD, static_cast<T *>(a.A[parity]), a.own[parity], a.own[parity ^ 1], parity, ahead,
                   (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kPartThreads)
     k_particles_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
 {
+    __shared__ Dev sD;
     const int i = batch_find(start, n, (int)blockIdx.x);
-    particles_body(I[i].D, parity, (int)blockIdx.x - __ldg(start + i));
+    copy_dev(sD, I[i].D);
+    particles_body(sD, parity, (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kBoxThreads)
     k_raster_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
 {
+    __shared__ Dev sD;
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
-    raster_body(a.D, a.own[parity ^ 1], a.D.geo_nxt, a.D.nxt, (int)blockIdx.x - __ldg(start + i));
+    copy_dev(sD, a.D);
+    raster_body(sD, a.own[parity ^ 1], sD.geo_nxt, sD.nxt, (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kBoxThreads)
     k_flags_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
 {
+    __shared__ Dev sD;
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
-    flags_body(a.D, a.own[parity], a.own[parity ^ 1], 1, (int)blockIdx.x - __ldg(start + i));
+    copy_dev(sD, a.D);
+    flags_body(sD, a.own[parity], a.own[parity ^ 1], 1, (int)blockIdx.x - __ldg(start + i));
 }
 
 // Geometry records of the current state and of the previous positions.

@@ -206,7 +206,7 @@ int lbm_batch_create(lbm_batch **out, lbm_handle *const *hs, int32_t n, void *d_
     return LBM_OK;
 }
 
-int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *choice)
+int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *choice, double *best_ms)
 {
     if (!b || reps < 1) return LBM_EINVAL;
     if (b->sticky) return b->sticky;
@@ -248,6 +248,7 @@ int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *choice)
     drop_graphs(b);
     if ((rc = upload_starts(b))) return rc;
     if (choice) *choice = best_tile;
+    if (best_ms) *best_ms = (double)best / reps;
     return LBM_OK;
 }
 

@@ -511,6 +511,16 @@ __device__ __forceinline__ int batch_find(const int *__restrict__ start, int n, 
     }
     return lo;
 }
+// Block-wide copy of an instance's Dev into shared memory (all threads of
+// the block call it; it ends with a barrier).
+__device__ __forceinline__ void copy_dev(Dev &dst, const Dev &src)
+{
+    static_assert(sizeof(Dev) % 4 == 0, "Dev is copied as 32-bit words");
+    const int t = (int)(threadIdx.y * blockDim.x + threadIdx.x), nt = (int)(blockDim.x * blockDim.y);
+    for (int w = t; w < (int)(sizeof(Dev) / 4); w += nt)
+        reinterpret_cast<int *>(&dst)[w] = __ldg(reinterpret_cast<const int *>(&src) + w);
+    __syncthreads();
+}
 // Per-instance arguments of the batched kernels (device table).
 struct InstArgs {
     Dev D;

@@ -79,7 +79,7 @@ _SIGS = [
                                           C.c_int32, C.c_double, _P, _P]),
     ("lbm_batch_footprint", C.c_int, [_P, C.c_int32, C.POINTER(C.c_size_t)]),
     ("lbm_batch_create", C.c_int, [C.POINTER(_P), _P, C.c_int32, _P, C.c_size_t, _P]),
-    ("lbm_batch_autotune", C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32)]),
+    ("lbm_batch_autotune", C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     ("lbm_batch_step", C.c_int, [_P, C.c_int32]),
     ("lbm_batch_sync", C.c_int, [_P, C.POINTER(C.c_int32)]),
     ("lbm_batch_launch_count", C.c_int64, [_P]),
@@ -338,8 +338,12 @@ class Batch:
         return sum(s.nx * s.ny for s in self.sims)
 
     def autotune(self, reps: int = 3) -> int:
+        """Pick the stream-collide tile shape; returns its index (the mean
+        time per stream-collide launch of that shape is in self.tuned_ms)."""
         c = C.c_int32()
-        _check(library().lbm_batch_autotune(self.h, int(reps), C.byref(c)), "lbm_batch_autotune")
+        ms = C.c_double()
+        _check(library().lbm_batch_autotune(self.h, int(reps), C.byref(c), C.byref(ms)), "lbm_batch_autotune")
+        self.tuned_ms = float(ms.value)
         return int(c.value)
 
     def step(self, n: int = 1):
