@@ -227,9 +227,9 @@ int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
 /* ---- batched instances --------------------------------------------------- */
 /* No counterpart in the paper, whose outlook runs several small tasks on one
  * GPU concurrently: a batch steps n independent simulations (handles from
- * lbm_init, same device, same storage, same step parity, i.e. created
- * together or stepped equally often) with one launch per step kernel over
- * all of them, replayed from a CUDA graph.  Every instance computes exactly
+ * lbm_init, same device, same storage, any number of steps already taken)
+ * with one launch per step kernel over all of them, replayed from a CUDA
+ * graph.  Every instance computes exactly
  * what lbm_step computes for it alone (bit for bit).
  *   lbm_batch_footprint  device workspace bytes for the batch's tables.
  *   lbm_batch_create     d_workspace: caller-owned device memory of at least
@@ -249,7 +249,8 @@ int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
  *   lbm_batch_sync       waits for the batch's stream and returns the first
  *                        sticky device error of any instance (its index in
  *                        *which, may be NULL), else LBM_OK.
- * Errors: LBM_EINVAL (mismatched handles, n < 1 or n > 4096), LBM_ENOSPC
+ * Errors: LBM_EINVAL (mixed storage, a handle twice, n < 1 or n > 4096, or
+ * from lbm_batch_step: a handle stepped on its own since), LBM_ENOSPC
  * (workspace too small), LBM_ECUDA. */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_footprint(lbm_handle *const *hs, int32_t n, size_t *bytes);
@@ -260,6 +261,52 @@ int lbm_batch_step(lbm_batch *b, int32_t nsteps);
 int lbm_batch_sync(lbm_batch *b, int32_t *which);
 int64_t lbm_batch_launch_count(lbm_batch *b); /* kernel launches enqueued by lbm_batch_step */
 int lbm_batch_destroy(lbm_batch *b);
+
+/* ---- serving -------------------------------------------------------------- */
+/* No counterpart in the paper (its outlook): a request loop over one
+ * caller-owned device memory pool.  Requests (domain, particles, params,
+ * step budget) queue in arrival order; each lbm_server_tick admits queued
+ * requests, head first, while the pool holds their workspace
+ * (lbm_query_footprint) and fewer than max_active run, advances every active
+ * request by the same number of steps (at most max_steps, and no further
+ * than the earliest budget ends) in one batch (lbm_batch_*), and retires the
+ * requests whose budget is spent: their fields and particles are copied to
+ * host memory held by the server and their device memory returns to the
+ * pool.  The batch is rebuilt whenever requests join or leave (continuous
+ * batching).  A request's result is the state lbm_step gives it alone, bit
+ * for bit, whatever it shared the device with.
+ *   lbm_server_create  d_pool: caller-owned device memory, 256-byte aligned,
+ *                      sub-allocated first-fit; stream: where all device work
+ *                      of the server runs.
+ *   lbm_server_submit  copies the inputs (validated as by lbm_init); *id
+ *                      receives the request's id.  LBM_ENOSPC when its
+ *                      workspace exceeds the whole pool.
+ *   lbm_server_tick    one round; synchronises the stream; *stats (may be
+ *                      NULL) receives its counts and the device time of its
+ *                      steps.
+ *   lbm_server_status  returns 0 queued, 1 active, 2 done, 3 failed (its
+ *                      error code in *err, may be NULL), -1 unknown id.
+ *   lbm_server_result  for a done request: rho - 1, ux, uy, T ([ny][nx] host
+ *                      arrays, NaN at solid nodes) and its n particles; the
+ *                      request is then forgotten.  A failed request returns
+ *                      its error code. */
+typedef struct {
+    int32_t active, queued;   /* after the round */
+    int32_t admitted, retired; /* during the round */
+    int32_t steps;            /* steps every active request took */
+    int32_t reserved;
+    double ms;                /* device time of those steps (CUDA events) */
+    int64_t updates;          /* lattice updates of the round */
+} lbm_server_stats;
+typedef struct lbm_server lbm_server;
+int lbm_server_create(lbm_server **s, void *d_pool, size_t pool_bytes, int32_t max_active, void *stream);
+int lbm_server_submit(lbm_server *s, const lbm_domain *d, const lbm_particle *p, int32_t n,
+                      const lbm_params *prm, int64_t steps, int64_t *id);
+int lbm_server_tick(lbm_server *s, int32_t max_steps, lbm_server_stats *stats);
+int lbm_server_status(lbm_server *s, int64_t id, int32_t *err);
+int lbm_server_result(lbm_server *s, int64_t id, float *drho, float *ux, float *uy, float *T, lbm_particle *p,
+                      int32_t n);
+int lbm_server_destroy(lbm_server *s);
 
 #ifdef __cplusplus
 }

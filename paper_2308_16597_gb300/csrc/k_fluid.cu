@@ -479,7 +479,8 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
     const int gx = (a.D.pitch / V + (int)blockDim.x - 1) / (int)blockDim.x;
     const int gy = (a.D.ny + (int)blockDim.y - 1) / (int)blockDim.y;
     const Blk blk{local % gx, local / gx, gx, gy};
-    sc_body<T, V>(a.D, static_cast<const T *>(a.A[parity]), static_cast<T *>(a.A[parity ^ 1]), resident / gx,
+    const int par = parity ^ a.poff;
+    sc_body<T, V>(a.D, static_cast<const T *>(a.A[par]), static_cast<T *>(a.A[par ^ 1]), resident / gx,
                   resident % gx, blk);
 }
 
@@ -493,8 +494,9 @@ __global__ void __launch_bounds__(128)
     copy_dev(sD, a.D);
     const int s0 = __ldg(start + i);
     const Blk blk{(int)blockIdx.x - s0, 0, __ldg(start + i + 1) - s0, 1};
-    boundary_body<T>(sD, static_cast<const T *>(a.A[parity]), static_cast<T *>(a.A[parity ^ 1]),
-                     a.own[parity], parity, blk);
+    const int par = parity ^ a.poff;
+    boundary_body<T>(sD, static_cast<const T *>(a.A[par]), static_cast<T *>(a.A[par ^ 1]), a.own[par], par,
+                     blk);
 }
 
 // Collision without streaming, for the initial state and for distributions

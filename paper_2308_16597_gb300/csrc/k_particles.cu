@@ -654,7 +654,8 @@ __global__ void __launch_bounds__(kLinkThreads)
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
-    links_body<T>(nullptr, sD, static_cast<T *>(a.A[parity]), a.own[parity], a.own[parity ^ 1], parity, ahead,
+    const int par = parity ^ a.poff;
+    links_body<T>(nullptr, sD, static_cast<T *>(a.A[par]), a.own[par], a.own[par ^ 1], par, ahead,
                   (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kPartThreads)
@@ -663,7 +664,7 @@ __global__ void __launch_bounds__(kPartThreads)
     __shared__ Dev sD;
     const int i = batch_find(start, n, (int)blockIdx.x);
     copy_dev(sD, I[i].D);
-    particles_body(sD, parity, (int)blockIdx.x - __ldg(start + i));
+    particles_body(sD, parity ^ I[i].poff, (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kBoxThreads)
     k_raster_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
@@ -672,7 +673,7 @@ __global__ void __launch_bounds__(kBoxThreads)
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
-    raster_body(sD, a.own[parity ^ 1], sD.geo_nxt, sD.nxt, (int)blockIdx.x - __ldg(start + i));
+    raster_body(sD, a.own[parity ^ a.poff ^ 1], sD.geo_nxt, sD.nxt, (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kBoxThreads)
     k_flags_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
@@ -681,7 +682,8 @@ __global__ void __launch_bounds__(kBoxThreads)
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
-    flags_body(sD, a.own[parity], a.own[parity ^ 1], 1, (int)blockIdx.x - __ldg(start + i));
+    const int par = parity ^ a.poff;
+    flags_body(sD, a.own[par], a.own[par ^ 1], 1, (int)blockIdx.x - __ldg(start + i));
 }
 
 // Geometry records of the current state and of the previous positions.

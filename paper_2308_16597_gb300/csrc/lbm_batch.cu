@@ -32,6 +32,7 @@ size_t table_bytes(int n)
 
 struct lbm_batch {
     std::vector<lbm_handle *> hs;
+    std::vector<int> poff; // per-instance parity offsets
     int n = 0, storage = 0, parity = 0, zone_max = 0;
     cudaStream_t stream = nullptr, cap = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -135,7 +136,7 @@ int check_handles(lbm_handle *const *hs, int32_t n)
     if (!hs || n < 1 || n > kMaxBatch) return LBM_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!hs[i] || hs[i]->sticky) return hs[i] ? hs[i]->sticky : LBM_EINVAL;
-        if (hs[i]->D.storage != hs[0]->D.storage || hs[i]->parity != hs[0]->parity) return LBM_EINVAL;
+        if (hs[i]->D.storage != hs[0]->D.storage) return LBM_EINVAL;
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return LBM_EINVAL;
     }
@@ -167,9 +168,10 @@ int lbm_batch_create(lbm_batch **out, lbm_handle *const *hs, int32_t n, void *d_
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_EINVAL;
     b->hs.assign(hs, hs + n);
+    b->poff.assign(n, 0);
     b->n = n;
     b->storage = hs[0]->D.storage;
-    b->parity = hs[0]->parity;
+    b->parity = 0; // instance i runs at parity b->parity ^ poff[i]
     b->stream = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_workspace);
     b->d_inst = reinterpret_cast<InstArgs *>(ws);
@@ -188,6 +190,9 @@ int lbm_batch_create(lbm_batch **out, lbm_handle *const *hs, int32_t n, void *d_
         inst[i].A[1] = h->A[1];
         inst[i].own[0] = h->own[0];
         inst[i].own[1] = h->own[1];
+        inst[i].poff = h->parity;
+        inst[i].pad = 0;
+        b->poff[i] = h->parity;
         b->zone_max = std::max(b->zone_max, h->D.zone_max);
     }
     if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
@@ -257,7 +262,7 @@ int lbm_batch_step(lbm_batch *b, int32_t nsteps)
     if (!b || nsteps < 0) return LBM_EINVAL;
     if (b->sticky) return b->sticky;
     for (int i = 0; i < b->n; ++i)
-        if (b->hs[i]->parity != b->parity) return LBM_EINVAL; // a handle was stepped on its own
+        if (b->hs[i]->parity != (b->parity ^ b->poff[i])) return LBM_EINVAL; // a handle was stepped on its own
     for (int32_t k = 0; k < nsteps; ++k) {
         int rc;
         if (!b->gexec[b->parity] && (rc = capture_batch(b, b->parity))) return rc;

@@ -526,6 +526,8 @@ struct InstArgs {
     Dev D;
     void *A[2];   // distribution buffers by step parity
     int *own[2];  // owner maps by step parity
+    int poff;     // the instance's step parity = the batch's parity ^ poff
+    int pad;
 };
 
 // ---------------------------------------------------------------------------

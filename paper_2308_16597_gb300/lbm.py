@@ -84,6 +84,12 @@ _SIGS = [
     ("lbm_batch_sync", C.c_int, [_P, C.POINTER(C.c_int32)]),
     ("lbm_batch_launch_count", C.c_int64, [_P]),
     ("lbm_batch_destroy", C.c_int, [_P]),
+    ("lbm_server_create", C.c_int, [C.POINTER(_P), _P, C.c_size_t, C.c_int32, _P]),
+    ("lbm_server_submit", C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int64, C.POINTER(C.c_int64)]),
+    ("lbm_server_tick", C.c_int, [_P, C.c_int32, _P]),
+    ("lbm_server_status", C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32)]),
+    ("lbm_server_result", C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_int32]),
+    ("lbm_server_destroy", C.c_int, [_P]),
 ]
 
 
@@ -360,6 +366,76 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             library().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class lbm_server_stats(C.Structure):
+    _fields_ = [("active", C.c_int32), ("queued", C.c_int32), ("admitted", C.c_int32),
+                ("retired", C.c_int32), ("steps", C.c_int32), ("reserved", C.c_int32),
+                ("ms", C.c_double), ("updates", C.c_int64)]
+
+
+SERVER_QUEUED, SERVER_ACTIVE, SERVER_DONE, SERVER_FAILED = 0, 1, 2, 3
+
+
+class Server:
+    """Request loop over one device memory pool (lbm_server_* in
+    include/lbm.h): submit simulations with a step budget, tick to admit,
+    advance and retire them, fetch the results of finished ones."""
+
+    def __init__(self, pool_bytes: int, max_active: int = 32, stream=None, device="cuda"):
+        import torch
+        lib = library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=device)
+        h = _P()
+        _check(lib.lbm_server_create(C.byref(h), self.pool.data_ptr(), int(pool_bytes), int(max_active),
+                                     self.stream.cuda_stream), "lbm_server_create")
+        self.h = h
+        self._shape = {}
+
+    def submit(self, domain: dict, particles, params: dict, steps: int, storage=LBM_STORE_FP32,
+               flags=0) -> int:
+        d = make_domain(**domain)
+        prm = make_params(**dict(params, storage=storage, flags=flags))
+        parts = pack_particles(particles)
+        rid = C.c_int64()
+        _check(library().lbm_server_submit(self.h, C.byref(d), parts.ctypes.data if len(parts) else None,
+                                           len(parts), C.byref(prm), int(steps), C.byref(rid)),
+               "lbm_server_submit")
+        self._shape[rid.value] = (int(domain["ny"]), int(domain["nx"]), len(parts))
+        return int(rid.value)
+
+    def tick(self, max_steps: int) -> dict:
+        st = lbm_server_stats()
+        _check(library().lbm_server_tick(self.h, int(max_steps), C.byref(st)), "lbm_server_tick")
+        return {k: getattr(st, k) for k, _ in st._fields_ if k != "reserved"}
+
+    def status(self, rid: int):
+        err = C.c_int32()
+        state = library().lbm_server_status(self.h, int(rid), C.byref(err))
+        return int(state), int(err.value)
+
+    def result(self, rid: int):
+        """(rho - 1, ux, uy, T) float32 [ny][nx] and the particles of a done
+        request (which the server then forgets)."""
+        ny, nx, n = self._shape[rid]
+        f = [np.empty((ny, nx), np.float32) for _ in range(4)]
+        parts = np.zeros(n, PARTICLE_DTYPE)
+        _check(library().lbm_server_result(self.h, int(rid), *[a.ctypes.data for a in f],
+                                           parts.ctypes.data if n else None, n), "lbm_server_result")
+        del self._shape[rid]
+        return tuple(f), parts
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().lbm_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
