@@ -438,14 +438,99 @@ def run_ensemble(args):
     return 0
 
 
+# ------------------------------------------------------------------------------ served stream
+def run_served(args):
+    """Poisson stream of 40 sedimentation requests (512^2-2048^2, 2000-20000
+    steps) through the request loop: aggregate MLUPS over the wall time from
+    the first arrival to the last result, p50/p99 per-step and per-request
+    latency."""
+    import torch
+    from paper_2308_16597_gb300 import build as B, lbm
+
+    rank, world, local = dist_env()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    reqs = W.served_stream(40, seed=5)
+    storage = STORAGE_CODES[args.storage]
+    free, _ = torch.cuda.mem_get_info(dev)
+    pool = int(min(0.6 * free, 64 << 30))
+    stream = torch.cuda.Stream(device=dev)
+    step_ms, step_w, lat, updates, dev_ms = [], [], [], 0, 0.0
+    max_active = 0
+    with torch.cuda.stream(stream):
+        srv = lbm.Server(pool, max_active=32, stream=stream)
+        clocks = ClockSampler(local)
+        clocks.start()
+        pending = list(reqs)
+        outstanding = {}
+        t0 = time.perf_counter()
+        while pending or outstanding:
+            now = time.perf_counter() - t0
+            while pending and pending[0][0] <= now:
+                t_arr, wl, steps = pending.pop(0)
+                rid = srv.submit(wl.domain, wl.particles, wl.params, steps, storage=storage)
+                outstanding[rid] = t_arr
+            st = srv.tick(args.tick_steps)
+            if st["steps"] == 0 and st["queued"] == 0 and not outstanding and pending:
+                time.sleep(max(0.0, pending[0][0] - (time.perf_counter() - t0)))
+                continue
+            if st["steps"]:
+                step_ms.append(st["ms"] / st["steps"])
+                step_w.append(st["steps"])
+                updates += st["updates"]
+                dev_ms += st["ms"]
+            max_active = max(max_active, st["active"] + st["retired"])
+            now = time.perf_counter() - t0
+            for rid in list(outstanding):
+                state, err = srv.status(rid)
+                if state == lbm.SERVER_FAILED:
+                    raise RuntimeError("request %d failed: %s" % (rid, lbm.lbm_strerror(err)))
+                if state == lbm.SERVER_DONE:
+                    srv.result(rid)
+                    lat.append(now - outstanding.pop(rid))
+        wall = time.perf_counter() - t0 - reqs[0][0]
+        clk = clocks.stop()
+        srv.close()
+    if rank == 0:
+        def pct(v, w, q):
+            o = np.argsort(v)
+            cw = np.cumsum(np.asarray(w, float)[o])
+            return float(np.asarray(v)[o][np.searchsorted(cw, q * cw[-1])])
+        line = {"metric": METRIC, "value": updates / wall / 1e6, "unit": UNIT, "n_gpus": world,
+                "steps": int(sum(step_w)), "warmup": 0, "ms_per_step": float(np.average(step_ms, weights=step_w)),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "served_poisson20_40req_seed5", "requests": len(reqs),
+                           "storage": args.storage, "pool_gb": pool / 1e9, "max_active": 32,
+                           "tick_steps": args.tick_steps, "peak_concurrent": max_active,
+                           "parallelism": "replicas%d" % world},
+                "latency": {"step_ms_p50": pct(step_ms, step_w, 0.5), "step_ms_p99": pct(step_ms, step_w, 0.99),
+                            "request_s_p50": float(np.percentile(lat, 50)),
+                            "request_s_p99": float(np.percentile(lat, 99))},
+                "device_mlups": updates / (dev_ms / 1e3) / 1e6,
+                "e2e": {"value": updates / wall / 1e6, "unit": UNIT,
+                        "includes": "submission of host inputs, admission, all steps, results read back"},
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cavity4000", "cavity2000", "cavity256", "cavity1024", "ensemble64"],
+    ap.add_argument("--workload", choices=["cavity4000", "cavity2000", "cavity256", "cavity1024", "ensemble64",
+                                           "served"],
                     default="cavity4000")
+    ap.add_argument("--tick-steps", type=int, default=100, help="served: steps per scheduling round")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -454,11 +539,11 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.workload == "ensemble64":
+    if args.workload in ("ensemble64", "served"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the 4000^2 workload only"}))
             return 0
-        return run_ensemble(args)
+        return run_ensemble(args) if args.workload == "ensemble64" else run_served(args)
     wl = {"cavity4000": W.sedimentation_4000, "cavity2000": W.sedimentation_2000,
           "cavity256": W.parity_256,
           "cavity1024": W.crop_1024}[args.workload]()

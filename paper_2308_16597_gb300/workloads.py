@@ -177,6 +177,39 @@ def ensemble(count: int = 64, seed: int = 4, sizes=(256, 512, 768, 1024), n_rang
     return out
 
 
+def served_stream(count: int = 40, seed: int = 5, rate: float = 20.0, sides=(512, 2048),
+                  n_range=(50, 1500), step_range=(2000, 20000), radius: float = 10.0,
+                  nu: float = 0.02, Pr: float = 0.71, u_ff: float = 0.04):
+    """Served stream of sedimentation requests: Poisson arrivals at `rate` per
+    second, square cavities with a side drawn from multiples of 256 in
+    `sides`, a disk count from n_range (capped to what fits in the upper 60 %
+    at a 25 % solid fraction), radius `radius`, step budgets uniform in
+    step_range, and g beta from the free-fall velocity sqrt(g beta dT H) =
+    u_ff on H = ny (Ra from 1e6 at 512 to 2e7 at 2048: one fixed Ra would
+    make the small cavities' flow too fast for the lattice).
+    Returns [(arrival_s, Workload, steps)]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    choices = list(range(sides[0], sides[1] + 1, 256))
+    for k in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        side = int(rng.choice(choices))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        upper = (side - 2 * (radius + S_REP + 1)) * (0.4 * side - 2 * (radius + S_REP))
+        n = max(1, min(n, int(0.25 * upper / (math.pi * radius ** 2))))
+        steps = int(rng.integers(step_range[0], step_range[1] + 1))
+        g = u_ff ** 2 / side
+        lo = radius + S_REP + 1.0
+        parts = rsa_disks(rng, n, radius, lo, side - 1 - lo, max(0.6 * side + radius + S_REP, lo),
+                          side - 1 - lo, min_gap=S_REP + 1.0)
+        parts["rho"] = 1.5
+        parts["T"] = 1.0
+        out.append((t, Workload("request%d_%d_%ddisks" % (k, side, n), cavity(side, side), parts,
+                                base_params(nu, Pr, g), steps), steps))
+    return out
+
+
 def random_state(nx: int, ny: int, seed: int, base_f, base_g, amp: float = 1e-3,
                  T_amp: float = 0.5):
     """Seeded perturbation of given per-direction base values (e.g. a rest
