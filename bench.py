@@ -134,21 +134,19 @@ def measured_peaks() -> dict:
 
 
 def profiled_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current source of the kernel's file; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch from the committed ncu record (profiles/traffic.txt),
+    if it was taken on the current source of the kernel's file; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    with open(path) as fh:
-        d = json.load(fh)
-    e = d.get(kernel)
-    if not e:
-        return None
-    src = os.path.join(ROOT, "paper_2308_16597_gb300", "csrc", e["source"])
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if digest != e.get("source_sha256_16"):
-        return None
-    return e["bytes_per_launch_full"]
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#") or f[0] != kernel or len(f) < 4:
+            continue
+        src = os.path.join(ROOT, "paper_2308_16597_gb300", "csrc", f[1])
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return int(f[3]) if digest == f[2] else None
+    return None
 
 
 # ------------------------------------------------------------------------------------ oracle
