@@ -68,6 +68,12 @@ extern "C" {
 /* lbm_params.flags */
 #define LBM_FLAG_FIXED_PARTICLES 1u /* particles keep their state (tests) */
 #define LBM_FLAG_NO_GRAPH 2u        /* launch kernels directly, no CUDA graph */
+/* Split stream-collide into a pass over the warp tiles away from every
+ * particle, run beside the particle kernels, and a pass over the rest after
+ * them.  Bit-identical to the default single pass; it pays only when few
+ * tiles are near particles (on the 4000^2 / 4800-disk benchmark, where 40 %
+ * are, it is slower). */
+#define LBM_FLAG_OVERLAP 4u
 
 typedef struct {
     int32_t nx, ny;    /* nodes per axis, >= 4 each */

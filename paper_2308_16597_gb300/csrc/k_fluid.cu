@@ -257,10 +257,18 @@ struct Vec<__half, 2> {
     __device__ static W pack(const float *v) { return __floats2half2_rn(v[0] * kHalfScale, v[1] * kHalfScale); }
 };
 
+// Whether warp tile t of row y is within reach of a particle this step.
+__device__ __forceinline__ bool tile_near(const Dev &D, int y, int t)
+{
+    const int b = y * D.near_tpr + t;
+    return (__ldg(D.near + (b >> 5)) >> (b & 31)) & 1u;
+}
+
 // Stream-collide kernel, V consecutive nodes per thread (one vector load and
 // one vector store per plane); FP32 runs V = 1, the 16-bit storages V = 2 so
-// that every load still moves four bytes.
-template <typename T, int V>
+// that every load still moves four bytes.  mode selects all warp tiles, or
+// only those away from / within reach of this step's particles.
+template <typename T, int V, int mode = kSCAll>
 __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
                                         int ahead_y, int ahead_x, const Blk blk)
 {
@@ -282,6 +290,12 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
         const int lo = max(xs - kAl, 0), hi = min(xs + span + kAl, D.pitch);
         const int p = threadIdx.x;
         for (int yy = yb; yy < min(yb + (int)blockDim.y, D.ny) && hi > lo; ++yy) {
+            if constexpr (mode != kSCAll) { // only rows of this pass's tiles
+                bool want = false;
+                for (int t = xs / (32 * V); t * 32 * V < min(xs + span, D.pitch); ++t)
+                    want |= tile_near(D, yy, t) == (mode == kSCNear);
+                if (!want) continue;
+            }
             int ys = yy - ey(pdir(p));
             if (ys < 0 || ys >= D.ny) {
                 if (!D.per_y) continue;
@@ -296,6 +310,9 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
     const int x0 = (blk.x * (int)blockDim.x + (int)threadIdx.x) * V;
     const int y = blk.y * (int)blockDim.y + (int)threadIdx.y;
     if (y >= D.ny) return; // uniform across the warp: blockDim.x is a multiple of 32
+    if constexpr (mode != kSCAll)
+        if (tile_near(D, y, (x0 - (lane * V)) / (32 * V)) != (mode == kSCNear))
+            return; // the other pass's tile (uniform across the warp)
     const bool act = x0 < D.pitch; // the pitch is a multiple of 32, so all V nodes are in the row
     float c[V][kPop];
     // A warp whose nodes and their neighbours all lie strictly inside the
@@ -449,11 +466,11 @@ __device__ __forceinline__ void boundary_body(const Dev &D, const T *__restrict_
     if (!ok) atomicOr(&D.status->err, kErrNumeric);
 }
 
-template <typename T, int V>
+template <typename T, int V, int mode>
 __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
     k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ahead_y, int ahead_x)
 {
-    sc_body<T, V>(D, Ain, Aout, ahead_y, ahead_x, this_blk());
+    sc_body<T, V, mode>(D, Ain, Aout, ahead_y, ahead_x, this_blk());
 }
 
 template <typename T>
@@ -560,16 +577,15 @@ __global__ void k_fields(const Dev D, const S *__restrict__ A, int row0, float *
 
 namespace {
 
-template <typename T, int V>
-cudaError_t stream_collide_t(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
-                             cudaStream_t s)
+template <typename T, int V, int mode>
+cudaError_t stream_collide_m(const Dev &D, const void *Ain, void *Aout, cudaStream_t s)
 {
     static int resident = 0;
     if (!resident) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide<T, V>, kSCThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide<T, V, mode>, kSCThreads, 0);
         resident = max(1, sms * per_sm);
     }
     const int tx = D.pitch / V; // threads per row (the pitch is a multiple of 32)
@@ -578,9 +594,19 @@ cudaError_t stream_collide_t(const Dev &D, const void *Ain, void *Aout, const in
     const int by = kSCThreads / bx;
     dim3 block(bx, by);
     dim3 grid((tx + bx - 1) / bx, (D.ny + by - 1) / by);
-    k_stream_collide<T, V><<<grid, block, 0, s>>>(D, static_cast<const T *>(Ain), static_cast<T *>(Aout),
-                                                  resident / (int)grid.x, resident % (int)grid.x);
+    k_stream_collide<T, V, mode><<<grid, block, 0, s>>>(D, static_cast<const T *>(Ain), static_cast<T *>(Aout),
+                                                        resident / (int)grid.x, resident % (int)grid.x);
     return cudaGetLastError();
+}
+
+template <typename T, int V>
+cudaError_t stream_collide_t(const Dev &D, const void *Ain, void *Aout, int mode, cudaStream_t s)
+{
+    switch (mode) {
+    case kSCFar: return stream_collide_m<T, V, kSCFar>(D, Ain, Aout, s);
+    case kSCNear: return stream_collide_m<T, V, kSCNear>(D, Ain, Aout, s);
+    default: return stream_collide_m<T, V, kSCAll>(D, Ain, Aout, s);
+    }
 }
 
 template <typename T>
@@ -619,13 +645,18 @@ cudaError_t fields_t(const Dev &D, const void *A, int row0, int rows, float *rho
 
 } // namespace
 
-cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
-                                  cudaStream_t s)
+int near_tiles_per_row(int storage, int pitch)
+{
+    const int span = 32 * (storage == LBM_STORE_FP32 ? 1 : 2);
+    return (pitch + span - 1) / span;
+}
+
+cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, int mode, cudaStream_t s)
 {
     switch (D.storage) {
-    case LBM_STORE_FP32: return stream_collide_t<float, 1>(D, Ain, Aout, own_cur, parity, s);
-    case LBM_STORE_BF16: return stream_collide_t<__nv_bfloat16, 2>(D, Ain, Aout, own_cur, parity, s);
-    case LBM_STORE_FP16: return stream_collide_t<__half, 2>(D, Ain, Aout, own_cur, parity, s);
+    case LBM_STORE_FP32: return stream_collide_t<float, 1>(D, Ain, Aout, mode, s);
+    case LBM_STORE_BF16: return stream_collide_t<__nv_bfloat16, 2>(D, Ain, Aout, mode, s);
+    case LBM_STORE_FP16: return stream_collide_t<__half, 2>(D, Ain, Aout, mode, s);
     default: return cudaErrorInvalidValue;
     }
 }

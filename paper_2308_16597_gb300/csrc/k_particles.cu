@@ -97,21 +97,17 @@ __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *tm, int x, in
 }
 
 // Fixed slot (Sec. 3) of the link from zone node (a, b) along e_k, or -1 for
-// a corner line that cannot carry a link.
+// a corner line that cannot carry a link.  Axis directions: e1/e3 by row b,
+// e2/e4 by column a (N lines each); diagonals: e5/e7 by a - b + N - 2, e6/e8
+// by a + b - 1 (2N - 3 lines each).  Branch-free, so that the lanes of a warp
+// with different directions do not diverge.
 __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 {
     const int M = 2 * N - 3;
-    switch (k) {
-    case 1: return b;
-    case 2: return N + a;
-    case 3: return 2 * N + b;
-    case 4: return 3 * N + a;
-    default: {
-        const int line = (k == 5 || k == 7) ? a - b + N - 2 : a + b - 1;
-        if (line < 0 || line >= M) return -1;
-        return 4 * N + (k - 5) * M + line;
-    }
-    }
+    const bool axis = k <= 4, odd = k & 1;
+    const int line = odd ? (axis ? b : a - b + N - 2) : (axis ? a : a + b - 1);
+    const int slot = axis ? (k - 1) * N + line : 4 * N + (k - 5) * M + line;
+    return (axis || (line >= 0 && line < M)) ? slot : -1;
 }
 
 // One CTA per particle.  Phases:
@@ -125,7 +121,7 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 //     places later in launch order (about one residency wave ahead), and a
 //     warp prefetches that particle's owner rows, so that the scattered
 //     reads of phases 1 and 4 hit L2;
-//  2. thread (b, k) intersects the fluid mask of zone row b with the owner
+//  2. thread (k, b) intersects the fluid mask of zone row b with the owner
 //     mask of row b + e_k,y shifted by e_k,x: each set bit is a link, which
 //     claims its fixed slot of the index array (direction k, line through
 //     the zone; Sec. 3) in an occupancy bitmap;
@@ -253,11 +249,15 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
     for (int w = tid; w < nw; w += kLinkThreads) occ[w] = 0u;
     __syncthreads();
 
-    // ---- 2. link detection: thread (b, k), one mask intersection per row
+    // ---- 2. link detection: warp w takes directions 2w + 1 and 2w + 2 (one
+    // direction per warp at a time, no divergence), lane l rows l, l + 32
+    static_assert(kLinkThreads == 128, "four warps cover the eight directions in pairs");
     {
         const unsigned long long Z = ((1ull << N) - 1ull) << off;
-        for (int e = tid; e < 8 * N; e += kLinkThreads) {
-            const int b = e >> 3, k = (e & 7) + 1, kx = ex(k), ky = ey(k);
+        for (int e = lane; e < 2 * 64; e += 32) {
+            const int k = 2 * warp + 1 + (e >> 6), b = e & 63;
+            if (b >= N) continue;
+            const int kx = ex(k), ky = ey(k);
             const unsigned long long o = Om[b + 2 + ky];
             unsigned long long m = Fm[b + 2] & (kx > 0 ? o >> 1 : kx < 0 ? o << 1 : o) & Z;
             while (m) {
@@ -418,7 +418,97 @@ __device__ __noinline__ void pair_force(float4 pa, float2 ca, float4 pb, float2 
     df_add(fh_y, fl_y, mag * dy / dist, 0.f);
 }
 
-__device__ __forceinline__ void particles_body(const Dev &D, int parity, const int blk)
+// Zone of a disk at (x, y) with radius r: N x N nodes from
+// (floor(x - r) - 1, floor(y - r) - 1); it holds every node of the disk and
+// every fluid node linked to it.
+struct Box {
+    int X0, Y0, N;
+};
+__device__ __forceinline__ Box box_of(const GeomRec &G) { return Box{G.X0, G.Y0, G.N}; }
+
+// Raster of one disk by one warp (lane per zone row).
+__device__ __forceinline__ void raster_one(const Dev &D, int *own, const GeomRec &G, double x, double y, double r,
+                                           int p)
+{
+    const int lane = threadIdx.x & 31;
+    const Box B = box_of(G);
+    const DiskDF dk = geom_df(G);
+    const int ic = G.ic; // the node of each row nearest the centre
+    for (int b = lane; b < B.N; b += 32) {
+        const int j = B.Y0 + b;
+        if (j < 0 || j >= D.ny) continue;
+        if (!in_disk_df(ic, j, dk, x, y, r)) continue; // then no node of the row is inside
+        float dyh, dyl;
+        df_offset(j, dk.yh, dk.yl, dyh, dyl);
+        const float h = sqrtf(fmaxf(dk.r2h - dyh * dyh, 0.f));
+        const int xmin = B.X0, xmax = B.X0 + B.N - 1;
+        int lo = min(ic, (int)ceilf(dk.xh - h)), hi = max(ic, (int)floorf(dk.xh + h));
+        lo = max(lo, xmin);
+        hi = min(hi, xmax);
+        while (lo > xmin && in_disk_df(lo - 1, j, dk, x, y, r)) --lo;
+        while (!in_disk_df(lo, j, dk, x, y, r)) ++lo;
+        while (hi < xmax && in_disk_df(hi + 1, j, dk, x, y, r)) ++hi;
+        while (!in_disk_df(hi, j, dk, x, y, r)) --hi;
+        lo = max(lo, 0);
+        hi = min(hi, D.nx - 1);
+        int *row = own + (long long)j * D.nx;
+        for (int i = lo; i <= hi; ++i) atomicMax(row + i, p);
+    }
+}
+
+// FP64 tail of the particle update for particle b: total force, Newton-Euler
+// step, domain checks, new state and geometry record.  (fxh + fxl, fyh + fyl:
+// the pair repulsion summed in double-float.)
+__device__ __forceinline__ void particle_tail(const Dev &D, int b, float fxh, float fxl, float fyh, float fyl)
+{
+    double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
+    double th = D.cur.th[b], om = D.cur.om[b];
+    const double r = D.cur.r[b], rho = D.cur.rho[b];
+    double Fx, Fy, Tz;
+    assemble_force(D.lsum[b], x, y, Fx, Fy, Tz);
+    D.force[3 * b + 0] = Fx;
+    D.force[3 * b + 1] = Fy;
+    D.force[3 * b + 2] = Tz;
+    const double Cb = kPi * r * r * (rho - D.rho_f) * D.g;
+    Fy -= (rho - D.rho_f) * kPi * r * r * D.g;
+    if (!D.per_x) {
+        Fx += repulsion((x + 0.5) - r, D.s_rep, D.eps_w, Cb);
+        Fx -= repulsion(((double)D.nx - 0.5 - x) - r, D.s_rep, D.eps_w, Cb);
+    }
+    if (!D.per_y) {
+        Fy += repulsion((y + 0.5) - r, D.s_rep, D.eps_w, Cb);
+        Fy -= repulsion(((double)D.ny - 0.5 - y) - r, D.s_rep, D.eps_w, Cb);
+    }
+    Fx += (double)fxh + (double)fxl;
+    Fy += (double)fyh + (double)fyl;
+    if (!D.fixed) {
+        const double M = rho * kPi * r * r, I = 0.5 * M * r * r;
+        const double ux1 = ux + Fx / M, uy1 = uy + Fy / M, om1 = om + Tz / I;
+        x += 0.5 * (ux + ux1);
+        y += 0.5 * (uy + uy1);
+        th += 0.5 * (om + om1);
+        ux = ux1;
+        uy = uy1;
+        om = om1;
+    }
+    // a disk that would leave the cavity, move a node or more in one step
+    // (beyond the reach of the near-tile bitmap), or whose state is no longer
+    // finite raises the (sticky) domain error and stays where it was, so that
+    // its zone stays inside the arrays every later kernel indexes
+    const double xo = D.cur.x[b], yo = D.cur.y[b];
+    if (!(x - r >= -0.5 && x + r <= (double)D.nx - 0.5 && y - r >= -0.5 && y + r <= (double)D.ny - 0.5 &&
+          fabs(x - xo) < 1.0 && fabs(y - yo) < 1.0)) {
+        atomicOr(&D.status->err, kErrDomain);
+        x = xo;
+        y = yo;
+    }
+    const double T = D.cur.T[b];
+    D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
+    D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T;
+    D.geo_nxt[b] = make_geom(x, y, r, ux, uy, om, T, rho, D.rho_f, D.g);
+}
+
+__device__ __forceinline__ void particles_body(const Dev &D, int parity, int *own_nxt, const int blk)
 {
     __shared__ float4 sp[kPartTile];
     __shared__ float2 sc[kPartTile];
@@ -461,60 +551,16 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, const i
         sred[2][warp] = fhy; sred[3][warp] = fly;
     }
     __syncthreads();
-    if (warp != 0 || lane >= kPartPerBlock) return;
     const int b = blk * kPartPerBlock + lane;
-    if (b >= D.np) return;
-    double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
-    double th = D.cur.th[b], om = D.cur.om[b];
-    const double r = D.cur.r[b], rho = D.cur.rho[b];
-    double Fx, Fy, Tz;
-    assemble_force(D.lsum[b], x, y, Fx, Fy, Tz);
-    D.force[3 * b + 0] = Fx;
-    D.force[3 * b + 1] = Fy;
-    D.force[3 * b + 2] = Tz;
-    const double Cb = kPi * r * r * (rho - D.rho_f) * D.g;
-    Fy -= (rho - D.rho_f) * kPi * r * r * D.g;
-    if (!D.per_x) {
-        Fx += repulsion((x + 0.5) - r, D.s_rep, D.eps_w, Cb);
-        Fx -= repulsion(((double)D.nx - 0.5 - x) - r, D.s_rep, D.eps_w, Cb);
-    }
-    if (!D.per_y) {
-        Fy += repulsion((y + 0.5) - r, D.s_rep, D.eps_w, Cb);
-        Fy -= repulsion(((double)D.ny - 0.5 - y) - r, D.s_rep, D.eps_w, Cb);
-    }
-    Fx += (double)sred[0][lane] + (double)sred[1][lane];
-    Fy += (double)sred[2][lane] + (double)sred[3][lane];
-    if (!D.fixed) {
-        const double M = rho * kPi * r * r, I = 0.5 * M * r * r;
-        const double ux1 = ux + Fx / M, uy1 = uy + Fy / M, om1 = om + Tz / I;
-        x += 0.5 * (ux + ux1);
-        y += 0.5 * (uy + uy1);
-        th += 0.5 * (om + om1);
-        ux = ux1;
-        uy = uy1;
-        om = om1;
-    }
-    // a disk that would leave the cavity, or whose state is no longer finite,
-    // raises the (sticky) domain error and stays where it was, so that its
-    // zone stays inside the arrays every later kernel indexes
-    if (!(x - r >= -0.5 && x + r <= (double)D.nx - 0.5 && y - r >= -0.5 && y + r <= (double)D.ny - 0.5)) {
-        atomicOr(&D.status->err, kErrDomain);
-        x = D.cur.x[b];
-        y = D.cur.y[b];
-    }
-    const double T = D.cur.T[b];
-    D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
-    D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T;
-    D.geo_nxt[b] = make_geom(x, y, r, ux, uy, om, T, rho, D.rho_f, D.g);
+    if (warp == 0 && lane < kPartPerBlock && b < D.np) particle_tail(D, b, sred[0][lane], sred[1][lane],
+                                                                      sred[2][lane], sred[3][lane]);
+    // then the owner map at the new positions: warp w rasters the block's
+    // particle w (its own new state only, so no other block is waited for)
+    __syncthreads();
+    if (a < D.np) raster_one(D, own_nxt, D.geo_nxt[a], D.nxt.x[a], D.nxt.y[a], D.nxt.r[a], a);
 }
 
-// Zone of a disk at (x, y) with radius r: N x N nodes from
-// (floor(x - r) - 1, floor(y - r) - 1); it holds every node of the disk and
-// every fluid node linked to it.
-struct Box {
-    int X0, Y0, N;
-};
-__device__ __forceinline__ Box box_of(const GeomRec &G) { return Box{G.X0, G.Y0, G.N}; }
+
 
 // Owner map: node (i,j) belongs to disk p iff (i - x)^2 + (j - y)^2 <= r^2
 // (exact FP64); where disks overlap the highest index wins (atomicMax, so
@@ -522,37 +568,13 @@ __device__ __forceinline__ Box box_of(const GeomRec &G) { return Box{G.X0, G.Y0,
 // lane per zone row: the predicate holds on one contiguous run of each row
 // (it is monotone in |i - x|), so the run is found from an FP32 estimate of
 // its ends and settled with the exact predicate at the ends only.
+
 __device__ __forceinline__ void raster_body(const Dev &D, int *own, const GeomRec *__restrict__ geo,
                                             const PartSoA &pos, const int blk)
 {
-    const int lane = threadIdx.x & 31;
     const int p = blk * (kBoxThreads / 32) + (threadIdx.x >> 5);
     if (p >= D.np) return;
-    const GeomRec G = geo[p];
-    const double x = pos.x[p], y = pos.y[p], r = pos.r[p]; // for the FP64 fallback only
-    const Box B = box_of(G);
-    const DiskDF dk = geom_df(G);
-    const int ic = G.ic; // the node of each row nearest the centre
-    for (int b = lane; b < B.N; b += 32) {
-        const int j = B.Y0 + b;
-        if (j < 0 || j >= D.ny) continue;
-        if (!in_disk_df(ic, j, dk, x, y, r)) continue; // then no node of the row is inside
-        float dyh, dyl;
-        df_offset(j, dk.yh, dk.yl, dyh, dyl);
-        const float h = sqrtf(fmaxf(dk.r2h - dyh * dyh, 0.f));
-        const int xmin = B.X0, xmax = B.X0 + B.N - 1;
-        int lo = min(ic, (int)ceilf(dk.xh - h)), hi = max(ic, (int)floorf(dk.xh + h));
-        lo = max(lo, xmin);
-        hi = min(hi, xmax);
-        while (lo > xmin && in_disk_df(lo - 1, j, dk, x, y, r)) --lo;
-        while (!in_disk_df(lo, j, dk, x, y, r)) ++lo;
-        while (hi < xmax && in_disk_df(hi + 1, j, dk, x, y, r)) ++hi;
-        while (!in_disk_df(hi, j, dk, x, y, r)) --hi;
-        lo = max(lo, 0);
-        hi = min(hi, D.nx - 1);
-        int *row = own + (long long)j * D.nx;
-        for (int i = lo; i <= hi; ++i) atomicMax(row + i, p);
-    }
+    raster_one(D, own, geo[p], pos.x[p], pos.y[p], pos.r[p], p);
 }
 
 // Flags over the rectangle that holds the particle's zones one step back, now
@@ -620,6 +642,25 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
     }
 }
 
+// Near-tile bitmap: every warp tile (one row, 32 V nodes) that meets a
+// particle's zone at the current position widened by kNearMargin nodes.  One
+// thread per particle and zone row; the bitmap is cleared beforehand.
+__global__ void __launch_bounds__(128) k_near_mask(const Dev D, int span)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Nm = D.zone_max + 2 * kNearMargin;
+    const int p = g / Nm, r = g - p * Nm;
+    if (p >= D.np) return;
+    const GeomRec G = D.geo_cur[p];
+    const int j = G.Y0 - kNearMargin + r;
+    if (r >= G.N + 2 * kNearMargin || j < 0 || j >= D.ny) return;
+    const int x0 = max(G.X0 - kNearMargin, 0), x1 = min(G.X0 + G.N - 1 + kNearMargin, D.pitch - 1);
+    for (int t = x0 / span; t <= x1 / span; ++t) {
+        const int b = j * D.near_tpr + t;
+        atomicOr(D.near + (b >> 5), 1u << (b & 31));
+    }
+}
+
 // ---- single-instance kernels
 template <typename T>
 __global__ void __launch_bounds__(kLinkThreads)
@@ -628,9 +669,9 @@ __global__ void __launch_bounds__(kLinkThreads)
 {
     links_body<T>(&tmA, D, A, own, own_nxt, parity, ahead, (int)blockIdx.x);
 }
-__global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int parity)
+__global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int parity, int *own_nxt)
 {
-    particles_body(D, parity, (int)blockIdx.x);
+    particles_body(D, parity, own_nxt, (int)blockIdx.x);
 }
 __global__ void __launch_bounds__(kBoxThreads)
     k_raster(const Dev D, int *own, const GeomRec *__restrict__ geo, const PartSoA pos)
@@ -664,7 +705,8 @@ __global__ void __launch_bounds__(kPartThreads)
     __shared__ Dev sD;
     const int i = batch_find(start, n, (int)blockIdx.x);
     copy_dev(sD, I[i].D);
-    particles_body(sD, parity ^ I[i].poff, (int)blockIdx.x - __ldg(start + i));
+    const int par = parity ^ I[i].poff;
+    particles_body(sD, par, I[i].own[par ^ 1], (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kBoxThreads)
     k_raster_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
@@ -875,10 +917,21 @@ void batch_blocks(const Dev &D, dim3 sc_block, int out[kBatchPhases])
     out[kBBoundary] = kBoundaryBlocksPerInstance;
 }
 
-cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s)
+cudaError_t launch_near_mask(const Dev &D, cudaStream_t s)
+{
+    const size_t words = ((size_t)D.ny * D.near_tpr + 31) / 32;
+    cudaError_t e = cudaMemsetAsync(D.near, 0, words * sizeof(unsigned), s);
+    if (e != cudaSuccess || D.np == 0) return e;
+    const int span = 32 * (D.storage == LBM_STORE_FP32 ? 1 : 2);
+    const long long threads = (long long)D.np * (D.zone_max + 2 * kNearMargin);
+    k_near_mask<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(D, span);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particles(const Dev &D, int parity, int *own_nxt, cudaStream_t s)
 {
     const int blocks = D.np > 0 ? (D.np + kPartPerBlock - 1) / kPartPerBlock : 1;
-    k_particles<<<blocks, kPartThreads, 0, s>>>(D, parity);
+    k_particles<<<blocks, kPartThreads, 0, s>>>(D, parity, own_nxt);
     return cudaGetLastError();
 }
 

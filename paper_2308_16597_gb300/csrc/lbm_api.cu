@@ -117,6 +117,7 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
     for (int a = 0; a < n; ++a) zmax = std::max(zmax, zone_size(p[a].r));
     L.newborn_cap = std::max(1024, 4 * n * zmax);
     L.newborn = take((size_t)L.newborn_cap * sizeof(int));
+    L.near = take(((size_t)d->ny * near_tiles_per_row(storage, L.pitch) + 31) / 32 * sizeof(unsigned));
     L.total = off;
 }
 
@@ -130,7 +131,8 @@ const char *kKernelNames[kNumKernelKinds] = {"link_gather_bb_force", "particle_u
                                              "owner_raster",
                                              "node_flags",           "stream_collide",
                                              "boundary_refill",
-                                             "init_collide",         "fields"};
+                                             "init_collide",         "fields",
+                                             "near_mask",            "stream_collide_near"};
 
 } // namespace
 
@@ -193,7 +195,8 @@ int timed(lbm_handle *h, int kind, cudaStream_t st, F &&launch)
 // One time step, in the order
 //   gather + bounce-back + force (particle state at n, owner map at n; also
 //   clears the other owner map over the zones at n - 1)
-//   -> particle update (n -> n+1) -> owner map and flags at n+1
+//   -> particle update (n -> n+1) with the raster of the new positions
+//   -> flags at n+1
 //   -> fused stream + collide of A_n into A_{n+1}, beside the general path
 //      (frame and newborn nodes, refill).
 int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
@@ -202,18 +205,38 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
     void *Ain = h->A[par], *Aout = h->A[par ^ 1];
     int *oc = h->own[par], *on = h->own[par ^ 1];
     int rc;
+    const bool serial = h->timing && st == h->stream; // per-kernel timing: one kernel at a time
+    const bool overlap = h->np > 0 && (h->prm.flags & LBM_FLAG_OVERLAP);
+    if (overlap) {
+        // the lattice away from every particle needs nothing of this step's
+        // particle work: stream-collide those tiles beside it
+        if (serial) {
+            if ((rc = timed(h, kKNearMask, st, [&] { return launch_near_mask(D, st); }))) return rc;
+            if ((rc = timed(h, kKStreamCollide, st, [&] { return launch_stream_collide(D, Ain, Aout, kSCFar, st); })))
+                return rc;
+        } else {
+            CK(h, cudaEventRecord(h->fork0, st));
+            CK(h, cudaStreamWaitEvent(h->far, h->fork0, 0));
+            if ((rc = timed(h, kKNearMask, h->far, [&] { return launch_near_mask(D, h->far); }))) return rc;
+            if ((rc = timed(h, kKStreamCollide, h->far,
+                            [&] { return launch_stream_collide(D, Ain, Aout, kSCFar, h->far); })))
+                return rc;
+            CK(h, cudaEventRecord(h->join0, h->far));
+        }
+    }
     if (h->np > 0) {
         if ((rc = timed(h, kKLinks, st, [&] { return launch_links(D, Ain, oc, on, par, h->tmA[par], st); }))) return rc;
     }
-    if ((rc = timed(h, kKParticles, st, [&] { return launch_particles(D, par, st); }))) return rc;
+    // particle update and raster of the new positions (one kernel)
+    if ((rc = timed(h, kKParticles, st, [&] { return launch_particles(D, par, on, st); }))) return rc;
     if (h->np > 0) {
-        if ((rc = timed(h, kKRaster, st, [&] { return launch_raster(D, on, D.geo_nxt, D.nxt, st); })))
-            return rc;
         if ((rc = timed(h, kKFlags, st, [&] { return launch_flags(D, oc, on, 1, st); }))) return rc;
     }
-    if (h->timing && st == h->stream) { // per-kernel timing: one stream, one kernel at a time
-        if ((rc = timed(h, kKStreamCollide, st, [&] { return launch_stream_collide(D, Ain, Aout, oc, par, st); })))
-            return rc;
+    if (overlap && !serial) CK(h, cudaStreamWaitEvent(st, h->join0, 0));
+    const int kind = overlap ? kKStreamCollideNear : kKStreamCollide;
+    const int mode = overlap ? kSCNear : kSCAll;
+    if (serial) {
+        if ((rc = timed(h, kind, st, [&] { return launch_stream_collide(D, Ain, Aout, mode, st); }))) return rc;
         return timed(h, kKBoundary, st, [&] { return launch_boundary(D, Ain, Aout, oc, par, st); });
     }
     // k_boundary and k_stream_collide write disjoint nodes of Aout and read
@@ -223,13 +246,16 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
     if ((rc = timed(h, kKBoundary, h->side, [&] { return launch_boundary(D, Ain, Aout, oc, par, h->side); })))
         return rc;
     CK(h, cudaEventRecord(h->join, h->side));
-    if ((rc = timed(h, kKStreamCollide, st, [&] { return launch_stream_collide(D, Ain, Aout, oc, par, st); })))
-        return rc;
+    if ((rc = timed(h, kind, st, [&] { return launch_stream_collide(D, Ain, Aout, mode, st); }))) return rc;
     CK(h, cudaStreamWaitEvent(st, h->join, 0));
     return LBM_OK;
 }
 
-int kernels_per_step(const lbm_handle *h) { return h->np > 0 ? 6 : 3; }
+int kernels_per_step(const lbm_handle *h)
+{
+    if (h->np == 0) return 3;
+    return (h->prm.flags & LBM_FLAG_OVERLAP) ? 7 : 5;
+}
 
 int capture(lbm_handle *h, int par)
 {
@@ -306,6 +332,8 @@ void fill_dev(lbm_handle *h)
     D.flags = reinterpret_cast<uint8_t *>(ws + L.flags);
     D.newborn = reinterpret_cast<int *>(ws + L.newborn);
     D.newborn_cap = L.newborn_cap;
+    D.near = reinterpret_cast<unsigned *>(ws + L.near);
+    D.near_tpr = near_tiles_per_row(P.storage, L.pitch);
     D.slot_node = reinterpret_cast<int *>(ws + L.slot_node);
     D.slot_q = reinterpret_cast<float *>(ws + L.slot_q);
     D.slot_base = reinterpret_cast<int *>(ws + L.slot_base);
@@ -426,8 +454,11 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
     };
     if (cudaMemsetAsync(h->D.status, 0, sizeof(Status), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
     if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->far, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join0, cudaEventDisableTiming) != cudaSuccess)
         return fail(LBM_ECUDA);
     if (prepare_links(h->D) != cudaSuccess) return fail(LBM_ECUDA);
     for (int b = 0; b < 2 && n > 0; ++b)
@@ -539,8 +570,14 @@ int lbm_destroy(lbm_handle *h)
         cudaStreamSynchronize(h->side);
         cudaStreamDestroy(h->side);
     }
+    if (h->far) {
+        cudaStreamSynchronize(h->far);
+        cudaStreamDestroy(h->far);
+    }
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
+    if (h->fork0) cudaEventDestroy(h->fork0);
+    if (h->join0) cudaEventDestroy(h->join0);
     for (auto &e : h->ev) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);

@@ -84,8 +84,8 @@ int upload_starts(lbm_batch *b)
 
 const int *starts(const lbm_batch *b, int ph) { return b->d_start + (size_t)ph * (b->n + 1); }
 
-// One step of every instance, in the order of lbm_step: links -> particles ->
-// raster -> flags -> stream-collide beside the general path.
+// One step of every instance, in the order of lbm_step: links -> particles
+// (and raster) -> flags -> stream-collide beside the general path.
 int enqueue_batch_step(lbm_batch *b, int par, cudaStream_t st)
 {
     const InstArgs *I = b->d_inst;
@@ -93,7 +93,6 @@ int enqueue_batch_step(lbm_batch *b, int par, cudaStream_t st)
     BCK(b, launch_links_batch(I, starts(b, kBLinks), n, b->total[kBLinks], b->storage, par, b->links_ahead,
                               b->links_smem, st));
     BCK(b, launch_particles_batch(I, starts(b, kBParticles), n, b->total[kBParticles], par, st));
-    BCK(b, launch_raster_batch(I, starts(b, kBRaster), n, b->total[kBRaster], par, st));
     BCK(b, launch_flags_batch(I, starts(b, kBFlags), n, b->total[kBFlags], par, st));
     BCK(b, cudaEventRecord(b->fork, st));
     BCK(b, cudaStreamWaitEvent(b->side, b->fork, 0));
@@ -269,7 +268,7 @@ int lbm_batch_step(lbm_batch *b, int32_t nsteps)
         BCK(b, cudaGraphLaunch(b->gexec[b->parity], b->stream));
         b->parity ^= 1;
         for (int i = 0; i < b->n; ++i) b->hs[i]->parity ^= 1;
-        for (int ph = 0; ph < kBatchPhases; ++ph) b->launches += b->total[ph] > 0;
+        for (int ph = 0; ph < kBatchPhases; ++ph) b->launches += ph != kBRaster && b->total[ph] > 0;
     }
     return LBM_OK;
 }

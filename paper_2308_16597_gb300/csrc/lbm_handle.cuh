@@ -14,7 +14,7 @@ struct Layout {
     long long ps = 0;
     size_t nslots = 0;
     size_t A[2], own[2], flags, slot_node, slot_q, slot_base, cur, nxt, prev, force, pos4, prc, lsum,
-        geo[3], status, pack, stage, newborn, total;
+        geo[3], status, pack, stage, newborn, near, total;
     int newborn_cap = 0;
     int stage_rows = 0;
 };
@@ -30,7 +30,8 @@ struct lbm_handle {
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
     cudaStream_t side = nullptr;           // branch for k_boundary beside k_stream_collide
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t far = nullptr;            // branch for the far-tile pass beside the particle kernels
+    cudaEvent_t fork = nullptr, join = nullptr, fork0 = nullptr, join0 = nullptr;
     lbm::Dev D;
     void *A[2]; // planes of D.storage elements
     int *own[2];

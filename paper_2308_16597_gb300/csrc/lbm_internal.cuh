@@ -118,6 +118,8 @@ struct Dev {
     uint8_t *flags;    // [ny][pitch]
     int *newborn;      // [newborn_cap]: j * nx + i of this step's newborn nodes off the cavity frame
     int newborn_cap;
+    unsigned *near;    // bit per warp tile (row, 32 V nodes) within reach of a particle this step
+    int near_tpr;      // warp tiles per row of that bitmap
     int *slot_node;    // [nslots]
     float *slot_q;     // [nslots]
     int *slot_base;    // [np + 1]
@@ -534,11 +536,22 @@ struct InstArgs {
 // Kernel launchers (defined in k_fluid.cu and k_particles.cu).
 // ---------------------------------------------------------------------------
 enum KernelKind { kKLinks = 0, kKParticles, kKRaster, kKFlags, kKStreamCollide,
-                  kKBoundary, kKInit, kKFields, kNumKernelKinds };
+                  kKBoundary, kKInit, kKFields, kKNearMask, kKStreamCollideNear, kNumKernelKinds };
+
+// Stream-collide passes: every warp tile, or only the tiles away from (far)
+// or within reach of (near) this step's particles.
+enum SCMode { kSCAll = 0, kSCFar = 1, kSCNear = 2 };
+// Nodes added around each particle's zone in the near-tile bitmap: covers the
+// zones one step back and one step ahead of a disk that moves less than one
+// node per step.
+constexpr int kNearMargin = 2;
 
 // Planes are passed untyped: their element type is D.storage.
-cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, const int *own_cur,
-                                  int parity, cudaStream_t s);
+cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, int mode, cudaStream_t s);
+// Near-tile bitmap of this step (clears it first).
+cudaError_t launch_near_mask(const Dev &D, cudaStream_t s);
+// Warp tiles per row of the near-tile bitmap for a storage and pitch.
+int near_tiles_per_row(int storage, int pitch);
 // Nodes the stream-collide kernel leaves to the general path: the cavity
 // frame (x = 0, nx - 1, y = 0, ny - 1) and the listed newborn nodes.
 cudaError_t launch_boundary(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
@@ -561,7 +574,8 @@ size_t link_smem_bytes(int N, int storage);
 // columns, shared memory within 200 KB).
 bool link_zone_supported(int N, int storage);
 cudaError_t prepare_links(Dev &D);
-cudaError_t launch_particles(const Dev &D, int parity, cudaStream_t s);
+// Particle update, then the raster of the new positions into own_nxt.
+cudaError_t launch_particles(const Dev &D, int parity, int *own_nxt, cudaStream_t s);
 cudaError_t launch_raster(const Dev &D, int *own, const struct GeomRec *geo, const PartSoA &pos,
                           cudaStream_t s);
 cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate,

@@ -74,7 +74,7 @@ def test_batch_equals_each_instance_alone(storage):
     assert choice in (0, 1, 2)
     b.step(steps - steps // 2)
     b.sync()
-    assert b.launch_count() == 6 * steps
+    assert b.launch_count() == 5 * steps  # links, particles (+ raster), flags, stream-collide, boundary
     for s, ref in zip(sims, alone):
         same(snapshot(s), ref)
     b.close()
@@ -153,3 +153,19 @@ def test_escaping_disk_raises_domain_error_and_is_held():
     assert np.all(got["x"] - got["r"] >= -0.5) and np.all(got["x"] + got["r"] <= wl.nx - 0.5)
     torch.cuda.synchronize()  # the context is intact
     s.close()
+
+
+@pytest.mark.parametrize("flags", [lbm.LBM_FLAG_OVERLAP, lbm.LBM_FLAG_OVERLAP | lbm.LBM_FLAG_NO_GRAPH,
+                                   lbm.LBM_FLAG_NO_GRAPH])
+def test_step_schedules_are_bit_identical(flags):
+    """Stream-collide split into a far-tile pass beside the particle kernels
+    and a near-tile pass after them gives exactly the state of the default
+    single pass after them, with or without graphs."""
+    wl = W.parity_256()
+    a = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    b = lbm.Simulation(wl.domain, wl.particles, wl.params, flags=flags)
+    a.step(60)
+    b.step(60)
+    same(snapshot(a), snapshot(b))
+    a.close()
+    b.close()
