@@ -268,9 +268,21 @@ __device__ __forceinline__ bool tile_near(const Dev &D, int y, int t)
 // one vector store per plane); FP32 runs V = 1, the 16-bit storages V = 2 so
 // that every load still moves four bytes.  mode selects all warp tiles, or
 // only those away from / within reach of this step's particles.
+// Look-ahead target of a grid launch: the block `ahead` places later in
+// launch order, ahead = ahead_y grid rows + ahead_x blocks (ahead_x < gx).
+__device__ __forceinline__ void ahead_block(const Blk &blk, int ahead_y, int ahead_x, int &bx, int &by)
+{
+    bx = blk.x + ahead_x;
+    by = blk.y + ahead_y;
+    if (bx >= blk.gx) {
+        bx -= blk.gx;
+        ++by;
+    }
+}
+
 template <typename T, int V, int mode = kSCAll>
-__device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
-                                        int ahead_y, int ahead_x, const Blk blk)
+__device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout, int pf_x,
+                                        int pf_y, const Blk blk)
 {
     using E = Elem<T>;
     using VW = typename Vec<T, V>::W;
@@ -278,13 +290,9 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
     const int lane = threadIdx.x & 31;
     const int span = (int)blockDim.x * V; // nodes of a row per block
     if (threadIdx.x < kPop && threadIdx.y == 0) {
-        // the block `ahead` places later in launch order: ahead = ahead_y
-        // grid rows + ahead_x blocks (ahead_x < blk.gx)
-        int bx = blk.x + ahead_x, by = blk.y + ahead_y;
-        if (bx >= blk.gx) {
-            bx -= blk.gx;
-            ++by;
-        }
+        // L2 prefetch of the source rows of the block at (pf_x, pf_y), the
+        // one that runs about a residency wave later
+        const int bx = pf_x, by = pf_y;
         const int yb = by * (int)blockDim.y;
         const int xs = bx * span;
         const int lo = max(xs - kAl, 0), hi = min(xs + span + kAl, D.pitch);
@@ -470,8 +478,12 @@ template <typename T, int V, int mode>
 __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
     k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ahead_y, int ahead_x)
 {
-    sc_body<T, V, mode>(D, Ain, Aout, ahead_y, ahead_x, this_blk());
+    const Blk blk = this_blk();
+    int bx, by;
+    ahead_block(blk, ahead_y, ahead_x, bx, by);
+    sc_body<T, V, mode>(D, Ain, Aout, bx, by, blk);
 }
+
 
 template <typename T>
 __global__ void __launch_bounds__(128)
@@ -497,8 +509,9 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 8 : 5)
     const int gy = (a.D.ny + (int)blockDim.y - 1) / (int)blockDim.y;
     const Blk blk{local % gx, local / gx, gx, gy};
     const int par = parity ^ a.poff;
-    sc_body<T, V>(a.D, static_cast<const T *>(a.A[par]), static_cast<T *>(a.A[par ^ 1]), resident / gx,
-                  resident % gx, blk);
+    int bx, by;
+    ahead_block(blk, resident / gx, resident % gx, bx, by);
+    sc_body<T, V>(a.D, static_cast<const T *>(a.A[par]), static_cast<T *>(a.A[par ^ 1]), bx, by, blk);
 }
 
 template <typename T>
