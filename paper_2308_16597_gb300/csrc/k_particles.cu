@@ -249,14 +249,12 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
     for (int w = tid; w < nw; w += kLinkThreads) occ[w] = 0u;
     __syncthreads();
 
-    // ---- 2. link detection: warp w takes directions 2w + 1 and 2w + 2 (one
-    // direction per warp at a time, no divergence), lane l rows l, l + 32
-    static_assert(kLinkThreads == 128, "four warps cover the eight directions in pairs");
+    // ---- 2. link detection: thread (k, b), one mask intersection per row;
+    // items run direction-major, so that a warp mostly holds one direction
     {
         const unsigned long long Z = ((1ull << N) - 1ull) << off;
-        for (int e = lane; e < 2 * 64; e += 32) {
-            const int k = 2 * warp + 1 + (e >> 6), b = e & 63;
-            if (b >= N) continue;
+        for (int e = tid; e < 8 * N; e += kLinkThreads) {
+            const int k = 1 + e / N, b = e - (k - 1) * N;
             const int kx = ex(k), ky = ey(k);
             const unsigned long long o = Om[b + 2 + ky];
             unsigned long long m = Fm[b + 2] & (kx > 0 ? o >> 1 : kx < 0 ? o << 1 : o) & Z;
@@ -580,23 +578,24 @@ __device__ __forceinline__ void raster_body(const Dev &D, int *own, const GeomRe
 // Flags over the rectangle that holds the particle's zones one step back, now
 // and next (so every node whose flag may have changed since the last step):
 // solid at the new time, newborn (solid before, fluid now) or fluid, from
-// the two owner maps.  Warp w takes rows w, w + 4, ... of the rectangle (four
-// at a time, all loads issued first), lane l columns l and l + 32.  During a
-// step each block also moves its particle's new state into the current slot
-// and keeps the old position for the next clear.
+// the two owner maps.  One warp per particle: rows eight at a time (all
+// loads issued first), lane l columns l and l + 32.  During a step the warp
+// also moves its particle's new state into the current slot and keeps the old
+// position for the next clear.
 __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__ own_cur,
                                            const int *__restrict__ own_nxt, int rotate, const int p)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int kW = kBoxThreads / 32, kU = 4;
+    const int lane = threadIdx.x & 31;
+    constexpr int kU = 8;
+    if (p >= D.np) return;
     const bool list = rotate != 0; // a step (not the initial flags): list the newborn nodes
     const Box Ba = box_of(D.geo_prev[p]), Bb = box_of(D.geo_cur[p]), Bc = box_of(D.geo_nxt[p]);
     if (rotate) {
         // the new state moves into the current slot (and the current position
         // into the previous one) while the other threads work on the flags;
         // every thread has read the three boxes before
-        __syncthreads();
-        switch (threadIdx.x) {
+        __syncwarp();
+        switch (lane) {
         case 0: D.px[p] = D.cur.x[p]; D.cur.x[p] = D.nxt.x[p]; break;
         case 1: D.py[p] = D.cur.y[p]; D.cur.y[p] = D.nxt.y[p]; break;
         case 2: D.cur.ux[p] = D.nxt.ux[p]; break;
@@ -611,13 +610,13 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
     const int Y0 = max(min(min(Ba.Y0, Bb.Y0), Bc.Y0), 0);
     const int X1 = min(max(max(Ba.X0 + Ba.N, Bb.X0 + Bb.N), Bc.X0 + Bc.N), D.nx); // exclusive
     const int Y1 = min(max(max(Ba.Y0 + Ba.N, Bb.Y0 + Bb.N), Bc.Y0 + Bc.N), D.ny);
-    for (int r0 = Y0 + warp; r0 < Y1; r0 += kW * kU) {
+    for (int r0 = Y0; r0 < Y1; r0 += kU) {
         int oc[kU][2], on[kU][2];
 #pragma unroll
         for (int t = 0; t < kU; ++t)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int j = r0 + t * kW, i = X0 + lane + 32 * h;
+                const int j = r0 + t, i = X0 + lane + 32 * h;
                 const bool v = j < Y1 && i < X1;
                 const long long n = (long long)j * D.nx + i;
                 oc[t][h] = v ? own_cur[n] : -3;
@@ -628,7 +627,7 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (oc[t][h] == -3) continue;
-                const int j = r0 + t * kW, i = X0 + lane + 32 * h;
+                const int j = r0 + t, i = X0 + lane + 32 * h;
                 const uint8_t f = on[t][h] >= 0 ? kSolid : oc[t][h] >= 0 ? kNewborn : kFluid;
                 D.flags[(long long)j * D.pitch + i] = f;
                 // each newborn node once: by the particle that owned it; frame
@@ -681,7 +680,7 @@ __global__ void __launch_bounds__(kBoxThreads)
 __global__ void __launch_bounds__(kBoxThreads)
     k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate)
 {
-    flags_body(D, own_cur, own_nxt, rotate, (int)blockIdx.x);
+    flags_body(D, own_cur, own_nxt, rotate, (int)blockIdx.x * (kBoxThreads / 32) + (int)(threadIdx.x >> 5));
 }
 
 // ---- batched kernels: one grid over all instances (InstArgs table, block
@@ -725,7 +724,8 @@ __global__ void __launch_bounds__(kBoxThreads)
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
     const int par = parity ^ a.poff;
-    flags_body(sD, a.own[par], a.own[par ^ 1], 1, (int)blockIdx.x - __ldg(start + i));
+    flags_body(sD, a.own[par], a.own[par ^ 1], 1,
+               ((int)blockIdx.x - __ldg(start + i)) * (kBoxThreads / 32) + (int)(threadIdx.x >> 5));
 }
 
 // Geometry records of the current state and of the previous positions.
@@ -911,7 +911,7 @@ void batch_blocks(const Dev &D, dim3 sc_block, int out[kBatchPhases])
     out[kBLinks] = D.np;
     out[kBParticles] = D.np > 0 ? (D.np + kPartPerBlock - 1) / kPartPerBlock : 1;
     out[kBRaster] = (D.np + kBoxThreads / 32 - 1) / (kBoxThreads / 32);
-    out[kBFlags] = D.np;
+    out[kBFlags] = (D.np + kBoxThreads / 32 - 1) / (kBoxThreads / 32);
     out[kBStream] = ((D.pitch / V + (int)sc_block.x - 1) / (int)sc_block.x) *
                     ((D.ny + (int)sc_block.y - 1) / (int)sc_block.y);
     out[kBBoundary] = kBoundaryBlocksPerInstance;
@@ -954,7 +954,8 @@ cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, i
                          cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
-    k_flags<<<D.np, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate);
+    const int per = kBoxThreads / 32;
+    k_flags<<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate);
     return cudaGetLastError();
 }
 
