@@ -1,0 +1,101 @@
+"""Host logic on the CPU: the synthetic workload generators of the batched
+and served forms (valid, non-overlapping, seeded), the bench helpers, and
+the argument checks of the batch and server entry points (which fail before
+touching a device)."""
+import ctypes as C
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_2308_16597_gb300 import workloads as W  # noqa: E402
+
+
+def _valid_layout(wl):
+    p = wl.particles
+    nx, ny = wl.nx, wl.ny
+    assert np.all(p["x"] - p["r"] >= W.S_REP) and np.all(p["x"] + p["r"] <= nx - 1 - W.S_REP)
+    assert np.all(p["y"] - p["r"] >= W.S_REP) and np.all(p["y"] + p["r"] <= ny - 1 - W.S_REP)
+    d = np.hypot(p["x"][:, None] - p["x"][None], p["y"][:, None] - p["y"][None])
+    rr = p["r"][:, None] + p["r"][None] + W.S_REP + 1.0
+    np.fill_diagonal(d, np.inf)
+    assert np.all(d >= rr - 1e-9)
+
+
+def test_ensemble_matches_its_recipe():
+    e = W.ensemble(64, seed=4)
+    assert len(e) == 64
+    for wl in e:
+        assert wl.nx in (256, 512, 768, 1024) and wl.ny in (256, 512, 768, 1024)
+        n = len(wl.particles)
+        assert 1 <= n <= 400
+        assert np.all((wl.particles["r"] >= 6.0) & (wl.particles["r"] <= 12.0))
+        Ra = wl.extra["Ra"]
+        assert 1e6 <= Ra <= 1e8
+        # g from Ra on H = ny
+        p = wl.params
+        assert p["g"] == pytest.approx(Ra * p["nu"] * p["alpha"] / wl.ny ** 3)
+        assert np.all(wl.particles["y"] >= 0.5 * wl.ny)
+    for wl in e[:8]:
+        _valid_layout(wl)
+    # seeded: the same call gives the same ensemble
+    f = W.ensemble(64, seed=4)
+    assert all(a.particles.tobytes() == b.particles.tobytes() for a, b in zip(e, f))
+
+
+def test_served_stream_matches_its_recipe():
+    s = W.served_stream(40, seed=5)
+    assert len(s) == 40
+    t = [a for a, _, _ in s]
+    assert all(b > a for a, b in zip(t, t[1:]))
+    gaps = np.diff([0.0] + t)
+    assert 0.02 < gaps.mean() < 0.08  # Poisson at 20/s
+    for _, wl, steps in s:
+        assert wl.nx == wl.ny and 512 <= wl.nx <= 2048 and wl.nx % 256 == 0
+        assert 2000 <= steps <= 20000
+        assert 1 <= len(wl.particles) <= 1500
+        assert np.all(wl.particles["r"] == 10.0)
+        assert math.sqrt(wl.params["g"] * wl.ny) == pytest.approx(0.04)
+    _valid_layout(s[0][1])
+
+
+def test_weighted_percentile():
+    import bench
+    v = [3.0, 1.0, 2.0, 10.0]
+    w = [1, 1, 1, 1]
+    assert bench.weighted_percentile(v, w, 0.5) == 2.0
+    assert bench.weighted_percentile(v, w, 0.99) == 10.0
+    # a heavily weighted value dominates
+    assert bench.weighted_percentile([1.0, 5.0], [99, 1], 0.5) == 1.0
+    assert bench.weighted_percentile([1.0, 5.0], [1, 99], 0.5) == 5.0
+
+
+def test_traffic_record_is_tied_to_the_kernel_source():
+    import bench
+    v = bench.profiled_traffic("stream_collide")
+    # either the record matches the current source or it is withheld
+    assert v is None or 1.5e9 < v < 2.0e9
+    assert bench.profiled_traffic("no_such_kernel") is None
+
+
+def test_batch_and_server_reject_bad_arguments():
+    from paper_2308_16597_gb300 import lbm
+    lib = lbm.library()
+    h = C.c_void_p()
+    size = C.c_size_t()
+    assert lib.lbm_batch_footprint(None, 0, C.byref(size)) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_create(C.byref(h), None, 1, None, 0, None) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_destroy(None) == lbm.LBM_EINVAL
+    assert lib.lbm_server_create(C.byref(h), None, 1 << 20, 4, None) == lbm.LBM_EINVAL
+    assert lib.lbm_server_create(C.byref(h), C.c_void_p(256), 1 << 20, 0, None) == lbm.LBM_EINVAL
+    assert lib.lbm_server_create(C.byref(h), C.c_void_p(100), 1 << 20, 4, None) == lbm.LBM_EINVAL
+    assert lib.lbm_server_submit(None, None, None, 0, None, 10, None) == lbm.LBM_EINVAL
+    assert lib.lbm_server_tick(None, 10, None) == lbm.LBM_EINVAL
+    assert lib.lbm_server_status(None, 1, None) == lbm.LBM_EINVAL
+    assert lib.lbm_server_destroy(None) == lbm.LBM_EINVAL
