@@ -215,7 +215,7 @@ def config_of(wl, args):
     p = wl.particles
     return {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "particles": int(len(p)),
             "radius": float(p["r"][0]) if len(p) else None,
-            "storage": getattr(args, "storage", "fp32"),
+            "storage": getattr(args, "storage", "fp32"), "links": getattr(args, "links", "index"),
             "density_ratio": float(p["rho"][0]) if len(p) else None,
             "parallelism": "replicas%d" % args.gpus,
             "l2": "no flush: the 1.8 GB distribution state is 14x the 129 MB L2"}
@@ -237,7 +237,8 @@ def run_ours(args, wl):
     nodes = wl.nx * wl.ny
     with torch.cuda.stream(stream):
         storage = STORAGE_CODES[args.storage]
-        sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream, storage=storage)
+        flags = lbm.LBM_FLAG_DIRECT_LINKS if args.links == "direct" else 0
+        sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream, storage=storage, flags=flags)
         sim.step(args.warmup)
         sim.sync()
         clocks = ClockSampler(local)
@@ -282,7 +283,7 @@ def run_ours(args, wl):
         pview = pinned_p.numpy().view(lbm.PARTICLE_DTYPE)
         fields = [torch.empty((wl.ny, wl.nx), dtype=torch.float32, pin_memory=True)
                   for _ in range(4)]
-        params = lbm.make_params(**dict(wl.params, storage=storage))
+        params = lbm.make_params(**dict(wl.params, storage=storage, flags=flags))
         dom = lbm.make_domain(**wl.domain)
         parts = lbm.pack_particles(wl.particles)
         ws_bytes = lbm.lbm_query_footprint(dom, parts, params)
@@ -339,6 +340,8 @@ def run_ours(args, wl):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_of(wl, args), "roofline": roofline, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel,
+            "particle_part_ms_per_step": sum(v["ms_per_step"] for k, v in per_kernel.items()
+                                             if k in ("link_gather_bb_force", "particle_update", "node_flags")),
             "whole_step_hbm_frac": B_LU * nodes / (step_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
@@ -541,6 +544,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--links", choices=["index", "direct"], default="index",
+                    help="links from the fixed index array (default) or by direct addressing (the paper's "
+                         "comparison, Table 1)")
     ap.add_argument("--storage", choices=sorted(STORAGE_CODES), default="fp32",
                     help="plane storage: FP32 (the headline), or BF16 / scaled FP16 deviations")
     args = ap.parse_args(argv)

@@ -74,6 +74,14 @@ extern "C" {
  * tiles are near particles (on the 4000^2 / 4800-disk benchmark, where 40 %
  * are, it is slower). */
 #define LBM_FLAG_OVERLAP 4u
+/* Direct addressing, the comparison of Sec. 3 (Table 1) for the fixed index
+ * array: links are found by one thread per lattice node testing its eight
+ * neighbours, and each link's force and torque bracket is added to its
+ * particle with FP64 atomics.  Same bounce-back values; forces agree with the
+ * default to rounding (the summation order is not fixed, so runs are not
+ * bit-reproducible), and lbm_get_slots does not see these links.  Not
+ * accepted by lbm_batch_create or lbm_server_submit. */
+#define LBM_FLAG_DIRECT_LINKS 8u
 
 typedef struct {
     int32_t nx, ny;    /* nodes per axis, >= 4 each */
@@ -255,7 +263,8 @@ int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
  *   lbm_batch_sync       waits for the batch's stream and returns the first
  *                        sticky device error of any instance (its index in
  *                        *which, may be NULL), else LBM_OK.
- * Errors: LBM_EINVAL (mixed storage, a handle twice, n < 1 or n > 4096, or
+ * Errors: LBM_EINVAL (mixed storage, a handle twice or with direct-addressed
+ * links, n < 1 or n > 4096, or
  * from lbm_batch_step: a handle stepped on its own since), LBM_ENOSPC
  * (workspace too small), LBM_ECUDA. */
 typedef struct lbm_batch lbm_batch;

@@ -463,7 +463,18 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, float fxh, fl
     double th = D.cur.th[b], om = D.cur.om[b];
     const double r = D.cur.r[b], rho = D.cur.rho[b];
     double Fx, Fy, Tz;
-    assemble_force(D.lsum[b], x, y, Fx, Fy, Tz);
+    if (D.direct) {
+        const DirectSums &ds = D.dsum[b];
+        LinkSums S;
+        S.fx_h = (float)ds.f[0]; S.fx_l = (float)(ds.f[0] - (double)S.fx_h);
+        S.fy_h = (float)ds.f[1]; S.fy_l = (float)(ds.f[1] - (double)S.fy_h);
+        S.tz_h = (float)ds.f[2]; S.tz_l = (float)(ds.f[2] - (double)S.tz_h);
+        S.ax_x = ds.c[0]; S.ax_y = ds.c[1]; S.ax_t = ds.c[2];
+        S.dg_x = ds.c[3]; S.dg_y = ds.c[4]; S.dg_t = ds.c[5];
+        assemble_force(S, x, y, Fx, Fy, Tz);
+    } else {
+        assemble_force(D.lsum[b], x, y, Fx, Fy, Tz);
+    }
     D.force[3 * b + 0] = Fx;
     D.force[3 * b + 1] = Fy;
     D.force[3 * b + 2] = Tz;
@@ -657,6 +668,109 @@ __global__ void __launch_bounds__(128) k_near_mask(const Dev D, int span)
     for (int t = x0 / span; t <= x1 / span; ++t) {
         const int b = j * D.near_tpr + t;
         atomicOr(D.near + (b >> 5), 1u << (b & 31));
+    }
+}
+
+// ---- direct addressing (comparison with the index array)
+// Per particle: clear its zone one step back in the next owner map, publish
+// its centre for the pair screening, zero its sums.
+__global__ void __launch_bounds__(kBoxThreads) k_direct_prep(const Dev D, int *__restrict__ own_nxt)
+{
+    const int p = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const GeomRec Gp = D.geo_prev[p];
+    for (int r = warp; r < Gp.N; r += kBoxThreads / 32) {
+        const int j = Gp.Y0 + r;
+        if (j < 0 || j >= D.ny) continue;
+        for (int c = lane; c < Gp.N; c += 32) {
+            const int i = Gp.X0 + c;
+            if (i >= 0 && i < D.nx) own_nxt[(long long)j * D.nx + i] = -1;
+        }
+    }
+    if (threadIdx.x == 0) {
+        const GeomRec G = D.geo_cur[p];
+        const DiskDF d0 = geom_df(G);
+        D.pos4[p] = make_float4(d0.xh, d0.yh, d0.xl, d0.yl);
+        D.prc[p] = make_float2(G.r, G.C);
+    }
+    if (threadIdx.x < 3) D.dsum[p].f[threadIdx.x] = 0.0;
+    if (threadIdx.x < 6) D.dsum[p].c[threadIdx.x] = 0;
+}
+
+// One thread per lattice node (the straightforward mapping the paper starts
+// from, Sec. 3): a fluid node tests its eight neighbours in the owner map
+// and, for each one owned by a particle, applies the same wall fraction,
+// bounce-back and momentum-exchange bracket as the index-array kernel, adding
+// the bracket to the particle's sums with FP64 atomics.  Only nodes next to
+// a disk do work, so most threads of a block idle.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_links_direct(const Dev D, T *A, const int *__restrict__ own, int parity)
+{
+    using E = Elem<T>;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    unsigned cnt[4] = {0u, 0u, 0u, 0u}; // links, linear, simple, thermal half-way
+    if (i < D.nx && own[(long long)j * D.nx + i] == -1) {
+        auto fluid = [&](int a, int b) {
+            return a >= 0 && a < D.nx && b >= 0 && b < D.ny && own[(long long)b * D.nx + a] == -1;
+        };
+        auto tv = [&](int t, int a, int b) -> float {
+            return E::ld(A[(long long)t * D.ps + (long long)b * D.pitch + a]);
+        };
+#pragma unroll 1
+        for (int k = 1; k < kQ9; ++k) {
+            const int kx = ex(k), ky = ey(k), si = i + kx, sj = j + ky;
+            if (si < 0 || si >= D.nx || sj < 0 || sj >= D.ny) continue;
+            const int p = own[(long long)sj * D.nx + si];
+            if (p < 0) continue;
+            const GeomRec G = D.geo_cur[p];
+            const DiskDF dk = geom_df(G);
+            float dxf, dyf;
+            const float q = link_q_df(i, j, k, dk, dxf, dyf);
+            const int kb = opp(k);
+            const int i1 = i - kx, j1 = j - ky, i2 = i - 2 * kx, j2 = j - 2 * ky;
+            const bool have1 = fluid(i1, j1), have2 = fluid(i2, j2);
+            const int ii1 = have1 ? i1 : i, jj1 = have1 ? j1 : j;
+            const int ii2 = have2 ? i2 : i, jj2 = have2 ? j2 : j;
+            const float fk0 = tv(k, i, j), fk1 = tv(k, ii1, jj1), fk2 = tv(k, ii2, jj2);
+            const float fb0 = tv(kb, i, j), fb1 = tv(kb, ii1, jj1);
+            const float rx = dxf + q * kx, ry = dyf + q * ky;
+            const float uwx = G.ux - G.om * ry, uwy = G.uy + G.om * rx;
+            const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy);
+            int lvl;
+            const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
+            const long long ns = (long long)sj * D.pitch + si;
+            A[kb * D.ps + ns] = E::st(fnew);
+            if (k <= 4) {
+                const float gnew = thermal32(q, tv(kQ9 + k, i, j), tv(kQ9 + k, ii1, jj1), tv(kQ9 + kb, i, j), have1,
+                                             G.wT);
+                A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
+                cnt[3] += !have1;
+            }
+            const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
+            const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
+            DirectSums &ds = D.dsum[p];
+            atomicAdd(&ds.f[0], (double)bx);
+            atomicAdd(&ds.f[1], (double)by);
+            atomicAdd(&ds.f[2], (double)(rx * by - ry * bx));
+            const int tz = i * ky - j * kx, o = k <= 4 ? 0 : 3;
+            if (kx) atomicAdd(&ds.c[o], kx);
+            if (ky) atomicAdd(&ds.c[o + 1], ky);
+            if (tz) atomicAdd(&ds.c[o + 2], tz);
+            cnt[0] += 1u;
+            cnt[1] += lvl == 1;
+            cnt[2] += lvl == 2;
+        }
+    }
+    // counters: one atomic per warp
+    const unsigned F = 0xffffffffu;
+    unsigned long long *C = D.status->cnt[parity];
+    const unsigned c0 = __reduce_add_sync(F, cnt[0]), c1 = __reduce_add_sync(F, cnt[1]);
+    const unsigned c2 = __reduce_add_sync(F, cnt[2]), c3 = __reduce_add_sync(F, cnt[3]);
+    if ((threadIdx.x & 31) == 0) {
+        if (c0) atomicAdd(&C[kCntLinks], (unsigned long long)c0);
+        if (c1) atomicAdd(&C[kCntBzLinear], (unsigned long long)c1);
+        if (c2) atomicAdd(&C[kCntBzSimple], (unsigned long long)c2);
+        if (c3) atomicAdd(&C[kCntThermHalf], (unsigned long long)c3);
     }
 }
 
@@ -925,6 +1039,25 @@ cudaError_t launch_near_mask(const Dev &D, cudaStream_t s)
     const int span = 32 * (D.storage == LBM_STORE_FP32 ? 1 : 2);
     const long long threads = (long long)D.np * (D.zone_max + 2 * kNearMargin);
     k_near_mask<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(D, span);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links_direct(const Dev &D, void *A, const int *own_cur, int *own_nxt, int parity,
+                                cudaStream_t s)
+{
+    if (D.np == 0) return cudaSuccess;
+    k_direct_prep<<<D.np, kBoxThreads, 0, s>>>(D, own_nxt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid((D.nx + 127) / 128, D.ny);
+    switch (D.storage) {
+    case LBM_STORE_FP32: k_links_direct<float><<<grid, 128, 0, s>>>(D, static_cast<float *>(A), own_cur, parity); break;
+    case LBM_STORE_BF16:
+        k_links_direct<__nv_bfloat16><<<grid, 128, 0, s>>>(D, static_cast<__nv_bfloat16 *>(A), own_cur, parity);
+        break;
+    case LBM_STORE_FP16: k_links_direct<__half><<<grid, 128, 0, s>>>(D, static_cast<__half *>(A), own_cur, parity); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -118,6 +118,7 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
     L.newborn_cap = std::max(1024, 4 * n * zmax);
     L.newborn = take((size_t)L.newborn_cap * sizeof(int));
     L.near = take(((size_t)d->ny * near_tiles_per_row(storage, L.pitch) + 31) / 32 * sizeof(unsigned));
+    L.dsum = take((size_t)n * sizeof(DirectSums));
     L.total = off;
 }
 
@@ -225,7 +226,11 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
         }
     }
     if (h->np > 0) {
-        if ((rc = timed(h, kKLinks, st, [&] { return launch_links(D, Ain, oc, on, par, h->tmA[par], st); }))) return rc;
+        if ((rc = timed(h, kKLinks, st, [&] {
+                 return D.direct ? launch_links_direct(D, Ain, oc, on, par, st)
+                                 : launch_links(D, Ain, oc, on, par, h->tmA[par], st);
+             })))
+            return rc;
     }
     // particle update and raster of the new positions (one kernel)
     if ((rc = timed(h, kKParticles, st, [&] { return launch_particles(D, par, on, st); }))) return rc;
@@ -254,7 +259,7 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
 int kernels_per_step(const lbm_handle *h)
 {
     if (h->np == 0) return 3;
-    return (h->prm.flags & LBM_FLAG_OVERLAP) ? 7 : 5;
+    return ((h->prm.flags & LBM_FLAG_OVERLAP) ? 7 : 5) + ((h->prm.flags & LBM_FLAG_DIRECT_LINKS) ? 1 : 0);
 }
 
 int capture(lbm_handle *h, int par)
@@ -333,6 +338,8 @@ void fill_dev(lbm_handle *h)
     D.newborn = reinterpret_cast<int *>(ws + L.newborn);
     D.newborn_cap = L.newborn_cap;
     D.near = reinterpret_cast<unsigned *>(ws + L.near);
+    D.dsum = reinterpret_cast<DirectSums *>(ws + L.dsum);
+    D.direct = (P.flags & LBM_FLAG_DIRECT_LINKS) ? 1 : 0;
     D.near_tpr = near_tiles_per_row(P.storage, L.pitch);
     D.slot_node = reinterpret_cast<int *>(ws + L.slot_node);
     D.slot_q = reinterpret_cast<float *>(ws + L.slot_q);

@@ -135,7 +135,7 @@ int check_handles(lbm_handle *const *hs, int32_t n)
     if (!hs || n < 1 || n > kMaxBatch) return LBM_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!hs[i] || hs[i]->sticky) return hs[i] ? hs[i]->sticky : LBM_EINVAL;
-        if (hs[i]->D.storage != hs[0]->D.storage) return LBM_EINVAL;
+        if (hs[i]->D.storage != hs[0]->D.storage || hs[i]->D.direct) return LBM_EINVAL;
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return LBM_EINVAL;
     }

@@ -129,6 +129,8 @@ struct Dev {
     float4 *pos4;      // [np]: centre as double-float (xh, yh, xl, yl) at the start of the step
     float2 *prc;       // [np]: (r, C = pi r^2 (rho_p - rho_f) g) in FP32 for the pair screening
     struct LinkSums *lsum; // [np]: link-kernel sums, assembled into force by the particle update
+    struct DirectSums *dsum; // [np]: the same sums accumulated by atomics (direct addressing)
+    int direct;            // links found by the node-parallel scan instead of the index array
     struct GeomRec *geo_prev, *geo_cur, *geo_nxt; // [np] each: FP32/int geometry of the three positions
     Status *status;
 };
@@ -303,6 +305,12 @@ struct LinkSums {
     float fx_h, fx_l, fy_h, fy_l, tz_h, tz_l;
     int ax_x, ax_y, ax_t, dg_x, dg_y, dg_t;
     int pad[4];
+};
+// Direct addressing: the variable parts in FP64 and the constant parts as
+// integers, accumulated link by link with atomics (order not fixed).
+struct DirectSums {
+    double f[3];  // Fx, Fy, Tz brackets
+    int c[6];     // ax_x, ax_y, ax_t, dg_x, dg_y, dg_t
 };
 // Per-link momentum-exchange sums of one warp.  Lane l accumulates links
 // l, l + 32, l + 64, ... in that order (add), then finish() combines the
@@ -550,6 +558,11 @@ constexpr int kNearMargin = 2;
 cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, int mode, cudaStream_t s);
 // Near-tile bitmap of this step (clears it first).
 cudaError_t launch_near_mask(const Dev &D, cudaStream_t s);
+// Direct addressing (the paper's comparison for its index array): a per-
+// particle preparation (owner-map clear, centres, zeroed sums) and one thread
+// per lattice node testing its eight neighbours.
+cudaError_t launch_links_direct(const Dev &D, void *A, const int *own_cur, int *own_nxt, int parity,
+                                cudaStream_t s);
 // Warp tiles per row of the near-tile bitmap for a storage and pitch.
 int near_tiles_per_row(int storage, int pitch);
 // Nodes the stream-collide kernel leaves to the general path: the cavity

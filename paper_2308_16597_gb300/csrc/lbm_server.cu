@@ -165,6 +165,7 @@ int lbm_server_submit(lbm_server *s, const lbm_domain *d, const lbm_particle *p,
                       int64_t steps, int64_t *id)
 {
     if (!s || !d || !prm || !id || steps < 1 || n < 0 || (n > 0 && !p)) return LBM_EINVAL;
+    if (prm->flags & LBM_FLAG_DIRECT_LINKS) return LBM_EINVAL; // batches use the index array
     size_t bytes = 0;
     int rc = lbm_query_footprint(d, p, n, prm, &bytes);
     if (rc) return rc;

@@ -285,3 +285,31 @@ def test_full_size_4000_cavity_two_steps():
     compare_fields(sim, ref, 1e-5)
     pg, po = sim.particles(), ref.particles()
     assert np.abs(pg["y"] - po["y"]).max() < 1e-8
+
+
+def test_direct_addressing_matches_the_index_array():
+    """The comparison of Sec. 3: links found by one thread per node, forces
+    summed with atomics.  Same bounce-back values and link counts; forces
+    equal to rounding, so the state after 100 steps matches the default to
+    rel-L2 1e-6 and both meet the oracle bound."""
+    wl = W.parity_256()
+    a = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    b = lbm.Simulation(wl.domain, wl.particles, wl.params, flags=lbm.LBM_FLAG_DIRECT_LINKS)
+    a.step(1)
+    b.step(1)
+    fa, fb = a.forces(), b.forces()
+    assert np.allclose(fa, fb, rtol=1e-9, atol=1e-12)
+    assert np.array_equal(a.counters(), b.counters())
+    a.step(99)
+    b.step(99)
+    for x, y in zip(a.fields(), b.fields()):
+        m = ~np.isnan(x)
+        assert np.array_equal(m, ~np.isnan(y))
+        assert rel_l2(x[m], y[m]) < 1e-6
+    pa, pb = a.particles(), b.particles()
+    assert np.abs(pa["x"] - pb["x"]).max() < 1e-9 and np.abs(pa["y"] - pb["y"]).max() < 1e-9
+    ref = orc.Oracle(wl.domain, wl.particles, wl.params)
+    ref.step(100)
+    compare_fields(b, ref, 1e-5)
+    a.close()
+    b.close()
