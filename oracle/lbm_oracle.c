@@ -293,6 +293,82 @@ static int in_disk(int32_t i, int32_t j, double x, double y, double r)
     return dx * dx + dy * dy <= r * r;
 }
 
+/* An ellipse is a particle with 0 < b != r; everything else is a disk of
+ * radius r. */
+static int is_ellipse(const orc_particle *P) { return P->b > 0.0 && P->b != P->r; }
+
+/* Cody-Waite argument reduction (pi/2 split into a 33-bit head and a tail, so
+ * that k * head is exact for |k| < 2^20) and Taylor polynomials of sin and
+ * cos on [-pi/4, pi/4] (terms to x^17 and x^16: truncation below 1e-17). */
+void orc_cos_sin(double theta, double *c, double *s)
+{
+    const double two_over_pi = 0.63661977236758134308;
+    const double pio2_hi = 1.5707963267341256e+00;
+    const double pio2_lo = 6.0771005065061922e-11;
+    double k = floor(theta * two_over_pi + 0.5);
+    double t = (theta - k * pio2_hi) - k * pio2_lo;
+    double t2 = t * t;
+    /* sin t = t (1 - t2/3! (1 - t2/(4 5) (1 - ...))) written as Horner in t2 */
+    double ps = 1.0 / 355687428096000.0;            /* 1/17! */
+    ps = ps * t2 - 1.0 / 1307674368000.0;           /* 1/15! */
+    ps = ps * t2 + 1.0 / 6227020800.0;              /* 1/13! */
+    ps = ps * t2 - 1.0 / 39916800.0;                /* 1/11! */
+    ps = ps * t2 + 1.0 / 362880.0;                  /* 1/9!  */
+    ps = ps * t2 - 1.0 / 5040.0;                    /* 1/7!  */
+    ps = ps * t2 + 1.0 / 120.0;                     /* 1/5!  */
+    ps = ps * t2 - 1.0 / 6.0;                       /* 1/3!  */
+    double sn = t + t * (t2 * ps);
+    double pc = 1.0 / 20922789888000.0;             /* 1/16! */
+    pc = pc * t2 - 1.0 / 87178291200.0;             /* 1/14! */
+    pc = pc * t2 + 1.0 / 479001600.0;               /* 1/12! */
+    pc = pc * t2 - 1.0 / 3628800.0;                 /* 1/10! */
+    pc = pc * t2 + 1.0 / 40320.0;                   /* 1/8!  */
+    pc = pc * t2 - 1.0 / 720.0;                     /* 1/6!  */
+    pc = pc * t2 + 1.0 / 24.0;                      /* 1/4!  */
+    pc = pc * t2 - 0.5;                             /* 1/2!  */
+    double cn = 1.0 + t2 * pc;
+    long long q = (long long)k & 3;
+    if (q == 0) { *c = cn; *s = sn; }
+    else if (q == 1) { *c = -sn; *s = cn; }
+    else if (q == 2) { *c = -cn; *s = -sn; }
+    else { *c = sn; *s = -cn; }
+}
+
+/* Offset of node (i, j) from the centre in the ellipse's frame (u along the
+ * major axis). */
+static void ellipse_frame(double dx, double dy, double c, double s, double *u, double *v)
+{
+    *u = dx * c + dy * s;
+    *v = dy * c - dx * s;
+}
+
+/* Inside iff u^2 / a^2 + v^2 / b^2 <= 1, evaluated as u^2 b^2 + v^2 a^2 <=
+ * a^2 b^2 (no division). */
+static int in_ellipse(int32_t i, int32_t j, const orc_particle *P)
+{
+    double c, s, u, v;
+    orc_cos_sin(P->theta, &c, &s);
+    ellipse_frame((double)i - P->x, (double)j - P->y, c, s, &u, &v);
+    double a2 = P->r * P->r, b2 = P->b * P->b;
+    return u * u * b2 + v * v * a2 <= a2 * b2;
+}
+
+int32_t orc_in_particle(int32_t i, int32_t j, const orc_particle *P)
+{
+    return is_ellipse(P) ? in_ellipse(i, j, P) : in_disk(i, j, P->x, P->y, P->r);
+}
+
+/* Support distance of the particle along the unit vector (nx, ny): r for a
+ * disk, sqrt(a^2 (n.u)^2 + b^2 (n.v)^2) for an ellipse. */
+double orc_support(const orc_particle *P, double nx, double ny)
+{
+    if (!is_ellipse(P)) return P->r;
+    double c, s, nu, nv;
+    orc_cos_sin(P->theta, &c, &s);
+    ellipse_frame(nx, ny, c, s, &nu, &nv);
+    return sqrt(P->r * P->r * nu * nu + P->b * P->b * nv * nv);
+}
+
 void orc_raster(int32_t nx, int32_t ny, const orc_particle *p, int32_t np, int32_t *owner)
 {
     for (int64_t n = 0; n < (int64_t)nx * ny; ++n) owner[n] = -1;
@@ -305,7 +381,7 @@ void orc_raster(int32_t nx, int32_t ny, const orc_particle *p, int32_t np, int32
         if (j1 > ny - 1) j1 = ny - 1;
         for (int32_t j = j0; j <= j1; ++j)
             for (int32_t i = i0; i <= i1; ++i)
-                if (in_disk(i, j, p[k].x, p[k].y, p[k].r)) owner[(int64_t)j * nx + i] = k;
+                if (orc_in_particle(i, j, &p[k])) owner[(int64_t)j * nx + i] = k;
     }
 }
 
@@ -329,6 +405,29 @@ double orc_link_q(int32_t i, int32_t j, int32_t k, double x, double y, double r)
     double disc = de * de - a * c;
     if (disc < 0.0) disc = 0.0;
     double t = c / (-de + sqrt(disc));
+    if (t > 1.0) t = 1.0;
+    return t;
+}
+
+/* q for a link to an ellipse: the smaller root t of F(d + t e) = 0 with
+ * F(w) = u(w)^2 b^2 + v(w)^2 a^2 - a^2 b^2 (the ellipse frame), i.e.
+ * P2 t^2 + 2 P1 t + P0 = 0, written t = P0 / (-P1 + sqrt(P1^2 - P2 P0));
+ * P0 > 0 (x_f is outside) and P1 < 0 on a link, so there is no
+ * cancellation.  For a disk the root is orc_link_q's. */
+double orc_link_q_particle(int32_t i, int32_t j, int32_t k, const orc_particle *P)
+{
+    if (!is_ellipse(P)) return orc_link_q(i, j, k, P->x, P->y, P->r);
+    double c, s, du, dv, eu, ev;
+    orc_cos_sin(P->theta, &c, &s);
+    ellipse_frame((double)i - P->x, (double)j - P->y, c, s, &du, &dv);
+    ellipse_frame((double)EX[k], (double)EY[k], c, s, &eu, &ev);
+    double a2 = P->r * P->r, b2 = P->b * P->b;
+    double P2 = eu * eu * b2 + ev * ev * a2;
+    double P1 = du * eu * b2 + dv * ev * a2;
+    double P0 = du * du * b2 + dv * dv * a2 - a2 * b2;
+    double disc = P1 * P1 - P2 * P0;
+    if (disc < 0.0) disc = 0.0;
+    double t = P0 / (-P1 + sqrt(disc));
     if (t > 1.0) t = 1.0;
     return t;
 }
@@ -386,7 +485,7 @@ int32_t orc_build_slots(int32_t nx, int32_t ny, const int32_t *owner, const orc_
                     if (!inside(nx, ny, si, sj) || owner[(int64_t)sj * nx + si] != pid) continue;
                     if (++found == 1) {
                         node = j * nx + i;
-                        q = (float)orc_link_q(i, j, k, p[pid].x, p[pid].y, p[pid].r);
+                        q = (float)orc_link_q_particle(i, j, k, &p[pid]);
                     }
                 }
                 if (found > 1) ++overflow;
@@ -418,7 +517,7 @@ int64_t orc_links_bruteforce(int32_t nx, int32_t ny, const int32_t *owner,
                     node[n] = j * nx + i;
                     dir[n] = k;
                     pid[n] = o;
-                    q[n] = orc_link_q(i, j, k, p[o].x, p[o].y, p[o].r);
+                    q[n] = orc_link_q_particle(i, j, k, &p[o]);
                 }
                 ++n;
             }
@@ -605,7 +704,7 @@ static void particle_links(orc_sim *s)
                 if (pid < 0) continue;
                 const orc_particle *P = &s->p[pid];
                 int32_t kb = OPP[k];
-                double q = orc_link_q(i, j, k, P->x, P->y, P->r);
+                double q = orc_link_q_particle(i, j, k, P);
                 double rx = ((double)i + q * EX[k]) - P->x;
                 double ry = ((double)j + q * EY[k]) - P->y;
                 double uwx = P->ux - P->omega * ry;
@@ -647,8 +746,14 @@ static void particle_links(orc_sim *s)
 void orc_integrate(const orc_particle *P, double Fx, double Fy, double Tz, orc_particle *R)
 {
     const double pi = 3.14159265358979323846;
-    double M = P->rho * pi * P->r * P->r;
-    double I = 0.5 * M * P->r * P->r;
+    double M, I;
+    if (is_ellipse(P)) { /* uniform ellipse: M = rho pi a b, I = M (a^2 + b^2) / 4 */
+        M = P->rho * pi * P->r * P->b;
+        I = 0.25 * M * (P->r * P->r + P->b * P->b);
+    } else {
+        M = P->rho * pi * P->r * P->r;
+        I = 0.5 * M * P->r * P->r;
+    }
     *R = *P;
     R->ux = P->ux + Fx / M;
     R->uy = P->uy + Fy / M;
@@ -671,33 +776,44 @@ static int particle_update(orc_sim *s)
     orc_particle *np_ = (orc_particle *)malloc(sizeof(orc_particle) * (s->np > 0 ? s->np : 1));
     for (int32_t a = 0; a < s->np; ++a) {
         const orc_particle *P = &s->p[a];
-        double Ca = pi * P->r * P->r * (P->rho - s->prm.rho_f) * s->prm.g;
+        const double Aa = is_ellipse(P) ? pi * P->r * P->b : pi * P->r * P->r; /* area */
+        double Ca = Aa * (P->rho - s->prm.rho_f) * s->prm.g;
         double Fx = s->force[3 * a + 0];
-        double Fy = s->force[3 * a + 1] - (P->rho - s->prm.rho_f) * pi * P->r * P->r * s->prm.g;
+        double Fy = s->force[3 * a + 1] - (P->rho - s->prm.rho_f) * Aa * s->prm.g;
         double Tz = s->force[3 * a + 2];
-        /* walls: the gap is the distance from the wall plane to the surface */
+        /* walls: the gap is the distance from the wall plane to the surface
+         * (the support distance along the wall normal for an ellipse) */
         if (!s->d.periodic_x) {
-            Fx += orc_repulsion((P->x + 0.5) - P->r, sr, ew, Ca);
-            Fx -= orc_repulsion(((double)nx - 0.5 - P->x) - P->r, sr, ew, Ca);
+            const double hx = orc_support(P, 1.0, 0.0);
+            Fx += orc_repulsion((P->x + 0.5) - hx, sr, ew, Ca);
+            Fx -= orc_repulsion(((double)nx - 0.5 - P->x) - hx, sr, ew, Ca);
         }
         if (!s->d.periodic_y) {
-            Fy += orc_repulsion((P->y + 0.5) - P->r, sr, ew, Ca);
-            Fy -= orc_repulsion(((double)ny - 0.5 - P->y) - P->r, sr, ew, Ca);
+            const double hy = orc_support(P, 0.0, 1.0);
+            Fy += orc_repulsion((P->y + 0.5) - hy, sr, ew, Ca);
+            Fy -= orc_repulsion(((double)ny - 0.5 - P->y) - hy, sr, ew, Ca);
         }
         for (int32_t b = 0; b < s->np; ++b) {
             if (b == a) continue;
             const orc_particle *Q = &s->p[b];
             double dx = P->x - Q->x, dy = P->y - Q->y;
             double dist = sqrt(dx * dx + dy * dy);
-            double gap = dist - P->r - Q->r;
+            /* the gap along the line of centres: centre distance minus both
+             * support distances along it (both radii for disks) */
+            double gap = (is_ellipse(P) || is_ellipse(Q))
+                             ? dist - orc_support(P, -dx / dist, -dy / dist) - orc_support(Q, dx / dist, dy / dist)
+                             : dist - P->r - Q->r;
             if (gap > sr) continue;
-            double Cb = pi * Q->r * Q->r * (Q->rho - s->prm.rho_f) * s->prm.g;
+            const double Ab = is_ellipse(Q) ? pi * Q->r * Q->b : pi * Q->r * Q->r;
+            double Cb = Ab * (Q->rho - s->prm.rho_f) * s->prm.g;
             double mag = orc_repulsion(gap, sr, ew, 0.5 * (Ca + Cb));
             Fx += mag * dx / dist;
             Fy += mag * dy / dist;
         }
         orc_particle R = *P;
         if (!s->prm.fixed_particles) orc_integrate(P, Fx, Fy, Tz, &R);
+        /* leaving the cavity: the zone (side from the major semi-axis) must
+         * stay inside */
         if (R.x - R.r < -0.5 || R.x + R.r > (double)nx - 0.5 || R.y - R.r < -0.5 ||
             R.y + R.r > (double)ny - 0.5)
             bad = 1;
@@ -780,7 +896,18 @@ static void refill(orc_sim *s)
             const orc_particle *P = &s->p[pid];
             s->counters[6]++;
             double dx = (double)i - P->x, dy = (double)j - P->y;
-            int32_t c = orc_refill_direction(dx, dy);
+            /* outward normal: x - x_c for a disk; the gradient of the
+             * ellipse function (u / a^2, v / b^2 in its frame) for an ellipse */
+            int32_t c;
+            if (is_ellipse(P)) {
+                double cs, sn, u, v;
+                orc_cos_sin(P->theta, &cs, &sn);
+                ellipse_frame(dx, dy, cs, sn, &u, &v);
+                double gu = u / (P->r * P->r), gv = v / (P->b * P->b);
+                c = orc_refill_direction(gu * cs - gv * sn, gu * sn + gv * cs);
+            } else {
+                c = orc_refill_direction(dx, dy);
+            }
             double uwx = P->ux - P->omega * dy;
             double uwy = P->uy + P->omega * dx;
             int64_t nb[3] = {n, n, n};

@@ -48,9 +48,10 @@ typedef struct {
     double ux, uy;     /* translational velocity */
     double theta;      /* orientation angle */
     double omega;      /* angular velocity (z) */
-    double r;          /* radius */
+    double r;          /* radius; for an ellipse the semi-major axis a */
     double rho;        /* density */
     double T;          /* surface temperature T_w */
+    double b;          /* semi-minor axis of an ellipse (major axis along theta); 0 for a disk */
 } orc_particle;
 
 typedef struct {
@@ -115,6 +116,16 @@ int64_t orc_links_bruteforce(int32_t nx, int32_t ny, const int32_t *owner,
                              int32_t *node, int32_t *dir, int32_t *pid, double *q);
 /* Wall distance fraction q along e_k from (i,j) to the circle (x,y,r). */
 double orc_link_q(int32_t i, int32_t j, int32_t k, double x, double y, double r);
+/* cos(theta), sin(theta) by Cody-Waite reduction to [-pi/4, pi/4] and Taylor
+ * polynomials, in a fixed order of IEEE operations (the GPU repeats it
+ * operation for operation, so both sides rotate ellipses identically). */
+void orc_cos_sin(double theta, double *c, double *s);
+/* Ellipse geometry (Sec. 2.6 elliptical particles): node inside the ellipse
+ * of particle P; wall fraction q of the link (i, j) -> (i, j) + e_k; support
+ * distance h(n) = max over the ellipse of (x - x_c) . n for a unit n. */
+int32_t orc_in_particle(int32_t i, int32_t j, const orc_particle *P);
+double orc_link_q_particle(int32_t i, int32_t j, int32_t k, const orc_particle *P);
+double orc_support(const orc_particle *P, double nx, double ny);
 
 /* --- node-level operators (exported for the pins) ------------------------- */
 void orc_moment_matrices(double M[81], double Minv[81], double N[25], double Ninv[25]);

@@ -21,7 +21,7 @@ _HDR = os.path.join(_HERE, "lbm_oracle.h")
 
 ORC_PARTICLE_DTYPE = np.dtype(
     [("x", "f8"), ("y", "f8"), ("ux", "f8"), ("uy", "f8"), ("theta", "f8"),
-     ("omega", "f8"), ("r", "f8"), ("rho", "f8"), ("T", "f8")])
+     ("omega", "f8"), ("r", "f8"), ("rho", "f8"), ("T", "f8"), ("b", "f8")])
 
 
 class _Domain(C.Structure):
@@ -104,6 +104,14 @@ def load():
     lib.orc_thermal_bb.restype = C.c_double
     lib.orc_repulsion.argtypes = [C.c_double] * 4
     lib.orc_repulsion.restype = C.c_double
+    lib.orc_cos_sin.argtypes = [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.orc_cos_sin.restype = None
+    lib.orc_in_particle.argtypes = [C.c_int32, C.c_int32, P]
+    lib.orc_in_particle.restype = C.c_int32
+    lib.orc_link_q_particle.argtypes = [C.c_int32, C.c_int32, C.c_int32, P]
+    lib.orc_link_q_particle.restype = C.c_double
+    lib.orc_support.argtypes = [P, C.c_double, C.c_double]
+    lib.orc_support.restype = C.c_double
     lib.orc_integrate.argtypes = [P, C.c_double, C.c_double, C.c_double, P]
     lib.orc_refill_direction.argtypes = [C.c_double, C.c_double]
     lib.orc_refill_direction.restype = C.c_int32
@@ -127,8 +135,14 @@ def _particles(p) -> np.ndarray:
         return np.zeros(0, ORC_PARTICLE_DTYPE)
     out = np.zeros(len(p), ORC_PARTICLE_DTYPE)
     for name in ORC_PARTICLE_DTYPE.names:
-        out[name] = np.asarray([q[name] for q in p], dtype=np.float64) if isinstance(p, list) \
-            else np.asarray(p[name], dtype=np.float64)
+        if isinstance(p, list):
+            if name == "b" and any(name not in q for q in p):
+                continue  # disks: b = 0
+            out[name] = np.asarray([q[name] for q in p], dtype=np.float64)
+        else:
+            if name == "b" and name not in (p.dtype.names or ()):
+                continue
+            out[name] = np.asarray(p[name], dtype=np.float64)
     return out
 
 
@@ -312,6 +326,27 @@ def thermal_bb(q, gk0, gk1, gb0, have1, Tw):
 
 def repulsion(gap, s, eps, Cf):
     return load().orc_repulsion(gap, s, eps, Cf)
+
+
+def cos_sin(theta):
+    c, s = C.c_double(), C.c_double()
+    load().orc_cos_sin(float(theta), C.byref(c), C.byref(s))
+    return c.value, s.value
+
+
+def in_particle(i, j, particle) -> bool:
+    p = _particles(particle if not isinstance(particle, dict) else [particle])
+    return bool(load().orc_in_particle(int(i), int(j), p.ctypes.data))
+
+
+def link_q_particle(i, j, k, particle) -> float:
+    p = _particles(particle if not isinstance(particle, dict) else [particle])
+    return load().orc_link_q_particle(int(i), int(j), int(k), p.ctypes.data)
+
+
+def support(particle, nx, ny) -> float:
+    p = _particles(particle if not isinstance(particle, dict) else [particle])
+    return load().orc_support(p.ctypes.data, float(nx), float(ny))
 
 
 def integrate(particle, Fx, Fy, Tz):

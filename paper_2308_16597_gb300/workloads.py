@@ -19,7 +19,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-PARTICLE_FIELDS = ("x", "y", "ux", "uy", "theta", "omega", "r", "rho", "T")
+# r: radius, or semi-major axis of an ellipse; b: semi-minor axis (0 for a disk)
+PARTICLE_FIELDS = ("x", "y", "ux", "uy", "theta", "omega", "r", "rho", "T", "b")
 PARTICLE_DTYPE = np.dtype([(n, "f8") for n in PARTICLE_FIELDS])
 
 S_REP = 3.0  # repulsion threshold, lattice units (Sec. 2.4)
