@@ -166,7 +166,7 @@ def cpu_baseline(wl: W.Workload, seconds: float = 12.0, max_steps: int = 400):
     dt = time.perf_counter() - t0
     return {"value": metrics.mlups(sample.nx, sample.ny, steps, dt), "unit": UNIT,
             "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
-            "sample": "%dx%d crop of the %s workload with %d disks, %d FP64 oracle steps"
+            "sample": "%dx%d crop of the %s workload with %d particles, %d FP64 oracle steps"
                       % (sample.nx, sample.ny, wl.name, len(sample.particles), steps),
             "seconds": dt}
 
@@ -198,7 +198,7 @@ def run_reference(args, wl):
     ref.step(args.steps)
     dt = time.perf_counter() - t0
     v = metrics.mlups(sample.nx, sample.ny, args.steps, dt)
-    sample_desc = "%dx%d crop of %s (%d disks), one FP64 oracle step per bench step" % (
+    sample_desc = "%dx%d crop of %s (%d particles), one FP64 oracle step per bench step" % (
         sample.nx, sample.ny, wl.name, len(sample.particles))
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
@@ -213,12 +213,16 @@ def run_reference(args, wl):
 
 def config_of(wl, args):
     p = wl.particles
+    es = 4 if getattr(args, "storage", "fp32") == "fp32" else 2
+    state_gb = 2 * 14 * ((wl.nx + 31) // 32 * 32) * wl.ny * es / 1e9  # both distribution buffers
     return {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "particles": int(len(p)),
             "radius": float(p["r"][0]) if len(p) else None,
+            "minor_axis": float(p["b"][0]) if len(p) and p["b"][0] > 0 else None,
             "storage": getattr(args, "storage", "fp32"), "links": getattr(args, "links", "index"),
             "density_ratio": float(p["rho"][0]) if len(p) else None,
             "parallelism": "replicas%d" % args.gpus,
-            "l2": "no flush: the 1.8 GB distribution state is 14x the 129 MB L2"}
+            "l2": "no flush: each step reads one distribution buffer and writes the other, %.2f GB "
+                  "together, %.1fx the 129 MB L2" % (state_gb, state_gb / 0.129)}
 
 
 # ------------------------------------------------------------------------------------ ours
@@ -279,7 +283,7 @@ def run_ours(args, wl):
     if not args.no_e2e:
         del sim
         torch.cuda.empty_cache()
-        pinned_p = torch.empty(len(wl.particles) * 72, dtype=torch.uint8, pin_memory=True)
+        pinned_p = torch.empty(len(wl.particles) * lbm.PARTICLE_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
         pview = pinned_p.numpy().view(lbm.PARTICLE_DTYPE)
         fields = [torch.empty((wl.ny, wl.nx), dtype=torch.float32, pin_memory=True)
                   for _ in range(4)]
@@ -301,7 +305,7 @@ def run_ours(args, wl):
         t1 = time.perf_counter()
         lbm.lbm_destroy(h)
         e2e_s = max_over_ranks(t1 - t0, world, dev)
-        pbytes = len(wl.particles) * 72
+        pbytes = len(wl.particles) * lbm.PARTICLE_DTYPE.itemsize
         e2e = {"value": aggregate_mlups(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": pbytes / e2e_steps,
                "d2h_bytes_per_step": pbytes + 4 * 4 * nodes / e2e_steps,
@@ -400,7 +404,7 @@ def run_ensemble(args):
         for s in sims:
             s.particles()
             f = s.fields()
-            d2h += len(s._parts) * 72 + sum(a.nbytes for a in f)
+            d2h += len(s._parts) * lbm.PARTICLE_DTYPE.itemsize + sum(a.nbytes for a in f)
         t_read = time.perf_counter() - t0
         clk = clocks.stop()
         batch.sync()
@@ -431,7 +435,7 @@ def run_ensemble(args):
                              "peak_source": peaks["source"] + " (hbm_gbs)",
                              "kernel_times_from": "the autotuner's timing of the chosen tile shape"},
                 "e2e": {"value": aggregate_mlups(nodes, args.steps, world, e2e_s), "unit": UNIT,
-                        "h2d_bytes_per_step": sum(len(w.particles) * 72 for w in wls) / args.steps,
+                        "h2d_bytes_per_step": sum(len(w.particles) * lbm.PARTICLE_DTYPE.itemsize for w in wls) / args.steps,
                         "d2h_bytes_per_step": d2h / args.steps,
                         "includes": "lbm_init of all instances from host particles, batch creation, "
                                     "the timed steps, and every instance's particles and fields read back"},
@@ -537,8 +541,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cavity4000", "cavity2000", "cavity256", "cavity1024", "ensemble64",
-                                           "served"],
+    ap.add_argument("--workload", choices=["cavity4000", "cavity2000", "cavity256", "cavity1024", "ellipses129",
+                                           "ensemble64", "served"],
                     default="cavity4000")
     ap.add_argument("--tick-steps", type=int, default=100, help="served: steps per scheduling round")
     ap.add_argument("--no-e2e", action="store_true")
@@ -559,7 +563,7 @@ def main(argv=None):
         return run_ensemble(args) if args.workload == "ensemble64" else run_served(args)
     wl = {"cavity4000": W.sedimentation_4000, "cavity2000": W.sedimentation_2000,
           "cavity256": W.parity_256,
-          "cavity1024": W.crop_1024}[args.workload]()
+          "cavity1024": W.crop_1024, "ellipses129": W.ellipse_cluster_129}[args.workload]()
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

@@ -90,15 +90,19 @@ typedef struct {
     double T_wall[4];  /* wall temperature at x = -1/2, x = nx-1/2, y = -1/2, y = ny-1/2 */
 } lbm_domain;
 
-/* One rigid disk (Sec. 2.2).  72 bytes, 9 doubles. */
+/* One rigid particle (Sec. 2.2): a disk of radius r, or an ellipse with
+ * semi-axes r (along the body axis at angle theta from +x) and b (the
+ * elliptical particles of Sec. 2.6 and Appendix A).  80 bytes, 10 doubles. */
 typedef struct {
     double x, y;    /* centre */
     double ux, uy;  /* translational velocity */
-    double theta;   /* orientation angle */
+    double theta;   /* orientation angle (radians; |theta| < 2^20 pi/2) */
     double omega;   /* angular velocity (z) */
-    double r;       /* radius, >= 1 */
+    double r;       /* radius of a disk, semi-major axis of an ellipse; >= 1 */
     double rho;     /* density */
     double T;       /* surface temperature T_w (Sec. 2.3) */
+    double b;       /* semi-minor axis: 0 or r for a disk, else an ellipse
+                     * with 1 <= b < r */
 } lbm_particle;
 
 typedef struct {
@@ -132,11 +136,12 @@ int lbm_query_footprint(const lbm_domain *d, const lbm_particle *p, int32_t n,
  * is a device pointer to at least the queried bytes, 256-byte aligned, owned
  * by the caller and left untouched after lbm_destroy.  stream is a
  * cudaStream_t (NULL = the legacy default stream).  The initial fluid is at
- * rest with unit density and temperature T_init; nodes inside disks are
- * solid.  The first step's pre-collision state is collided here, so the
+ * rest with unit density and temperature T_init; nodes inside particles
+ * are solid.  The first step's pre-collision state is collided here, so the
  * stored state is always post-collision.  Synchronous.
- * Errors: LBM_EINVAL (bad sizes or rates, overlapping disks, disks crossing a
- * wall or, with a periodic axis, the domain edge), LBM_ENOSPC, LBM_ECUDA. */
+ * Errors: LBM_EINVAL (bad sizes or rates; particles whose circles of radius
+ * r overlap, or that cross a wall or, with a periodic axis, the domain edge;
+ * an ellipse with b < 1, b > r or |theta| > 1.6e6), LBM_ENOSPC, LBM_ECUDA. */
 int lbm_init(lbm_handle **h, const lbm_domain *d, const lbm_particle *p, int32_t n,
              const lbm_params *prm, void *d_workspace, size_t ws_bytes, void *stream);
 
@@ -181,7 +186,7 @@ int lbm_get_slots(lbm_handle *h, int32_t *node, float *q, int64_t cap, int64_t *
  * plane_stride elements apart, with pitch = nx rounded up to a multiple of 32
  * and plane_stride = pitch * ny rounded up to a multiple of 64; the owner map
  * (int32 [ny][nx]); the node flags (uint8 [ny][pitch]); the particle state as
- * 9 arrays of n doubles (x, y, ux, uy, theta, omega, r, rho, T); the previous
+ * 10 arrays of n doubles (x, y, ux, uy, theta, omega, r, rho, T, b); the previous
  * positions (2 arrays of n doubles).  Synchronises. */
 int lbm_state_bytes(lbm_handle *h, size_t *bytes);
 int lbm_get_state(lbm_handle *h, void *host_buf, size_t bytes);

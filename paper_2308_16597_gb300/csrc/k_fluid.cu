@@ -50,7 +50,7 @@ __device__ float pull_general(const Dev &D, const T *__restrict__ A, int x, int 
 
 // Values pulled into a node on the general path; for a newborn node the
 // refilling of Sec. 2.5 instead: e_c maximises n . e_c (FP64, ties to the
-// lowest index, n from the new centre), f is extrapolated from the nodes
+// lowest index, n the outward normal at the new position), f is extrapolated from the nodes
 // x + m e_c (m = 1, 2, 3) that are fluid at both times (quadratic, linear,
 // copy, or f_eq(1, u_w)), its momentum is set to rho u_w, and
 // g = g_eq(T_w, u_w).
@@ -69,10 +69,15 @@ __device__ __forceinline__ int slow_node(const Dev &D, const T *__restrict__ A,
     const int pid = own_cur[(long long)y * D.nx + x];
     const double xc = D.cur.x[pid], yc = D.cur.y[pid];
     const double dx = __dsub_rn((double)x, xc), dy = __dsub_rn((double)y, yc);
+    // outward normal: (dx, dy) for a disk, the gradient of the ellipse form
+    // for an ellipse
+    double nx = dx, ny = dy;
+    const double pr = D.cur.r[pid], pb = D.cur.b[pid];
+    if (is_ellipse(pr, pb)) ell_normal(ell_frame(xc, yc, D.cur.th[pid], pr, pb), dx, dy, nx, ny);
     int c = 1;
-    double best = __dadd_rn(__dmul_rn((double)ex(1), dx), __dmul_rn((double)ey(1), dy));
+    double best = __dadd_rn(__dmul_rn((double)ex(1), nx), __dmul_rn((double)ey(1), ny));
     for (int k = 2; k < kQ9; ++k) {
-        double v = __dadd_rn(__dmul_rn((double)ex(k), dx), __dmul_rn((double)ey(k), dy));
+        double v = __dadd_rn(__dmul_rn((double)ex(k), nx), __dmul_rn((double)ey(k), ny));
         if (v > best) {
             best = v;
             c = k;

@@ -98,6 +98,9 @@ __global__ void __launch_bounds__(kThreads) k_static_gather(View v, unsigned cha
     const int p = blockIdx.x;
     const double xc = v.P[p].x, yc = v.P[p].y, r = v.P[p].r;
     const DiskDF dk = disk_df(xc, yc, r);
+    const bool ell = is_ellipse(r, v.P[p].b);
+    EllFrame E{};
+    if (ell) E = ell_frame(xc, yc, v.P[p].theta, r, v.P[p].b);
     const int N = zone_size(r), cap = 12 * N - 12;
     const int X0 = (int)floor(xc - r) - 1, Y0 = (int)floor(yc - r) - 1;
     const int base = s.base[p];
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_static_gather(View v, unsigned cha
         }
         float dxf, dyf;
         s.node[base + t0] = found > 1 ? -2 : found ? fj * v.nx + fi : -1;
-        s.q[base + t0] = found ? link_q_df(fi, fj, k, dk, dxf, dyf) : 0.f;
+        s.q[base + t0] = !found ? 0.f : ell ? link_q_ellipse(fi, fj, k, E, dxf, dyf) : link_q_df(fi, fj, k, dk, dxf, dyf);
     }
 }
 
@@ -146,6 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned ch
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double xc = v.P[p].x, yc = v.P[p].y, r = v.P[p].r;
     const DiskDF dk = disk_df(xc, yc, r);
+    const bool ell = is_ellipse(r, v.P[p].b);
     const float Ux = (float)v.P[p].ux, Uy = (float)v.P[p].uy, Om = (float)v.P[p].omega;
     const float wT = (float)(0.2 * v.P[p].T);
     const int N = zone_size(r), cap = 12 * N - 12;
@@ -194,7 +198,9 @@ __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned ch
         float dxh, dxl, dyh, dyl;
         df_offset(fi, dk.xh, dk.xl, dxh, dxl);
         df_offset(fj, dk.yh, dk.yl, dyh, dyl);
-        const float dxf = dxh + dxl, dyf = dyh + dyl;
+        // an ellipse: the offset rounded from FP64, as the step's link kernel has it
+        const float dxf = ell ? (float)((double)fi - xc) : dxh + dxl;
+        const float dyf = ell ? (float)((double)fj - yc) : dyh + dyl;
         const float rx = dxf + q * kx, ry = dyf + q * ky;
         const float uwx = Ux - Om * ry, uwy = Uy + Om * rx;
         const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy);

@@ -11,6 +11,7 @@
 //                owner map is cleared over the old zones by k_links).
 #include <cudaTypedefs.h>
 
+#include <climits>
 #include <mutex>
 
 #include "lbm_internal.cuh"
@@ -144,6 +145,7 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
     extern __shared__ __align__(16) unsigned char lsm[];
     __shared__ int s_nvalid;
     __shared__ unsigned s_over;
+    __shared__ EllFrame s_ell;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const GeomRec G = D.geo_cur[p];
     const int N = G.N, cap = 12 * N - 12;
@@ -191,6 +193,7 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
         const DiskDF d0 = geom_df(G);
         D.pos4[p] = make_float4(d0.xh, d0.yh, d0.xl, d0.yl);
         D.prc[p] = make_float2(G.r, G.C);
+        if (G.r < 0.f) s_ell = ell_frame(D.cur.x[p], D.cur.y[p], D.cur.th[p], D.cur.r[p], D.cur.b[p]);
     }
     {
         // owner rows in chunks of four per warp, all four loads issued before
@@ -302,6 +305,7 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
 
     // ---- 4. bounce-back and momentum exchange, thread i on the i-th link
     const DiskDF dk = geom_df(G);
+    const bool ell = G.r < 0.f; // an ellipse: q in FP64
     const float Ux = G.ux, Uy = G.uy, Om_ = G.om, wT = G.wT;
     // populations of fluid nodes: no CTA writes them during this kernel
     const T *Ar = A;
@@ -315,7 +319,7 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
         const int kx = ex(k), ky = ey(k);
         const int fi = X0 + ((inf >> 4) & 255), fj = Y0 + (inf >> 12);
         float dxf, dyf;
-        const float q = link_q_df(fi, fj, k, dk, dxf, dyf);
+        const float q = ell ? link_q_ellipse(fi, fj, k, s_ell, dxf, dyf) : link_q_df(fi, fj, k, dk, dxf, dyf);
         D.slot_node[base + sl] = fj * D.nx + fi;
         D.slot_q[base + sl] = q;
 
@@ -397,6 +401,36 @@ __device__ __forceinline__ double repulsion(double gap, double s, double eps, do
 constexpr int kPartTile = 1600;
 constexpr int kPartPerBlock = kPartThreads / 32;
 
+// Support distance of particle p along the unit vector (nx, ny): its radius
+// for a disk.
+__device__ __forceinline__ double support_of(const Dev &D, int p, double nx, double ny)
+{
+    const double r = D.cur.r[p], b = D.cur.b[p];
+    if (!is_ellipse(r, b)) return r;
+    return ell_support(ell_frame(0.0, 0.0, D.cur.th[p], r, b), nx, ny);
+}
+
+// Pair repulsion on particle a from particle b when either is an ellipse, in
+// FP64: the gap along the line of centres is the centre distance minus both
+// support distances along it.
+__device__ __noinline__ void pair_force_ellipse(const Dev &D, int a, int b, float &fh_x, float &fl_x,
+                                                float &fh_y, float &fl_y)
+{
+    const double dx = D.cur.x[a] - D.cur.x[b], dy = D.cur.y[a] - D.cur.y[b];
+    const double dist = sqrt(dx * dx + dy * dy);
+    const double gap = dist - support_of(D, a, -dx / dist, -dy / dist) - support_of(D, b, dx / dist, dy / dist);
+    if (gap > D.s_rep) return;
+    auto scale = [&](int p) {
+        const double r = D.cur.r[p], pb = D.cur.b[p];
+        return kPi * r * (is_ellipse(r, pb) ? pb : r) * (D.cur.rho[p] - D.rho_f) * D.g;
+    };
+    const double mag = repulsion(gap, D.s_rep, D.eps_w, 0.5 * (scale(a) + scale(b)));
+    const double fx = mag * dx / dist, fy = mag * dy / dist;
+    const float hx = (float)fx, hy = (float)fy;
+    df_add(fh_x, fl_x, hx, (float)(fx - (double)hx));
+    df_add(fh_y, fl_y, hy, (float)(fy - (double)hy));
+}
+
 // Pair repulsion on disk a from disk b (FP32 from double-float centres).
 __device__ __noinline__ void pair_force(float4 pa, float2 ca, float4 pb, float2 cb, float s_rep,
                                         float inv_eps, float &fh_x, float &fl_x, float &fh_y,
@@ -424,12 +458,62 @@ struct Box {
 };
 __device__ __forceinline__ Box box_of(const GeomRec &G) { return Box{G.X0, G.Y0, G.N}; }
 
-// Raster of one disk by one warp (lane per zone row).
+// Raster of one ellipse by one warp (lane per zone row).  Along a row the
+// ellipse form is a convex quadratic in i, so the inside nodes form one run;
+// when the run is not empty the node nearest the vertex of the parabola lies
+// in it (checked with its two neighbours, against rounding of the vertex).
+// The run's ends are estimated from the quadratic's roots (FP32) and settled
+// with the predicate at the ends only: FP32 outside the rounding band, the
+// exact FP64 form inside it.
+__device__ __noinline__ void raster_ellipse(const Dev &D, int *own, const Box B, const GeomRec G, double x, double y,
+                                            double th, double r, double pb, int p)
+{
+    const int lane = threadIdx.x & 31;
+    const int xmin = B.X0, xmax = B.X0 + B.N - 1;
+    const EllDF F = ell_df(G.xh, G.xl, G.yh, G.yl, G.w0, G.w1, r, pb);
+    auto inside = [&](int i, int j) -> bool {
+        const int side = ell_side_df(i, j, F);
+        if (side) return side < 0;
+        return in_ellipse(i, j, ell_frame(x, y, th, r, pb));
+    };
+    const float c = F.c, s = F.s;
+    const float A2 = c * c * F.b2 + s * s * F.a2; // dx^2 coefficient
+    const float Bc = c * s * (F.b2 - F.a2);       // half the dx dy coefficient
+    const float Cc = s * s * F.b2 + c * c * F.a2; // dy^2 coefficient
+    for (int b = lane; b < B.N; b += 32) {
+        const int j = B.Y0 + b;
+        if (j < 0 || j >= D.ny) continue;
+        float dyh, dyl;
+        df_offset(j, G.yh, G.yl, dyh, dyl);
+        const float dy = dyh + dyl;
+        const float B1 = Bc * dy, C0 = Cc * dy * dy - F.ab;
+        const float mid = (G.xh - B1 / A2) + G.xl;
+        const int im = (int)floorf(mid + 0.5f);
+        const int in = inside(im, j) ? im : inside(im - 1, j) ? im - 1 : inside(im + 1, j) ? im + 1 : INT_MIN;
+        if (in == INT_MIN) continue; // then no node of the row is inside
+        const float h = sqrtf(fmaxf(B1 * B1 - A2 * C0, 0.f)) / A2;
+        int lo = max(min(in, (int)ceilf(mid - h)), xmin), hi = min(max(in, (int)floorf(mid + h)), xmax);
+        while (lo > xmin && inside(lo - 1, j)) --lo;
+        while (!inside(lo, j)) ++lo;
+        while (hi < xmax && inside(hi + 1, j)) ++hi;
+        while (!inside(hi, j)) --hi;
+        lo = max(lo, 0);
+        hi = min(hi, D.nx - 1);
+        int *row = own + (long long)j * D.nx;
+        for (int i = lo; i <= hi; ++i) atomicMax(row + i, p);
+    }
+}
+
+// Raster of one particle by one warp (lane per zone row).
 __device__ __forceinline__ void raster_one(const Dev &D, int *own, const GeomRec &G, double x, double y, double r,
-                                           int p)
+                                           double th, double pb, int p)
 {
     const int lane = threadIdx.x & 31;
     const Box B = box_of(G);
+    if (G.r < 0.f) {
+        raster_ellipse(D, own, B, G, x, y, th, r, pb, p);
+        return;
+    }
     const DiskDF dk = geom_df(G);
     const int ic = G.ic; // the node of each row nearest the centre
     for (int b = lane; b < B.N; b += 32) {
@@ -454,6 +538,15 @@ __device__ __forceinline__ void raster_one(const Dev &D, int *own, const GeomRec
     }
 }
 
+// Support distances of an ellipse along the wall normals x-hat and y-hat
+// (kept out of line: the disk path does not carry its registers).
+__device__ __noinline__ void wall_supports(double th, double r, double b, double &hx, double &hy)
+{
+    const EllFrame E = ell_frame(0.0, 0.0, th, r, b);
+    hx = ell_support(E, 1.0, 0.0);
+    hy = ell_support(E, 0.0, 1.0);
+}
+
 // FP64 tail of the particle update for particle b: total force, Newton-Euler
 // step, domain checks, new state and geometry record.  (fxh + fxl, fyh + fyl:
 // the pair repulsion summed in double-float.)
@@ -461,7 +554,11 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, float fxh, fl
 {
     double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
     double th = D.cur.th[b], om = D.cur.om[b];
-    const double r = D.cur.r[b], rho = D.cur.rho[b];
+    const double r = D.cur.r[b], rho = D.cur.rho[b], pb = D.cur.b[b];
+    // an ellipse: area pi r b, wall gaps to its support distances along the
+    // wall normals, I = M (r^2 + b^2) / 4
+    const bool ell = is_ellipse(r, pb);
+    const double rb = ell ? pb : r;
     double Fx, Fy, Tz;
     if (D.direct) {
         const DirectSums &ds = D.dsum[b];
@@ -478,20 +575,22 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, float fxh, fl
     D.force[3 * b + 0] = Fx;
     D.force[3 * b + 1] = Fy;
     D.force[3 * b + 2] = Tz;
-    const double Cb = kPi * r * r * (rho - D.rho_f) * D.g;
-    Fy -= (rho - D.rho_f) * kPi * r * r * D.g;
+    const double Cb = kPi * r * rb * (rho - D.rho_f) * D.g;
+    Fy -= (rho - D.rho_f) * kPi * r * rb * D.g;
+    double hx = r, hy = r;
+    if (ell) wall_supports(th, r, pb, hx, hy);
     if (!D.per_x) {
-        Fx += repulsion((x + 0.5) - r, D.s_rep, D.eps_w, Cb);
-        Fx -= repulsion(((double)D.nx - 0.5 - x) - r, D.s_rep, D.eps_w, Cb);
+        Fx += repulsion((x + 0.5) - hx, D.s_rep, D.eps_w, Cb);
+        Fx -= repulsion(((double)D.nx - 0.5 - x) - hx, D.s_rep, D.eps_w, Cb);
     }
     if (!D.per_y) {
-        Fy += repulsion((y + 0.5) - r, D.s_rep, D.eps_w, Cb);
-        Fy -= repulsion(((double)D.ny - 0.5 - y) - r, D.s_rep, D.eps_w, Cb);
+        Fy += repulsion((y + 0.5) - hy, D.s_rep, D.eps_w, Cb);
+        Fy -= repulsion(((double)D.ny - 0.5 - y) - hy, D.s_rep, D.eps_w, Cb);
     }
     Fx += (double)fxh + (double)fxl;
     Fy += (double)fyh + (double)fyl;
     if (!D.fixed) {
-        const double M = rho * kPi * r * r, I = 0.5 * M * r * r;
+        const double M = rho * kPi * r * rb, I = ell ? 0.25 * M * (r * r + pb * pb) : 0.5 * M * r * r;
         const double ux1 = ux + Fx / M, uy1 = uy + Fy / M, om1 = om + Tz / I;
         x += 0.5 * (ux + ux1);
         y += 0.5 * (uy + uy1);
@@ -513,8 +612,8 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, float fxh, fl
     }
     const double T = D.cur.T[b];
     D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
-    D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T;
-    D.geo_nxt[b] = make_geom(x, y, r, ux, uy, om, T, rho, D.rho_f, D.g);
+    D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T; D.nxt.b[b] = pb;
+    D.geo_nxt[b] = make_geom(x, y, r, pb, th, ux, uy, om, T, rho, D.rho_f, D.g);
 }
 
 __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *own_nxt, const int blk)
@@ -548,9 +647,11 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
         if (!me) continue;
         for (int u = lane; u < nb; u += 32) {
             const float4 o = sp[u];
-            const float dxf = pa.x - o.x, dyf = pa.y - o.y, lim = ca.x + sc[u].x + reach;
+            // (r < 0 marks an ellipse: screened by its circumscribed circle)
+            const float dxf = pa.x - o.x, dyf = pa.y - o.y, lim = fabsf(ca.x) + fabsf(sc[u].x) + reach;
             if (dxf * dxf + dyf * dyf > lim * lim || t0 + u == a) continue;
-            pair_force(pa, ca, o, sc[u], s_rep, inv_eps, fhx, flx, fhy, fly);
+            if (ca.x < 0.f || sc[u].x < 0.f) pair_force_ellipse(D, a, t0 + u, fhx, flx, fhy, fly);
+            else pair_force(pa, ca, o, sc[u], s_rep, inv_eps, fhx, flx, fhy, fly);
         }
     }
     warp_df_sum(fhx, flx);
@@ -566,13 +667,15 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
     // then the owner map at the new positions: warp w rasters the block's
     // particle w (its own new state only, so no other block is waited for)
     __syncthreads();
-    if (a < D.np) raster_one(D, own_nxt, D.geo_nxt[a], D.nxt.x[a], D.nxt.y[a], D.nxt.r[a], a);
+    if (a < D.np)
+        raster_one(D, own_nxt, D.geo_nxt[a], D.nxt.x[a], D.nxt.y[a], D.nxt.r[a], D.nxt.th[a], D.nxt.b[a], a);
 }
 
 
 
 // Owner map: node (i,j) belongs to disk p iff (i - x)^2 + (j - y)^2 <= r^2
-// (exact FP64); where disks overlap the highest index wins (atomicMax, so
+// (exact FP64; for an ellipse u^2 b^2 + v^2 a^2 <= a^2 b^2 in its frame);
+// where particles overlap the highest index wins (atomicMax, so
 // the result does not depend on the launch order).  One warp per disk, one
 // lane per zone row: the predicate holds on one contiguous run of each row
 // (it is monotone in |i - x|), so the run is found from an FP32 estimate of
@@ -583,7 +686,7 @@ __device__ __forceinline__ void raster_body(const Dev &D, int *own, const GeomRe
 {
     const int p = blk * (kBoxThreads / 32) + (threadIdx.x >> 5);
     if (p >= D.np) return;
-    raster_one(D, own, geo[p], pos.x[p], pos.y[p], pos.r[p], p);
+    raster_one(D, own, geo[p], pos.x[p], pos.y[p], pos.r[p], pos.th[p], pos.b[p], p);
 }
 
 // Flags over the rectangle that holds the particle's zones one step back, now
@@ -723,9 +826,12 @@ __global__ void __launch_bounds__(128)
             const int p = own[(long long)sj * D.nx + si];
             if (p < 0) continue;
             const GeomRec G = D.geo_cur[p];
-            const DiskDF dk = geom_df(G);
             float dxf, dyf;
-            const float q = link_q_df(i, j, k, dk, dxf, dyf);
+            const float q = G.r < 0.f ? link_q_ellipse(i, j, k,
+                                                       ell_frame(D.cur.x[p], D.cur.y[p], D.cur.th[p], D.cur.r[p],
+                                                                 D.cur.b[p]),
+                                                       dxf, dyf)
+                                      : link_q_df(i, j, k, geom_df(G), dxf, dyf);
             const int kb = opp(k);
             const int i1 = i - kx, j1 = j - ky, i2 = i - 2 * kx, j2 = j - 2 * ky;
             const bool have1 = fluid(i1, j1), have2 = fluid(i2, j2);
@@ -782,7 +888,7 @@ __global__ void __launch_bounds__(kLinkThreads)
 {
     links_body<T>(&tmA, D, A, own, own_nxt, parity, ahead, (int)blockIdx.x);
 }
-__global__ void __launch_bounds__(kPartThreads) k_particles(const Dev D, int parity, int *own_nxt)
+__global__ void __launch_bounds__(kPartThreads, 4) k_particles(const Dev D, int parity, int *own_nxt)
 {
     particles_body(D, parity, own_nxt, (int)blockIdx.x);
 }
@@ -812,7 +918,7 @@ __global__ void __launch_bounds__(kLinkThreads)
     links_body<T>(nullptr, sD, static_cast<T *>(a.A[par]), a.own[par], a.own[par ^ 1], par, ahead,
                   (int)blockIdx.x - __ldg(start + i));
 }
-__global__ void __launch_bounds__(kPartThreads)
+__global__ void __launch_bounds__(kPartThreads, 4)
     k_particles_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
 {
     __shared__ Dev sD;
@@ -847,12 +953,14 @@ __global__ void k_geom_init(const Dev D)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= D.np) return;
-    const GeomRec G = make_geom(D.cur.x[a], D.cur.y[a], D.cur.r[a], D.cur.ux[a], D.cur.uy[a],
-                                D.cur.om[a], D.cur.T[a], D.cur.rho[a], D.rho_f, D.g);
+    const GeomRec G = make_geom(D.cur.x[a], D.cur.y[a], D.cur.r[a], D.cur.b[a], D.cur.th[a], D.cur.ux[a],
+                                D.cur.uy[a], D.cur.om[a], D.cur.T[a], D.cur.rho[a], D.rho_f, D.g);
     D.geo_cur[a] = G;
     D.geo_nxt[a] = G;
-    D.geo_prev[a] = make_geom(D.px[a], D.py[a], D.cur.r[a], 0.0, 0.0, 0.0, D.cur.T[a], D.cur.rho[a],
-                              D.rho_f, D.g);
+    // (the orientation one step back is not kept: the current one, which
+    // only shapes the raster of that owner map inside the same zone)
+    D.geo_prev[a] = make_geom(D.px[a], D.py[a], D.cur.r[a], D.cur.b[a], D.cur.th[a], 0.0, 0.0, 0.0, D.cur.T[a],
+                              D.cur.rho[a], D.rho_f, D.g);
 }
 
 __global__ void k_pack_particles(const Dev D, lbm_particle *out)
@@ -862,7 +970,7 @@ __global__ void k_pack_particles(const Dev D, lbm_particle *out)
     lbm_particle P;
     P.x = D.cur.x[a]; P.y = D.cur.y[a]; P.ux = D.cur.ux[a]; P.uy = D.cur.uy[a];
     P.theta = D.cur.th[a]; P.omega = D.cur.om[a]; P.r = D.cur.r[a]; P.rho = D.cur.rho[a];
-    P.T = D.cur.T[a];
+    P.T = D.cur.T[a]; P.b = D.cur.b[a];
     out[a] = P;
 }
 

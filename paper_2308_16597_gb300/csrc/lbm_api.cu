@@ -45,10 +45,13 @@ int validate(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_pa
     double rmax = 0.0;
     for (int a = 0; a < n; ++a) {
         const lbm_particle &P = p[a];
-        const double v[] = {P.x, P.y, P.ux, P.uy, P.theta, P.omega, P.r, P.rho, P.T};
+        const double v[] = {P.x, P.y, P.ux, P.uy, P.theta, P.omega, P.r, P.rho, P.T, P.b};
         for (double x : v)
             if (!finite(x)) return LBM_EINVAL;
-        if (P.r < 1.0 || P.rho <= 0.0) return LBM_EINVAL;
+        if (P.r < 1.0 || P.rho <= 0.0 || P.b < 0.0) return LBM_EINVAL;
+        // an ellipse: 1 <= b < r, and theta within the exact range of the
+        // angle reduction by pi/2
+        if (is_ellipse(P.r, P.b) && (P.b < 1.0 || P.b > P.r || std::fabs(P.theta) > 1.6e6)) return LBM_EINVAL;
         // the link kernel holds a particle's zone in shared memory
         if (!link_zone_supported(zone_size(P.r), prm->storage)) return LBM_EINVAL;
         // a disk stays inside the cavity; next to a periodic seam it keeps two
@@ -99,8 +102,8 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
     L.slot_node = take(L.nslots * sizeof(int));
     L.slot_q = take(L.nslots * sizeof(float));
     L.slot_base = take((size_t)(n + 1) * sizeof(int));
-    L.cur = take((size_t)9 * n * sizeof(double));
-    L.nxt = take((size_t)9 * n * sizeof(double));
+    L.cur = take((size_t)kPartFields * n * sizeof(double));
+    L.nxt = take((size_t)kPartFields * n * sizeof(double));
     L.prev = take((size_t)2 * n * sizeof(double));
     L.force = take((size_t)3 * n * sizeof(double));
     L.pos4 = take((size_t)n * sizeof(float4));
@@ -125,7 +128,7 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
 PartSoA soa_at(char *base, size_t off, int n)
 {
     double *b = reinterpret_cast<double *>(base + off);
-    return PartSoA{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n, b + 7 * n, b + 8 * n};
+    return PartSoA{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n, b + 7 * n, b + 8 * n, b + 9 * n};
 }
 
 const char *kKernelNames[kNumKernelKinds] = {"link_gather_bb_force", "particle_update",
@@ -368,11 +371,11 @@ int upload_particles(lbm_handle *h, const lbm_particle *p)
 {
     const int n = h->np;
     if (n == 0) return LBM_OK;
-    std::vector<double> soa((size_t)9 * n);
+    std::vector<double> soa((size_t)kPartFields * n);
     for (int a = 0; a < n; ++a) {
-        const double v[9] = {p[a].x, p[a].y, p[a].ux, p[a].uy, p[a].theta, p[a].omega,
-                             p[a].r, p[a].rho, p[a].T};
-        for (int f = 0; f < 9; ++f) soa[(size_t)f * n + a] = v[f];
+        const double v[kPartFields] = {p[a].x, p[a].y, p[a].ux, p[a].uy, p[a].theta, p[a].omega,
+                                       p[a].r, p[a].rho, p[a].T, p[a].b};
+        for (int f = 0; f < kPartFields; ++f) soa[(size_t)f * n + a] = v[f];
     }
     const size_t bytes = soa.size() * sizeof(double);
     CK(h, cudaMemcpyAsync(h->D.cur.x, soa.data(), bytes, cudaMemcpyHostToDevice, h->stream));
@@ -621,7 +624,7 @@ static size_t state_parts(const lbm_handle *h, size_t sz[5])
     sz[0] = (size_t)kPop * h->L.ps * storage_bytes(h->D.storage);
     sz[1] = (size_t)h->d.nx * h->d.ny * sizeof(int);
     sz[2] = (size_t)h->L.pitch * h->d.ny;
-    sz[3] = (size_t)9 * h->np * sizeof(double);
+    sz[3] = (size_t)kPartFields * h->np * sizeof(double);
     sz[4] = (size_t)2 * h->np * sizeof(double);
     return sz[0] + sz[1] + sz[2] + sz[3] + sz[4];
 }

@@ -97,8 +97,9 @@ struct Status {
 
 // Structure-of-arrays particle state on the device (FP64).
 struct PartSoA {
-    double *x, *y, *ux, *uy, *th, *om, *r, *rho, *T;
+    double *x, *y, *ux, *uy, *th, *om, *r, *rho, *T, *b;
 };
+constexpr int kPartFields = 10; // doubles per particle in a PartSoA
 
 // Everything a kernel needs, passed by value.
 struct Dev {
@@ -127,7 +128,7 @@ struct Dev {
     double *px, *py;   // positions one step back (boxes to clear)
     double *force;     // [3 np]: hydrodynamic Fx, Fy, Tz of the last step
     float4 *pos4;      // [np]: centre as double-float (xh, yh, xl, yl) at the start of the step
-    float2 *prc;       // [np]: (r, C = pi r^2 (rho_p - rho_f) g) in FP32 for the pair screening
+    float2 *prc;       // [np]: (GeomRec r, C) in FP32 for the pair screening (r < 0: an ellipse)
     struct LinkSums *lsum; // [np]: link-kernel sums, assembled into force by the particle update
     struct DirectSums *dsum; // [np]: the same sums accumulated by atomics (direct addressing)
     int direct;            // links found by the node-parallel scan instead of the index array
@@ -160,6 +161,119 @@ __device__ __forceinline__ double link_q(int i, int j, int k, double xc, double 
     if (disc < 0.0) disc = 0.0;
     double t = __ddiv_rn(c, __dadd_rn(-de, __dsqrt_rn(disc)));
     return t > 1.0 ? 1.0 : t;
+}
+
+// ---------------------------------------------------------------------------
+// Elliptical particles (Sec. 2.6, Appendix A): semi-axes a = r along the body
+// axis at angle theta and b; 0 < b != r.  Every operation below is a
+// correctly rounded FP64 operation with no FMA contraction, so the owner map
+// and the wall fractions are reproducible bit for bit by any implementation
+// of the same expressions.  The ellipse lies inside the circle of radius r,
+// so the zone of a disk of radius r holds it and its links.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline bool is_ellipse(double r, double b) { return b > 0.0 && b != r; }
+
+// cos and sin of theta: Cody-Waite reduction by pi/2 (pi/2 split into a
+// 33-bit head, so k times the head is exact for |k| < 2^20, and a tail), then
+// the Taylor series of sin (to t^17) and cos (to t^16) on [-pi/4, pi/4] in
+// Horner form, truncation below 1e-17; the quadrant k mod 4 picks the signs.
+__device__ __forceinline__ void cos_sin_rn(double theta, double &c, double &s)
+{
+    const double two_over_pi = 0.63661977236758134308;
+    const double pio2_hi = 1.5707963267341256e+00;
+    const double pio2_lo = 6.0771005065061922e-11;
+    const double k = floor(__dadd_rn(__dmul_rn(theta, two_over_pi), 0.5));
+    const double t = __dsub_rn(__dsub_rn(theta, __dmul_rn(k, pio2_hi)), __dmul_rn(k, pio2_lo));
+    const double t2 = __dmul_rn(t, t);
+    // odd series: 1/17!, -1/15!, ..., -1/3!; even series: 1/16!, ..., -1/2!
+    // (each 1/n! correctly rounded to FP64, written out)
+    const double sc[8] = {2.8114572543455206e-15, -7.647163731819816e-13, 1.6059043836821613e-10,
+                          -2.505210838544172e-08, 2.7557319223985893e-06, -0.0001984126984126984,
+                          0.008333333333333333,   -0.16666666666666666};
+    const double cc[8] = {4.779477332387385e-14,  -1.1470745597729725e-11, 2.08767569878681e-09,
+                          -2.755731922398589e-07, 2.48015873015873e-05,    -0.001388888888888889,
+                          0.041666666666666664,   -0.5};
+    double ps = sc[0], pc = cc[0];
+#pragma unroll
+    for (int n = 1; n < 8; ++n) {
+        ps = __dadd_rn(__dmul_rn(ps, t2), sc[n]);
+        pc = __dadd_rn(__dmul_rn(pc, t2), cc[n]);
+    }
+    const double sn = __dadd_rn(t, __dmul_rn(t, __dmul_rn(t2, ps)));
+    const double cn = __dadd_rn(1.0, __dmul_rn(t2, pc));
+    const long long q = (long long)k & 3;
+    c = q == 0 ? cn : q == 1 ? -sn : q == 2 ? -cn : sn;
+    s = q == 0 ? sn : q == 1 ? cn : q == 2 ? -sn : -cn;
+}
+
+// An ellipse in the form its predicates use: centre, cos/sin of theta, a^2, b^2.
+struct EllFrame {
+    double x, y, c, s, a2, b2;
+};
+__device__ __forceinline__ EllFrame ell_frame(double x, double y, double th, double r, double b)
+{
+    EllFrame E;
+    E.x = x;
+    E.y = y;
+    cos_sin_rn(th, E.c, E.s);
+    E.a2 = __dmul_rn(r, r);
+    E.b2 = __dmul_rn(b, b);
+    return E;
+}
+// (dx, dy) in the body frame: u along the major axis, v along the minor one.
+__device__ __forceinline__ void ell_uv(const EllFrame &E, double dx, double dy, double &u, double &v)
+{
+    u = __dadd_rn(__dmul_rn(dx, E.c), __dmul_rn(dy, E.s));
+    v = __dsub_rn(__dmul_rn(dy, E.c), __dmul_rn(dx, E.s));
+}
+// u^2 b^2 + v^2 a^2 (the ellipse is where it is <= a^2 b^2)
+__device__ __forceinline__ double ell_form(const EllFrame &E, double u, double v)
+{
+    return __dadd_rn(__dmul_rn(__dmul_rn(u, u), E.b2), __dmul_rn(__dmul_rn(v, v), E.a2));
+}
+__device__ __forceinline__ bool in_ellipse(int i, int j, const EllFrame &E)
+{
+    double u, v;
+    ell_uv(E, __dsub_rn((double)i, E.x), __dsub_rn((double)j, E.y), u, v);
+    return ell_form(E, u, v) <= __dmul_rn(E.a2, E.b2);
+}
+// Wall fraction q of the link (i, j) -> (i, j) + e_k on the ellipse: the
+// smaller root t of F(d + t e) = 0, F(w) = u(w)^2 b^2 + v(w)^2 a^2 - a^2 b^2,
+// i.e. P2 t^2 + 2 P1 t + P0 = 0, as t = P0 / (-P1 + sqrt(P1^2 - P2 P0))
+// (P0 > 0 outside, P1 < 0 towards the ellipse: no cancellation).  Also
+// returns d = (i, j) - centre rounded to FP32.
+__device__ __forceinline__ float link_q_ellipse(int i, int j, int k, const EllFrame &E, float &dxf, float &dyf)
+{
+    const double dx = __dsub_rn((double)i, E.x), dy = __dsub_rn((double)j, E.y);
+    double du, dv, eu, ev;
+    ell_uv(E, dx, dy, du, dv);
+    ell_uv(E, (double)ex(k), (double)ey(k), eu, ev);
+    const double P2 = ell_form(E, eu, ev);
+    const double P1 = __dadd_rn(__dmul_rn(__dmul_rn(du, eu), E.b2), __dmul_rn(__dmul_rn(dv, ev), E.a2));
+    const double P0 = __dsub_rn(ell_form(E, du, dv), __dmul_rn(E.a2, E.b2));
+    double disc = __dsub_rn(__dmul_rn(P1, P1), __dmul_rn(P2, P0));
+    if (disc < 0.0) disc = 0.0;
+    double t = __ddiv_rn(P0, __dadd_rn(-P1, __dsqrt_rn(disc)));
+    dxf = (float)dx;
+    dyf = (float)dy;
+    return (float)(t > 1.0 ? 1.0 : t);
+}
+// Outward normal at an offset (dx, dy) from the centre, unnormalised: the
+// gradient of u^2 / a^2 + v^2 / b^2 (up to a factor 2) in lattice axes.
+__device__ __forceinline__ void ell_normal(const EllFrame &E, double dx, double dy, double &nx, double &ny)
+{
+    double u, v;
+    ell_uv(E, dx, dy, u, v);
+    const double gu = __ddiv_rn(u, E.a2), gv = __ddiv_rn(v, E.b2);
+    nx = __dsub_rn(__dmul_rn(gu, E.c), __dmul_rn(gv, E.s));
+    ny = __dadd_rn(__dmul_rn(gu, E.s), __dmul_rn(gv, E.c));
+}
+// Support distance along the unit vector n: sqrt(a^2 (n.u)^2 + b^2 (n.v)^2).
+__device__ __forceinline__ double ell_support(const EllFrame &E, double nx, double ny)
+{
+    double u, v;
+    ell_uv(E, nx, ny, u, v);
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(__dmul_rn(E.a2, u), u), __dmul_rn(__dmul_rn(E.b2, v), v)));
 }
 
 // Effective zone of Sec. 3: N = ceil(2r) + 3 nodes per side starting at
@@ -265,24 +379,67 @@ __device__ __forceinline__ float link_q_df(int i, int j, int k, const DiskDF &D,
     return fminf(c / (sqrtf(disc) - de), 1.f);
 }
 
+// The ellipse predicate decided in FP32 (offsets from the double-float
+// centre, FP32 cos/sin, a^2, b^2), except inside a band around the boundary
+// wide enough to hold every FP32 rounding: with R = r + 3 bounding |d| on the
+// zone, the FP32 value of F = u^2 b^2 + v^2 a^2 - a^2 b^2 is within
+// 3.3e-6 R^2 a^2 of the exact one, and the band is 1e-5 R^2 a^2.  Outside the
+// band the FP32 sign is the exact sign.
+struct EllDF {
+    float xh, xl, yh, yl, c, s, a2, b2, ab, band;
+};
+__device__ __forceinline__ EllDF ell_df(float xh, float xl, float yh, float yl, float c, float s, double r,
+                                        double b)
+{
+    EllDF E;
+    E.xh = xh; E.xl = xl; E.yh = yh; E.yl = yl; E.c = c; E.s = s;
+    E.a2 = (float)(r * r);
+    E.b2 = (float)(b * b);
+    E.ab = (float)(r * r * b * b);
+    const float R = (float)r + 3.f;
+    E.band = 1e-5f * R * R * E.a2;
+    return E;
+}
+// -1: inside, +1: outside, 0: inside the band (decide in FP64).
+__device__ __forceinline__ int ell_side_df(int i, int j, const EllDF &E)
+{
+    float dxh, dxl, dyh, dyl;
+    df_offset(i, E.xh, E.xl, dxh, dxl);
+    df_offset(j, E.yh, E.yl, dyh, dyl);
+    const float dx = dxh + dxl, dy = dyh + dyl;
+    const float u = dx * E.c + dy * E.s, v = dy * E.c - dx * E.s;
+    const float F = (u * u) * E.b2 + (v * v) * E.a2 - E.ab;
+    return F < -E.band ? -1 : F > E.band ? 1 : 0;
+}
+
 // Geometry of one disk position in the forms the per-warp kernels use, built
 // once per particle and step in FP64 (one lane per particle) so that no warp
 // repeats FP64 work: the double-float centre and r^2, the zone (origin, side),
 // the row centre index floor(x + 1/2), FP32 velocities and 2 w_k T_w, and the
-// radius and repulsion force scale C = pi r^2 (rho_p - rho_f) g.
+// radius (negated for an ellipse, whose semi-major axis it is) and repulsion
+// force scale C = A (rho_p - rho_f) g with the area A = pi r^2 (pi r b for an
+// ellipse).  w0, w1: r^2 as double-float for a disk; cos theta and sin theta
+// in FP32 for an ellipse.
 struct GeomRec {
-    float xh, xl, yh, yl, r2h, r2l, r, C;
+    float xh, xl, yh, yl, w0, w1, r, C;
     int X0, Y0, N, ic;
     float ux, uy, om, wT;
 };
-__device__ __forceinline__ GeomRec make_geom(double x, double y, double r, double ux, double uy,
-                                             double om, double T, double rho, double rho_f, double g)
+__device__ __forceinline__ GeomRec make_geom(double x, double y, double r, double b, double th, double ux,
+                                             double uy, double om, double T, double rho, double rho_f, double g)
 {
     GeomRec G;
     const DiskDF d = disk_df(x, y, r);
-    G.xh = d.xh; G.xl = d.xl; G.yh = d.yh; G.yl = d.yl; G.r2h = d.r2h; G.r2l = d.r2l;
-    G.r = (float)r;
-    G.C = (float)(3.14159265358979323846 * r * r * (rho - rho_f) * g);
+    G.xh = d.xh; G.xl = d.xl; G.yh = d.yh; G.yl = d.yl; G.w0 = d.r2h; G.w1 = d.r2l;
+    const bool ell = is_ellipse(r, b);
+    if (ell) {
+        double c, s;
+        cos_sin_rn(th, c, s);
+        G.w0 = (float)c;
+        G.w1 = (float)s;
+    }
+    G.r = ell ? -(float)r : (float)r;
+    G.C = (float)(3.14159265358979323846 * r * (ell ? b : r) * (rho - rho_f) * g);
     G.N = zone_size(r);
     G.X0 = (int)floor(x - r) - 1;
     G.Y0 = (int)floor(y - r) - 1;
@@ -293,7 +450,7 @@ __device__ __forceinline__ GeomRec make_geom(double x, double y, double r, doubl
 __device__ __forceinline__ DiskDF geom_df(const GeomRec &G)
 {
     DiskDF d;
-    d.xh = G.xh; d.xl = G.xl; d.yh = G.yh; d.yl = G.yl; d.r2h = G.r2h; d.r2l = G.r2l;
+    d.xh = G.xh; d.xl = G.xl; d.yh = G.yh; d.yl = G.yl; d.r2h = G.w0; d.r2l = G.w1;
     return d;
 }
 

@@ -26,7 +26,7 @@ LBM_STORE_FP32, LBM_STORE_BF16, LBM_STORE_FP16 = 0, 1, 2
 LBM_FLAG_FIXED_PARTICLES, LBM_FLAG_NO_GRAPH, LBM_FLAG_OVERLAP, LBM_FLAG_DIRECT_LINKS = 1, 2, 4, 8
 
 PARTICLE_DTYPE = np.dtype([(n, "f8") for n in
-                           ("x", "y", "ux", "uy", "theta", "omega", "r", "rho", "T")])
+                           ("x", "y", "ux", "uy", "theta", "omega", "r", "rho", "T", "b")])
 
 
 class LbmError(RuntimeError):
@@ -149,8 +149,10 @@ def make_params(nu, alpha, g=0.0, beta=1.0, T0=0.0, rho_f=1.0, T_init=0.0, s_e=0
 def pack_particles(parts) -> np.ndarray:
     out = np.zeros(0 if parts is None else len(parts), PARTICLE_DTYPE)
     if parts is not None and len(parts):
+        have = parts.dtype.names or ()
         for n in PARTICLE_DTYPE.names:
-            out[n] = np.asarray(parts[n], dtype=np.float64)
+            if n in have:  # "b" may be absent: disks
+                out[n] = np.asarray(parts[n], dtype=np.float64)
     return np.ascontiguousarray(out)
 
 

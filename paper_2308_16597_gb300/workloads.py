@@ -142,6 +142,50 @@ def sedimentation_2000(seed: int = 2000) -> Workload:
                          name="cavity2000_1200disks_r10", steps=1000)
 
 
+def ellipses_256(seed: int = 1657, n: int = 6, a: float = 12.0, b: float = 6.0) -> Workload:
+    """256x256 cavity, n hot ellipses with semi-axes a = 12, b = 6 (the 2:1
+    aspect ratio of Sec. 2.6.3), orientations uniform in [0, pi), in the upper
+    half; density ratio 1.5, g = 1e-5, Pr = 0.71, nu = 0.02.  Placement keeps
+    the circumscribed circles (radius a) apart by the repulsion range."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo = a + S_REP + 1.0
+    parts = rsa_disks(rng, n, a, lo, 255 - lo, 128.0 + a + S_REP, 255 - lo, min_gap=S_REP + 1.0)
+    parts["b"] = b
+    parts["theta"] = rng.uniform(0.0, math.pi, n)
+    parts["rho"] = 1.5
+    parts["T"] = 1.0
+    return Workload("cavity256_%dellipses" % n, cavity(256, 256), parts, base_params(0.02, 0.71, 1e-5), 1000)
+
+
+def ellipse_cluster_129(seed: int = 129, ring_step: float = 56.0) -> Workload:
+    """Sec. 2.6.3, elliptical hot particles in a cold cavity (Table of that
+    case): 1000 x 2000 l.u., 129 ellipses A x B = 50 x 25 l.u. (semi-axes 25
+    and 12.5), density 1.5, nu = 0.01, alpha = 0.002 (Pr = 5),
+    g = 9.8e-7, beta = 8.16e-3, Delta_T = 1 (particles hot, walls and fluid
+    cold).  The cluster: one particle at (W/2, 3H/4) and rings of 6, 12, 18,
+    24, 31 and 37 around it.  The ring spacing is not given; ring m sits at
+    radius 56 m, so that the circumscribed circles of neighbours on and
+    between rings stay the repulsion range apart.  Each ring starts at a
+    seeded angle; orientations are uniform in [0, pi)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W_, H_ = 1000, 2000
+    xs, ys = [0.5 * W_], [0.75 * H_]
+    for m, count in enumerate((6, 12, 18, 24, 31, 37), start=1):
+        phase = rng.uniform(0.0, 2.0 * math.pi)
+        ang = phase + 2.0 * math.pi * np.arange(count) / count
+        xs.extend(0.5 * W_ + m * ring_step * np.cos(ang))
+        ys.extend(0.75 * H_ + m * ring_step * np.sin(ang))
+    n = len(xs)
+    parts = np.zeros(n, PARTICLE_DTYPE)
+    parts["x"], parts["y"] = xs, ys
+    parts["r"], parts["b"] = 25.0, 12.5
+    parts["theta"] = rng.uniform(0.0, math.pi, n)
+    parts["rho"] = 1.5
+    parts["T"] = 1.0
+    prm = base_params(0.01, 5.0, 9.8e-7, beta=8.16e-3)
+    return Workload("cavity1000x2000_129ellipses", cavity(W_, H_), parts, prm, 10000)
+
+
 def crop_1024(seed: int = 3) -> Workload:
     """1024x1024 crop with 300 disks r = 10 in the upper half (reduced storage)."""
     return sedimentation(1024, 1024, 300, 10.0, 1.5, 0.5, seed, nu=0.02, Pr=0.71, g=1e-5,

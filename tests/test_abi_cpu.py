@@ -64,7 +64,8 @@ def test_footprint_counts_every_buffer(lib):
 
 
 @pytest.mark.parametrize("bad", ["nx", "nu", "alpha", "rate", "storage", "overlap", "wall", "radius",
-                                 "reserved"])
+                                 "reserved", "minor_below_1", "minor_above_r", "minor_negative",
+                                 "minor_nan", "angle_out_of_range"])
 def test_invalid_arguments_are_rejected(lib, bad):
     d, p, prm = _setup()
     if bad == "nx":
@@ -85,9 +86,38 @@ def test_invalid_arguments_are_rejected(lib, bad):
         p["r"][0] = 0.5
     elif bad == "reserved":
         d.reserved = 1
+    elif bad == "minor_below_1":
+        p["b"][0] = 0.5
+    elif bad == "minor_above_r":
+        p["b"][0] = p["r"][0] + 0.5
+    elif bad == "minor_negative":
+        p["b"][0] = -1.0
+    elif bad == "minor_nan":
+        p["b"][0] = np.nan
+    elif bad == "angle_out_of_range":
+        p["b"][0], p["theta"][0] = 2.0, 2e6
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_query_footprint(d, p, prm)
     assert e.value.code == lbm.LBM_EINVAL
+
+
+def test_disks_and_ellipses_are_accepted(lib):
+    """b = 0 and b = r are disks; 1 <= b < r an ellipse (any angle up to
+    1.6e6 rad); the footprint does not depend on b (the zone is the
+    circumscribed disk's)."""
+    d, p, prm = _setup()
+    ref = lbm.lbm_query_footprint(d, p, prm)
+    for b, th in ((0.0, 0.0), (5.0, 3.0), (1.0, -7.5), (4.99, 1.5e6)):
+        p["b"][:] = b
+        p["theta"][:] = th
+        assert lbm.lbm_query_footprint(d, p, prm) == ref
+
+
+def test_particle_struct_matches_the_dtype(lib):
+    """lbm_particle is ten doubles: the Python record has the same layout."""
+    assert lbm.PARTICLE_DTYPE.itemsize == 80
+    assert lbm.PARTICLE_DTYPE.names[-1] == "b"
+    assert W.PARTICLE_DTYPE == lbm.PARTICLE_DTYPE
 
 
 def test_strerror_covers_every_code(lib):

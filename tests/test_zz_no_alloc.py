@@ -22,12 +22,13 @@ def _layout(nx, ny):
     return pitch, ps
 
 
-def test_noalloc_forces_match_the_step_kernel_on_two_calls():
+@pytest.mark.parametrize("make", [W.parity_256, W.ellipses_256])
+def test_noalloc_forces_match_the_step_kernel_on_two_calls(make):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import __graft_entry__ as g
     g.build()
-    wl = W.parity_256()
+    wl = make()
     nx, ny, n = wl.nx, wl.ny, len(wl.particles)
     pitch, ps = _layout(nx, ny)
     sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
@@ -36,8 +37,9 @@ def test_noalloc_forces_match_the_step_kernel_on_two_calls():
     a_bytes = 14 * ps * 4
     own_bytes = nx * ny * 4
     flag_bytes = pitch * ny
-    soa = state[a_bytes + own_bytes + flag_bytes:a_bytes + own_bytes + flag_bytes + 9 * n * 8]
-    soa = soa.view(np.float64).reshape(9, n)
+    nf = len(lbm.PARTICLE_DTYPE.names)  # particle state: nf arrays of n doubles
+    soa = state[a_bytes + own_bytes + flag_bytes:a_bytes + own_bytes + flag_bytes + nf * n * 8]
+    soa = soa.view(np.float64).reshape(nf, n)
     parts = np.zeros(n, lbm.PARTICLE_DTYPE)
     for f, name in enumerate(lbm.PARTICLE_DTYPE.names):
         parts[name] = soa[f]
