@@ -9,8 +9,6 @@
 //   k_raster, k_flags
 //                owner map and node flags at the new positions (the
 //                owner map is cleared over the old zones by k_links).
-#include <cudaTypedefs.h>
-
 #include <climits>
 #include <mutex>
 
@@ -40,8 +38,6 @@ __device__ __forceinline__ T warp_sum(T v)
 
 } // namespace
 
-constexpr int kTilePlanes = 12; // planes the rules read: f1..f8, g1..g4
-
 // Double-float warp sum (lane 0 receives the result).
 __device__ __forceinline__ void warp_df_sum(float &h, float &l)
 {
@@ -53,20 +49,12 @@ __device__ __forceinline__ void warp_df_sum(float &h, float &l)
     }
 }
 
-// The link kernel's window for zones of side N and es-byte elements: the
-// zone plus the two-node margin of the bounce-back stencil, wy = N + 4 rows
-// of wx columns.  Its first column is the zone's first column minus two,
-// rounded down to a multiple of al = 16 / es elements (a tensor prefetch box
-// starts on a 16-byte boundary), so wx = N + 3 + al rounded up to a multiple
-// of al; wx is at most 64 (the fluid and owner masks of a row are 64-bit
-// words).
-__host__ __device__ inline int link_tile_al(int es) { return 16 / es; }
+// The link kernel's window for zones of side N: the zone plus the two-node
+// margin of the bounce-back stencil, wy = N + 4 rows of wx = N + 4 columns
+// from (X0 - 2, Y0 - 2); wx is at most 64 (the fluid and owner masks of a row
+// are 64-bit words).
 __host__ __device__ inline int link_tile_wy(int N) { return N + 4; }
-__host__ __device__ inline int link_tile_wx(int N, int es)
-{
-    const int al = link_tile_al(es);
-    return (N + 3 + al + al - 1) / al * al;
-}
+__host__ __device__ inline int link_tile_wx(int N) { return N + 4; }
 __host__ __device__ inline int link_occ_words(int N) { return (12 * N - 12 + 31) / 32; }
 
 // Shared memory: the fluid and owner row masks [wy] (u64 each), slot occupancy words and their prefix [words], and per
@@ -82,19 +70,7 @@ size_t link_smem_bytes(int N, int storage)
 
 bool link_zone_supported(int N, int storage)
 {
-    return link_tile_wx(N, storage_bytes(storage)) <= 64 && link_smem_bytes(N, storage) <= (size_t)200 * 1024;
-}
-
-// Global plane of window plane t: f1..f8 then g1..g4.
-__device__ __forceinline__ int tile_global_plane(int t) { return t < 8 ? t + 1 : t + 2; }
-
-// Tensor prefetch of one box into L2 (no completion to wait for).
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *tm, int x, int y, int z)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];" ::"l"(
-                     reinterpret_cast<unsigned long long>(tm)),
-                 "r"(x), "r"(y), "r"(z)
-                 : "memory");
+    return link_tile_wx(N) <= 64 && link_smem_bytes(N, storage) <= (size_t)200 * 1024;
 }
 
 // Fixed slot (Sec. 3) of the link from zone node (a, b) along e_k, or -1 for
@@ -117,11 +93,13 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 //  1. the warps read the owner map over the particle's window (zone plus
 //     the two-node margin of the bounce-back stencil) and record per row a
 //     fluid mask and an owned-by-this-particle mask (one ballot per 32
-//     nodes); thread 0 issues tensor prefetches into L2 of the window of
-//     the 12 planes the rules read (f1..f8, g1..g4) for the particle `ahead`
-//     places later in launch order (about one residency wave ahead), and a
-//     warp prefetches that particle's owner rows, so that the scattered
-//     reads of phases 1 and 4 hit L2;
+//     nodes); a warp prefetches into L2 the owner rows of the particle
+//     `ahead` places later in launch order (one residency wave ahead).
+//     (Prefetching the populations of that particle's window as well, by
+//     tensor or row prefetches, or of this particle's links as they are
+//     found, measured slower: the kernel is bound by its latency chains and
+//     issue, not by DRAM, and the extra traffic and instructions cost more
+//     than the hits gained);
 //  2. thread (k, b) intersects the fluid mask of zone row b with the owner
 //     mask of row b + e_k,y shifted by e_k,x: each set bit is a link, which
 //     claims its fixed slot of the index array (direction k, line through
@@ -137,11 +115,10 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 //     and the momentum-exchange bracket of Eq. force / Eq. torque, stored per
 //     link and summed by one warp in link order.
 template <typename T>
-__device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D, T *A, const int *__restrict__ own,
+__device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__restrict__ own,
                                            int *__restrict__ own_nxt, int parity, int ahead, const int p)
 {
     using E = Elem<T>;
-    constexpr int es = (int)sizeof(T), al = 16 / es;
     extern __shared__ __align__(16) unsigned char lsm[];
     __shared__ int s_nvalid;
     __shared__ unsigned s_over;
@@ -153,8 +130,8 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
     const int base = D.slot_base[p];
 
     const int Nm = D.zone_max;
-    const int wy = link_tile_wy(Nm), wx = link_tile_wx(Nm, es);
-    const int XA = (X0 - 2) & ~(al - 1), YA = Y0 - 2, off = X0 - XA;
+    const int wy = link_tile_wy(Nm), wx = link_tile_wx(Nm);
+    const int XA = X0 - 2, YA = Y0 - 2, off = 2;
     unsigned long long *Fm = reinterpret_cast<unsigned long long *>(lsm); // [wy]
     unsigned long long *Om = Fm + wy;                                       // [wy]
     const int nw = link_occ_words(Nm), capm = 12 * Nm - 12;
@@ -182,14 +159,9 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
         }
     }
 
-    // ---- 1. owner masks (all warps) and look-ahead prefetches
+    // ---- 1. owner masks (all warps) and the look-ahead prefetch
     if (tid == 0) {
         s_over = 0u;
-        if (p + ahead < D.np && tmA) {
-            const GeomRec Ga = D.geo_cur[p + ahead];
-            for (int t = 0; t < kTilePlanes; ++t)
-                tma_prefetch_3d(tmA, (Ga.X0 - 2) & ~(al - 1), Ga.Y0 - 2, tile_global_plane(t));
-        }
         const DiskDF d0 = geom_df(G);
         D.pos4[p] = make_float4(d0.xh, d0.yh, d0.xl, d0.yl);
         D.prc[p] = make_float2(G.r, G.C);
@@ -228,25 +200,11 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
     // L2 prefetch of the owner rows of the particle `ahead` places later
     if (warp == 1 && p + ahead < D.np) {
         const GeomRec Ga = D.geo_cur[p + ahead];
-        const int xa = (Ga.X0 - 2) & ~(al - 1), ya = Ga.Y0 - 2;
+        const int xa = Ga.X0 - 2, ya = Ga.Y0 - 2;
         for (int r = lane; r < 2 * wy; r += 32) {
             const int j = ya + (r >> 1), i = min(max(xa + (r & 1) * (wx - 1), 0), D.nx - 1);
             if (j >= 0 && j < D.ny)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(own + (long long)j * D.nx + i) : "memory");
-        }
-    }
-    // without a tensor map (batched form): the window rows of the 12 planes,
-    // one L2 prefetch per row end
-    if (!tmA && warp >= 2 && p + ahead < D.np) {
-        const GeomRec Ga = D.geo_cur[p + ahead];
-        const int xa = (Ga.X0 - 2) & ~(al - 1), ya = Ga.Y0 - 2;
-        for (int r = tid - 64; r < 2 * kTilePlanes * wy; r += kLinkThreads - 64) {
-            const int row = r >> 1, t = row / wy, j = ya + row % wy;
-            const int i = min(max(xa + (r & 1) * (wx - 1), 0), D.pitch - 1);
-            if (j >= 0 && j < D.ny)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (long long)tile_global_plane(t) * D.ps +
-                                                            (long long)j * D.pitch + i)
-                             : "memory");
         }
     }
     for (int w = tid; w < nw; w += kLinkThreads) occ[w] = 0u;
@@ -309,8 +267,8 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
     const float Ux = G.ux, Uy = G.uy, Om_ = G.om, wT = G.wT;
     // populations of fluid nodes: no CTA writes them during this kernel
     const T *Ar = A;
-    auto tv = [&](int t, int i, int j) -> float {
-        return E::ld(__ldg(Ar + (long long)tile_global_plane(t) * D.ps + (long long)j * D.pitch + i));
+    auto tv = [&](int plane, int i, int j) -> float {
+        return E::ld(__ldg(Ar + (long long)plane * D.ps + (long long)j * D.pitch + i));
     };
     auto fluid = [&](int i, int j) -> bool { return (Fm[j - YA] >> (i - XA)) & 1ull; };
     for (int li = tid; li < nvalid; li += kLinkThreads) {
@@ -332,8 +290,8 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
         const bool have2 = fluid(i2, j2);
         const int ii1 = have1 ? i1 : fi, jj1 = have1 ? j1 : fj;
         const int ii2 = have2 ? i2 : fi, jj2 = have2 ? j2 : fj;
-        const float fk0 = tv(k - 1, fi, fj), fk1 = tv(k - 1, ii1, jj1), fk2 = tv(k - 1, ii2, jj2);
-        const float fb0 = tv(kb - 1, fi, fj), fb1 = tv(kb - 1, ii1, jj1);
+        const float fk0 = tv(k, fi, fj), fk1 = tv(k, ii1, jj1), fk2 = tv(k, ii2, jj2);
+        const float fb0 = tv(kb, fi, fj), fb1 = tv(kb, ii1, jj1);
         const float rx = dxf + q * kx, ry = dyf + q * ky;
         const float uwx = Ux - Om_ * ry, uwy = Uy + Om_ * rx;
         const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy); // 2 w rho0 e_kbar.u_w / c_s^2
@@ -342,8 +300,8 @@ __device__ __forceinline__ void links_body(const CUtensorMap *tmA, const Dev &D,
         const long long ns = (long long)(fj + ky) * D.pitch + (fi + kx);
         A[kb * D.ps + ns] = E::st(fnew);
         if (k <= 4) {
-            const float gnew = thermal32(q, tv(8 + k - 1, fi, fj), tv(8 + k - 1, ii1, jj1),
-                                         tv(8 + kb - 1, fi, fj), have1, wT);
+            const float gnew = thermal32(q, tv(kQ9 + k, fi, fj), tv(kQ9 + k, ii1, jj1),
+                                         tv(kQ9 + kb, fi, fj), have1, wT);
             A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
         }
         // momentum exchange: with f = w + f~ the bracket of Eq. force is
@@ -881,12 +839,17 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---- single-instance kernels
+// 16 CTAs per SM (the 2,048-thread limit; 32 registers): the kernel is
+// latency-bound, and 16 particles in flight per SM instead of the 9 that 56
+// registers allow beat the few spilled registers (80 against 91 us per step
+// on the 4000^2 / 4800-disk benchmark).
+constexpr int kLinkCtasPerSm = 16;
 template <typename T>
-__global__ void __launch_bounds__(kLinkThreads)
-    k_links(const __grid_constant__ CUtensorMap tmA, const Dev D, T *A, const int *__restrict__ own,
+__global__ void __launch_bounds__(kLinkThreads, kLinkCtasPerSm)
+    k_links(const Dev D, T *A, const int *__restrict__ own,
             int *__restrict__ own_nxt, int parity, int ahead)
 {
-    links_body<T>(&tmA, D, A, own, own_nxt, parity, ahead, (int)blockIdx.x);
+    links_body<T>(D, A, own, own_nxt, parity, ahead, (int)blockIdx.x);
 }
 __global__ void __launch_bounds__(kPartThreads, 4) k_particles(const Dev D, int parity, int *own_nxt)
 {
@@ -907,7 +870,7 @@ __global__ void __launch_bounds__(kBoxThreads)
 // offsets `start`).  The link kernel's look-ahead prefetch stays within the
 // instance and uses per-row L2 prefetches instead of a tensor map.
 template <typename T>
-__global__ void __launch_bounds__(kLinkThreads)
+__global__ void __launch_bounds__(kLinkThreads, kLinkCtasPerSm)
     k_links_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity, int ahead)
 {
     __shared__ Dev sD;
@@ -915,7 +878,7 @@ __global__ void __launch_bounds__(kLinkThreads)
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
     const int par = parity ^ a.poff;
-    links_body<T>(nullptr, sD, static_cast<T *>(a.A[par]), a.own[par], a.own[par ^ 1], par, ahead,
+    links_body<T>(sD, static_cast<T *>(a.A[par]), a.own[par], a.own[par ^ 1], par, ahead,
                   (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kPartThreads, 4)
@@ -1011,64 +974,27 @@ cudaError_t prepare_links(Dev &D)
 }
 
 cudaError_t launch_links(const Dev &D, void *A, const int *own_cur, int *own_nxt, int parity,
-                         const CUtensorMap &tmA, cudaStream_t s)
+                         cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
     const size_t smem = link_smem_bytes(D.zone_max, D.storage);
     const int grid = D.np;
     switch (D.storage) {
     case LBM_STORE_FP32:
-        k_links<float><<<grid, kLinkThreads, smem, s>>>(tmA, D, static_cast<float *>(A), own_cur, own_nxt, parity,
+        k_links<float><<<grid, kLinkThreads, smem, s>>>(D, static_cast<float *>(A), own_cur, own_nxt, parity,
                                                         D.link_ahead);
         break;
     case LBM_STORE_BF16:
-        k_links<__nv_bfloat16><<<grid, kLinkThreads, smem, s>>>(tmA, D, static_cast<__nv_bfloat16 *>(A), own_cur,
+        k_links<__nv_bfloat16><<<grid, kLinkThreads, smem, s>>>(D, static_cast<__nv_bfloat16 *>(A), own_cur,
                                                                 own_nxt, parity, D.link_ahead);
         break;
     case LBM_STORE_FP16:
-        k_links<__half><<<grid, kLinkThreads, smem, s>>>(tmA, D, static_cast<__half *>(A), own_cur, own_nxt, parity,
+        k_links<__half><<<grid, kLinkThreads, smem, s>>>(D, static_cast<__half *>(A), own_cur, own_nxt, parity,
                                                          D.link_ahead);
         break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
-}
-
-// 3-D tensor map over one distribution buffer: x (pitch columns), y (ny
-// rows), plane (kPop planes), in the storage element type, box wx x wy x 1
-// of the link tile.  Reads outside the tensor return zeros.
-cudaError_t make_plane_map(const Dev &D, const void *A, CUtensorMap *m)
-{
-    static std::mutex mu;
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (!encode) {
-            void *fn = nullptr;
-            cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                             cudaEnableDefault, &q);
-            if (e != cudaSuccess) return e;
-            if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-        }
-    }
-    const int es = storage_bytes(D.storage);
-    const int N = D.zone_max > 0 ? D.zone_max : 4;
-    const cuuint64_t dims[3] = {(cuuint64_t)D.pitch, (cuuint64_t)D.ny, (cuuint64_t)kPop};
-    const cuuint64_t strides[2] = {(cuuint64_t)D.pitch * es, (cuuint64_t)D.ps * es};
-    const cuuint32_t box[3] = {(cuuint32_t)link_tile_wx(N, es), (cuuint32_t)link_tile_wy(N), 1u};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    if (box[0] > 256 || box[1] > 256 || (box[0] * es) % 16 != 0 || strides[0] % 16 != 0 || strides[1] % 16 != 0 ||
-        (reinterpret_cast<uintptr_t>(A) & 15) != 0)
-        return cudaErrorInvalidValue;
-    const CUtensorMapDataType dt = D.storage == LBM_STORE_BF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                   : D.storage == LBM_STORE_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const CUresult r = encode(m, dt, 3, const_cast<void *>(A), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // ---- batched launches (one grid over all instances)

@@ -231,7 +231,7 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
     if (h->np > 0) {
         if ((rc = timed(h, kKLinks, st, [&] {
                  return D.direct ? launch_links_direct(D, Ain, oc, on, par, st)
-                                 : launch_links(D, Ain, oc, on, par, h->tmA[par], st);
+                                 : launch_links(D, Ain, oc, on, par, st);
              })))
             return rc;
     }
@@ -471,8 +471,6 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
         cudaEventCreateWithFlags(&h->join0, cudaEventDisableTiming) != cudaSuccess)
         return fail(LBM_ECUDA);
     if (prepare_links(h->D) != cudaSuccess) return fail(LBM_ECUDA);
-    for (int b = 0; b < 2 && n > 0; ++b)
-        if (make_plane_map(h->D, h->A[b], &h->tmA[b]) != cudaSuccess) return fail(LBM_ECUDA);
     if (n > 0) {
         std::vector<int> base(n + 1, 0);
         for (int a = 0; a < n; ++a) base[a + 1] = base[a] + slot_capacity(p[a].r);

@@ -37,7 +37,6 @@ struct lbm_handle {
     int *own[2];
     int parity = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    CUtensorMap tmA[2]; // link-tile tensor maps over A[0] and A[1]
     bool timing = false;
     struct Ev {
         cudaEvent_t a, b;

@@ -3,7 +3,6 @@
 // helpers and the kernel launchers.  Not part of the public ABI (lbm.h).
 #pragma once
 
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -733,10 +732,7 @@ cudaError_t launch_init_collide(const Dev &D, const void *Ain, void *Aout, float
 cudaError_t launch_fields(const Dev &D, const void *A, int row0, int rows, float *rho, float *ux,
                           float *uy, float *T, cudaStream_t s);
 cudaError_t launch_links(const Dev &D, void *A, const int *own_cur, int *own_nxt, int parity,
-                         const CUtensorMap &tmA, cudaStream_t s);
-// 3-D tensor map (x, y, plane) over one distribution buffer, for the link
-// kernel's TMA tile loads.
-cudaError_t make_plane_map(const Dev &D, const void *A, CUtensorMap *m);
+                         cudaStream_t s);
 // Shared memory of the link kernel for zones of side N; prepare_links sets the
 // kernel's shared-memory limit and D.link_ahead (call outside stream capture).
 size_t link_smem_bytes(int N, int storage);
