@@ -82,6 +82,12 @@ extern "C" {
  * bit-reproducible), and lbm_get_slots does not see these links.  Not
  * accepted by lbm_batch_create or lbm_server_submit. */
 #define LBM_FLAG_DIRECT_LINKS 8u
+/* Screen particle pairs by testing all pairs instead of the neighbouring
+ * cells of the screening grid.  The pair forces are summed in exact fixed
+ * point, so the result is bit-identical either way (the grid itself falls
+ * back to all pairs for a step after one of its cells overflowed); for
+ * tests. */
+#define LBM_FLAG_ALL_PAIRS 16u
 
 typedef struct {
     int32_t nx, ny;    /* nodes per axis, >= 4 each */

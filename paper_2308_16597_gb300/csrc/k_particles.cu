@@ -38,17 +38,6 @@ __device__ __forceinline__ T warp_sum(T v)
 
 } // namespace
 
-// Double-float warp sum (lane 0 receives the result).
-__device__ __forceinline__ void warp_df_sum(float &h, float &l)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_down_sync(0xffffffffu, h, o);
-        const float l2 = __shfl_down_sync(0xffffffffu, l, o);
-        df_add(h, l, h2, l2);
-    }
-}
-
 // The link kernel's window for zones of side N: the zone plus the two-node
 // margin of the bounce-back stencil, wy = N + 4 rows of wx = N + 4 columns
 // from (X0 - 2, Y0 - 2); wx is at most 64 (the fluid and owner masks of a row
@@ -85,6 +74,18 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
     const int line = odd ? (axis ? b : a - b + N - 2) : (axis ? a : a + b - 1);
     const int slot = axis ? (k - 1) * N + line : 4 * N + (k - 5) * M + line;
     return (axis || (line >= 0 && line < M)) ? slot : -1;
+}
+
+// Counts (and overflow flag) of the screening grid of the next step, which
+// the particle update of this step fills: block p of the np blocks of a
+// per-particle kernel clears its share.  The grid was last read by the
+// previous step's update.
+__device__ __forceinline__ void clear_cells_slice(const Dev &D, int parity, int p, int tid, int nthreads)
+{
+    int *grid = D.cells[parity ^ 1];
+    const int nc = D.cell_gx * D.cell_gy + 1, per = (nc + D.np - 1) / D.np;
+    const int c1 = min(nc, (p + 1) * per);
+    for (int c = p * per + tid; c < c1; c += nthreads) grid[c] = 0;
 }
 
 // One CTA per particle.  Phases:
@@ -145,8 +146,11 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
     int *lcode = reinterpret_cast<int *>(ltq + capm);
     int *ltz = lcode + capm;
 
-    // ---- 0. the owner map the raster fills next (positions n + 1) still
-    // holds positions n - 1: clear this particle's zone of that time
+    // ---- 0. the screening grid the particle update fills next: this CTA's
+    // slice of its counts; the owner map the raster fills next (positions
+    // n + 1) still holds positions n - 1: clear this particle's zone of that
+    // time
+    clear_cells_slice(D, parity, p, tid, kLinkThreads);
     {
         const GeomRec Gp = D.geo_prev[p];
         for (int r = warp; r < Gp.N; r += kLinkThreads / 32) {
@@ -347,17 +351,31 @@ __device__ __forceinline__ double repulsion(double gap, double s, double eps, do
 // Total force = hydrodynamic (assembled from the link sums) + buoyant weight
 // -(rho_p - rho_f) pi r^2 g y-hat + repulsion (walls, and every other disk
 // with C_ab the mean of the two force scales C = pi r^2 (rho_p - rho_f) g).
-// Each block takes 8 particles: warp w screens particle w against all disks
-// in shared-memory tiles of 1600 (FP32 centres with a one-lattice-unit
-// margin; a tile is loaded with all its loads in flight at once) and
-// evaluates the pairs in reach from double-float centre differences; lane l
-// of warp 0 then sums, integrates and stores particle l in FP64.  Small
+// Each block takes 8 particles: warp w screens particle w against the
+// particles listed in the 3 x 3 cells of the screening grid around its cell
+// (filled with the step's starting positions by the previous update; every
+// pair in reach is among them), or, when a cell of that grid overflowed,
+// against all particles in shared-memory tiles of 1600, and evaluates the
+// pairs in reach from double-float centre differences, summed in 64-bit
+// fixed point so that the result is the same whichever way the pairs were
+// found and in whatever order; lane l of warp 0 then sums, integrates and
+// stores particle l in FP64 and enters it in the next step's grid.  Small
 // blocks let four of them share an SM, so that the latency of one block's
-// tile loads and FP64 tail overlaps the others' work.  Integration:
+// loads and FP64 tail overlaps the others' work.  Integration:
 // U' = U + F/M, X' = X + (U + U')/2, Omega' = Omega + T/I,
 // theta' = theta + (Omega + Omega')/2 with M = rho_p pi r^2 and I = M r^2 / 2.
 constexpr int kPartTile = 1600;
 constexpr int kPartPerBlock = kPartThreads / 32;
+
+// Entry of particle b at (xh, yh) in a screening grid (cleared beforehand);
+// a full cell flags the grid, whose next screening then scans all pairs.
+__device__ __forceinline__ void cell_insert(const Dev &D, int *grid, int b, float xh, float yh)
+{
+    const int ncell = D.cell_gx * D.cell_gy, c = cell_of(D, xh, yh);
+    const int k = atomicAdd(grid + c, 1);
+    if (k < kCellCap) grid[ncell + 1 + c * kCellCap + k] = b;
+    else grid[ncell] = 1;
+}
 
 // Support distance of particle p along the unit vector (nx, ny): its radius
 // for a disk.
@@ -371,8 +389,7 @@ __device__ __forceinline__ double support_of(const Dev &D, int p, double nx, dou
 // Pair repulsion on particle a from particle b when either is an ellipse, in
 // FP64: the gap along the line of centres is the centre distance minus both
 // support distances along it.
-__device__ __noinline__ void pair_force_ellipse(const Dev &D, int a, int b, float &fh_x, float &fl_x,
-                                                float &fh_y, float &fl_y)
+__device__ __noinline__ void pair_force_ellipse(const Dev &D, int a, int b, long long &sx, long long &sy)
 {
     const double dx = D.cur.x[a] - D.cur.x[b], dy = D.cur.y[a] - D.cur.y[b];
     const double dist = sqrt(dx * dx + dy * dy);
@@ -383,16 +400,13 @@ __device__ __noinline__ void pair_force_ellipse(const Dev &D, int a, int b, floa
         return kPi * r * (is_ellipse(r, pb) ? pb : r) * (D.cur.rho[p] - D.rho_f) * D.g;
     };
     const double mag = repulsion(gap, D.s_rep, D.eps_w, 0.5 * (scale(a) + scale(b)));
-    const double fx = mag * dx / dist, fy = mag * dy / dist;
-    const float hx = (float)fx, hy = (float)fy;
-    df_add(fh_x, fl_x, hx, (float)(fx - (double)hx));
-    df_add(fh_y, fl_y, hy, (float)(fy - (double)hy));
+    sx += fix_of(mag * dx / dist);
+    sy += fix_of(mag * dy / dist);
 }
 
 // Pair repulsion on disk a from disk b (FP32 from double-float centres).
 __device__ __noinline__ void pair_force(float4 pa, float2 ca, float4 pb, float2 cb, float s_rep,
-                                        float inv_eps, float &fh_x, float &fl_x, float &fh_y,
-                                        float &fl_y)
+                                        float inv_eps, long long &sx, long long &sy)
 {
     float hx, ex_, hy, ey_;
     two_sum(pa.x, -pb.x, hx, ex_);
@@ -404,8 +418,20 @@ __device__ __noinline__ void pair_force(float4 pa, float2 ca, float4 pb, float2 
     if (gap > s_rep) return;
     const float t = (gap - s_rep) / s_rep;
     const float mag = 0.5f * (ca.y + cb.y) * inv_eps * t * t;
-    df_add(fh_x, fl_x, mag * dx / dist, 0.f);
-    df_add(fh_y, fl_y, mag * dy / dist, 0.f);
+    sx += fix_of(mag * dx / dist);
+    sy += fix_of(mag * dy / dist);
+}
+
+// Screening of particle a (position pa, (r, C) ca) against candidate b:
+// circumscribed circles within reach (r < 0 marks an ellipse), then the
+// pair force.
+__device__ __forceinline__ void screen_pair(const Dev &D, int a, float4 pa, float2 ca, int b, float4 pb, float2 cb,
+                                            float s_rep, float inv_eps, long long &sx, long long &sy)
+{
+    const float dxf = pa.x - pb.x, dyf = pa.y - pb.y, lim = fabsf(ca.x) + fabsf(cb.x) + s_rep + 1.f;
+    if (dxf * dxf + dyf * dyf > lim * lim || b == a) return;
+    if (ca.x < 0.f || cb.x < 0.f) pair_force_ellipse(D, a, b, sx, sy);
+    else pair_force(pa, ca, pb, cb, s_rep, inv_eps, sx, sy);
 }
 
 // Zone of a disk at (x, y) with radius r: N x N nodes from
@@ -506,9 +532,10 @@ __device__ __noinline__ void wall_supports(double th, double r, double b, double
 }
 
 // FP64 tail of the particle update for particle b: total force, Newton-Euler
-// step, domain checks, new state and geometry record.  (fxh + fxl, fyh + fyl:
-// the pair repulsion summed in double-float.)
-__device__ __forceinline__ void particle_tail(const Dev &D, int b, float fxh, float fxl, float fyh, float fyl)
+// step, domain checks, new state and geometry record, and the entry of the
+// new position in the screening grid of the next step.  (pfx, pfy: the pair
+// repulsion.)
+__device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, double pfx, double pfy)
 {
     double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
     double th = D.cur.th[b], om = D.cur.om[b];
@@ -545,8 +572,8 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, float fxh, fl
         Fy += repulsion((y + 0.5) - hy, D.s_rep, D.eps_w, Cb);
         Fy -= repulsion(((double)D.ny - 0.5 - y) - hy, D.s_rep, D.eps_w, Cb);
     }
-    Fx += (double)fxh + (double)fxl;
-    Fy += (double)fyh + (double)fyl;
+    Fx += pfx;
+    Fy += pfy;
     if (!D.fixed) {
         const double M = rho * kPi * r * rb, I = ell ? 0.25 * M * (r * r + pb * pb) : 0.5 * M * r * r;
         const double ux1 = ux + Fx / M, uy1 = uy + Fy / M, om1 = om + Tz / I;
@@ -571,14 +598,16 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, float fxh, fl
     const double T = D.cur.T[b];
     D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
     D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T; D.nxt.b[b] = pb;
-    D.geo_nxt[b] = make_geom(x, y, r, pb, th, ux, uy, om, T, rho, D.rho_f, D.g);
+    const GeomRec Gn = make_geom(x, y, r, pb, th, ux, uy, om, T, rho, D.rho_f, D.g);
+    D.geo_nxt[b] = Gn;
+    cell_insert(D, D.cells[parity ^ 1], b, Gn.xh, Gn.yh);
 }
 
 __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *own_nxt, const int blk)
 {
     __shared__ float4 sp[kPartTile];
     __shared__ float2 sc[kPartTile];
-    __shared__ float sred[4][kPartPerBlock];
+    __shared__ long long sred[2][kPartPerBlock];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int a = blk * kPartPerBlock + warp;
     if (blk == 0 && threadIdx.x < kNumCounters) D.status->cnt[parity ^ 1][threadIdx.x] = 0ull;
@@ -591,37 +620,67 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
         ca = D.prc[a];
     }
     const float s_rep = (float)D.s_rep, inv_eps = (float)(1.0 / D.eps_w);
-    const float reach = s_rep + 1.f;
-    float fhx = 0.f, flx = 0.f, fhy = 0.f, fly = 0.f;
-    for (int t0 = 0; t0 < D.np; t0 += kPartTile) {
-        const int nb = min(kPartTile, D.np - t0);
-        __syncthreads();
-#pragma unroll 8
-        for (int k = threadIdx.x; k < nb; k += kPartThreads) {
-            sp[k] = D.pos4[t0 + k];
-            sc[k] = D.prc[t0 + k];
+    long long sx = 0, sy = 0; // pair repulsion, fixed point
+    const int *grid = D.cells[parity];
+    const int gx = D.cell_gx, gy = D.cell_gy, ncell = gx * gy;
+    if (!grid[ncell] && !D.all_pairs) {
+        // candidates from the 3 x 3 cells around a's cell: lane l < 9 holds
+        // cell l's count; candidate t goes to lane t mod 32
+        int cnt = 0, cell = 0;
+        if (me && lane < 9) {
+            const int c0 = cell_of(D, pa.x, pa.y);
+            const int cx = c0 % gx + lane % 3 - 1, cy = c0 / gx + lane / 3 - 1;
+            if (cx >= 0 && cx < gx && cy >= 0 && cy < gy) {
+                cell = cy * gx + cx;
+                cnt = min(__ldg(grid + cell), kCellCap);
+            }
         }
-        __syncthreads();
-        if (!me) continue;
-        for (int u = lane; u < nb; u += 32) {
-            const float4 o = sp[u];
-            // (r < 0 marks an ellipse: screened by its circumscribed circle)
-            const float dxf = pa.x - o.x, dyf = pa.y - o.y, lim = fabsf(ca.x) + fabsf(sc[u].x) + reach;
-            if (dxf * dxf + dyf * dyf > lim * lim || t0 + u == a) continue;
-            if (ca.x < 0.f || sc[u].x < 0.f) pair_force_ellipse(D, a, t0 + u, fhx, flx, fhy, fly);
-            else pair_force(pa, ca, o, sc[u], s_rep, inv_eps, fhx, flx, fhy, fly);
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, inc, 8), excl = inc - cnt;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            int b = -1;
+#pragma unroll
+            for (int l = 0; l < 9; ++l) {
+                const int e = __shfl_sync(0xffffffffu, excl, l), n = __shfl_sync(0xffffffffu, cnt, l);
+                const int c = __shfl_sync(0xffffffffu, cell, l);
+                if (t >= e && t < e + n) b = __ldg(grid + ncell + 1 + c * kCellCap + (t - e));
+            }
+            if (b >= 0) screen_pair(D, a, pa, ca, b, D.pos4[b], D.prc[b], s_rep, inv_eps, sx, sy);
+        }
+    } else {
+        // a cell overflowed: every pair, in shared-memory tiles
+        for (int t0 = 0; t0 < D.np; t0 += kPartTile) {
+            const int nb = min(kPartTile, D.np - t0);
+            __syncthreads();
+#pragma unroll 8
+            for (int k = threadIdx.x; k < nb; k += kPartThreads) {
+                sp[k] = D.pos4[t0 + k];
+                sc[k] = D.prc[t0 + k];
+            }
+            __syncthreads();
+            if (!me) continue;
+            for (int u = lane; u < nb; u += 32) screen_pair(D, a, pa, ca, t0 + u, sp[u], sc[u], s_rep, inv_eps, sx, sy);
         }
     }
-    warp_df_sum(fhx, flx);
-    warp_df_sum(fhy, fly);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
     if (lane == 0) {
-        sred[0][warp] = fhx; sred[1][warp] = flx;
-        sred[2][warp] = fhy; sred[3][warp] = fly;
+        sred[0][warp] = sx;
+        sred[1][warp] = sy;
     }
     __syncthreads();
     const int b = blk * kPartPerBlock + lane;
-    if (warp == 0 && lane < kPartPerBlock && b < D.np) particle_tail(D, b, sred[0][lane], sred[1][lane],
-                                                                      sred[2][lane], sred[3][lane]);
+    if (warp == 0 && lane < kPartPerBlock && b < D.np)
+        particle_tail(D, b, parity, fix_value(sred[0][lane]), fix_value(sred[1][lane]));
     // then the owner map at the new positions: warp w rasters the block's
     // particle w (its own new state only, so no other block is waited for)
     __syncthreads();
@@ -735,9 +794,10 @@ __global__ void __launch_bounds__(128) k_near_mask(const Dev D, int span)
 // ---- direct addressing (comparison with the index array)
 // Per particle: clear its zone one step back in the next owner map, publish
 // its centre for the pair screening, zero its sums.
-__global__ void __launch_bounds__(kBoxThreads) k_direct_prep(const Dev D, int *__restrict__ own_nxt)
+__global__ void __launch_bounds__(kBoxThreads) k_direct_prep(const Dev D, int *__restrict__ own_nxt, int parity)
 {
     const int p = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    clear_cells_slice(D, parity, p, threadIdx.x, kBoxThreads);
     const GeomRec Gp = D.geo_prev[p];
     for (int r = warp; r < Gp.N; r += kBoxThreads / 32) {
         const int j = Gp.Y0 + r;
@@ -926,6 +986,16 @@ __global__ void k_geom_init(const Dev D)
                               D.cur.rho[a], D.rho_f, D.g);
 }
 
+// The screening grid of the current positions (its counts cleared
+// beforehand), for the first update after init or restore.
+__global__ void k_cells_init(const Dev D, int *grid)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= D.np) return;
+    const GeomRec G = D.geo_cur[a];
+    cell_insert(D, grid, a, G.xh, G.yh);
+}
+
 __global__ void k_pack_particles(const Dev D, lbm_particle *out)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1080,7 +1150,7 @@ cudaError_t launch_links_direct(const Dev &D, void *A, const int *own_cur, int *
                                 cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
-    k_direct_prep<<<D.np, kBoxThreads, 0, s>>>(D, own_nxt);
+    k_direct_prep<<<D.np, kBoxThreads, 0, s>>>(D, own_nxt, parity);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid((D.nx + 127) / 128, D.ny);
@@ -1114,6 +1184,18 @@ cudaError_t launch_geom_init(const Dev &D, cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
     k_geom_init<<<(D.np + 127) / 128, 128, 0, s>>>(D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cells_init(const Dev &D, int parity, cudaStream_t s)
+{
+    const size_t counts = ((size_t)D.cell_gx * D.cell_gy + 1) * sizeof(int);
+    for (int b = 0; b < 2; ++b) {
+        const cudaError_t e = cudaMemsetAsync(D.cells[b], 0, counts, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (D.np == 0) return cudaSuccess;
+    k_cells_init<<<(D.np + 127) / 128, 128, 0, s>>>(D, D.cells[parity]);
     return cudaGetLastError();
 }
 

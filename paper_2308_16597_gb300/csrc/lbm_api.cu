@@ -83,7 +83,7 @@ int validate(const lbm_domain *d, const lbm_particle *p, int32_t n, const lbm_pa
     return LBM_OK;
 }
 
-void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, Layout &L)
+void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, double s_rep, Layout &L)
 {
     L.pitch = (int)round_up((size_t)d->nx, 32);
     L.ps = (long long)round_up((size_t)L.pitch * d->ny, 64);
@@ -122,6 +122,17 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
     L.newborn = take((size_t)L.newborn_cap * sizeof(int));
     L.near = take(((size_t)d->ny * near_tiles_per_row(storage, L.pitch) + 31) / 32 * sizeof(unsigned));
     L.dsum = take((size_t)n * sizeof(DirectSums));
+    // cell grid of the pair screening: side 2 r_max + s + 2 (every pair in
+    // reach lies in neighbouring cells), grown to hold at most 4 Mi cells
+    double rmax = 1.0;
+    for (int a = 0; a < n; ++a) rmax = std::max(rmax, p[a].r);
+    double side = 2.0 * rmax + std::max(s_rep, 0.0) + 2.0;
+    side = std::max(side, std::sqrt((double)d->nx * d->ny / (double)(1 << 22)));
+    L.cell_side = side;
+    L.cell_gx = n > 0 ? std::max(1, (int)std::ceil(d->nx / side)) : 1;
+    L.cell_gy = n > 0 ? std::max(1, (int)std::ceil(d->ny / side)) : 1;
+    const size_t ncell = (size_t)L.cell_gx * L.cell_gy;
+    for (int b = 0; b < 2; ++b) L.cells[b] = take((ncell + 1 + ncell * kCellCap) * sizeof(int));
     L.total = off;
 }
 
@@ -343,6 +354,7 @@ void fill_dev(lbm_handle *h)
     D.near = reinterpret_cast<unsigned *>(ws + L.near);
     D.dsum = reinterpret_cast<DirectSums *>(ws + L.dsum);
     D.direct = (P.flags & LBM_FLAG_DIRECT_LINKS) ? 1 : 0;
+    D.all_pairs = (P.flags & LBM_FLAG_ALL_PAIRS) ? 1 : 0;
     D.near_tpr = near_tiles_per_row(P.storage, L.pitch);
     D.slot_node = reinterpret_cast<int *>(ws + L.slot_node);
     D.slot_q = reinterpret_cast<float *>(ws + L.slot_q);
@@ -359,6 +371,10 @@ void fill_dev(lbm_handle *h)
     D.geo_cur = reinterpret_cast<GeomRec *>(ws + L.geo[1]);
     D.geo_nxt = reinterpret_cast<GeomRec *>(ws + L.geo[2]);
     D.status = reinterpret_cast<Status *>(ws + L.status);
+    D.cell_gx = L.cell_gx;
+    D.cell_gy = L.cell_gy;
+    D.cell_inv = (float)(1.0 / L.cell_side);
+    for (int b = 0; b < 2; ++b) D.cells[b] = reinterpret_cast<int *>(ws + L.cells[b]);
     for (int b = 0; b < 2; ++b) {
         h->A[b] = ws + L.A[b];
         h->own[b] = reinterpret_cast<int *>(ws + L.own[b]);
@@ -394,6 +410,7 @@ int rebuild_maps(lbm_handle *h)
     CK(h, cudaMemsetAsync(h->D.flags, 0, (size_t)h->L.pitch * h->d.ny, h->stream));
     int *oc = h->own[h->parity];
     CK(h, launch_geom_init(h->D, h->stream));
+    CK(h, launch_cells_init(h->D, h->parity, h->stream));
     CK(h, launch_raster(h->D, oc, h->D.geo_cur, h->D.cur, h->stream));
     CK(h, launch_flags(h->D, oc, oc, 0, h->stream));
     // the owner map one step back, which the first clear expects in the other buffer
@@ -430,7 +447,7 @@ int lbm_query_footprint(const lbm_domain *d, const lbm_particle *p, int32_t n, c
     int rc = validate(d, p, n, prm);
     if (rc) return rc;
     Layout L;
-    layout(d, p, n, prm->storage, L);
+    layout(d, p, n, prm->storage, prm->s_rep, L);
     *bytes = L.total;
     return LBM_OK;
 }
@@ -448,7 +465,7 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
     h->d = *d;
     h->prm = *prm;
     h->np = n;
-    layout(d, p, n, prm->storage, h->L);
+    layout(d, p, n, prm->storage, prm->s_rep, h->L);
     if (ws_bytes < h->L.total) {
         delete h;
         return LBM_ENOSPC;
@@ -670,6 +687,7 @@ int lbm_set_state(lbm_handle *h, const void *buf, size_t bytes)
         prev.x = h->D.px;
         prev.y = h->D.py;
         CK(h, launch_geom_init(h->D, h->stream));
+        CK(h, launch_cells_init(h->D, h->parity, h->stream));
         CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, h->stream));
     }
     return sync_status(h);

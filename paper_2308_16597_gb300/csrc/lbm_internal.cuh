@@ -132,8 +132,29 @@ struct Dev {
     struct DirectSums *dsum; // [np]: the same sums accumulated by atomics (direct addressing)
     int direct;            // links found by the node-parallel scan instead of the index array
     struct GeomRec *geo_prev, *geo_cur, *geo_nxt; // [np] each: FP32/int geometry of the three positions
+    // pair screening: a grid of square cells of side 1 / cell_inv >= 2 r_max
+    // + s + 2, so that every pair in reach sits in the same or neighbouring
+    // cells; per parity [cell_gx * cell_gy + 1] counts (the last one flags an
+    // overflowing cell), then kCellCap particle ids per cell
+    int cell_gx, cell_gy;
+    float cell_inv;
+    int *cells[2];
+    int all_pairs; // screen all pairs instead (LBM_FLAG_ALL_PAIRS)
     Status *status;
 };
+constexpr int kCellCap = 16;
+__device__ __forceinline__ int cell_of(const Dev &D, float xh, float yh)
+{
+    const int cx = min(max((int)(xh * D.cell_inv), 0), D.cell_gx - 1);
+    const int cy = min(max((int)(yh * D.cell_inv), 0), D.cell_gy - 1);
+    return cy * D.cell_gx + cx;
+}
+// Pair forces are summed in 64-bit fixed point (units of 2^-40): integer
+// addition is exact and associative, so the sum does not depend on the order
+// in which a particle's neighbours are found.
+__device__ __forceinline__ long long fix_of(float v) { return __float2ll_rn(v * 0x1p40f); }
+__device__ __forceinline__ long long fix_of(double v) { return __double2ll_rn(v * 0x1p40); }
+__device__ __forceinline__ double fix_value(long long v) { return (double)v * 0x1p-40; }
 
 // ---------------------------------------------------------------------------
 // Exact FP64 geometry shared by raster, gather and refill.  Every operation is
@@ -750,6 +771,9 @@ cudaError_t launch_pack_particles(const Dev &D, lbm_particle *out, cudaStream_t 
 // Geometry records of the current state (into cur, nxt and prev) and of the
 // previous positions (into prev), for init and restore.
 cudaError_t launch_geom_init(const Dev &D, cudaStream_t s);
+// Screening grids: both cleared, the one of step parity `parity` filled with
+// the current positions (after launch_geom_init).
+cudaError_t launch_cells_init(const Dev &D, int parity, cudaStream_t s);
 
 // Batched step kernels over an InstArgs table (one grid over all instances;
 // `start` holds the n + 1 block offsets of the launch, `total` its blocks).
