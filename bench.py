@@ -133,19 +133,20 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu record (profiles/traffic.txt),
-    if it was taken on the current source of the kernel's file; else None."""
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu record (profiles/traffic.txt)
+    for this kernel and workload, if it was taken on the current source of the
+    kernel's file; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         f = line.split()
-        if not f or f[0].startswith("#") or f[0] != kernel or len(f) < 4:
+        if not f or f[0].startswith("#") or len(f) < 5 or f[0] != kernel or f[1] != workload:
             continue
-        src = os.path.join(ROOT, "paper_2308_16597_gb300", "csrc", f[1])
+        src = os.path.join(ROOT, "paper_2308_16597_gb300", "csrc", f[2])
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return int(f[3]) if digest == f[2] else None
+        return int(f[4]) if digest == f[3] else None
     return None
 
 
@@ -326,11 +327,12 @@ def run_ours(args, wl):
     B_LU = metrics.bytes_per_update(STORAGE_BYTES[args.storage])
     peaks = measured_peaks()
     achieved = B_LU * nodes / avg_s / 1e9
-    traffic = profiled_traffic("stream_collide" if args.storage == "fp32"
-                               else "stream_collide_" + args.storage)
+    traffic = profiled_traffic("stream_collide" if args.storage == "fp32" else "stream_collide_" + args.storage,
+                               wl.name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_stream_collide (far-tile + near-tile passes of one step)",
+                "kernel": "k_stream_collide" + (" (far-tile + near-tile passes of one step)"
+                                                if "stream_collide_near" in ktimes else ""),
                 "algorithmic_bytes_per_launch": B_LU * nodes,
                 "avg_launch_ms": avg_s * 1e3, "peak_source": peaks["source"] + " (hbm_gbs)",
                 "kernel_times_from": "a second pass of the same number of steps, launched "

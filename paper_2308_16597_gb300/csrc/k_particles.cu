@@ -442,20 +442,35 @@ struct Box {
 };
 __device__ __forceinline__ Box box_of(const GeomRec &G) { return Box{G.X0, G.Y0, G.N}; }
 
-// Raster of one ellipse by one warp (lane per zone row).  Along a row the
-// ellipse form is a convex quadratic in i, so the inside nodes form one run;
-// when the run is not empty the node nearest the vertex of the parabola lies
-// in it (checked with its two neighbours, against rounding of the vertex).
-// The run's ends are estimated from the quadratic's roots (FP32) and settled
-// with the predicate at the ends only: FP32 outside the rounding band, the
-// exact FP64 form inside it.
-__device__ __noinline__ void raster_ellipse(const Dev &D, int *own, const Box B, const GeomRec G, double x, double y,
-                                            double th, double r, double pb, int p)
+// Writes of a warp's raster: lane l holds the run [lo, hi] of zone row
+// b0 + l (empty when lo > hi); the warp then stores row after row, lanes on
+// consecutive nodes, so each row's atomicMax requests coalesce.
+__device__ __forceinline__ void write_runs(const Dev &D, int *own, const Box &B, int b0, int lo, int hi, int p)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, nr = min(32, B.N - b0);
+    for (int r = 0; r < nr; ++r) {
+        const int l = __shfl_sync(0xffffffffu, lo, r), h = __shfl_sync(0xffffffffu, hi, r);
+        int *row = own + (long long)(B.Y0 + b0 + r) * D.nx;
+        for (int i = l + lane; i <= h; i += 32) atomicMax(row + i, p);
+    }
+}
+
+// Run of row j of one ellipse.  Along a row the ellipse form is a convex
+// quadratic in i, so the inside nodes form one run; when the run is not
+// empty the node nearest the vertex of the parabola lies in it (checked with
+// its two neighbours, against rounding of the vertex).  The run's ends are
+// estimated from the quadratic's roots (FP32) and settled with the predicate
+// at the ends only: FP32 outside the rounding band, the exact FP64 form
+// inside it.
+__device__ __noinline__ void ellipse_run(const Dev &D, const Box B, const GeomRec G, double x, double y, double th,
+                                         double r, double pb, int j, int &lo_out, int &hi_out)
+{
+    lo_out = 1;
+    hi_out = 0;
+    if (j < 0 || j >= D.ny) return;
     const int xmin = B.X0, xmax = B.X0 + B.N - 1;
     const EllDF F = ell_df(G.xh, G.xl, G.yh, G.yl, G.w0, G.w1, r, pb);
-    auto inside = [&](int i, int j) -> bool {
+    auto inside = [&](int i) -> bool {
         const int side = ell_side_df(i, j, F);
         if (side) return side < 0;
         return in_ellipse(i, j, ell_frame(x, y, th, r, pb));
@@ -464,61 +479,66 @@ __device__ __noinline__ void raster_ellipse(const Dev &D, int *own, const Box B,
     const float A2 = c * c * F.b2 + s * s * F.a2; // dx^2 coefficient
     const float Bc = c * s * (F.b2 - F.a2);       // half the dx dy coefficient
     const float Cc = s * s * F.b2 + c * c * F.a2; // dy^2 coefficient
-    for (int b = lane; b < B.N; b += 32) {
-        const int j = B.Y0 + b;
-        if (j < 0 || j >= D.ny) continue;
-        float dyh, dyl;
-        df_offset(j, G.yh, G.yl, dyh, dyl);
-        const float dy = dyh + dyl;
-        const float B1 = Bc * dy, C0 = Cc * dy * dy - F.ab;
-        const float mid = (G.xh - B1 / A2) + G.xl;
-        const int im = (int)floorf(mid + 0.5f);
-        const int in = inside(im, j) ? im : inside(im - 1, j) ? im - 1 : inside(im + 1, j) ? im + 1 : INT_MIN;
-        if (in == INT_MIN) continue; // then no node of the row is inside
-        const float h = sqrtf(fmaxf(B1 * B1 - A2 * C0, 0.f)) / A2;
-        int lo = max(min(in, (int)ceilf(mid - h)), xmin), hi = min(max(in, (int)floorf(mid + h)), xmax);
-        while (lo > xmin && inside(lo - 1, j)) --lo;
-        while (!inside(lo, j)) ++lo;
-        while (hi < xmax && inside(hi + 1, j)) ++hi;
-        while (!inside(hi, j)) --hi;
-        lo = max(lo, 0);
-        hi = min(hi, D.nx - 1);
-        int *row = own + (long long)j * D.nx;
-        for (int i = lo; i <= hi; ++i) atomicMax(row + i, p);
-    }
+    float dyh, dyl;
+    df_offset(j, G.yh, G.yl, dyh, dyl);
+    const float dy = dyh + dyl;
+    const float B1 = Bc * dy, C0 = Cc * dy * dy - F.ab;
+    const float mid = (G.xh - B1 / A2) + G.xl;
+    const int im = (int)floorf(mid + 0.5f);
+    const int in = inside(im) ? im : inside(im - 1) ? im - 1 : inside(im + 1) ? im + 1 : INT_MIN;
+    if (in == INT_MIN) return; // then no node of the row is inside
+    const float h = sqrtf(fmaxf(B1 * B1 - A2 * C0, 0.f)) / A2;
+    int lo = max(min(in, (int)ceilf(mid - h)), xmin), hi = min(max(in, (int)floorf(mid + h)), xmax);
+    while (lo > xmin && inside(lo - 1)) --lo;
+    while (!inside(lo)) ++lo;
+    while (hi < xmax && inside(hi + 1)) ++hi;
+    while (!inside(hi)) --hi;
+    lo_out = max(lo, 0);
+    hi_out = min(hi, D.nx - 1);
 }
 
-// Raster of one particle by one warp (lane per zone row).
+// Run of row j of one disk: the node nearest the centre decides whether the
+// row meets the disk; the ends come from an FP32 estimate settled with the
+// exact predicate.
+__device__ __forceinline__ void disk_run(const Dev &D, const Box &B, const GeomRec &G, double x, double y, double r,
+                                         int j, int &lo_out, int &hi_out)
+{
+    lo_out = 1;
+    hi_out = 0;
+    if (j < 0 || j >= D.ny) return;
+    const DiskDF dk = geom_df(G);
+    const int ic = G.ic; // the node of each row nearest the centre
+    if (!in_disk_df(ic, j, dk, x, y, r)) return; // then no node of the row is inside
+    float dyh, dyl;
+    df_offset(j, dk.yh, dk.yl, dyh, dyl);
+    const float h = sqrtf(fmaxf(dk.r2h - dyh * dyh, 0.f));
+    const int xmin = B.X0, xmax = B.X0 + B.N - 1;
+    int lo = min(ic, (int)ceilf(dk.xh - h)), hi = max(ic, (int)floorf(dk.xh + h));
+    lo = max(lo, xmin);
+    hi = min(hi, xmax);
+    while (lo > xmin && in_disk_df(lo - 1, j, dk, x, y, r)) --lo;
+    while (!in_disk_df(lo, j, dk, x, y, r)) ++lo;
+    while (hi < xmax && in_disk_df(hi + 1, j, dk, x, y, r)) ++hi;
+    while (!in_disk_df(hi, j, dk, x, y, r)) --hi;
+    lo_out = max(lo, 0);
+    hi_out = min(hi, D.nx - 1);
+}
+
+// Raster of one particle by one warp: lane per zone row for the runs, then
+// coalesced writes.
 __device__ __forceinline__ void raster_one(const Dev &D, int *own, const GeomRec &G, double x, double y, double r,
                                            double th, double pb, int p)
 {
     const int lane = threadIdx.x & 31;
     const Box B = box_of(G);
-    if (G.r < 0.f) {
-        raster_ellipse(D, own, B, G, x, y, th, r, pb, p);
-        return;
-    }
-    const DiskDF dk = geom_df(G);
-    const int ic = G.ic; // the node of each row nearest the centre
-    for (int b = lane; b < B.N; b += 32) {
-        const int j = B.Y0 + b;
-        if (j < 0 || j >= D.ny) continue;
-        if (!in_disk_df(ic, j, dk, x, y, r)) continue; // then no node of the row is inside
-        float dyh, dyl;
-        df_offset(j, dk.yh, dk.yl, dyh, dyl);
-        const float h = sqrtf(fmaxf(dk.r2h - dyh * dyh, 0.f));
-        const int xmin = B.X0, xmax = B.X0 + B.N - 1;
-        int lo = min(ic, (int)ceilf(dk.xh - h)), hi = max(ic, (int)floorf(dk.xh + h));
-        lo = max(lo, xmin);
-        hi = min(hi, xmax);
-        while (lo > xmin && in_disk_df(lo - 1, j, dk, x, y, r)) --lo;
-        while (!in_disk_df(lo, j, dk, x, y, r)) ++lo;
-        while (hi < xmax && in_disk_df(hi + 1, j, dk, x, y, r)) ++hi;
-        while (!in_disk_df(hi, j, dk, x, y, r)) --hi;
-        lo = max(lo, 0);
-        hi = min(hi, D.nx - 1);
-        int *row = own + (long long)j * D.nx;
-        for (int i = lo; i <= hi; ++i) atomicMax(row + i, p);
+    for (int b0 = 0; b0 < B.N; b0 += 32) {
+        const int j = B.Y0 + b0 + lane;
+        int lo = 1, hi = 0;
+        if (b0 + lane < B.N) {
+            if (G.r < 0.f) ellipse_run(D, B, G, x, y, th, r, pb, j, lo, hi);
+            else disk_run(D, B, G, x, y, r, j, lo, hi);
+        }
+        write_runs(D, own, B, b0, lo, hi, p);
     }
 }
 
@@ -531,11 +551,17 @@ __device__ __noinline__ void wall_supports(double th, double r, double b, double
     hy = ell_support(E, 0.0, 1.0);
 }
 
+// New state of a particle as the raster needs it.
+struct RasterIn {
+    GeomRec G;
+    double x, y, r, th, b;
+};
+
 // FP64 tail of the particle update for particle b: total force, Newton-Euler
 // step, domain checks, new state and geometry record, and the entry of the
 // new position in the screening grid of the next step.  (pfx, pfy: the pair
-// repulsion.)
-__device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, double pfx, double pfy)
+// repulsion; out: the new state for the raster.)
+__device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, double pfx, double pfy, RasterIn &out)
 {
     double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
     double th = D.cur.th[b], om = D.cur.om[b];
@@ -600,6 +626,8 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, d
     D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T; D.nxt.b[b] = pb;
     const GeomRec Gn = make_geom(x, y, r, pb, th, ux, uy, om, T, rho, D.rho_f, D.g);
     D.geo_nxt[b] = Gn;
+    out.G = Gn;
+    out.x = x; out.y = y; out.r = r; out.th = th; out.b = pb;
     cell_insert(D, D.cells[parity ^ 1], b, Gn.xh, Gn.yh);
 }
 
@@ -608,6 +636,7 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
     __shared__ float4 sp[kPartTile];
     __shared__ float2 sc[kPartTile];
     __shared__ long long sred[2][kPartPerBlock];
+    __shared__ RasterIn sras[kPartPerBlock]; // the tail's results, handed to the raster warps
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int a = blk * kPartPerBlock + warp;
     if (blk == 0 && threadIdx.x < kNumCounters) D.status->cnt[parity ^ 1][threadIdx.x] = 0ull;
@@ -680,12 +709,14 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
     __syncthreads();
     const int b = blk * kPartPerBlock + lane;
     if (warp == 0 && lane < kPartPerBlock && b < D.np)
-        particle_tail(D, b, parity, fix_value(sred[0][lane]), fix_value(sred[1][lane]));
+        particle_tail(D, b, parity, fix_value(sred[0][lane]), fix_value(sred[1][lane]), sras[lane]);
     // then the owner map at the new positions: warp w rasters the block's
     // particle w (its own new state only, so no other block is waited for)
     __syncthreads();
-    if (a < D.np)
-        raster_one(D, own_nxt, D.geo_nxt[a], D.nxt.x[a], D.nxt.y[a], D.nxt.r[a], D.nxt.th[a], D.nxt.b[a], a);
+    if (a < D.np) {
+        const RasterIn &R = sras[warp];
+        raster_one(D, own_nxt, R.G, R.x, R.y, R.r, R.th, R.b, a);
+    }
 }
 
 
@@ -709,24 +740,28 @@ __device__ __forceinline__ void raster_body(const Dev &D, int *own, const GeomRe
 // Flags over the rectangle that holds the particle's zones one step back, now
 // and next (so every node whose flag may have changed since the last step):
 // solid at the new time, newborn (solid before, fluid now) or fluid, from
-// the two owner maps.  One warp per particle: rows eight at a time (all
-// loads issued first), lane l columns l and l + 32.  During a step the warp
-// also moves its particle's new state into the current slot and keeps the old
-// position for the next clear.
+// the two owner maps.  A team of TEAM warps per particle (one warp for zones
+// of up to 32 rows, the whole 4-warp block for larger ones): team warp w
+// takes rows w kU .. w kU + kU - 1 of every TEAM kU rows, eight at a time
+// (all loads issued first), lane l columns l and l + 32 of every 64.  During
+// a step team warp 0 also moves the particle's new state into the current
+// slot and keeps the old position for the next clear.
+template <int TEAM>
 __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__ own_cur,
                                            const int *__restrict__ own_nxt, int rotate, const int p)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, tw = (threadIdx.x >> 5) % TEAM;
     constexpr int kU = 8;
-    if (p >= D.np) return;
+    if (p >= D.np) return; // uniform across the team
     const bool list = rotate != 0; // a step (not the initial flags): list the newborn nodes
     const Box Ba = box_of(D.geo_prev[p]), Bb = box_of(D.geo_cur[p]), Bc = box_of(D.geo_nxt[p]);
     if (rotate) {
         // the new state moves into the current slot (and the current position
         // into the previous one) while the other threads work on the flags;
-        // every thread has read the three boxes before
-        __syncwarp();
-        switch (lane) {
+        // every thread of the team has read the three boxes before
+        if (TEAM == 1) __syncwarp();
+        else __syncthreads();
+        if (tw == 0) switch (lane) {
         case 0: D.px[p] = D.cur.x[p]; D.cur.x[p] = D.nxt.x[p]; break;
         case 1: D.py[p] = D.cur.y[p]; D.cur.y[p] = D.nxt.y[p]; break;
         case 2: D.cur.ux[p] = D.nxt.ux[p]; break;
@@ -741,36 +776,39 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
     const int Y0 = max(min(min(Ba.Y0, Bb.Y0), Bc.Y0), 0);
     const int X1 = min(max(max(Ba.X0 + Ba.N, Bb.X0 + Bb.N), Bc.X0 + Bc.N), D.nx); // exclusive
     const int Y1 = min(max(max(Ba.Y0 + Ba.N, Bb.Y0 + Bb.N), Bc.Y0 + Bc.N), D.ny);
-    for (int r0 = Y0; r0 < Y1; r0 += kU) {
-        int oc[kU][2], on[kU][2];
+    for (int c0 = X0; c0 < X1; c0 += 64)
+        for (int r0 = Y0 + tw * kU; r0 < Y1; r0 += TEAM * kU) {
+            int oc[kU][2], on[kU][2];
 #pragma unroll
-        for (int t = 0; t < kU; ++t)
+            for (int t = 0; t < kU; ++t)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = r0 + t, i = X0 + lane + 32 * h;
-                const bool v = j < Y1 && i < X1;
-                const long long n = (long long)j * D.nx + i;
-                oc[t][h] = v ? own_cur[n] : -3;
-                on[t][h] = v ? own_nxt[n] : -3;
-            }
-#pragma unroll
-        for (int t = 0; t < kU; ++t)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (oc[t][h] == -3) continue;
-                const int j = r0 + t, i = X0 + lane + 32 * h;
-                const uint8_t f = on[t][h] >= 0 ? kSolid : oc[t][h] >= 0 ? kNewborn : kFluid;
-                D.flags[(long long)j * D.pitch + i] = f;
-                // each newborn node once: by the particle that owned it; frame
-                // nodes are always on the general path
-                if (list && f == kNewborn && oc[t][h] == p && i > 0 && i < D.nx - 1 && j > 0 && j < D.ny - 1) {
-                    const unsigned at = atomicAdd(&D.status->nb, 1u);
-                    if (at < (unsigned)D.newborn_cap) D.newborn[at] = j * D.nx + i;
-                    else atomicOr(&D.status->err, kErrOverflow);
+                for (int h = 0; h < 2; ++h) {
+                    const int j = r0 + t, i = c0 + lane + 32 * h;
+                    const bool v = j < Y1 && i < X1;
+                    const long long n = (long long)j * D.nx + i;
+                    oc[t][h] = v ? own_cur[n] : -3;
+                    on[t][h] = v ? own_nxt[n] : -3;
                 }
-            }
-    }
+#pragma unroll
+            for (int t = 0; t < kU; ++t)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (oc[t][h] == -3) continue;
+                    const int j = r0 + t, i = c0 + lane + 32 * h;
+                    const uint8_t f = on[t][h] >= 0 ? kSolid : oc[t][h] >= 0 ? kNewborn : kFluid;
+                    D.flags[(long long)j * D.pitch + i] = f;
+                    // each newborn node once: by the particle that owned it;
+                    // frame nodes are always on the general path
+                    if (list && f == kNewborn && oc[t][h] == p && i > 0 && i < D.nx - 1 && j > 0 &&
+                        j < D.ny - 1) {
+                        const unsigned at = atomicAdd(&D.status->nb, 1u);
+                        if (at < (unsigned)D.newborn_cap) D.newborn[at] = j * D.nx + i;
+                        else atomicOr(&D.status->err, kErrOverflow);
+                    }
+                }
+        }
 }
+constexpr int kFlagTeamRows = 32; // zones up to this side: one warp per particle
 
 // Near-tile bitmap: every warp tile (one row, 32 V nodes) that meets a
 // particle's zone at the current position widened by kNearMargin nodes.  One
@@ -920,10 +958,12 @@ __global__ void __launch_bounds__(kBoxThreads)
 {
     raster_body(D, own, geo, pos, (int)blockIdx.x);
 }
-__global__ void __launch_bounds__(kBoxThreads)
+template <int TEAM>
+__global__ void __launch_bounds__(kBoxThreads, 9)
     k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate)
 {
-    flags_body(D, own_cur, own_nxt, rotate, (int)blockIdx.x * (kBoxThreads / 32) + (int)(threadIdx.x >> 5));
+    flags_body<TEAM>(D, own_cur, own_nxt, rotate,
+                     (int)blockIdx.x * (kBoxThreads / 32 / TEAM) + (int)(threadIdx.x >> 5) / TEAM);
 }
 
 // ---- batched kernels: one grid over all instances (InstArgs table, block
@@ -967,8 +1007,8 @@ __global__ void __launch_bounds__(kBoxThreads)
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
     const int par = parity ^ a.poff;
-    flags_body(sD, a.own[par], a.own[par ^ 1], 1,
-               ((int)blockIdx.x - __ldg(start + i)) * (kBoxThreads / 32) + (int)(threadIdx.x >> 5));
+    flags_body<1>(sD, a.own[par], a.own[par ^ 1], 1,
+                  ((int)blockIdx.x - __ldg(start + i)) * (kBoxThreads / 32) + (int)(threadIdx.x >> 5));
 }
 
 // Geometry records of the current state and of the previous positions.
@@ -1204,7 +1244,10 @@ cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, i
 {
     if (D.np == 0) return cudaSuccess;
     const int per = kBoxThreads / 32;
-    k_flags<<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate);
+    if (D.zone_max + 2 <= kFlagTeamRows)
+        k_flags<1><<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate);
+    else
+        k_flags<kBoxThreads / 32><<<D.np, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate);
     return cudaGetLastError();
 }
 

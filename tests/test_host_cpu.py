@@ -77,10 +77,12 @@ def test_weighted_percentile():
 
 def test_traffic_record_is_tied_to_the_kernel_source():
     import bench
-    v = bench.profiled_traffic("stream_collide")
+    v = bench.profiled_traffic("stream_collide", "cavity4000_4800disks_r10")
     # either the record matches the current source or it is withheld
     assert v is None or 1.5e9 < v < 2.0e9
-    assert bench.profiled_traffic("no_such_kernel") is None
+    assert bench.profiled_traffic("no_such_kernel", "cavity4000_4800disks_r10") is None
+    # a record of one workload is not reported for another
+    assert bench.profiled_traffic("stream_collide", "cavity1000x2000_129ellipses") is None
 
 
 def test_batch_and_server_reject_bad_arguments():
