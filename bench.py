@@ -332,7 +332,7 @@ def run_ours(args, wl):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": "k_stream_collide" + (" (far-tile + near-tile passes of one step)"
-                                                if "stream_collide_near" in ktimes else ""),
+                                                if ktimes.get("stream_collide_near", (0.0, 0))[1] else ""),
                 "algorithmic_bytes_per_launch": B_LU * nodes,
                 "avg_launch_ms": avg_s * 1e3, "peak_source": peaks["source"] + " (hbm_gbs)",
                 "kernel_times_from": "a second pass of the same number of steps, launched "

@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(kThreads) k_static_gather(View v, unsigned cha
 }
 
 // Phase 2: bounce-back and momentum exchange on the gathered slots, with the
-// same device helpers, link order (the valid slots in slot order), per-link
-// arithmetic, one-warp reduction and FP64 assembly as the workspace kernels.
+// same device helpers, per-link arithmetic, exact fixed-point sums (here by
+// one warp over the valid slots in slot order) and FP64 assembly as the
+// workspace kernels, so the forces agree bit for bit.
 // Shared memory: the compacted slot list and the per-link results,
 // 24 bytes per slot of the largest zone.
 __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned char *scratch, int capm)

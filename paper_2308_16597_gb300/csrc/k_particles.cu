@@ -46,15 +46,15 @@ __host__ __device__ inline int link_tile_wy(int N) { return N + 4; }
 __host__ __device__ inline int link_tile_wx(int N) { return N + 4; }
 __host__ __device__ inline int link_occ_words(int N) { return (12 * N - 12 + 31) / 32; }
 
-// Shared memory: the fluid and owner row masks [wy] (u64 each), slot occupancy words and their prefix [words], and per
-// slot / per link: the link node, the compacted slot list, three FP32
-// brackets and two integer words.
+// Shared memory: the fluid and owner row masks [wy] (u64 each), slot
+// occupancy words and their prefix [words], and per slot the link node and
+// the compacted slot list.
 size_t link_smem_bytes(int N, int storage)
 {
     (void)storage;
     const size_t cap = (size_t)12 * N - 12;
     return (size_t)2 * link_tile_wy(N) * sizeof(unsigned long long) +
-           (size_t)2 * link_occ_words(N) * sizeof(unsigned) + cap * 7 * sizeof(int);
+           (size_t)2 * link_occ_words(N) * sizeof(unsigned) + cap * 2 * sizeof(int);
 }
 
 bool link_zone_supported(int N, int storage)
@@ -106,15 +106,15 @@ __device__ __forceinline__ void clear_cells_slice(const Dev &D, int parity, int 
 //     claims its fixed slot of the index array (direction k, line through
 //     the zone; Sec. 3) in an occupancy bitmap;
 //  3. the occupied slots are compacted in slot order (popcount prefix), so
-//     thread i takes the i-th link: the work is balanced and the reduction
-//     order is fixed, hence the forces are bit-reproducible;
+//     thread i takes the i-th link and the work is balanced;
 //  4. each link: wall fraction q, curved bounce-back of f and g (Sec. 2.3)
 //     from the populations read at x_f, x_f - e_k and x_f - 2 e_k,
 //     written into the solid node x_f + e_k (direction kbar) of A in HBM,
 //     where the next pull stream picks it up (one link per (solid node, kbar),
 //     and every read is of a fluid node, so the writes never race the reads),
-//     and the momentum-exchange bracket of Eq. force / Eq. torque, stored per
-//     link and summed by one warp in link order.
+//     and the momentum-exchange bracket of Eq. force / Eq. torque, summed
+//     in exact fixed point per thread, per warp and over the warps (so the
+//     forces are bit-reproducible).
 template <typename T>
 __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__restrict__ own,
                                            int *__restrict__ own_nxt, int parity, int ahead, const int p)
@@ -140,11 +140,6 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
     unsigned *pre = occ + nw;                               // [nw]
     int *info = reinterpret_cast<int *>(pre + nw);          // [cap] k | a << 4 | b << 12 of the slot's link
     int *list = info + capm;                                // [cap] valid slots in order
-    float *lbx = reinterpret_cast<float *>(list + capm);    // [cap] per-link brackets
-    float *lby = lbx + capm;
-    float *ltq = lby + capm;
-    int *lcode = reinterpret_cast<int *>(ltq + capm);
-    int *ltz = lcode + capm;
 
     // ---- 0. the screening grid the particle update fills next: this CTA's
     // slice of its counts; the owner map the raster fills next (positions
@@ -275,58 +270,89 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
         return E::ld(__ldg(Ar + (long long)plane * D.ps + (long long)j * D.pitch + i));
     };
     auto fluid = [&](int i, int j) -> bool { return (Fm[j - YA] >> (i - XA)) & 1ull; };
-    for (int li = tid; li < nvalid; li += kLinkThreads) {
-        const int sl = list[li];
-        const int inf = info[sl], k = inf & 15;
-        const int kx = ex(k), ky = ey(k);
-        const int fi = X0 + ((inf >> 4) & 255), fj = Y0 + (inf >> 12);
-        float dxf, dyf;
-        const float q = ell ? link_q_ellipse(fi, fj, k, s_ell, dxf, dyf) : link_q_df(fi, fj, k, dk, dxf, dyf);
-        D.slot_node[base + sl] = fj * D.nx + fi;
-        D.slot_q[base + sl] = q;
+    // one round per kLinkThreads links: every warp sums its round at once
+    // (exact integer sums), lane 0 adds it to the warp's total; no
+    // accumulator stays live across rounds
+    __shared__ LinkSums s_ws[kLinkThreads / 32];
+    __shared__ int s_wc[kLinkThreads / 32][3];
+    const int rounds = (nvalid + kLinkThreads - 1) / kLinkThreads;
+    for (int it = 0; it < rounds; ++it) {
+        const int li = it * kLinkThreads + tid;
+        LinkAcc acc;
+        if (li < nvalid) {
+            const int sl = list[li];
+            const int inf = info[sl], k = inf & 15;
+            const int kx = ex(k), ky = ey(k);
+            const int fi = X0 + ((inf >> 4) & 255), fj = Y0 + (inf >> 12);
+            float dxf, dyf;
+            const float q = ell ? link_q_ellipse(fi, fj, k, s_ell, dxf, dyf) : link_q_df(fi, fj, k, dk, dxf, dyf);
+            D.slot_node[base + sl] = fj * D.nx + fi;
+            D.slot_q[base + sl] = q;
 
-        // curved bounce-back in deviation form: every rule is an affine
-        // combination of populations of equal weight, so it holds for
-        // f~ = f - w unchanged
-        const int kb = opp(k);
-        const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
-        const bool have1 = fluid(i1, j1);
-        const bool have2 = fluid(i2, j2);
-        const int ii1 = have1 ? i1 : fi, jj1 = have1 ? j1 : fj;
-        const int ii2 = have2 ? i2 : fi, jj2 = have2 ? j2 : fj;
-        const float fk0 = tv(k, fi, fj), fk1 = tv(k, ii1, jj1), fk2 = tv(k, ii2, jj2);
-        const float fb0 = tv(kb, fi, fj), fb1 = tv(kb, ii1, jj1);
-        const float rx = dxf + q * kx, ry = dyf + q * ky;
-        const float uwx = Ux - Om_ * ry, uwy = Uy + Om_ * rx;
-        const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy); // 2 w rho0 e_kbar.u_w / c_s^2
-        int lvl;
-        const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
-        const long long ns = (long long)(fj + ky) * D.pitch + (fi + kx);
-        A[kb * D.ps + ns] = E::st(fnew);
-        if (k <= 4) {
-            const float gnew = thermal32(q, tv(kQ9 + k, fi, fj), tv(kQ9 + k, ii1, jj1),
-                                         tv(kQ9 + kb, fi, fj), have1, wT);
-            A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
+            // curved bounce-back in deviation form: every rule is an affine
+            // combination of populations of equal weight, so it holds for
+            // f~ = f - w unchanged
+            const int kb = opp(k);
+            const int i1 = fi - kx, j1 = fj - ky, i2 = fi - 2 * kx, j2 = fj - 2 * ky;
+            const bool have1 = fluid(i1, j1);
+            const bool have2 = fluid(i2, j2);
+            const int ii1 = have1 ? i1 : fi, jj1 = have1 ? j1 : fj;
+            const int ii2 = have2 ? i2 : fi, jj2 = have2 ? j2 : fj;
+            const float fk0 = tv(k, fi, fj), fk1 = tv(k, ii1, jj1), fk2 = tv(k, ii2, jj2);
+            const float fb0 = tv(kb, fi, fj), fb1 = tv(kb, ii1, jj1);
+            const float rx = dxf + q * kx, ry = dyf + q * ky;
+            const float uwx = Ux - Om_ * ry, uwy = Uy + Om_ * rx;
+            const float wall = 6.f * w9(k) * -(kx * uwx + ky * uwy); // 2 w rho0 e_kbar.u_w / c_s^2
+            int lvl;
+            const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
+            const long long ns = (long long)(fj + ky) * D.pitch + (fi + kx);
+            A[kb * D.ps + ns] = E::st(fnew);
+            if (k <= 4) {
+                const float gnew = thermal32(q, tv(kQ9 + k, fi, fj), tv(kQ9 + k, ii1, jj1),
+                                             tv(kQ9 + kb, fi, fj), have1, wT);
+                A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
+            }
+            // momentum exchange: with f = w + f~ the bracket of Eq. force is
+            // 2 w_k e_k + [f~_k^+ (e_k - u_w) - f~_kbar (e_kbar - u_w)]; the
+            // constant part and its torque 2 w_k ((i - x_c) e_k,y - (j - y_c) e_k,x)
+            // (q drops out) are kept as exact integer sums, assembled in FP64 by
+            // the particle update
+            const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
+            const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
+            acc.add(bx, by, rx * by - ry * bx, k, lvl, k <= 4 && !have1, fi * ky - fj * kx);
         }
-        // momentum exchange: with f = w + f~ the bracket of Eq. force is
-        // 2 w_k e_k + [f~_k^+ (e_k - u_w) - f~_kbar (e_kbar - u_w)]; the
-        // constant part and its torque 2 w_k ((i - x_c) e_k,y - (j - y_c) e_k,x)
-        // (q drops out) are kept as exact integer sums, assembled in FP64 by
-        // the particle update
-        const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);
-        const float by = fk0 * (ky - uwy) - fnew * (-ky - uwy);
-        lbx[li] = bx;
-        lby[li] = by;
-        ltq[li] = rx * by - ry * bx;
-        lcode[li] = k | (lvl << 4) | ((k <= 4 && !have1) ? 64 : 0);
-        ltz[li] = fi * ky - fj * kx;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        LinkSums S;
-        int c3[3];
-        reduce_links(lbx, lby, ltq, lcode, ltz, nvalid, S, c3);
+        LinkSums Sw;
+        int c3w[3];
+        acc.finish(Sw, c3w);
         if (lane == 0) {
+            if (it == 0) {
+                s_ws[warp] = Sw;
+                s_wc[warp][0] = c3w[0]; s_wc[warp][1] = c3w[1]; s_wc[warp][2] = c3w[2];
+            } else {
+                add_sums(s_ws[warp], Sw);
+                s_wc[warp][0] += c3w[0]; s_wc[warp][1] += c3w[1]; s_wc[warp][2] += c3w[2];
+            }
+        }
+    }
+    if (rounds == 0 && lane == 0) { // no link
+        LinkSums Sz;
+        Sz.fx = Sz.fy = Sz.tz = 0;
+        Sz.ax_x = Sz.ax_y = Sz.ax_t = Sz.dg_x = Sz.dg_y = Sz.dg_t = 0;
+        s_ws[warp] = Sz;
+        s_wc[warp][0] = s_wc[warp][1] = s_wc[warp][2] = 0;
+    }
+    // ---- 5. the particle's sums over the warps (exact integer sums, so the
+    // grouping does not matter)
+    __syncthreads();
+    if (tid == 0) {
+        LinkSums S = s_ws[0];
+        int c3[3] = {s_wc[0][0], s_wc[0][1], s_wc[0][2]};
+#pragma unroll
+        for (int w = 1; w < kLinkThreads / 32; ++w) {
+            add_sums(S, s_ws[w]);
+            c3[0] += s_wc[w][0]; c3[1] += s_wc[w][1]; c3[2] += s_wc[w][2];
+        }
+        {
             D.lsum[p] = S;
             unsigned long long *C = D.status->cnt[parity];
             if (c3[0]) atomicAdd(&C[kCntBzLinear], (unsigned long long)c3[0]);
@@ -574,9 +600,9 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, d
     if (D.direct) {
         const DirectSums &ds = D.dsum[b];
         LinkSums S;
-        S.fx_h = (float)ds.f[0]; S.fx_l = (float)(ds.f[0] - (double)S.fx_h);
-        S.fy_h = (float)ds.f[1]; S.fy_l = (float)(ds.f[1] - (double)S.fy_h);
-        S.tz_h = (float)ds.f[2]; S.tz_l = (float)(ds.f[2] - (double)S.tz_h);
+        S.fx = fix_force(ds.f[0]);
+        S.fy = fix_force(ds.f[1]);
+        S.tz = fix_torque(ds.f[2]);
         S.ax_x = ds.c[0]; S.ax_y = ds.c[1]; S.ax_t = ds.c[2];
         S.dg_x = ds.c[3]; S.dg_y = ds.c[4]; S.dg_t = ds.c[5];
         assemble_force(S, x, y, Fx, Fy, Tz);

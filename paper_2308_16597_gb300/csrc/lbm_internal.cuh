@@ -475,36 +475,41 @@ __device__ __forceinline__ DiskDF geom_df(const GeomRec &G)
 }
 
 // Per-particle sums of the link kernel: the variable part of Eq. force /
-// Eq. torque as double-float, and the exact integer sums of the constant part
-// 2 w_k e_k (axis links: 2w = 2/9, diagonal: 1/18) and its torque moment
-// 2 w_k (i e_k,y - j e_k,x).
+// Eq. torque in 64-bit fixed point (units of 2^-50 for the force, 2^-46 for
+// the torque: integer addition is exact and associative, so the sums do not
+// depend on how the links are grouped or ordered), and the exact integer
+// sums of the constant part 2 w_k e_k (axis links: 2w = 2/9, diagonal: 1/18)
+// and its torque moment 2 w_k (i e_k,y - j e_k,x).
 struct LinkSums {
-    float fx_h, fx_l, fy_h, fy_l, tz_h, tz_l;
+    long long fx, fy, tz;
     int ax_x, ax_y, ax_t, dg_x, dg_y, dg_t;
     int pad[4];
 };
+__device__ __forceinline__ long long fix_force(float v) { return __float2ll_rn(v * 0x1p50f); }
+__device__ __forceinline__ long long fix_torque(float v) { return __float2ll_rn(v * 0x1p46f); }
+__device__ __forceinline__ long long fix_force(double v) { return __double2ll_rn(v * 0x1p50); }
+__device__ __forceinline__ long long fix_torque(double v) { return __double2ll_rn(v * 0x1p46); }
 // Direct addressing: the variable parts in FP64 and the constant parts as
 // integers, accumulated link by link with atomics (order not fixed).
 struct DirectSums {
     double f[3];  // Fx, Fy, Tz brackets
     int c[6];     // ax_x, ax_y, ax_t, dg_x, dg_y, dg_t
 };
-// Per-link momentum-exchange sums of one warp.  Lane l accumulates links
-// l, l + 32, l + 64, ... in that order (add), then finish() combines the
-// lanes by a fixed shuffle tree; every kernel that sums links does exactly
-// this, so their results agree bit for bit.  bx, by, tq: the variable part
-// of Eq. force / Eq. torque of a link; k its direction; lvl its Bouzidi
-// fallback level; half whether its thermal rule fell back to half-way; tz
-// the torque moment i e_k,y - j e_k,x of its constant part.
+// Per-link momentum-exchange sums.  Each thread adds its links (add), then
+// finish() sums a warp's threads; the sums are exact, so every kernel that
+// sums links gets the same bits however it distributes them.  bx, by, tq:
+// the variable part of Eq. force / Eq. torque of a link; k its direction;
+// lvl its Bouzidi fallback level; half whether its thermal rule fell back to
+// half-way; tz the torque moment i e_k,y - j e_k,x of its constant part.
 struct LinkAcc {
-    float fxh = 0.f, fxl = 0.f, fyh = 0.f, fyl = 0.f, tqh = 0.f, tql = 0.f;
+    long long fx = 0, fy = 0, tq = 0;
     int axx = 0, axy = 0, axt = 0, dgx = 0, dgy = 0, dgt = 0, cl = 0, cs = 0, ct = 0;
 
-    __device__ __forceinline__ void add(float bx, float by, float tq, int k, int lvl, bool half, int tz)
+    __device__ __forceinline__ void add(float bx, float by, float t, int k, int lvl, bool half, int tz)
     {
-        df_add(fxh, fxl, bx, 0.f);
-        df_add(fyh, fyl, by, 0.f);
-        df_add(tqh, tql, tq, 0.f);
+        fx += fix_force(bx);
+        fy += fix_force(by);
+        tq += fix_torque(t);
         cl += lvl == 1;
         cs += lvl == 2;
         ct += half;
@@ -515,20 +520,14 @@ struct LinkAcc {
     // simple, thermal half-way) on every lane.
     __device__ __forceinline__ void finish(LinkSums &S, int *cnt3)
     {
+        const unsigned F = 0xffffffffu;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const unsigned F = 0xffffffffu;
-            float h2 = __shfl_down_sync(F, fxh, o), l2 = __shfl_down_sync(F, fxl, o);
-            df_add(fxh, fxl, h2, l2);
-            h2 = __shfl_down_sync(F, fyh, o); l2 = __shfl_down_sync(F, fyl, o);
-            df_add(fyh, fyl, h2, l2);
-            h2 = __shfl_down_sync(F, tqh, o); l2 = __shfl_down_sync(F, tql, o);
-            df_add(tqh, tql, h2, l2);
+            fx += __shfl_xor_sync(F, fx, o);
+            fy += __shfl_xor_sync(F, fy, o);
+            tq += __shfl_xor_sync(F, tq, o);
         }
-        const unsigned F = 0xffffffffu;
-        S.fx_h = __shfl_sync(F, fxh, 0); S.fx_l = __shfl_sync(F, fxl, 0);
-        S.fy_h = __shfl_sync(F, fyh, 0); S.fy_l = __shfl_sync(F, fyl, 0);
-        S.tz_h = __shfl_sync(F, tqh, 0); S.tz_l = __shfl_sync(F, tql, 0);
+        S.fx = fx; S.fy = fy; S.tz = tq;
         S.ax_x = (int)__reduce_add_sync(F, (unsigned)axx);
         S.ax_y = (int)__reduce_add_sync(F, (unsigned)axy);
         S.ax_t = (int)__reduce_add_sync(F, (unsigned)axt);
@@ -541,6 +540,13 @@ struct LinkAcc {
         cnt3[2] = (int)__reduce_add_sync(F, (unsigned)ct);
     }
 };
+// S += T (the sums of another group of links).
+__device__ __forceinline__ void add_sums(LinkSums &S, const LinkSums &T)
+{
+    S.fx += T.fx; S.fy += T.fy; S.tz += T.tz;
+    S.ax_x += T.ax_x; S.ax_y += T.ax_y; S.ax_t += T.ax_t;
+    S.dg_x += T.dg_x; S.dg_y += T.dg_y; S.dg_t += T.dg_t;
+}
 
 // Reduction of per-link results stored in shared memory, by one warp, in
 // link order.  code: k | fallback level << 4 | thermal half-way << 6.
@@ -564,9 +570,9 @@ __device__ __forceinline__ void assemble_force(const LinkSums &S, double xc, dou
     const double Fcx = cax * (double)S.ax_x + cdg * (double)S.dg_x;
     const double Fcy = cax * (double)S.ax_y + cdg * (double)S.dg_y;
     const double Tc = cax * (double)S.ax_t + cdg * (double)S.dg_t - xc * Fcy + yc * Fcx;
-    Fx = Fcx + ((double)S.fx_h + (double)S.fx_l);
-    Fy = Fcy + ((double)S.fy_h + (double)S.fy_l);
-    Tz = Tc + ((double)S.tz_h + (double)S.tz_l);
+    Fx = Fcx + (double)S.fx * 0x1p-50;
+    Fy = Fcy + (double)S.fy * 0x1p-50;
+    Tz = Tc + (double)S.tz * 0x1p-46;
 }
 
 // Bouzidi quadratic bounce-back (Sec. 2.3) in deviation form, with the
