@@ -338,6 +338,18 @@ void fill_dev(lbm_handle *h)
     D.q_k = (float)(1.0 / (P.alpha / 0.2 + 0.5));
     D.q_e = (float)(P.q_e > 0 ? P.q_e : 1.0);
     D.q_nu = (float)(P.q_nu > 0 ? P.q_nu : 1.0);
+    {
+        // a_i = (m_i - s_i (m_i - m_eq,i) + (1 - s_i / 2) F_i) / |M_i|^2 with
+        // |M_i|^2 = 36 (e, eps), 12 (q), 4 (p); D2Q5 norms 1/2, 1/20, 1/4
+        const double se = D.s_e, sp = D.s_eps, sq = D.s_q, sn = D.s_nu, qk = D.q_k, qe = D.q_e, qn = D.q_nu;
+        D.kA1 = (float)((1.0 - se) / 36.0); D.kB1 = (float)(se / 36.0); D.kC1 = (float)((1.0 - 0.5 * se) / 6.0);
+        D.kA2 = (float)((1.0 - sp) / 36.0); D.kB2 = (float)(sp / 36.0); D.kC2 = (float)((1.0 - 0.5 * sp) / 6.0);
+        D.kA4 = (float)((1.0 - sq) / 12.0); D.kB4 = (float)(sq / 12.0); D.kC4 = (float)((1.0 - 0.5 * sq) / 12.0);
+        D.kA7 = (float)((1.0 - sn) / 4.0); D.kB7 = (float)(sn / 4.0); D.kC7 = (float)((1.0 - 0.5 * sn) / 2.0);
+        D.kC8 = (float)((1.0 - 0.5 * sn) / 4.0);
+        D.kG1 = (float)(0.5 * (1.0 - qk)); D.kG2 = (float)(0.5 * qk);
+        D.kG3 = (float)(0.05 * (1.0 - qe)); D.kG4 = (float)(0.1 * qe); D.kG5 = (float)(0.25 * (1.0 - qn));
+    }
     D.gbeta = (float)(P.g * P.beta);
     D.T0 = (float)P.T0;
     D.bfx = (float)P.body_fx;

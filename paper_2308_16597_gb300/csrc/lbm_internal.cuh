@@ -108,6 +108,8 @@ struct Dev {
     int per_x, per_y;
     // physics (FP32 for the lattice, FP64 for particles)
     float s_e, s_eps, s_q, s_nu, q_k, q_e, q_nu;
+    // the relaxation rates folded with the moment norms (see collide())
+    float kA1, kB1, kC1, kA2, kB2, kC2, kA4, kB4, kC4, kA7, kB7, kC7, kC8, kG1, kG2, kG3, kG4, kG5;
     float gbeta, T0, bfx, bfy;
     float Twall[4];
     double g, rho_f, eps_w, s_rep;
