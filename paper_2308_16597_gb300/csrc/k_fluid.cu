@@ -297,19 +297,18 @@ __device__ __forceinline__ void ahead_block(const Blk &blk, int ahead_y, int ahe
     }
 }
 
-template <typename T, int V, int mode = kSCAll>
-__device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout, int pf_x,
-                                        int pf_y, const Blk blk)
+// Look-ahead prefetch of a block: lanes 0..13 of its first row of threads
+// issue one bulk L2 prefetch each of the 14 source row segments of block
+// (bx, by) of a grid over D (in a pass, only of rows holding that pass's
+// tiles).
+template <typename T, int V, int mode>
+__device__ __forceinline__ void prefetch_block(const Dev &D, const T *__restrict__ Ain, int bx, int by)
 {
-    using E = Elem<T>;
-    using VW = typename Vec<T, V>::W;
     constexpr int kAl = 16 / (int)sizeof(T); // elements per 16 bytes
-    const int lane = threadIdx.x & 31;
-    const int span = (int)blockDim.x * V; // nodes of a row per block
+    const int span = (int)blockDim.x * V;   // nodes of a row per block
     if (threadIdx.x < kPop && threadIdx.y == 0) {
         // L2 prefetch of the source rows of the block at (pf_x, pf_y), the
         // one that runs about a residency wave later
-        const int bx = pf_x, by = pf_y;
         const int yb = by * (int)blockDim.y;
         const int xs = bx * span;
         const int lo = max(xs - kAl, 0), hi = min(xs + span + kAl, D.pitch);
@@ -332,6 +331,17 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
                          : "memory");
         }
     }
+}
+
+// pf_x < 0: no look-ahead prefetch here (the caller issues its own).
+template <typename T, int V, int mode = kSCAll>
+__device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout, int pf_x,
+                                        int pf_y, const Blk blk)
+{
+    using E = Elem<T>;
+    using VW = typename Vec<T, V>::W;
+    const int lane = threadIdx.x & 31;
+    if (pf_x >= 0) prefetch_block<T, V, mode>(D, Ain, pf_x, pf_y);
     const int x0 = (blk.x * (int)blockDim.x + (int)threadIdx.x) * V;
     const int y = blk.y * (int)blockDim.y + (int)threadIdx.y;
     if (y >= D.ny) return; // uniform across the warp: blockDim.x is a multiple of 32
@@ -491,10 +501,11 @@ __device__ __forceinline__ void boundary_body(const Dev &D, const T *__restrict_
     if (!ok) atomicOr(&D.status->err, kErrNumeric);
 }
 
-// FP32: 10 blocks per SM (48 registers), which measured best (268 us against
-// 272 with 8 blocks and 279 with 12, on the 4000^2 benchmark).
+// Blocks per SM that measured best on the 4000^2 benchmark: FP32 10 (48
+// registers; 268 us against 272 with 8 and 279 with 12), 16-bit storage 8
+// (62 registers; BF16 209 us against 220 with 7 and 219 with 10).
 template <typename T, int V, int mode>
-__global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 5)
+__global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 8)
     k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ahead_y, int ahead_x)
 {
     const Blk blk = this_blk();
@@ -514,13 +525,25 @@ __global__ void __launch_bounds__(128)
 
 // Batched forms: one grid over all instances.  Stream-collide blocks are
 // laid out per instance as gx x gy tiles of the instance's lattice (gx from
-// its pitch), and each block prefetches the block `resident` places later
-// within its own instance.
+// its pitch), and each block prefetches the block `resident` places later in
+// the launch over all instances (often one of a later instance: prefetching
+// only within the block's own instance left most blocks of small instances
+// without a prefetch).
 template <typename T, int V>
-__global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 5)
-    k_stream_collide_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity,
-                           int resident)
+__global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 8)
+    k_stream_collide_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int total,
+                           int parity, int resident)
 {
+    // the look-ahead target is the block `resident` places later in the
+    // launch over all instances, which is often in a later instance
+    const int tg = (int)blockIdx.x + resident;
+    if (threadIdx.x < kPop && threadIdx.y == 0 && tg < total) {
+        const int j = batch_find(start, n, tg);
+        const InstArgs &t = I[j];
+        const int lt = tg - __ldg(start + j);
+        const int gxt = (t.D.pitch / V + (int)blockDim.x - 1) / (int)blockDim.x;
+        prefetch_block<T, V, kSCAll>(t.D, static_cast<const T *>(t.A[parity ^ t.poff]), lt % gxt, lt / gxt);
+    }
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
     const int local = (int)blockIdx.x - __ldg(start + i);
@@ -528,9 +551,7 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 5)
     const int gy = (a.D.ny + (int)blockDim.y - 1) / (int)blockDim.y;
     const Blk blk{local % gx, local / gx, gx, gy};
     const int par = parity ^ a.poff;
-    int bx, by;
-    ahead_block(blk, resident / gx, resident % gx, bx, by);
-    sc_body<T, V>(a.D, static_cast<const T *>(a.A[par]), static_cast<T *>(a.A[par ^ 1]), bx, by, blk);
+    sc_body<T, V>(a.D, static_cast<const T *>(a.A[par]), static_cast<T *>(a.A[par ^ 1]), -1, 0, blk);
 }
 
 template <typename T>
@@ -710,13 +731,13 @@ cudaError_t launch_stream_collide_batch(const InstArgs *I, const int *start, int
     if (total <= 0) return cudaSuccess;
     switch (storage) {
     case LBM_STORE_FP32:
-        k_stream_collide_batch<float, 1><<<total, block, 0, s>>>(I, start, n, parity, resident);
+        k_stream_collide_batch<float, 1><<<total, block, 0, s>>>(I, start, n, total, parity, resident);
         break;
     case LBM_STORE_BF16:
-        k_stream_collide_batch<__nv_bfloat16, 2><<<total, block, 0, s>>>(I, start, n, parity, resident);
+        k_stream_collide_batch<__nv_bfloat16, 2><<<total, block, 0, s>>>(I, start, n, total, parity, resident);
         break;
     case LBM_STORE_FP16:
-        k_stream_collide_batch<__half, 2><<<total, block, 0, s>>>(I, start, n, parity, resident);
+        k_stream_collide_batch<__half, 2><<<total, block, 0, s>>>(I, start, n, total, parity, resident);
         break;
     default: return cudaErrorInvalidValue;
     }
