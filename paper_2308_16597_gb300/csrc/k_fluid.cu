@@ -127,82 +127,133 @@ __device__ __forceinline__ int slow_node(const Dev &D, const T *__restrict__ A,
     return 4 - nvalid;
 }
 
-// MRT collision of one node in deviation form (Eq. f with Guo forcing in
-// moment space, Eq. g), in place on c[14].  Returns false for a non-finite
-// or non-physical density/temperature.
-__device__ __forceinline__ bool collide(const Dev &D, float *c)
+// Arithmetic of the collision on one node (float) or on two nodes at once
+// (float2, Blackwell's paired FP32 instructions).  Every operation is a
+// round-to-nearest add, multiply or fused multiply-add, so both forms give
+// the same bits per node, and no kernel that inlines them fuses differently.
+template <typename F>
+struct FOps;
+template <>
+struct FOps<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+    static __device__ __forceinline__ float bc(float v) { return v; }
+    static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.f, a); }
+};
+template <>
+struct FOps<float2> {
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    // a - b = RN(b (-1) + a): exact product, one rounding
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b)
+    {
+        return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+    }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
+    static __device__ __forceinline__ float2 rcp(float2 a)
+    {
+        return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y));
+    }
+};
+__device__ __forceinline__ bool phys_ok(float rho, float T)
 {
-    // Every product is an explicit fmaf or a round-to-nearest multiply, so no
-    // kernel that inlines this (single or batched stream-collide, boundary,
-    // init) fuses differently: all give the same bits.
-    const float f0 = c[0], f1 = c[1], f2 = c[2], f3 = c[3], f4 = c[4];
-    const float f5 = c[5], f6 = c[6], f7 = c[7], f8 = c[8];
+    return (rho > 0.25f) && (rho < 4.f) && (fabsf(T) < 1e30f);
+}
+
+// MRT collision in deviation form (Eq. f with Guo forcing in moment space,
+// Eq. g), in place on c[14] (one node per lane of F).  ok: whether each
+// node's density and temperature are finite and physical.
+template <typename F>
+__device__ __forceinline__ void collide_t(const Dev &D, F *c, bool &ok0, bool &ok1)
+{
+    using O = FOps<F>;
+    const F f0 = c[0], f1 = c[1], f2 = c[2], f3 = c[3], f4 = c[4];
+    const F f5 = c[5], f6 = c[6], f7 = c[7], f8 = c[8];
     // pair sums and differences shared by the moments
-    const float u13 = f1 + f3, d13 = f1 - f3, u24 = f2 + f4, d24 = f2 - f4;
-    const float s56 = f5 + f6, d56 = f5 - f6, s78 = f7 + f8, d87 = f8 - f7;
-    const float sa = u13 + u24, sd = s56 + s78;
-    const float drho = (f0 + sa) + sd;
-    const float rho = 1.f + drho;
-    const float e = d56 + d87, g = s56 - s78;
-    const float jx = d13 + e, jy = d24 + g;
-    const float T = (c[9] + c[10]) + (c[11] + c[12]) + c[13];
-    const float Fx = D.bfx;
-    const float Fy = fmaf(__fmul_rn(rho, D.gbeta), T - D.T0, D.bfy);
-    const float inv = __fdividef(1.f, rho);
-    const float ux = __fmul_rn(fmaf(0.5f, Fx, jx), inv), uy = __fmul_rn(fmaf(0.5f, Fy, jy), inv);
-    const float m1 = fmaf(2.f, sd, fmaf(-4.f, f0, -sa)); // -4 f0 - sa + 2 sd
-    const float m2 = fmaf(4.f, f0, fmaf(-2.f, sa, sd));  // 4 f0 - 2 sa + sd
-    const float m4 = fmaf(-2.f, d13, e);                 // 2 (f3 - f1) + (f5 - f6) + (f8 - f7)
-    const float m6 = fmaf(-2.f, d24, g);                 // 2 (f4 - f2) + (f5 + f6) - (f7 + f8)
-    const float m7 = u13 - u24;
-    const float m8 = (f5 + f7) - (f6 + f8);
-    const float uu = fmaf(ux, ux, __fmul_rn(uy, uy));
-    const float uF = fmaf(ux, Fx, __fmul_rn(uy, Fy));
-    const float ru = __fmul_rn(__fmul_rn(3.f, rho), uu);
+    const F u13 = O::add(f1, f3), d13 = O::sub(f1, f3), u24 = O::add(f2, f4), d24 = O::sub(f2, f4);
+    const F s56 = O::add(f5, f6), d56 = O::sub(f5, f6), s78 = O::add(f7, f8), d87 = O::sub(f8, f7);
+    const F sa = O::add(u13, u24), sd = O::add(s56, s78);
+    const F drho = O::add(O::add(f0, sa), sd);
+    const F rho = O::add(O::bc(1.f), drho);
+    const F e = O::add(d56, d87), g = O::sub(s56, s78);
+    const F jx = O::add(d13, e), jy = O::add(d24, g);
+    const F T = O::add(O::add(O::add(c[9], c[10]), O::add(c[11], c[12])), c[13]);
+    const F Fx = O::bc(D.bfx);
+    const F Fy = O::fma(O::mul(rho, O::bc(D.gbeta)), O::sub(T, O::bc(D.T0)), O::bc(D.bfy));
+    const F inv = O::rcp(rho);
+    const F ux = O::mul(O::fma(O::bc(0.5f), Fx, jx), inv), uy = O::mul(O::fma(O::bc(0.5f), Fy, jy), inv);
+    const F m1 = O::fma(O::bc(2.f), sd, O::fma(O::bc(-4.f), f0, O::sub(O::bc(0.f), sa))); // -4 f0 - sa + 2 sd
+    const F m2 = O::fma(O::bc(4.f), f0, O::fma(O::bc(-2.f), sa, sd));                     // 4 f0 - 2 sa + sd
+    const F m4 = O::fma(O::bc(-2.f), d13, e); // 2 (f3 - f1) + (f5 - f6) + (f8 - f7)
+    const F m6 = O::fma(O::bc(-2.f), d24, g); // 2 (f4 - f2) + (f5 + f6) - (f7 + f8)
+    const F m7 = O::sub(u13, u24);
+    const F m8 = O::sub(O::add(f5, f7), O::add(f6, f8));
+    const F uu = O::fma(ux, ux, O::mul(uy, uy));
+    const F uF = O::fma(ux, Fx, O::mul(uy, Fy));
+    const F ru = O::mul(O::mul(O::bc(3.f), rho), uu);
     // a_i = post-collision moment i / |M_i|^2, the rates and norms folded
     // into the coefficients k*: m_i - s_i (m_i - m_eq,i) + (1 - s_i / 2) F_i
-    const float a0 = __fmul_rn(drho, 1.f / 9.f);
-    const float a1 = fmaf(D.kA1, m1, fmaf(D.kB1, fmaf(-2.f, drho, ru), __fmul_rn(D.kC1, uF)));
-    const float a2 = fmaf(D.kA2, m2, fmaf(D.kB2, drho - ru, __fmul_rn(-D.kC2, uF)));
-    const float a3 = __fmul_rn(jx + Fx, 1.f / 6.f), a5 = __fmul_rn(jy + Fy, 1.f / 6.f);
-    const float rux = __fmul_rn(rho, ux), ruy = __fmul_rn(rho, uy);
-    const float a4 = fmaf(D.kA4, m4, fmaf(-D.kB4, rux, __fmul_rn(-D.kC4, Fx)));
-    const float a6 = fmaf(D.kA4, m6, fmaf(-D.kB4, ruy, __fmul_rn(-D.kC4, Fy)));
-    const float pxx = fmaf(ux, ux, __fmul_rn(-uy, uy)); // ux^2 - uy^2
-    const float fxx = fmaf(ux, Fx, __fmul_rn(-uy, Fy)); // ux Fx - uy Fy
-    const float fxy = fmaf(ux, Fy, __fmul_rn(uy, Fx));  // ux Fy + uy Fx
-    const float a7 = fmaf(D.kA7, m7, fmaf(D.kB7, __fmul_rn(rho, pxx), __fmul_rn(D.kC7, fxx)));
-    const float a8 = fmaf(D.kA7, m8, fmaf(D.kB7, __fmul_rn(rux, uy), __fmul_rn(D.kC8, fxy)));
+    const F a0 = O::mul(drho, O::bc(1.f / 9.f));
+    const F a1 = O::fma(O::bc(D.kA1), m1,
+                        O::fma(O::bc(D.kB1), O::fma(O::bc(-2.f), drho, ru), O::mul(O::bc(D.kC1), uF)));
+    const F a2 = O::fma(O::bc(D.kA2), m2, O::fma(O::bc(D.kB2), O::sub(drho, ru), O::mul(O::bc(-D.kC2), uF)));
+    const F a3 = O::mul(O::add(jx, Fx), O::bc(1.f / 6.f)), a5 = O::mul(O::add(jy, Fy), O::bc(1.f / 6.f));
+    const F rux = O::mul(rho, ux), ruy = O::mul(rho, uy);
+    const F a4 = O::fma(O::bc(D.kA4), m4, O::fma(O::bc(-D.kB4), rux, O::mul(O::bc(-D.kC4), Fx)));
+    const F a6 = O::fma(O::bc(D.kA4), m6, O::fma(O::bc(-D.kB4), ruy, O::mul(O::bc(-D.kC4), Fy)));
+    const F pxx = O::fma(ux, ux, O::mul(O::sub(O::bc(0.f), uy), uy)); // ux^2 - uy^2
+    const F fxx = O::fma(ux, Fx, O::mul(O::sub(O::bc(0.f), uy), Fy)); // ux Fx - uy Fy
+    const F fxy = O::fma(ux, Fy, O::mul(uy, Fx));                     // ux Fy + uy Fx
+    const F a7 = O::fma(O::bc(D.kA7), m7, O::fma(O::bc(D.kB7), O::mul(rho, pxx), O::mul(O::bc(D.kC7), fxx)));
+    const F a8 = O::fma(O::bc(D.kA7), m8, O::fma(O::bc(D.kB7), O::mul(rux, uy), O::mul(O::bc(D.kC8), fxy)));
     // f = M^T a
-    const float base = fmaf(-2.f, a2, a0 - a1), dbase = fmaf(2.f, a1, a0 + a2);
-    const float h34 = fmaf(-2.f, a4, a3), h56 = fmaf(-2.f, a6, a5), s34 = a3 + a4, s56a = a5 + a6;
-    c[0] = fmaf(4.f, a2, fmaf(-4.f, a1, a0));
-    c[1] = (base + h34) + a7;
-    c[2] = (base + h56) - a7;
-    c[3] = (base - h34) + a7;
-    c[4] = (base - h56) - a7;
-    c[5] = ((dbase + s34) + s56a) + a8;
-    c[6] = ((dbase - s34) + s56a) - a8;
-    c[7] = ((dbase - s34) - s56a) + a8;
-    c[8] = ((dbase + s34) - s56a) - a8;
+    const F base = O::fma(O::bc(-2.f), a2, O::sub(a0, a1)), dbase = O::fma(O::bc(2.f), a1, O::add(a0, a2));
+    const F h34 = O::fma(O::bc(-2.f), a4, a3), h56 = O::fma(O::bc(-2.f), a6, a5);
+    const F s34 = O::add(a3, a4), s56a = O::add(a5, a6);
+    c[0] = O::fma(O::bc(4.f), a2, O::fma(O::bc(-4.f), a1, a0));
+    c[1] = O::add(O::add(base, h34), a7);
+    c[2] = O::sub(O::add(base, h56), a7);
+    c[3] = O::add(O::sub(base, h34), a7);
+    c[4] = O::sub(O::sub(base, h56), a7);
+    c[5] = O::add(O::add(O::add(dbase, s34), s56a), a8);
+    c[6] = O::sub(O::add(O::sub(dbase, s34), s56a), a8);
+    c[7] = O::add(O::sub(O::sub(dbase, s34), s56a), a8);
+    c[8] = O::sub(O::sub(O::add(dbase, s34), s56a), a8);
     // D2Q5: n = (T, g1-g3, g2-g4, -4g0 + g1+g2+g3+g4, g1-g2+g3-g4),
     // n_eq = (T, T ux, T uy, -2T, 0); g = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4) n
-    const float g0 = c[9], g1 = c[10], g2 = c[11], g3 = c[12], g4 = c[13];
-    const float n1 = g1 - g3, n2 = g2 - g4;
-    const float n3 = fmaf(-4.f, g0, (g1 + g2) + (g3 + g4));
-    const float n4 = (g1 + g3) - (g2 + g4);
-    const float b0 = __fmul_rn(T, 0.2f);
-    const float b1 = fmaf(D.kG1, n1, __fmul_rn(D.kG2, __fmul_rn(T, ux)));
-    const float b2 = fmaf(D.kG1, n2, __fmul_rn(D.kG2, __fmul_rn(T, uy)));
-    const float b3 = fmaf(D.kG3, n3, __fmul_rn(-D.kG4, T));
-    const float b4 = __fmul_rn(D.kG5, n4);
-    const float b03 = b0 + b3;
-    c[9] = fmaf(-4.f, b3, b0);
-    c[10] = (b03 + b1) + b4;
-    c[11] = (b03 + b2) - b4;
-    c[12] = (b03 - b1) + b4;
-    c[13] = (b03 - b2) - b4;
-    return (rho > 0.25f) && (rho < 4.f) && (fabsf(T) < 1e30f);
+    const F g0 = c[9], g1 = c[10], g2 = c[11], g3 = c[12], g4 = c[13];
+    const F n1 = O::sub(g1, g3), n2 = O::sub(g2, g4);
+    const F n3 = O::fma(O::bc(-4.f), g0, O::add(O::add(g1, g2), O::add(g3, g4)));
+    const F n4 = O::sub(O::add(g1, g3), O::add(g2, g4));
+    const F b0 = O::mul(T, O::bc(0.2f));
+    const F b1 = O::fma(O::bc(D.kG1), n1, O::mul(O::bc(D.kG2), O::mul(T, ux)));
+    const F b2 = O::fma(O::bc(D.kG1), n2, O::mul(O::bc(D.kG2), O::mul(T, uy)));
+    const F b3 = O::fma(O::bc(D.kG3), n3, O::mul(O::bc(-D.kG4), T));
+    const F b4 = O::mul(O::bc(D.kG5), n4);
+    const F b03 = O::add(b0, b3);
+    c[9] = O::fma(O::bc(-4.f), b3, b0);
+    c[10] = O::add(O::add(b03, b1), b4);
+    c[11] = O::sub(O::add(b03, b2), b4);
+    c[12] = O::add(O::sub(b03, b1), b4);
+    c[13] = O::sub(O::sub(b03, b2), b4);
+    if constexpr (sizeof(F) == sizeof(float)) {
+        ok0 = phys_ok(reinterpret_cast<const float &>(rho), reinterpret_cast<const float &>(T));
+        ok1 = ok0;
+    } else {
+        const float2 r2 = reinterpret_cast<const float2 &>(rho), t2 = reinterpret_cast<const float2 &>(T);
+        ok0 = phys_ok(r2.x, t2.x);
+        ok1 = phys_ok(r2.y, t2.y);
+    }
+}
+// One node: false for a non-finite or non-physical density/temperature.
+__device__ __forceinline__ bool collide(const Dev &D, float *c)
+{
+    bool ok, unused;
+    collide_t<float>(D, c, ok, unused);
+    return ok;
 }
 
 // Per-thread counts of newborn nodes and of refill fallbacks (linear, copy,
@@ -420,20 +471,46 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
     }
     if (!act) return;
     bool ok = true, gen[V], anygen = false;
+    if constexpr (V == 2) {
+        // both nodes collided at once on paired FP32 instructions; solid
+        // nodes (and the padding past nx) are zeroed after
+        bool fluid[2];
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-        const int x = x0 + k;
-        const uint8_t fl = D.flags[(long long)y * D.pitch + x];
-        gen[k] = false;
-        if (x < D.nx && fl != kSolid) {
+        for (int k = 0; k < 2; ++k) {
+            const int x = x0 + k;
+            const uint8_t fl = D.flags[(long long)y * D.pitch + x];
+            fluid[k] = x < D.nx && fl != kSolid;
             // frame and newborn nodes belong to k_boundary, which writes them
-            gen[k] = fl == kNewborn || y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1;
-            if (!gen[k]) ok &= collide(D, c[k]);
-        } else {
-#pragma unroll
-            for (int p = 0; p < kPop; ++p) c[k][p] = 0.f;
+            gen[k] = fluid[k] && (fl == kNewborn || y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1);
+            anygen |= gen[k];
         }
-        anygen |= gen[k];
+        float2 cc[kPop];
+#pragma unroll
+        for (int p = 0; p < kPop; ++p) cc[p] = make_float2(c[0][p], c[1][p]);
+        bool ok0, ok1;
+        collide_t<float2>(D, cc, ok0, ok1);
+#pragma unroll
+        for (int p = 0; p < kPop; ++p) {
+            c[0][p] = fluid[0] ? cc[p].x : 0.f;
+            c[1][p] = fluid[1] ? cc[p].y : 0.f;
+        }
+        ok = (!fluid[0] || gen[0] || ok0) && (!fluid[1] || gen[1] || ok1);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int x = x0 + k;
+            const uint8_t fl = D.flags[(long long)y * D.pitch + x];
+            gen[k] = false;
+            if (x < D.nx && fl != kSolid) {
+                // frame and newborn nodes belong to k_boundary, which writes them
+                gen[k] = fl == kNewborn || y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1;
+                if (!gen[k]) ok &= collide(D, c[k]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < kPop; ++p) c[k][p] = 0.f;
+            }
+            anygen |= gen[k];
+        }
     }
     T *dst = Aout + (long long)y * D.pitch + x0;
     if (!anygen) {
