@@ -544,7 +544,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["cavity4000", "cavity2000", "cavity256", "cavity1024", "ellipses129",
-                                           "ensemble64", "served"],
+                                           "paper4800", "ensemble64", "served"],
                     default="cavity4000")
     ap.add_argument("--tick-steps", type=int, default=100, help="served: steps per scheduling round")
     ap.add_argument("--no-e2e", action="store_true")
@@ -565,7 +565,8 @@ def main(argv=None):
         return run_ensemble(args) if args.workload == "ensemble64" else run_served(args)
     wl = {"cavity4000": W.sedimentation_4000, "cavity2000": W.sedimentation_2000,
           "cavity256": W.parity_256,
-          "cavity1024": W.crop_1024, "ellipses129": W.ellipse_cluster_129}[args.workload]()
+          "cavity1024": W.crop_1024, "ellipses129": W.ellipse_cluster_129,
+          "paper4800": W.paper_4800}[args.workload]()
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

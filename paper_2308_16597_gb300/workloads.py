@@ -133,6 +133,25 @@ def sedimentation_4000(seed: int = 16597) -> Workload:
                          name="cavity4000_4800disks_r10", steps=10000)
 
 
+def paper_4800(spacing: float = 50.0) -> Workload:
+    """The paper's own 4800-particle benchmark (Sec. 2.6.3 and its parameter
+    table): 4000 x 4000 l.u., 4800 hot disks of diameter 40 l.u. (solid
+    fraction 37.7 %) in 60 lines of 80 in the upper part of the cavity,
+    rho_p = 1.1, nu = 0.01, alpha = 0.002 (Pr = 5), g = 7.84e-6,
+    beta = 1.20e-2, Delta_T = 1.  The line spacing is not given; the disks sit
+    on a square lattice of pitch 50 l.u. (80 x 50 = 4000) from the top."""
+    n_x, n_y = 80, 60
+    parts = np.zeros(n_x * n_y, PARTICLE_DTYPE)
+    i, j = np.meshgrid(np.arange(n_x), np.arange(n_y))
+    parts["x"] = 0.5 * spacing + spacing * i.ravel()
+    parts["y"] = 4000.0 - 0.5 * spacing - spacing * j.ravel()
+    parts["r"] = 20.0
+    parts["rho"] = 1.1
+    parts["T"] = 1.0
+    return Workload("cavity4000_4800disks_d40_paper", cavity(4000, 4000), parts,
+                    base_params(0.01, 5.0, 7.84e-6, beta=1.2e-2), 6000)
+
+
 def sedimentation_2000(seed: int = 2000) -> Workload:
     """2000x2000 quarter-area version of sedimentation_4000 (1200 disks, same
     density, Ra = 1e8 on H = 2000): the profiling case, 0.46 GB of state."""

@@ -272,11 +272,13 @@ def test_kernel_timing_counts_launches():
 
 # --------------------------------------------------------------------------- full size
 @pytest.mark.slow
-def test_full_size_4000_cavity_two_steps():
-    """The 4000^2 / 4800-disk workload in the benchmark's launch
-    configuration: owner map bit-exact at init and every field within FP32
-    tolerance of the oracle after two steps."""
-    wl = W.sedimentation_4000()
+@pytest.mark.parametrize("make", [W.sedimentation_4000, W.paper_4800])
+def test_full_size_4000_cavity_two_steps(make):
+    """The 4000^2 / 4800-disk workloads (r = 10 at 9.4 % solid, and the
+    paper's d = 40 at 37.7 %) in the benchmark's launch configuration: owner
+    map bit-exact at init and every field within FP32 tolerance of the oracle
+    after two steps."""
+    wl = make()
     sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
     ref = orc.Oracle(wl.domain, wl.particles, wl.params)
     assert np.array_equal(sim.owner(), ref.owner())
