@@ -766,8 +766,8 @@ __device__ __forceinline__ void raster_body(const Dev &D, int *own, const GeomRe
 // Flags over the rectangle that holds the particle's zones one step back, now
 // and next (so every node whose flag may have changed since the last step):
 // solid at the new time, newborn (solid before, fluid now) or fluid, from
-// the two owner maps.  A team of TEAM warps per particle (one warp for zones
-// of up to 32 rows, the whole 4-warp block for larger ones): team warp w
+// the two owner maps.  A team of TEAM warps per particle (one warp when the
+// particles alone fill the GPU, else 2 or 4): team warp w
 // takes rows w kU .. w kU + kU - 1 of every TEAM kU rows, eight at a time
 // (all loads issued first), lane l columns l and l + 32 of every 64.  During
 // a step team warp 0 also moves the particle's new state into the current
@@ -778,16 +778,22 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
 {
     const int lane = threadIdx.x & 31, tw = (threadIdx.x >> 5) % TEAM;
     constexpr int kU = 8;
-    if (p >= D.np) return; // uniform across the team
+    // a team past the last particle still reaches the block barrier below
+    const bool act = p < D.np; // uniform across the team
     const bool list = rotate != 0; // a step (not the initial flags): list the newborn nodes
-    const Box Ba = box_of(D.geo_prev[p]), Bb = box_of(D.geo_cur[p]), Bc = box_of(D.geo_nxt[p]);
+    Box Ba{0, 0, 0}, Bb{0, 0, 0}, Bc{0, 0, 0};
+    if (act) {
+        Ba = box_of(D.geo_prev[p]);
+        Bb = box_of(D.geo_cur[p]);
+        Bc = box_of(D.geo_nxt[p]);
+    }
     if (rotate) {
         // the new state moves into the current slot (and the current position
         // into the previous one) while the other threads work on the flags;
         // every thread of the team has read the three boxes before
         if (TEAM == 1) __syncwarp();
         else __syncthreads();
-        if (tw == 0) switch (lane) {
+        if (act && tw == 0) switch (lane) {
         case 0: D.px[p] = D.cur.x[p]; D.cur.x[p] = D.nxt.x[p]; break;
         case 1: D.py[p] = D.cur.y[p]; D.cur.y[p] = D.nxt.y[p]; break;
         case 2: D.cur.ux[p] = D.nxt.ux[p]; break;
@@ -798,6 +804,7 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
         default: break;
         }
     }
+    if (!act) return;
     const int X0 = max(min(min(Ba.X0, Bb.X0), Bc.X0), 0);
     const int Y0 = max(min(min(Ba.Y0, Bb.Y0), Bc.Y0), 0);
     const int X1 = min(max(max(Ba.X0 + Ba.N, Bb.X0 + Bb.N), Bc.X0 + Bc.N), D.nx); // exclusive
@@ -834,7 +841,6 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
                 }
         }
 }
-constexpr int kFlagTeamRows = 32; // zones up to this side: one warp per particle
 
 // Near-tile bitmap: every warp tile (one row, 32 V nodes) that meets a
 // particle's zone at the current position widened by kNearMargin nodes.  One
@@ -1095,6 +1101,7 @@ void *link_kernel_for(int storage)
 cudaError_t prepare_links(Dev &D)
 {
     D.link_ahead = 1;
+    D.flag_team = 1;
     if (D.np == 0) return cudaSuccess;
     const size_t smem = link_smem_bytes(D.zone_max, D.storage);
     const void *fn = link_kernel_for(D.storage);
@@ -1106,6 +1113,10 @@ cudaError_t prepare_links(Dev &D)
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLinkThreads, smem)) != cudaSuccess)
         return e;
     D.link_ahead = max(1, sms * per_sm); // particles (CTAs) resident at once
+    // flags: one warp per particle when there are enough particles to fill
+    // the GPU (about 36 warps per SM), else teams of 2 or 4 warps
+    const int warps = sms * 36;
+    D.flag_team = D.np * 2 > warps ? 1 : D.np * 4 > warps ? 2 : 4;
     return cudaSuccess;
 }
 
@@ -1269,11 +1280,13 @@ cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, i
                          cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
-    const int per = kBoxThreads / 32;
-    if (D.zone_max + 2 <= kFlagTeamRows)
-        k_flags<1><<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate);
-    else
-        k_flags<kBoxThreads / 32><<<D.np, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate);
+    const int per = kBoxThreads / 32 / max(D.flag_team, 1); // particles per block
+    const int grid = (D.np + per - 1) / per;
+    switch (D.flag_team) {
+    case 4: k_flags<4><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate); break;
+    case 2: k_flags<2><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate); break;
+    default: k_flags<1><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate); break;
+    }
     return cudaGetLastError();
 }
 

@@ -116,6 +116,7 @@ struct Dev {
     int fixed;
     int zone_max;      // largest zone side N over the particles (sizes the link kernel's tile)
     int link_ahead;    // link-kernel CTAs resident on the GPU (distance of its L2 prefetch)
+    int flag_team;     // warps per particle in the flags kernel (1, 2 or 4)
     // device buffers
     uint8_t *flags;    // [ny][pitch]
     int *newborn;      // [newborn_cap]: j * nx + i of this step's newborn nodes off the cavity frame

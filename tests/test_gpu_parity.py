@@ -204,6 +204,25 @@ def test_cavity_256_eight_disks_100_steps():
     print("rel-L2 after 100 steps:", errs)
 
 
+@pytest.mark.slow
+def test_cavity_256_eight_disks_1000_steps():
+    """The same run over 1000 steps: particle centres stay within 1e-4
+    lattice units of the FP64 oracle at every 100th step; the fields, which
+    the settling flow amplifies, within rel-L2 1e-4."""
+    wl = W.parity_256()
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    ref = orc.Oracle(wl.domain, wl.particles, wl.params)
+    worst = 0.0
+    for _ in range(10):
+        sim.step(100)
+        assert ref.step(100) == 0
+        pg, po = sim.particles(), ref.particles()
+        worst = max(worst, np.abs(pg["x"] - po["x"]).max(), np.abs(pg["y"] - po["y"]).max())
+        assert worst < 1e-4, worst
+    errs = compare_fields(sim, ref, 1e-4)
+    print("1000 steps: centres within %.2e lu, fields rel-L2 %s" % (worst, errs))
+
+
 def test_moving_disk_refills_like_the_oracle():
     parts = np.zeros(2, W.PARTICLE_DTYPE)
     parts["x"], parts["y"] = [40.3, 90.6], [50.2, 47.7]
