@@ -2,13 +2,17 @@
 //   k_links      indirect-addressing gather of fluid-particle links into the
 //                fixed index array (Sec. 3), curved bounce-back of f and g on
 //                each link (Sec. 2.3) and the momentum-exchange force and
-//                torque (Sec. 2.4, Eq. force / Eq. torque) reduced per
-//                particle in FP64;
-//   k_particles  Newton-Euler update with gravity, buoyancy and spring
-//                repulsion (Sec. 2.2, Sec. 2.4);
-//   k_raster, k_flags
-//                owner map and node flags at the new positions (the
-//                owner map is cleared over the old zones by k_links).
+//                torque (Sec. 2.4, Eq. force / Eq. torque) summed per
+//                particle in exact fixed point;
+//   k_particles  pair screening through the cell grid, Newton-Euler update
+//                with gravity, buoyancy and spring repulsion (Sec. 2.2,
+//                Sec. 2.4) in FP64, and the raster of the new positions into
+//                the next owner map (cleared over the old zones by k_links);
+//   k_flags      node flags at the new positions and the newborn list;
+// plus the initialisation kernels (k_raster, k_geom_init, k_cells_init), the
+// direct-addressing comparison (k_direct_prep, k_links_direct), the near-tile
+// bitmap of the opt-in split stream-collide (k_near_mask) and the batched
+// forms of the step kernels.
 #include <climits>
 #include <mutex>
 
@@ -89,12 +93,15 @@ __device__ __forceinline__ void clear_cells_slice(const Dev &D, int parity, int 
 }
 
 // One CTA per particle.  Phases:
-//  0. clear the particle's zone one step back in the owner map that the
+//  0. clear this CTA's share of the screening grid the update fills next,
+//     and the particle's zone one step back in the owner map that the
 //     raster fills next;
 //  1. the warps read the owner map over the particle's window (zone plus
 //     the two-node margin of the bounce-back stencil) and record per row a
 //     fluid mask and an owned-by-this-particle mask (one ballot per 32
-//     nodes); a warp prefetches into L2 the owner rows of the particle
+//     nodes); thread 0 publishes the particle's screening record (and the
+//     FP64 frame of an ellipse); a warp prefetches into L2 the owner rows of
+//     the particle
 //     `ahead` places later in launch order (one residency wave ahead).
 //     (Prefetching the populations of that particle's window as well, by
 //     tensor or row prefetches, or of this particle's links as they are
@@ -389,7 +396,8 @@ __device__ __forceinline__ double repulsion(double gap, double s, double eps, do
 // blocks let four of them share an SM, so that the latency of one block's
 // loads and FP64 tail overlaps the others' work.  Integration:
 // U' = U + F/M, X' = X + (U + U')/2, Omega' = Omega + T/I,
-// theta' = theta + (Omega + Omega')/2 with M = rho_p pi r^2 and I = M r^2 / 2.
+// theta' = theta + (Omega + Omega')/2 with M = rho_p pi r^2 and I = M r^2 / 2
+// (M = rho_p pi r b and I = M (r^2 + b^2) / 4 for an ellipse).
 constexpr int kPartTile = 1600;
 constexpr int kPartPerBlock = kPartThreads / 32;
 
@@ -750,10 +758,11 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
 // Owner map: node (i,j) belongs to disk p iff (i - x)^2 + (j - y)^2 <= r^2
 // (exact FP64; for an ellipse u^2 b^2 + v^2 a^2 <= a^2 b^2 in its frame);
 // where particles overlap the highest index wins (atomicMax, so
-// the result does not depend on the launch order).  One warp per disk, one
-// lane per zone row: the predicate holds on one contiguous run of each row
-// (it is monotone in |i - x|), so the run is found from an FP32 estimate of
-// its ends and settled with the exact predicate at the ends only.
+// the result does not depend on the launch order).  One warp per particle,
+// one lane per zone row: the predicate holds on one contiguous run of each
+// row (it is monotone in |i - x|), so the run is found from an FP32 estimate
+// of its ends and settled with the exact predicate at the ends only; the
+// runs are then written row by row with coalesced atomicMax requests.
 
 __device__ __forceinline__ void raster_body(const Dev &D, int *own, const GeomRec *__restrict__ geo,
                                             const PartSoA &pos, const int blk)
@@ -999,8 +1008,8 @@ __global__ void __launch_bounds__(kBoxThreads, 9)
 }
 
 // ---- batched kernels: one grid over all instances (InstArgs table, block
-// offsets `start`).  The link kernel's look-ahead prefetch stays within the
-// instance and uses per-row L2 prefetches instead of a tensor map.
+// offsets `start`).  The link kernel's look-ahead owner-row prefetch stays
+// within the instance.
 template <typename T>
 __global__ void __launch_bounds__(kLinkThreads, kLinkCtasPerSm)
     k_links_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity, int ahead)
