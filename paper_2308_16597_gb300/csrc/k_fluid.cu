@@ -1,6 +1,6 @@
 // Fused pull-stream + MRT collision of the flow (D2Q9) and temperature (D2Q5)
-// distributions with Boussinesq buoyancy (Sec. 2.1, Eq. f and Eq. g), with the
-// refilling of newborn nodes (Sec. 2.5) folded into the pull.
+// distributions with Boussinesq buoyancy (Sec. 2.1, Eq. f and Eq. g), and the
+// refilling of newborn nodes (Sec. 2.5) on the general path.
 //
 // Layout: 14 planes (9 flow deviations f~ = f - w, 5 temperature populations
 // g) of [ny][pitch] elements (FP32, BF16 or scaled FP16; arithmetic in FP32),
@@ -13,6 +13,8 @@
 // frame (walls, periodic seams) and newborn nodes take a general (scalar)
 // path in a second, small kernel (k_boundary) that runs concurrently with
 // the streaming kernel and keeps that code and its registers out of it.
+// With 16-bit storage a thread holds two nodes, collided together on paired
+// FP32 instructions.
 #include "lbm_internal.cuh"
 
 namespace lbm {
