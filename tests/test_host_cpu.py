@@ -64,6 +64,39 @@ def test_served_stream_matches_its_recipe():
     _valid_layout(s[0][1])
 
 
+def test_paper_shaped_benchmark_matches_its_recipe():
+    """60 lines of 80 disks of diameter 40 on a 50 l.u. lattice in the upper
+    part of the 4000^2 cavity: 37.7 % solid, clear of the walls and of each
+    other by more than the repulsion range."""
+    wl = W.paper_4800()
+    p = wl.particles
+    assert len(p) == 4800 and np.all(p["r"] == 20.0) and np.all(p["b"] == 0.0)
+    assert len(np.unique(p["y"])) == 60 and len(np.unique(p["x"])) == 80
+    assert len(p) * math.pi * 20.0 ** 2 / (4000.0 * 4000.0) == pytest.approx(0.377, abs=5e-4)
+    assert np.all(p["x"] - 20.0 > W.S_REP) and np.all(p["x"] + 20.0 < 3999.0 - W.S_REP)
+    assert np.all(p["y"] + 20.0 < 3999.0 - W.S_REP) and p["y"].min() > 1000.0
+    # nearest neighbours on the lattice are 50 apart: a gap of 10 l.u.
+    assert np.diff(np.unique(p["x"])).min() == 50.0 and np.diff(np.unique(p["y"])).min() == 50.0
+    prm = wl.params
+    assert prm["nu"] / prm["alpha"] == pytest.approx(5.0) and np.all(p["rho"] == 1.1)
+
+
+def test_ellipse_cluster_matches_its_recipe():
+    """One ellipse at (W/2, 3H/4) and rings of 6, 12, 18, 24, 31, 37 around
+    it; semi-axes 25 and 12.5; circumscribed circles clear of each other."""
+    wl = W.ellipse_cluster_129()
+    p = wl.particles
+    assert len(p) == 129 and np.all(p["r"] == 25.0) and np.all(p["b"] == 12.5)
+    dist = np.hypot(p["x"] - 500.0, p["y"] - 1500.0)
+    rings = np.round(dist / 56.0).astype(int)
+    assert np.array_equal(np.bincount(rings), [1, 6, 12, 18, 24, 31, 37])
+    d = np.hypot(p["x"][:, None] - p["x"][None], p["y"][:, None] - p["y"][None])
+    np.fill_diagonal(d, np.inf)
+    assert d.min() >= 50.0 + W.S_REP
+    assert np.all((p["theta"] >= 0.0) & (p["theta"] < math.pi))
+    assert len(p) * math.pi * 25.0 * 12.5 / (1000.0 * 2000.0) == pytest.approx(0.063, abs=5e-4)
+
+
 def test_weighted_percentile():
     import bench
     v = [3.0, 1.0, 2.0, 10.0]
