@@ -392,7 +392,8 @@ __device__ __forceinline__ double repulsion(double gap, double s, double eps, do
 // pairs in reach from double-float centre differences, summed in 64-bit
 // fixed point so that the result is the same whichever way the pairs were
 // found and in whatever order; lane l of warp 0 then sums, integrates and
-// stores particle l in FP64 and enters it in the next step's grid.  Small
+// stores particle l in FP64, and warp w enters particle w in the next step's
+// grid and rasters it.  Small
 // blocks let four of them share an SM, so that the latency of one block's
 // loads and FP64 tail overlaps the others' work.  Integration:
 // U' = U + F/M, X' = X + (U + U')/2, Omega' = Omega + T/I,
@@ -592,9 +593,8 @@ struct RasterIn {
 };
 
 // FP64 tail of the particle update for particle b: total force, Newton-Euler
-// step, domain checks, new state and geometry record, and the entry of the
-// new position in the screening grid of the next step.  (pfx, pfy: the pair
-// repulsion; out: the new state for the raster.)
+// step, domain checks, new state and geometry record.  (pfx, pfy: the pair
+// repulsion; out: the new state for the raster and the next screening grid.)
 __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, double pfx, double pfy, RasterIn &out)
 {
     double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
@@ -662,7 +662,6 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, d
     D.geo_nxt[b] = Gn;
     out.G = Gn;
     out.x = x; out.y = y; out.r = r; out.th = th; out.b = pb;
-    cell_insert(D, D.cells[parity ^ 1], b, Gn.xh, Gn.yh);
 }
 
 __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *own_nxt, const int blk)
@@ -749,6 +748,9 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
     __syncthreads();
     if (a < D.np) {
         const RasterIn &R = sras[warp];
+        // the new position into the next step's screening grid (its atomic
+        // round trip overlaps the raster)
+        if (lane == 0) cell_insert(D, D.cells[parity ^ 1], a, R.G.xh, R.G.yh);
         raster_one(D, own_nxt, R.G, R.x, R.y, R.r, R.th, R.b, a);
     }
 }
