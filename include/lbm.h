@@ -168,6 +168,13 @@ int lbm_get_fields(lbm_handle *h, float *drho, float *ux, float *uy, float *T, i
 
 /* Copy the particle states (host, n entries) after synchronising. */
 int lbm_get_particles(lbm_handle *h, lbm_particle *out, int32_t n);
+/* The same copy, enqueued on the handle's stream after the steps enqueued so
+ * far; the call returns at once.  out (host, n entries; page-locked for the
+ * copy to overlap the following steps) holds the states once the stream has
+ * reached the copy, e.g. after lbm_sync, which also reports device errors;
+ * calls are ordered on the stream.  Errors: LBM_EINVAL, or a sticky error
+ * already reported. */
+int lbm_get_particles_async(lbm_handle *h, lbm_particle *out, int32_t n);
 
 /* Hydrodynamic force (Fx, Fy) and torque Tz of the last step, 3 doubles per
  * particle (host), after synchronising. */

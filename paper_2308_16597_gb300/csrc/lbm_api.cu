@@ -587,6 +587,19 @@ int lbm_get_particles(lbm_handle *h, lbm_particle *out, int32_t n)
     return sync_status(h);
 }
 
+int lbm_get_particles_async(lbm_handle *h, lbm_particle *out, int32_t n)
+{
+    if (!h || n != h->np || (n > 0 && !out)) return LBM_EINVAL;
+    if (h->sticky) return h->sticky;
+    if (n > 0) {
+        lbm_particle *pk = reinterpret_cast<lbm_particle *>(h->ws + h->L.pack);
+        CK(h, launch_pack_particles(h->D, pk, h->stream));
+        CK(h, cudaMemcpyAsync(out, pk, (size_t)n * sizeof(lbm_particle), cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
+    return LBM_OK;
+}
+
 int lbm_get_forces(lbm_handle *h, double *out, int32_t n)
 {
     if (!h || n != h->np || (n > 0 && !out)) return LBM_EINVAL;

@@ -61,6 +61,7 @@ _SIGS = [
     ("lbm_sync", C.c_int, [_P]),
     ("lbm_get_fields", C.c_int, [_P, _P, _P, _P, _P, C.c_int32]),
     ("lbm_get_particles", C.c_int, [_P, _P, C.c_int32]),
+    ("lbm_get_particles_async", C.c_int, [_P, _P, C.c_int32]),
     ("lbm_get_forces", C.c_int, [_P, _P, C.c_int32]),
     ("lbm_destroy", C.c_int, [_P]),
     ("lbm_strerror", C.c_char_p, [C.c_int]),
@@ -194,6 +195,13 @@ def lbm_get_fields(h, drho_ptr, ux_ptr, uy_ptr, T_ptr, on_device: int):
 def lbm_get_particles(h, out: np.ndarray):
     _check(library().lbm_get_particles(h, out.ctypes.data if len(out) else None, len(out)),
            "lbm_get_particles")
+
+
+def lbm_get_particles_async(h, out: np.ndarray):
+    """Enqueue the copy of the particle states into out (page-locked for
+    overlap); valid after lbm_sync."""
+    _check(library().lbm_get_particles_async(h, out.ctypes.data if len(out) else None, len(out)),
+           "lbm_get_particles_async")
 
 
 def lbm_get_forces(h, out: np.ndarray, n: int):

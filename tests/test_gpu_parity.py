@@ -267,6 +267,22 @@ def test_checkpoint_restore_is_bit_exact():
     assert np.array_equal(a.particles(), b.particles())
 
 
+def test_async_particle_read_back_equals_the_synchronous_one():
+    wl = W.parity_256()
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    pinned = torch.empty(len(wl.particles) * lbm.PARTICLE_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+    view = pinned.numpy().view(lbm.PARTICLE_DTYPE)
+    snaps = []
+    for _ in range(3):
+        sim.step(7)
+        lbm.lbm_get_particles_async(sim.h, view)
+        sim.sync()
+        snaps.append(view.copy())
+        assert view.tobytes() == sim.particles().tobytes()
+    assert snaps[0].tobytes() != snaps[2].tobytes()  # the disks moved
+    sim.close()
+
+
 def test_workspace_too_small_is_rejected():
     wl = W.parity_256()
     d = lbm.make_domain(**wl.domain)
