@@ -216,27 +216,56 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
     for (int w = tid; w < nw; w += kLinkThreads) occ[w] = 0u;
     __syncthreads();
 
-    // ---- 2. link detection: thread (k, b), one mask intersection per row;
-    // items run direction-major, so that a warp mostly holds one direction
+    // ---- 2. link detection: item (k, b), one mask intersection per row;
+    // items run direction-major.  A warp's links are spread evenly over its
+    // lanes (a prefix sum of the items' bit counts; lane j takes the j-th
+    // link of the warp), since a few rows (the flat top and bottom of a disk
+    // for e2 / e4) hold many links and most hold one
     {
+        const unsigned F = 0xffffffffu;
         const unsigned long long Z = ((1ull << N) - 1ull) << off;
-        for (int e = tid; e < 8 * N; e += kLinkThreads) {
-            const int k = 1 + e / N, b = e - (k - 1) * N;
-            const int kx = ex(k), ky = ey(k);
-            const unsigned long long o = Om[b + 2 + ky];
-            unsigned long long m = Fm[b + 2] & (kx > 0 ? o >> 1 : kx < 0 ? o << 1 : o) & Z;
-            while (m) {
-                const int c = __ffsll((long long)m) - 1;
-                m &= m - 1ull;
-                const int a = c - off;
-                const int sl = slot_of(k, a, b, N);
+        for (int e0 = warp * 32; e0 < 8 * N; e0 += kLinkThreads) {
+            const int e = e0 + lane;
+            unsigned long long m = 0ull;
+            int k = 1, b = 0;
+            if (e < 8 * N) {
+                k = 1 + e / N;
+                b = e - (k - 1) * N;
+                const int kx = ex(k), ky = ey(k);
+                const unsigned long long o = Om[b + 2 + ky];
+                m = Fm[b + 2] & (kx > 0 ? o >> 1 : kx < 0 ? o << 1 : o) & Z;
+            }
+            const int cnt = __popcll(m);
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(F, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const int total = __shfl_sync(F, inc, 31), excl = inc - cnt;
+            for (int j0 = 0; j0 < total; j0 += 32) {
+                const int j = j0 + lane;
+                // the item holding link j: the last lane whose first link is
+                // at or before j
+                int l = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int ec = __shfl_sync(F, excl, l + step);
+                    if (ec <= j) l += step;
+                }
+                unsigned long long ml = __shfl_sync(F, m, l);
+                const int kl = __shfl_sync(F, k, l), bl = __shfl_sync(F, b, l), el = __shfl_sync(F, excl, l);
+                if (j >= total) continue;
+                for (int t = j - el; t > 0; --t) ml &= ml - 1ull; // drop the lower links of the item
+                const int a = (__ffsll((long long)ml) - 1) - off;
+                const int sl = slot_of(kl, a, bl, N);
                 if (sl < 0) {
                     s_over = 1u;
                     continue;
                 }
                 const unsigned bit = 1u << (sl & 31);
                 if (atomicOr(&occ[sl >> 5], bit) & bit) s_over = 1u;
-                else info[sl] = k | (a << 4) | (b << 12);
+                else info[sl] = kl | (a << 4) | (bl << 12);
             }
         }
     }
