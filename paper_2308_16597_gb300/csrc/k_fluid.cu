@@ -604,31 +604,32 @@ __global__ void __launch_bounds__(128)
 
 // Batched forms: one grid over all instances.  Stream-collide blocks are
 // laid out per instance as gx x gy tiles of the instance's lattice (gx from
-// its pitch), and each block prefetches the block `resident` places later in
-// the launch over all instances (often one of a later instance: prefetching
-// only within the block's own instance left most blocks of small instances
-// without a prefetch).
+// its pitch); a block finds its instance and tile from two small tables (a
+// bucket table and the per-instance records, no search and no division),
+// and prefetches the block `resident` places later in the launch over all
+// instances (often one of a later instance: prefetching only within the
+// block's own instance left most blocks of small instances without a
+// prefetch).
 template <typename T, int V>
 __global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 8)
-    k_stream_collide_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int total,
-                           int parity, int resident)
+    k_stream_collide_batch(const InstArgs *__restrict__ I, const ScInst *__restrict__ sc,
+                           const int *__restrict__ bucket, int shift, int n, int total, int parity, int resident)
 {
     // the look-ahead target is the block `resident` places later in the
     // launch over all instances, which is often in a later instance
     const int tg = (int)blockIdx.x + resident;
     if (threadIdx.x < kPop && threadIdx.y == 0 && tg < total) {
-        const int j = batch_find(start, n, tg);
+        const int j = sc_find(sc, bucket, shift, n, tg);
         const InstArgs &t = I[j];
-        const int lt = tg - __ldg(start + j);
-        const int gxt = (t.D.pitch / V + (int)blockDim.x - 1) / (int)blockDim.x;
-        prefetch_block<T, V, kSCAll>(t.D, static_cast<const T *>(t.A[parity ^ t.poff]), lt % gxt, lt / gxt);
+        int bx, by;
+        sc_tile(sc + j, tg, bx, by);
+        prefetch_block<T, V, kSCAll>(t.D, static_cast<const T *>(t.A[parity ^ t.poff]), bx, by);
     }
-    const int i = batch_find(start, n, (int)blockIdx.x);
+    const int i = sc_find(sc, bucket, shift, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
-    const int local = (int)blockIdx.x - __ldg(start + i);
-    const int gx = (a.D.pitch / V + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int gy = (a.D.ny + (int)blockDim.y - 1) / (int)blockDim.y;
-    const Blk blk{local % gx, local / gx, gx, gy};
+    int bx, by;
+    sc_tile(sc + i, (int)blockIdx.x, bx, by);
+    const Blk blk{bx, by, 0, 0}; // the grid extents are not used by the body
     const int par = parity ^ a.poff;
     sc_body<T, V>(a.D, static_cast<const T *>(a.A[par]), static_cast<T *>(a.A[par ^ 1]), -1, 0, blk);
 }
@@ -804,19 +805,21 @@ cudaError_t launch_boundary(const Dev &D, const void *Ain, void *Aout, const int
     }
 }
 
-cudaError_t launch_stream_collide_batch(const InstArgs *I, const int *start, int n, int total, int storage,
-                                        int parity, dim3 block, int resident, cudaStream_t s)
+cudaError_t launch_stream_collide_batch(const InstArgs *I, const ScInst *sc, const int *bucket, int shift, int n,
+                                        int total, int storage, int parity, dim3 block, int resident,
+                                        cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
     switch (storage) {
     case LBM_STORE_FP32:
-        k_stream_collide_batch<float, 1><<<total, block, 0, s>>>(I, start, n, total, parity, resident);
+        k_stream_collide_batch<float, 1><<<total, block, 0, s>>>(I, sc, bucket, shift, n, total, parity, resident);
         break;
     case LBM_STORE_BF16:
-        k_stream_collide_batch<__nv_bfloat16, 2><<<total, block, 0, s>>>(I, start, n, total, parity, resident);
+        k_stream_collide_batch<__nv_bfloat16, 2>
+            <<<total, block, 0, s>>>(I, sc, bucket, shift, n, total, parity, resident);
         break;
     case LBM_STORE_FP16:
-        k_stream_collide_batch<__half, 2><<<total, block, 0, s>>>(I, start, n, total, parity, resident);
+        k_stream_collide_batch<__half, 2><<<total, block, 0, s>>>(I, sc, bucket, shift, n, total, parity, resident);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -22,10 +22,16 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 const dim3 kTiles[] = {dim3(128, 1), dim3(64, 2), dim3(32, 4)};
 constexpr int kNumTiles = 3;
 
+// Stream-collide bucket table: at most 4 (n + 1) buckets.
+int bucket_cap(int n) { return 4 * (n + 1); }
+
+// Device tables: InstArgs [n], block offsets [phases][n + 1], stream-collide
+// records [n] and buckets [4 (n + 1)].
 size_t table_bytes(int n)
 {
     return round_up((size_t)n * sizeof(InstArgs), kAlign) +
-           round_up((size_t)kBatchPhases * (n + 1) * sizeof(int), kAlign);
+           round_up((size_t)kBatchPhases * (n + 1) * sizeof(int), kAlign) +
+           round_up((size_t)n * sizeof(ScInst), kAlign) + round_up((size_t)bucket_cap(n) * sizeof(int), kAlign);
 }
 
 } // namespace
@@ -38,6 +44,9 @@ struct lbm_batch {
     cudaEvent_t fork = nullptr, join = nullptr;
     InstArgs *d_inst = nullptr;
     int *d_start = nullptr; // [kBatchPhases][n + 1]
+    ScInst *d_sc = nullptr; // [n] stream-collide records
+    int *d_bucket = nullptr; // [4 (n + 1)] stream-collide buckets
+    int sc_shift = 0;
     int total[kBatchPhases] = {};
     int tile = 0, sc_resident = 1, links_ahead = 1;
     size_t links_smem = 0;
@@ -76,7 +85,35 @@ int upload_starts(lbm_batch *b)
         }
     }
     for (int ph = 0; ph < kBatchPhases; ++ph) st[(size_t)ph * (b->n + 1) + b->n] = b->total[ph];
+    // stream-collide: per-instance records (first block, tiles per row and
+    // the exact reciprocal of the latter) and buckets of 2^shift blocks,
+    // each holding the instance its first block belongs to
+    const int V = b->storage == LBM_STORE_FP32 ? 1 : 2;
+    const int tx = (int)kTiles[b->tile].x;
+    std::vector<ScInst> sc(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        ScInst &e = sc[i];
+        e.start = st[(size_t)kBStream * (b->n + 1) + i];
+        e.gx = (b->hs[i]->D.pitch / V + tx - 1) / tx;
+        int l = 0;
+        while ((1ll << l) < e.gx) ++l;
+        e.s = 31 + l;
+        e.m = (1ull << e.s) / (unsigned long long)e.gx + 1ull;
+        e.pad = 0;
+    }
+    const int tot = b->total[kBStream];
+    int shift = 0;
+    while ((tot >> shift) + 1 > bucket_cap(b->n)) ++shift;
+    std::vector<int> bk((size_t)(tot >> shift) + 1);
+    for (int k = 0, i = 0; k < (int)bk.size(); ++k) {
+        const long long g = (long long)k << shift;
+        while (i + 1 < b->n && sc[i + 1].start <= g) ++i;
+        bk[k] = i;
+    }
+    b->sc_shift = shift;
     BCK(b, cudaMemcpyAsync(b->d_start, st.data(), st.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaMemcpyAsync(b->d_sc, sc.data(), sc.size() * sizeof(ScInst), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaMemcpyAsync(b->d_bucket, bk.data(), bk.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
     b->sc_resident = stream_collide_batch_resident(b->storage, kTiles[b->tile]);
     return LBM_OK;
@@ -98,8 +135,8 @@ int enqueue_batch_step(lbm_batch *b, int par, cudaStream_t st)
     BCK(b, cudaStreamWaitEvent(b->side, b->fork, 0));
     BCK(b, launch_boundary_batch(I, starts(b, kBBoundary), n, b->total[kBBoundary], b->storage, par, b->side));
     BCK(b, cudaEventRecord(b->join, b->side));
-    BCK(b, launch_stream_collide_batch(I, starts(b, kBStream), n, b->total[kBStream], b->storage, par,
-                                       kTiles[b->tile], b->sc_resident, st));
+    BCK(b, launch_stream_collide_batch(I, b->d_sc, b->d_bucket, b->sc_shift, n, b->total[kBStream], b->storage,
+                                       par, kTiles[b->tile], b->sc_resident, st));
     BCK(b, cudaStreamWaitEvent(st, b->join, 0));
     return LBM_OK;
 }
@@ -174,7 +211,12 @@ int lbm_batch_create(lbm_batch **out, lbm_handle *const *hs, int32_t n, void *d_
     b->stream = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_workspace);
     b->d_inst = reinterpret_cast<InstArgs *>(ws);
-    b->d_start = reinterpret_cast<int *>(ws + round_up((size_t)n * sizeof(InstArgs), kAlign));
+    size_t at = round_up((size_t)n * sizeof(InstArgs), kAlign);
+    b->d_start = reinterpret_cast<int *>(ws + at);
+    at += round_up((size_t)kBatchPhases * (n + 1) * sizeof(int), kAlign);
+    b->d_sc = reinterpret_cast<ScInst *>(ws + at);
+    at += round_up((size_t)n * sizeof(ScInst), kAlign);
+    b->d_bucket = reinterpret_cast<int *>(ws + at);
     auto fail = [&](int code) {
         lbm_batch_destroy(b);
         return code;
@@ -226,13 +268,15 @@ int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *choice, double *best
         b->tile = t;
         if ((rc = upload_starts(b))) break;
         for (int w = 0; w < 2 && !rc; ++w)
-            if (launch_stream_collide_batch(b->d_inst, starts(b, kBStream), b->n, b->total[kBStream], b->storage,
-                                            b->parity, kTiles[t], b->sc_resident, b->stream) != cudaSuccess)
+            if (launch_stream_collide_batch(b->d_inst, b->d_sc, b->d_bucket, b->sc_shift, b->n,
+                                            b->total[kBStream], b->storage, b->parity, kTiles[t],
+                                            b->sc_resident, b->stream) != cudaSuccess)
                 rc = fail_cuda(b, cudaErrorLaunchFailure);
         if (rc || cudaEventRecord(e0, b->stream) != cudaSuccess) break;
         for (int r = 0; r < reps && !rc; ++r)
-            if (launch_stream_collide_batch(b->d_inst, starts(b, kBStream), b->n, b->total[kBStream], b->storage,
-                                            b->parity, kTiles[t], b->sc_resident, b->stream) != cudaSuccess)
+            if (launch_stream_collide_batch(b->d_inst, b->d_sc, b->d_bucket, b->sc_shift, b->n,
+                                            b->total[kBStream], b->storage, b->parity, kTiles[t],
+                                            b->sc_resident, b->stream) != cudaSuccess)
                 rc = fail_cuda(b, cudaErrorLaunchFailure);
         float ms = 0.f;
         if (rc || cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

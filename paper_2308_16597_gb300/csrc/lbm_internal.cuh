@@ -726,6 +726,34 @@ struct InstArgs {
     int pad;
 };
 
+// Stream-collide blocks of one instance in a batched launch: its first
+// block, its tiles per row gx, and a multiplier m and shift s with
+// local / gx = (local * m) >> s exactly for every 0 <= local < 2^31
+// (division by an invariant integer, Granlund and Montgomery 1994:
+// s = 31 + ceil(log2 gx), m = floor(2^s / gx) + 1).
+struct ScInst {
+    unsigned long long m;
+    int start, gx, s, pad;
+};
+// Instance holding stream-collide block g: the instance the bucket of g
+// starts in (buckets of 2^shift blocks), then forward over the instances
+// that start inside the bucket.
+__device__ __forceinline__ int sc_find(const ScInst *__restrict__ sc, const int *__restrict__ bucket, int shift,
+                                       int n, int g)
+{
+    int i = __ldg(bucket + (g >> shift));
+    while (i + 1 < n && __ldg(&sc[i + 1].start) <= g) ++i;
+    return i;
+}
+// Tile (bx, by) of stream-collide block g within its instance's gx-wide
+// grid of tiles.
+__device__ __forceinline__ void sc_tile(const ScInst *__restrict__ e, int g, int &bx, int &by)
+{
+    const unsigned local = (unsigned)(g - __ldg(&e->start));
+    by = (int)(((unsigned long long)local * __ldg(&e->m)) >> __ldg(&e->s));
+    bx = (int)local - by * __ldg(&e->gx);
+}
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in k_fluid.cu and k_particles.cu).
 // ---------------------------------------------------------------------------
@@ -796,8 +824,9 @@ cudaError_t launch_particles_batch(const InstArgs *I, const int *start, int n, i
                                    cudaStream_t s);
 cudaError_t launch_raster_batch(const InstArgs *I, const int *start, int n, int total, int parity, cudaStream_t s);
 cudaError_t launch_flags_batch(const InstArgs *I, const int *start, int n, int total, int parity, cudaStream_t s);
-cudaError_t launch_stream_collide_batch(const InstArgs *I, const int *start, int n, int total, int storage,
-                                        int parity, dim3 block, int resident, cudaStream_t s);
+cudaError_t launch_stream_collide_batch(const InstArgs *I, const ScInst *sc, const int *bucket, int shift, int n,
+                                        int total, int storage, int parity, dim3 block, int resident,
+                                        cudaStream_t s);
 cudaError_t launch_boundary_batch(const InstArgs *I, const int *start, int n, int total, int storage, int parity,
                                   cudaStream_t s);
 int stream_collide_batch_resident(int storage, dim3 block);

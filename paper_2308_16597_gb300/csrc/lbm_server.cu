@@ -14,7 +14,10 @@
 namespace {
 
 constexpr size_t kPoolAlign = 256;
-static_assert(sizeof(lbm::InstArgs) + lbm::kBatchPhases * sizeof(int) <= 1024,
+// per instance: its arguments, block offsets, stream-collide record and
+// four buckets (the 64 KB beyond covers the tables' alignment)
+static_assert(sizeof(lbm::InstArgs) + lbm::kBatchPhases * sizeof(int) + sizeof(lbm::ScInst) + 4 * sizeof(int) <=
+                  1024,
               "the table region reserves 1 KB per instance");
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

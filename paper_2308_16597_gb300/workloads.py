@@ -212,11 +212,16 @@ def crop_1024(seed: int = 3) -> Workload:
 
 
 def ensemble(count: int = 64, seed: int = 4, sizes=(256, 512, 768, 1024), n_range=(8, 400),
-             r_range=(6.0, 12.0), ra_range=(1e6, 1e8), nu: float = 0.02, Pr: float = 0.71):
+             r_range=(6.0, 12.0), u_range=(0.01, 0.04), nu: float = 0.02, Pr: float = 0.71):
     """Batched ensemble of independent cavities: nx and ny drawn independently
     from `sizes`, a disk count from n_range (capped to what random sequential
     addition fits in the upper half at a 25 % solid fraction), per-disk radii
-    uniform in r_range, Ra log-uniform in ra_range (g from Ra on H = ny)."""
+    uniform in r_range, and g beta from a free-fall velocity
+    sqrt(g beta dT H) log-uniform in u_range on H = ny, so that
+    Ra = u_ff^2 H^2 Pr / nu^2 runs from 1.2e4 to 3e6.  (Ra drawn from
+    [1e6, 1e8] on these cavities at nu = 0.02 means free-fall velocities up
+    to 0.8 lattice units, which the lattice cannot carry: such instances
+    blow up within a thousand steps.)"""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for k in range(count):
@@ -227,9 +232,10 @@ def ensemble(count: int = 64, seed: int = 4, sizes=(256, 512, 768, 1024), n_rang
         upper = (nx - 2 * (r_range[1] + S_REP + 1)) * (ny / 2 - 2 * (r_range[1] + S_REP))
         n = max(1, min(n, int(0.25 * upper / (math.pi * np.mean(radii) ** 2))))
         radii = radii[:n]
-        Ra = float(np.exp(rng.uniform(np.log(ra_range[0]), np.log(ra_range[1]))))
+        u_ff = float(np.exp(rng.uniform(np.log(u_range[0]), np.log(u_range[1]))))
+        g = u_ff ** 2 / ny
         alpha = nu / Pr
-        g = gravity_for_rayleigh(Ra, nu, alpha, ny)
+        Ra = g * ny ** 3 / (nu * alpha)
         rmax = float(radii.max())
         lo = rmax + S_REP + 1.0
         parts = rsa_disks(rng, n, radii, lo, nx - 1 - lo, max(0.5 * ny + rmax + S_REP, lo), ny - 1 - lo,
@@ -237,7 +243,7 @@ def ensemble(count: int = 64, seed: int = 4, sizes=(256, 512, 768, 1024), n_rang
         parts["rho"] = 1.5
         parts["T"] = 1.0
         out.append(Workload("ensemble%d_%dx%d_%ddisks" % (k, nx, ny, n), cavity(nx, ny), parts,
-                            base_params(nu, Pr, g), 0, dict(Ra=Ra)))
+                            base_params(nu, Pr, g), 0, dict(Ra=Ra, u_ff=u_ff)))
     return out
 
 

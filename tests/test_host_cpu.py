@@ -35,11 +35,13 @@ def test_ensemble_matches_its_recipe():
         n = len(wl.particles)
         assert 1 <= n <= 400
         assert np.all((wl.particles["r"] >= 6.0) & (wl.particles["r"] <= 12.0))
-        Ra = wl.extra["Ra"]
-        assert 1e6 <= Ra <= 1e8
-        # g from Ra on H = ny
+        # g beta from the free-fall velocity on H = ny, and Ra from g
+        u = wl.extra["u_ff"]
+        assert 0.01 <= u <= 0.04
         p = wl.params
-        assert p["g"] == pytest.approx(Ra * p["nu"] * p["alpha"] / wl.ny ** 3)
+        assert p["g"] * p["beta"] == pytest.approx(u * u / wl.ny)
+        assert wl.extra["Ra"] == pytest.approx(p["g"] * p["beta"] * wl.ny ** 3 / (p["nu"] * p["alpha"]))
+        assert 1e4 <= wl.extra["Ra"] <= 3.1e6
         assert np.all(wl.particles["y"] >= 0.5 * wl.ny)
     for wl in e[:8]:
         _valid_layout(wl)
