@@ -403,12 +403,14 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
             return; // the other pass's tile (uniform across the warp)
     const bool act = x0 < D.pitch; // the pitch is a multiple of 32, so all V nodes are in the row
     float c[V][kPop];
-    // A warp whose nodes and their neighbours all lie strictly inside the
-    // cavity (the common case) pulls without any wall, seam or range test.
-    // (Letting the first and last warp of a row in as well, with range-checked
-    // edge loads, measured slower on small cavities.)
-    const int xw = x0 - lane * V; // first node of the warp (a warp spans one row)
-    const bool interior = y >= 1 && y + 1 < D.ny && xw >= 1 && xw + 32 * V + 1 <= D.nx;
+    // A warp off the first and last row (the common case) pulls without any
+    // wall, seam or range test.  In the first and last warp of a row, the
+    // reads past the row's ends (x = -1, x >= nx, lanes past the pitch) land
+    // in the previous plane (every plane with e_x = 1 has index p >= 1), the
+    // next row or the buffer's tail pad, so they stay inside the allocation;
+    // the values they bring feed only the frame nodes x = 0 and x = nx - 1,
+    // which k_boundary writes, and the padding past nx, which is zeroed.
+    const bool interior = y >= 1 && y + 1 < D.ny;
     if (interior) {
         const T *b0 = Ain + (long long)y * D.pitch + x0;
 #pragma unroll

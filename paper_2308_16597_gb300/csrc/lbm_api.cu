@@ -16,6 +16,7 @@ using namespace lbm;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr size_t kDistTailPad = 256; // bytes after each distribution buffer
 constexpr size_t kStageBytes = size_t(4) << 20;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -96,7 +97,9 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
         return o;
     };
     const size_t nn = (size_t)d->nx * d->ny;
-    for (int b = 0; b < 2; ++b) L.A[b] = take((size_t)kPop * L.ps * storage_bytes(storage));
+    // each distribution buffer has a tail pad: the stream-collide fast path
+    // reads up to 33 elements past the last row of the last plane
+    for (int b = 0; b < 2; ++b) L.A[b] = take((size_t)kPop * L.ps * storage_bytes(storage) + kDistTailPad);
     for (int b = 0; b < 2; ++b) L.own[b] = take(nn * sizeof(int));
     L.flags = take((size_t)L.pitch * d->ny);
     L.slot_node = take(L.nslots * sizeof(int));
