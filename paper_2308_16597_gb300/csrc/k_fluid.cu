@@ -479,10 +479,12 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
         // both nodes collided at once on paired FP32 instructions; solid
         // nodes (and the padding past nx) are zeroed after
         bool fluid[2];
+        // both nodes' flags in one 2-byte load (x0 is even)
+        const unsigned short fl2 = *reinterpret_cast<const unsigned short *>(D.flags + (long long)y * D.pitch + x0);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int x = x0 + k;
-            const uint8_t fl = D.flags[(long long)y * D.pitch + x];
+            const unsigned fl = (fl2 >> (8 * k)) & 0xffu;
             fluid[k] = x < D.nx && fl != kSolid;
             // frame and newborn nodes belong to k_boundary, which writes them
             gen[k] = fluid[k] && (fl == kNewborn || y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1);
@@ -495,8 +497,15 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
         collide_t<float2>(D, cc, ok0, ok1);
 #pragma unroll
         for (int p = 0; p < kPop; ++p) {
-            c[0][p] = fluid[0] ? cc[p].x : 0.f;
-            c[1][p] = fluid[1] ? cc[p].y : 0.f;
+            c[0][p] = cc[p].x;
+            c[1][p] = cc[p].y;
+        }
+        if (!(fluid[0] && fluid[1])) { // solid nodes and the padding past nx hold zeros
+#pragma unroll
+            for (int p = 0; p < kPop; ++p) {
+                if (!fluid[0]) c[0][p] = 0.f;
+                if (!fluid[1]) c[1][p] = 0.f;
+            }
         }
         ok = (!fluid[0] || gen[0] || ok0) && (!fluid[1] || gen[1] || ok1);
     } else {
