@@ -169,6 +169,42 @@ def test_slots_match_brute_force_links_for_random_radii(seed):
     assert sim.counters()[7] == len(bn)
 
 
+def test_largest_supported_disks_slots_and_forces():
+    """Radii 28.0 and 28.4: link windows of 63 and 64 columns (zones of 59 and
+    60 nodes plus the two-node margins), the limit of the 64-bit row masks, so
+    both 32-column ballot words of every row are in use.  Owner map, slots and
+    q bit-exact / within 1e-6, every brute-force link found, first-step
+    forces and fields as for the small disks."""
+    nx, ny = 200, 160
+    parts = np.zeros(2, W.PARTICLE_DTYPE)
+    parts["x"], parts["y"] = [55.3, 140.6], [80.2, 78.9]
+    parts["r"] = [28.0, 28.4]
+    parts["rho"], parts["T"] = 1.5, 1.0
+    assert [orc.zone_size(r) + 4 for r in parts["r"]] == [63, 64]
+    prm = W.base_params(0.05, 0.71, 1e-4, fixed_particles=1)
+    dom = W.cavity(nx, ny)
+    sim = lbm.Simulation(dom, parts, prm)
+    ref = orc.Oracle(dom, parts, prm)
+    own = orc.raster(nx, ny, parts)
+    assert np.array_equal(sim.owner(), own)
+    f, g = W.random_state(nx, ny, 5, *base_f(), amp=1e-2)
+    sim.set_distributions(f, g)
+    ref.set_state(f, g)
+    sim.step(1)
+    ref.step(1)
+    node, q = sim.slots()
+    onode, oq, over = orc.build_slots(nx, ny, own, parts)
+    assert over == 0 and np.array_equal(node, onode)
+    assert same_q(q, oq)
+    bn, bd, bp, bq = orc.links_bruteforce(nx, ny, own, parts)
+    assert (node >= 0).sum() == len(bn) and sim.counters()[7] == len(bn)
+    Fg, Fo = sim.forces(), ref.forces()
+    assert np.abs(Fg[:, :2] - Fo[:, :2]).max() <= 1e-6 * np.abs(Fo[:, :2]).max()
+    assert np.abs(Fg[:, 2] - Fo[:, 2]).max() <= 1e-5 * np.abs(Fo[:, 2]).max()
+    compare_fields(sim, ref, 1e-6)
+    sim.close()
+
+
 # --------------------------------------------------------------------------- coupled
 def test_first_step_forces_match_the_oracle():
     wl = W.parity_256()

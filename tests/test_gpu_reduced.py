@@ -57,6 +57,45 @@ def test_rest_state_is_exact_in_reduced_storage(storage):
 
 
 @pytest.mark.parametrize("storage", ["bf16", "fp16"])
+@pytest.mark.parametrize("shape,periodic", [((257, 64), (1, 0)), ((300, 37), (0, 0)), ((70, 50), (0, 1))])
+def test_ragged_widths_node_by_node(storage, shape, periodic):
+    """With 16-bit storage a thread holds two nodes, so a warp spans 64 nodes;
+    where the pitch (nx rounded up to 32) is an odd multiple of 32 the last
+    warp of each row runs past it, and the first and last warp of a row read
+    past the row's ends.  Node by node, each field stays within a few
+    roundings of its populations: |error| <= 8 u S with S the sum of the
+    node's |f - w| (rho - 1, ux, uy) or |g| (T) in the oracle's state, after
+    1 and 3 steps from a random state.  A single wrongly pulled population
+    moves a field by about S / 5, many times the bound."""
+    nx, ny = shape
+    dom = W.cavity(nx, ny, T_wall=(0.3, 0.8, 1.0, 0.1), periodic_x=periodic[0], periodic_y=periodic[1])
+    prm = W.base_params(0.03, 0.71, 3e-3, body_fx=1e-5)
+    w9, w5 = orc.feq(1.0, 0.0, 0.0), orc.geq(1.0, 0.0, 0.0)
+    f, g = W.random_state(nx, ny, 7, w9, w5, amp=2e-2)
+    sim = lbm.Simulation(dom, None, prm, storage=STORAGE[storage])
+    ref = orc.Oracle(dom, None, prm)
+    sim.set_distributions(f, g)
+    ref.set_state(f, g)
+    u = UNIT_ROUNDOFF[storage]
+    for steps in (1, 3):
+        sim.step(steps)
+        ref.step(steps)
+        fo, go = ref.state()
+        Sf = np.abs(fo - w9[:, None, None]).sum(0)
+        Sg = np.abs(go).sum(0)
+        got, exp = sim.fields(), ref.fields()
+        worst = 0.0
+        for name, a, b, S in zip(("rho-1", "ux", "uy", "T"), got, exp, (Sf, Sf, Sf, Sg)):
+            if name == "rho-1":
+                b = b - 1.0
+            r = np.abs(a.astype(np.float64) - b) / (u * S)
+            worst = max(worst, float(r.max()))
+            assert np.all(r <= 8.0), (name, steps, float(r.max()), np.unravel_index(int(r.argmax()), r.shape))
+        print(storage, shape, steps, "worst error / (u S):", worst)
+    sim.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
 def test_state_bytes_halve(storage):
     wl = W.parity_256()
     a = lbm.Simulation(wl.domain, wl.particles, wl.params)
