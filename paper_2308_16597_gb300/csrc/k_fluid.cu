@@ -284,8 +284,9 @@ __device__ __noinline__ void flush_counters(const Dev &D, int parity, const unsi
 // `ahead` positions later in launch order, where `ahead` is the number of
 // blocks resident on the GPU.  By the time that block runs its loads hit L2,
 // so the memory latency of one wave overlaps the collisions of the previous
-// wave without holding registers.  (Measured on the 4000^2 benchmark case:
-// 0.73 of the copy bandwidth, against 0.56 without the prefetch.)
+// wave without holding registers.  (On the 4000^2 benchmark case, when it
+// was introduced: 0.73 of the copy bandwidth against 0.56 without it, about
+// 53 us per launch.)
 // ---------------------------------------------------------------------------
 constexpr int kSCThreads = 128;
 
@@ -593,7 +594,8 @@ __device__ __forceinline__ void boundary_body(const Dev &D, const T *__restrict_
 
 // Blocks per SM that measured best on the 4000^2 benchmark: FP32 10 (48
 // registers; 268 us against 272 with 8 and 279 with 12), 16-bit storage 8
-// (62 registers; BF16 209 us against 220 with 7 and 219 with 10).
+// (at most 64 registers; before the paired collision, BF16 209 us against
+// 220 with 7 and 219 with 10 blocks).
 template <typename T, int V, int mode>
 __global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 8)
     k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ahead_y, int ahead_x)
