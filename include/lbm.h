@@ -188,10 +188,13 @@ const char *lbm_strerror(int code);
  * -1 for fluid.  Synchronises. */
 int lbm_get_owner(lbm_handle *h, int32_t *out);
 /* Fixed index array of the last step (Sec. 3), host copies: per particle
- * 12N - 12 slots in the order e1..e8, lines within a direction as described
- * in the design notes; node = j*nx + i of the fluid node or -1; q = wall
- * fraction (float).  *count receives the total slot count; cap bounds the
- * copy.  Synchronises. */
+ * 12N - 12 slots in the order e1..e8, and within a direction by line index
+ * in the particle's N x N zone with zone node (a, b): row b for e1/e3 and
+ * column a for e2/e4 (N lines each), a - b + N - 2 for e5/e7 and a + b - 1
+ * for e6/e8 (2N - 3 lines each; the two single-node corner lines of each
+ * diagonal family carry no link and have no slot); node = j*nx + i of the
+ * fluid node or -1; q = wall fraction (float).  *count receives the total
+ * slot count; cap bounds the copy.  Synchronises. */
 int lbm_get_slots(lbm_handle *h, int32_t *node, float *q, int64_t cap, int64_t *count);
 /* Raw state for checkpoint/restore between handles created with identical
  * arguments, in this order: the 14 distribution planes (9 flow deviations

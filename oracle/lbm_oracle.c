@@ -146,9 +146,10 @@ void orc_geq(double T, double ux, double uy, double out[5])
 }
 
 /* Eq. f at one node: m = M f; rho = sum f; u = (sum e f + F/2)/rho (Sec. 2.1);
- * m+ = m - S (m - m_eq) + (I - S/2) F_m; f+ = M^-1 m+.  The equilibrium
- * moments are those of the second-order equilibrium and F_m the moments of
- * the Guo forcing term (readings stated in the design notes). */
+ * m+ = m - S (m - m_eq) + (I - S/2) F_m; f+ = M^-1 m+.  The paper defers M,
+ * m_eq and the forcing to earlier work: M is the Lallemand-Luo D2Q9 basis,
+ * m_eq the moments of the second-order equilibrium and F_m the moments of
+ * the Guo forcing term. */
 static void collide_f(const orc_ops *o, const double f[9], double Fx, double Fy, double out[9])
 {
     double m[9];

@@ -280,6 +280,48 @@ def test_moving_disk_refills_like_the_oracle():
     assert np.abs(pg["x"] - po["x"]).max() < 1e-6
 
 
+def state_flags(sim, nx, ny):
+    """Node flags (0 fluid, 1 solid, 2 newborn) from the raw state image, laid
+    out as include/lbm.h states: 14 FP32 planes of plane_stride elements, the
+    int32 owner map [ny][nx], then the uint8 flags [ny][pitch]."""
+    pitch = (nx + 31) // 32 * 32
+    stride = (pitch * ny + 63) // 64 * 64
+    buf = sim.get_state()
+    off = 14 * stride * 4 + nx * ny * 4
+    return buf[off:off + ny * pitch].reshape(ny, pitch)[:, :nx]
+
+
+def test_node_flags_are_bit_exact():
+    """After every step the flags are the node classes of Sec. 2.3 and 2.5
+    from the owner maps before and after it: solid where a particle holds the
+    node after the step, newborn where one held it before and none does
+    after, fluid elsewhere; both owner maps from the oracle's raster of the
+    GPU's positions.  Two translating disks and a translating, spinning
+    ellipse uncover nodes every step."""
+    parts = np.zeros(3, W.PARTICLE_DTYPE)
+    parts["x"], parts["y"] = [40.3, 90.6, 140.2], [50.2, 47.7, 52.9]
+    parts["r"], parts["b"] = [8.5, 8.5, 11.0], [0.0, 0.0, 5.0]
+    parts["theta"] = [0.0, 0.0, 0.7]
+    parts["rho"], parts["T"] = 1.5, 1.0
+    parts["ux"], parts["uy"] = [0.04, -0.03, 0.02], [-0.02, 0.035, -0.03]
+    parts["omega"] = [0.0, 0.0, 0.02]
+    nx, ny = 180, 100
+    sim = lbm.Simulation(W.cavity(nx, ny), parts, W.base_params(0.05, 0.71, 1e-4))
+    assert np.array_equal(state_flags(sim, nx, ny), (orc.raster(nx, ny, parts) >= 0).astype(np.uint8))
+    newborn = 0
+    for _ in range(25):
+        p0 = sim.particles()
+        sim.step(1)
+        p1 = sim.particles()
+        o0, o1 = orc.raster(nx, ny, p0), orc.raster(nx, ny, p1)
+        exp = np.where(o1 >= 0, 1, np.where(o0 >= 0, 2, 0)).astype(np.uint8)
+        assert np.array_equal(state_flags(sim, nx, ny), exp)
+        assert sim.counters()[6] == (exp == 2).sum()
+        newborn += int((exp == 2).sum())
+    assert newborn > 0
+    sim.close()
+
+
 # --------------------------------------------------------------------------- runtime
 def test_runs_are_deterministic_and_graphs_match_direct_launches():
     wl = W.parity_256()
