@@ -53,8 +53,11 @@ extern "C" {
 #define LBM_ENUMERIC (-3)  /* non-finite density or temperature on the device */
 #define LBM_EDOMAIN (-4)   /* a particle crossed a cavity wall */
 #define LBM_EOVERFLOW (-5) /* a line of the fixed index array holds two links */
-#define LBM_ETIMEOUT (-6)  /* a bounded device wait gave up */
+#define LBM_ETIMEOUT (-6)  /* a bounded device wait gave up (reserved: no kernel of
+                              this library waits on another) */
 #define LBM_ECUDA (-7)     /* a CUDA runtime call failed */
+#define LBM_EBOUNDS (-8)   /* an index outside the buffer it addresses, skipped
+                              (reported only by builds with -DLBM_CHECK) */
 
 /* lbm_domain.bc bits: periodic axes (tests); unset = no-slip walls. */
 #define LBM_BC_PERIODIC_X 1u
@@ -209,7 +212,9 @@ int lbm_get_state(lbm_handle *h, void *host_buf, size_t bytes);
 int lbm_set_state(lbm_handle *h, const void *host_buf, size_t bytes);
 /* Replace the distributions by pre-collision values f[9][ny][nx] and
  * g[5][ny][nx] (host FP64) and collide them, as lbm_init does for its
- * initial state.  Values at solid nodes are ignored.  Synchronises. */
+ * initial state.  Values at solid nodes are ignored; a non-finite or
+ * non-physical value at a fluid node makes the call return LBM_ENUMERIC,
+ * which stays set on the handle (sticky).  Synchronises. */
 int lbm_set_distributions(lbm_handle *h, const double *f, const double *g);
 /* Counters of the last step: [0] Bouzidi quadratic->linear fallbacks,
  * [1] ->simple, [2] thermal ->half-way, [3] refill quadratic->linear,

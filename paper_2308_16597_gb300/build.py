@@ -48,16 +48,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra=None, out: str | None = None) -> str:
+    """Compile and link; returns the library's path.  out: a directory for
+    the objects and the library of a variant build (for instance the
+    bounds-checked one, extra=["-DLBM_CHECK"]), leaving the default build
+    alone."""
+    if out is None and not force and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    os.makedirs(LIBDIR, exist_ok=True)
+    build_dir = BUILD if out is None else os.path.join(out, "_build")
+    lib = LIB if out is None else os.path.join(out, "liblbm_gb300.so")
+    os.makedirs(build_dir, exist_ok=True)
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
     extra = list(extra or [])
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
         if verbose:
@@ -73,11 +79,11 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
             print(text, flush=True)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -399,6 +399,9 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
     const int x0 = (blk.x * (int)blockDim.x + (int)threadIdx.x) * V;
     const int y = blk.y * (int)blockDim.y + (int)threadIdx.y;
     if (y >= D.ny) return; // uniform across the warp: blockDim.x is a multiple of 32
+    // a warp wholly past the pitch (where the grid's last block of a row
+    // overhangs it) has no node: it returns before its first load
+    if (x0 - lane * V >= D.pitch) return;
     if constexpr (mode != kSCAll)
         if (tile_near(D, y, (x0 - (lane * V)) / (32 * V)) != (mode == kSCNear))
             return; // the other pass's tile (uniform across the warp)
@@ -406,10 +409,11 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
     float c[V][kPop];
     // A warp off the first and last row (the common case) pulls without any
     // wall, seam or range test.  In the first and last warp of a row, the
-    // reads past the row's ends (x = -1, x >= nx, lanes past the pitch) land
-    // in the previous plane (every plane with e_x = 1 has index p >= 1), the
-    // next row or the buffer's tail pad, so they stay inside the allocation;
-    // the values they bring feed only the frame nodes x = 0 and x = nx - 1,
+    // reads past the row's ends (x = -1, x >= nx, lanes past the pitch: at
+    // most 32 V + 1 elements, since a warp starts below the pitch) land in
+    // the previous plane (every plane with e_x = 1 has index p >= 1), the
+    // next row or the buffer's tail pad, so they stay inside the buffer; the
+    // values they bring feed only the frame nodes x = 0 and x = nx - 1,
     // which k_boundary writes, and the padding past nx, which is zeroed.
     const bool interior = y >= 1 && y + 1 < D.ny;
     if (interior) {
@@ -419,20 +423,25 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
             const int d = pdir(p);
             const int dx = ex(d), dy = ey(d);
             const T *src = b0 + (long long)p * D.ps - (long long)dy * D.pitch;
+            const long long e = (long long)(src - Ain); // element index, for the bounds checks
             float v[V];
-            Vec<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src)), v);
+            if (in_bounds(D, e, D.a_elems - V + 1)) Vec<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src)), v);
+            else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) v[k] = 0.f;
+            }
             if (dx == 0) {
 #pragma unroll
                 for (int k = 0; k < V; ++k) c[k][p] = v[k];
             } else if (dx == 1) { // pull from x - 1
                 float l = __shfl_up_sync(kFull, v[V - 1], 1);
-                if (lane == 0) l = E::ld(__ldg(src - 1));
+                if (lane == 0) l = in_bounds(D, e - 1, D.a_elems) ? E::ld(__ldg(src - 1)) : 0.f;
                 c[0][p] = l;
 #pragma unroll
                 for (int k = 1; k < V; ++k) c[k][p] = v[k - 1];
             } else { // pull from x + 1
                 float r = __shfl_down_sync(kFull, v[0], 1);
-                if (lane == 31) r = E::ld(__ldg(src + V));
+                if (lane == 31) r = in_bounds(D, e + V, D.a_elems) ? E::ld(__ldg(src + V)) : 0.f;
 #pragma unroll
                 for (int k = 0; k + 1 < V; ++k) c[k][p] = v[k + 1];
                 c[V - 1][p] = r;
@@ -526,21 +535,25 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
             anygen |= gen[k];
         }
     }
-    T *dst = Aout + (long long)y * D.pitch + x0;
+    const long long d0 = (long long)y * D.pitch + x0;
+    T *dst = Aout + d0;
     if (!anygen) {
 #pragma unroll
         for (int p = 0; p < kPop; ++p) {
             float v[V];
 #pragma unroll
             for (int k = 0; k < V; ++k) v[k] = c[k][p];
-            *reinterpret_cast<VW *>(dst + (long long)p * D.ps) = Vec<T, V>::pack(v);
+            if (in_bounds(D, d0 + (long long)p * D.ps, D.a_elems - V + 1))
+                *reinterpret_cast<VW *>(dst + (long long)p * D.ps) = Vec<T, V>::pack(v);
         }
     } else {
 #pragma unroll
         for (int k = 0; k < V; ++k)
             if (!gen[k]) {
 #pragma unroll
-                for (int p = 0; p < kPop; ++p) dst[(long long)p * D.ps + k] = E::st(c[k][p]);
+                for (int p = 0; p < kPop; ++p)
+                    if (in_bounds(D, d0 + (long long)p * D.ps + k, D.a_elems))
+                        dst[(long long)p * D.ps + k] = E::st(c[k][p]);
             }
     }
     if (!ok) atomicOr(&D.status->err, kErrNumeric);

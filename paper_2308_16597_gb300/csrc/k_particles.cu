@@ -89,7 +89,8 @@ __device__ __forceinline__ void clear_cells_slice(const Dev &D, int parity, int 
     int *grid = D.cells[parity ^ 1];
     const int nc = D.cell_gx * D.cell_gy + 1, per = (nc + D.np - 1) / D.np;
     const int c1 = min(nc, (p + 1) * per);
-    for (int c = p * per + tid; c < c1; c += nthreads) grid[c] = 0;
+    for (int c = p * per + tid; c < c1; c += nthreads)
+        if (in_bounds(D, c, (long long)nc * (1 + kCellCap))) grid[c] = 0;
 }
 
 // One CTA per particle.  Phases:
@@ -289,7 +290,7 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
     for (int sl = tid; sl < cap; sl += kLinkThreads) {
         const unsigned w = occ[sl >> 5], bit = 1u << (sl & 31);
         if (w & bit) list[pre[sl >> 5] + __popc(w & (bit - 1u))] = sl;
-        else {
+        else if (in_bounds(D, (long long)base + sl, D.nslots)) {
             D.slot_node[base + sl] = -1;
             D.slot_q[base + sl] = 0.f;
         }
@@ -303,7 +304,8 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
     // populations of fluid nodes: no CTA writes them during this kernel
     const T *Ar = A;
     auto tv = [&](int plane, int i, int j) -> float {
-        return E::ld(__ldg(Ar + (long long)plane * D.ps + (long long)j * D.pitch + i));
+        const long long e = (long long)plane * D.ps + (long long)j * D.pitch + i;
+        return in_bounds(D, e, D.a_elems) ? E::ld(__ldg(Ar + e)) : 0.f;
     };
     auto fluid = [&](int i, int j) -> bool { return (Fm[j - YA] >> (i - XA)) & 1ull; };
     // one round per kLinkThreads links: every warp sums its round at once
@@ -322,8 +324,10 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
             const int fi = X0 + ((inf >> 4) & 255), fj = Y0 + (inf >> 12);
             float dxf, dyf;
             const float q = ell ? link_q_ellipse(fi, fj, k, s_ell, dxf, dyf) : link_q_df(fi, fj, k, dk, dxf, dyf);
-            D.slot_node[base + sl] = fj * D.nx + fi;
-            D.slot_q[base + sl] = q;
+            if (in_bounds(D, (long long)base + sl, D.nslots)) {
+                D.slot_node[base + sl] = fj * D.nx + fi;
+                D.slot_q[base + sl] = q;
+            }
 
             // curved bounce-back in deviation form: every rule is an affine
             // combination of populations of equal weight, so it holds for
@@ -342,11 +346,11 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
             int lvl;
             const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
             const long long ns = (long long)(fj + ky) * D.pitch + (fi + kx);
-            A[kb * D.ps + ns] = E::st(fnew);
+            if (in_bounds(D, kb * D.ps + ns, D.a_elems)) A[kb * D.ps + ns] = E::st(fnew);
             if (k <= 4) {
                 const float gnew = thermal32(q, tv(kQ9 + k, fi, fj), tv(kQ9 + k, ii1, jj1),
                                              tv(kQ9 + kb, fi, fj), have1, wT);
-                A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
+                if (in_bounds(D, (kQ9 + kb) * D.ps + ns, D.a_elems)) A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
             }
             // momentum exchange: with f = w + f~ the bracket of Eq. force is
             // 2 w_k e_k + [f~_k^+ (e_k - u_w) - f~_kbar (e_kbar - u_w)]; the
@@ -436,9 +440,12 @@ constexpr int kPartPerBlock = kPartThreads / 32;
 __device__ __forceinline__ void cell_insert(const Dev &D, int *grid, int b, float xh, float yh)
 {
     const int ncell = D.cell_gx * D.cell_gy, c = cell_of(D, xh, yh);
+    const long long size = (long long)(ncell + 1) + (long long)ncell * kCellCap;
+    if (!in_bounds(D, c, ncell)) return;
     const int k = atomicAdd(grid + c, 1);
-    if (k < kCellCap) grid[ncell + 1 + c * kCellCap + k] = b;
-    else grid[ncell] = 1;
+    if (k < kCellCap) {
+        if (in_bounds(D, ncell + 1 + (long long)c * kCellCap + k, size)) grid[ncell + 1 + c * kCellCap + k] = b;
+    } else grid[ncell] = 1;
 }
 
 // Support distance of particle p along the unit vector (nx, ny): its radius
@@ -514,8 +521,9 @@ __device__ __forceinline__ void write_runs(const Dev &D, int *own, const Box &B,
     const int lane = threadIdx.x & 31, nr = min(32, B.N - b0);
     for (int r = 0; r < nr; ++r) {
         const int l = __shfl_sync(0xffffffffu, lo, r), h = __shfl_sync(0xffffffffu, hi, r);
-        int *row = own + (long long)(B.Y0 + b0 + r) * D.nx;
-        for (int i = l + lane; i <= h; i += 32) atomicMax(row + i, p);
+        const long long j0 = (long long)(B.Y0 + b0 + r) * D.nx;
+        for (int i = l + lane; i <= h; i += 32)
+            if (in_bounds(D, j0 + i, (long long)D.nx * D.ny)) atomicMax(own + j0 + i, p);
     }
 }
 
@@ -869,7 +877,8 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
                     if (oc[t][h] == -3) continue;
                     const int j = r0 + t, i = c0 + lane + 32 * h;
                     const uint8_t f = on[t][h] >= 0 ? kSolid : oc[t][h] >= 0 ? kNewborn : kFluid;
-                    D.flags[(long long)j * D.pitch + i] = f;
+                    if (in_bounds(D, (long long)j * D.pitch + i, (long long)D.ny * D.pitch))
+                        D.flags[(long long)j * D.pitch + i] = f;
                     // each newborn node once: by the particle that owned it;
                     // frame nodes are always on the general path
                     if (list && f == kNewborn && oc[t][h] == p && i > 0 && i < D.nx - 1 && j > 0 &&
@@ -973,11 +982,11 @@ __global__ void __launch_bounds__(128)
             int lvl;
             const float fnew = bouzidi32(q, fk0, fk1, fk2, fb0, fb1, have1, have2, wall, lvl);
             const long long ns = (long long)sj * D.pitch + si;
-            A[kb * D.ps + ns] = E::st(fnew);
+            if (in_bounds(D, kb * D.ps + ns, D.a_elems)) A[kb * D.ps + ns] = E::st(fnew);
             if (k <= 4) {
                 const float gnew = thermal32(q, tv(kQ9 + k, i, j), tv(kQ9 + k, ii1, jj1), tv(kQ9 + kb, i, j), have1,
                                              G.wT);
-                A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
+                if (in_bounds(D, (kQ9 + kb) * D.ps + ns, D.a_elems)) A[(kQ9 + kb) * D.ps + ns] = E::st(gnew);
                 cnt[3] += !have1;
             }
             const float bx = fk0 * (kx - uwx) - fnew * (-kx - uwx);

@@ -307,6 +307,7 @@ int device_error(lbm_handle *h)
     if (err & kErrDomain) return LBM_EDOMAIN;
     if (err & kErrOverflow) return LBM_EOVERFLOW;
     if (err & kErrTimeout) return LBM_ETIMEOUT;
+    if (err & kErrBounds) return LBM_EBOUNDS;
     return LBM_OK;
 }
 
@@ -380,6 +381,8 @@ void fill_dev(lbm_handle *h)
     D.py = D.px + h->np;
     D.force = reinterpret_cast<double *>(ws + L.force);
     D.pos4 = reinterpret_cast<float4 *>(ws + L.pos4);
+    D.nslots = (long long)L.nslots;
+    D.a_elems = (long long)kPop * L.ps + (long long)(kDistTailPad / storage_bytes(D.storage));
     D.prc = reinterpret_cast<float2 *>(ws + L.prc);
     D.lsum = reinterpret_cast<LinkSums *>(ws + L.lsum);
     D.geo_prev = reinterpret_cast<GeomRec *>(ws + L.geo[0]);
@@ -451,6 +454,7 @@ const char *lbm_strerror(int code)
     case LBM_EOVERFLOW: return "a fixed index array line holds more than one link";
     case LBM_ETIMEOUT: return "a bounded device wait gave up";
     case LBM_ECUDA: return "CUDA runtime error";
+    case LBM_EBOUNDS: return "an index outside its buffer (bounds-checked build)";
     default: return "unknown error";
     }
 }
@@ -737,7 +741,9 @@ int lbm_set_distributions(lbm_handle *h, const double *f, const double *g)
             for (int i = 0; i < nx; ++i) {
                 const size_t s = (size_t)j * nx + i;
                 const double v = p < kQ9 ? f[(size_t)p * nn + s] - w9d(p) : g[(size_t)(p - kQ9) * nn + s];
-                const float x = std::isfinite(v) ? (float)v : 0.f;
+                // a non-finite value stays so: at a fluid node the collision
+                // reports it (LBM_ENUMERIC), at a solid node it is dropped
+                const float x = (float)v;
                 const size_t at = (size_t)p * ps + (size_t)j * pitch + i;
                 if (h->D.storage == LBM_STORE_BF16) reinterpret_cast<__nv_bfloat16 *>(img.data())[at] = Elem<__nv_bfloat16>::st(x);
                 else if (h->D.storage == LBM_STORE_FP16) reinterpret_cast<__half *>(img.data())[at] = Elem<__half>::st(x);

@@ -81,6 +81,7 @@ constexpr unsigned kErrNumeric = 1u;
 constexpr unsigned kErrDomain = 2u;
 constexpr unsigned kErrOverflow = 4u;
 constexpr unsigned kErrTimeout = 8u;
+constexpr unsigned kErrBounds = 16u; // builds with -DLBM_CHECK only
 
 // Counter slots (see lbm_get_counters).
 enum { kCntBzLinear = 0, kCntBzSimple, kCntThermHalf, kCntRfLinear, kCntRfCopy, kCntRfEq,
@@ -123,6 +124,8 @@ struct Dev {
     int newborn_cap;
     unsigned *near;    // bit per warp tile (row, 32 V nodes) within reach of a particle this step
     int near_tpr;      // warp tiles per row of that bitmap
+    long long nslots;  // slots of the fixed index array
+    long long a_elems; // elements of each distribution buffer, its tail pad included
     int *slot_node;    // [nslots]
     float *slot_q;     // [nslots]
     int *slot_base;    // [np + 1]
@@ -146,6 +149,25 @@ struct Dev {
     Status *status;
 };
 constexpr int kCellCap = 16;
+
+// Bounds-checked builds (-DLBM_CHECK): in_bounds(D, i, n) is false for an
+// index i outside [0, n) and records kErrBounds (LBM_EBOUNDS at the next
+// synchronising call); the caller then skips the access.  The checks stand
+// in for a memory checker: they cover the scattered writes of the particle
+// kernels and every read of the stream-collide fast path.  Without
+// LBM_CHECK the function is constant true and compiles away.
+__device__ __forceinline__ bool in_bounds(const Dev &D, long long i, long long n)
+{
+#ifdef LBM_CHECK
+    if (i < 0 || i >= n) {
+        atomicOr(&D.status->err, kErrBounds);
+        return false;
+    }
+#else
+    (void)D; (void)i; (void)n;
+#endif
+    return true;
+}
 __device__ __forceinline__ int cell_of(const Dev &D, float xh, float yh)
 {
     const int cx = min(max((int)(xh * D.cell_inv), 0), D.cell_gx - 1);

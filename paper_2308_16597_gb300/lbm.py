@@ -17,9 +17,12 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "liblbm_gb300.so")
+# LBM_LIBRARY selects another build of the same library (the bounds-checked
+# one of the tests); it is never a fallback: a missing library raises.
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_PKG, "_lib", "liblbm_gb300.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOSPC, LBM_ENUMERIC = 0, -1, -2, -3
+LBM_EBOUNDS = -8
 LBM_EDOMAIN, LBM_EOVERFLOW, LBM_ETIMEOUT, LBM_ECUDA = -4, -5, -6, -7
 LBM_BC_PERIODIC_X, LBM_BC_PERIODIC_Y = 1, 2
 LBM_STORE_FP32, LBM_STORE_BF16, LBM_STORE_FP16 = 0, 1, 2

@@ -361,6 +361,35 @@ def test_async_particle_read_back_equals_the_synchronous_one():
     sim.close()
 
 
+def test_injected_nan_is_reported_and_held():
+    """Host-side fault injection: a NaN handed to lbm_set_distributions inside
+    a disk is ignored (solid nodes carry no distributions); at a fluid node
+    the collision reports it as LBM_ENUMERIC, and the error stays set on the
+    handle for the calls after it."""
+    wl = W.parity_256()
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params)
+    f, g = W.random_state(wl.nx, wl.ny, 3, *base_f(), amp=1e-2)
+    own = sim.owner()
+    js, is_ = np.nonzero(own >= 0)
+    f_solid = f.copy()
+    f_solid[3, js[0], is_[0]] = np.nan
+    sim.set_distributions(f_solid, g)
+    sim.step(5)
+    assert np.isfinite(sim.particles()["x"]).all()
+    jf, if_ = np.nonzero(own < 0)
+    k = len(jf) // 2
+    g_fluid = g.copy()
+    g_fluid[2, jf[k], if_[k]] = np.nan
+    with pytest.raises(lbm.LbmError) as e:
+        sim.set_distributions(f, g_fluid)
+    assert e.value.code == lbm.LBM_ENUMERIC
+    with pytest.raises(lbm.LbmError) as e:
+        sim.step(1)
+        sim.particles()
+    assert e.value.code == lbm.LBM_ENUMERIC
+    sim.close()
+
+
 def test_workspace_too_small_is_rejected():
     wl = W.parity_256()
     d = lbm.make_domain(**wl.domain)
