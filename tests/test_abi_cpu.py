@@ -121,7 +121,7 @@ def test_particle_struct_matches_the_dtype(lib):
 
 
 def test_strerror_covers_every_code(lib):
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):  # LBM_OK .. LBM_EBOUNDS
         assert lbm.lbm_strerror(code) != "unknown error"
 
 
