@@ -8,8 +8,9 @@ sized for) against the buffer they address; an index outside it is skipped
 and reported as LBM_EBOUNDS at the next synchronising call.  The test builds
 it beside the default library and runs, in a child process that loads it,
 the cases that reach the edges: FP32 disks and ellipses that move, the
-largest supported disks, 16-bit storage on widths whose pitch is an odd
-multiple of 32, periodic seams, the split stream-collide, and a batch.
+largest supported disks, ragged widths in every storage (where the last
+block of a row overhangs the pitch, and for 16-bit storage a warp of 64
+nodes straddles it), periodic seams, the split stream-collide, and a batch.
 """
 import os
 import subprocess
@@ -53,7 +54,7 @@ CHILD = textwrap.dedent(r"""
 
     w9 = np.array([4/9] + [1/9] * 4 + [1/36] * 4)
     w5 = np.array([0.6] + [0.1] * 4)
-    for storage in (lbm.LBM_STORE_BF16, lbm.LBM_STORE_FP16):
+    for storage in (lbm.LBM_STORE_FP32, lbm.LBM_STORE_BF16, lbm.LBM_STORE_FP16):
         for (nx, ny), per in (((257, 64), (1, 0)), ((300, 37), (0, 0)), ((70, 50), (0, 1))):
             dom = W.cavity(nx, ny, T_wall=(0.3, 0.8, 1.0, 0.1), periodic_x=per[0], periodic_y=per[1])
             s = lbm.Simulation(dom, None, W.base_params(0.03, 0.71, 3e-3), storage=storage)
