@@ -141,3 +141,15 @@ def test_product_path_has_no_oracle_import():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", text, flags=re.M), f
                 assert "lbm_oracle" not in text, f
+
+
+def test_bounds_checked_variant_builds_beside_the_default(lib, tmp_path):
+    """build(extra=["-DLBM_CHECK"], out=dir) puts the checked library in dir,
+    exporting the same entry points, and leaves the default library alone."""
+    before = os.path.getmtime(lbm.LIB_PATH)
+    path = B.build(force=True, extra=["-DLBM_CHECK"], out=str(tmp_path))
+    assert os.path.dirname(path) == str(tmp_path) and os.path.exists(path)
+    assert os.path.getmtime(lbm.LIB_PATH) == before
+    checked = C.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(checked, name), name
