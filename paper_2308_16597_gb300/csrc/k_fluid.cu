@@ -43,11 +43,16 @@ __device__ float pull_general(const Dev &D, const T *__restrict__ A, int x, int 
         if (D.per_y) ys = ys < 0 ? ys + D.ny : ys - D.ny;
         else wall = true;
     }
-    if (!wall) return E::ld(A[(long long)p * D.ps + (long long)ys * D.pitch + xs]);
+    if (!wall) {
+        const long long e = (long long)p * D.ps + (long long)ys * D.pitch + xs;
+        return in_bounds(D, e, D.a_elems) ? E::ld(A[e]) : 0.f;
+    }
     const long long self = (long long)y * D.pitch + x;
-    if (p < kQ9) return E::ld(A[(long long)opp(d) * D.ps + self]);
+    const long long e = (long long)(p < kQ9 ? opp(d) : kQ9 + opp(d)) * D.ps + self;
+    const float v = in_bounds(D, e, D.a_elems) ? E::ld(A[e]) : 0.f;
+    if (p < kQ9) return v;
     const int side = d == 1 ? 0 : d == 3 ? 1 : d == 2 ? 2 : 3;
-    return -E::ld(A[(long long)(kQ9 + opp(d)) * D.ps + self]) + 2.f * w5(d) * D.Twall[side];
+    return -v + 2.f * w5(d) * D.Twall[side];
 }
 
 // Values pulled into a node on the general path; for a newborn node the
@@ -599,7 +604,8 @@ __device__ __forceinline__ void boundary_body(const Dev &D, const T *__restrict_
         }
         ok &= collide(D, c);
 #pragma unroll
-        for (int p = 0; p < kPop; ++p) Aout[(long long)p * D.ps + o] = E::st(c[p]);
+        for (int p = 0; p < kPop; ++p)
+            if (in_bounds(D, (long long)p * D.ps + o, D.a_elems)) Aout[(long long)p * D.ps + o] = E::st(c[p]);
     }
     flush_counters(D, parity, n4);
     if (!ok) atomicOr(&D.status->err, kErrNumeric);
