@@ -136,3 +136,31 @@ def test_batch_and_server_reject_bad_arguments():
     assert lib.lbm_server_tick(None, 10, None) == lbm.LBM_EINVAL
     assert lib.lbm_server_status(None, 1, None) == lbm.LBM_EINVAL
     assert lib.lbm_server_destroy(None) == lbm.LBM_EINVAL
+
+
+def test_stream_collide_overrun_fits_the_tail_pad():
+    """Launch geometry of the stream-collide fast path, restated: pitch = nx
+    rounded up to 32, V nodes per thread (1 for FP32, 2 for 16-bit storage),
+    128-thread blocks (fewer when a row has fewer threads), a warp wholly past
+    the pitch returns before its first load.  A running warp reads its lanes'
+    V-vectors and one element right of its last lane, so on the last row of
+    the last plane it reads at most 32 V + 1 - (pitch - xw) elements past the
+    buffer's planes; that must fit the 256-byte tail pad for every width."""
+    pad_bytes = 256
+    for V, es in ((1, 4), (2, 2)):
+        worst = 0
+        for nx in range(3, 2100):
+            pitch = (nx + 31) // 32 * 32
+            tx = pitch // V
+            bx = min((tx + 31) // 32 * 32, 128)
+            threads = (tx + bx - 1) // bx * bx
+            for xw in range(0, threads * V, 32 * V):
+                if xw >= pitch:
+                    continue  # returns before its first load
+                worst = max(worst, xw + 32 * V + 1 - pitch)
+        assert worst * es <= pad_bytes, (V, worst)
+        assert worst == (1 if V == 1 else 33)
+    # without the early return the overhanging warps would read far past it
+    # (16-bit storage, nx = 257: pitch 288, warps up to x = 448)
+    pitch, V = 288, 2
+    assert (448 + 32 * V + 1 - pitch) * 2 > pad_bytes
