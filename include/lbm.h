@@ -216,9 +216,12 @@ int lbm_set_state(lbm_handle *h, const void *host_buf, size_t bytes);
  * non-physical value at a fluid node makes the call return LBM_ENUMERIC,
  * which stays set on the handle (sticky).  Synchronises. */
 int lbm_set_distributions(lbm_handle *h, const double *f, const double *g);
-/* Counters of the last step: [0] Bouzidi quadratic->linear fallbacks,
- * [1] ->simple, [2] thermal ->half-way, [3] refill quadratic->linear,
- * [4] ->copy, [5] ->equilibrium, [6] newborn nodes, [7] links. */
+/* Counters of the last step (Sec. 2.3 fallbacks of the bounce-back rules,
+ * Sec. 2.5 refill classes, Sec. 3 link count) into the caller's host array
+ * out8[8]: [0] Bouzidi quadratic->linear fallbacks, [1] ->simple,
+ * [2] thermal ->half-way, [3] refill quadratic->linear, [4] ->copy,
+ * [5] ->equilibrium, [6] newborn nodes, [7] links.  Synchronises; returns
+ * the handle's sticky error instead when one is set. */
 int lbm_get_counters(lbm_handle *h, int64_t *out8);
 /* Kernel timing: while enabled, lbm_step launches directly (no graph) and
  * brackets every kernel with CUDA events on the handle's stream.
