@@ -164,3 +164,42 @@ def test_stream_collide_overrun_fits_the_tail_pad():
     # (16-bit storage, nx = 257: pitch 288, warps up to x = 448)
     pitch, V = 288, 2
     assert (448 + 32 * V + 1 - pitch) * 2 > pad_bytes
+
+
+def test_batched_block_lookup_finds_every_tile():
+    """The batched stream-collide's block -> (instance, tile) mapping,
+    restated: per-instance first block and tiles per row gx with the
+    multiplier m = floor(2^s / gx) + 1, s = 31 + ceil(log2 gx), and buckets
+    of 2^shift blocks (at most 4 (n + 1) of them) holding the instance of
+    their first block, then a forward step over the instances starting in
+    the bucket.  Every block of random uneven batches lands on its own
+    instance and tile."""
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        n = int(rng.integers(1, 70))
+        gx = rng.integers(1, 400, n)
+        gy = rng.integers(1, 300, n)
+        blocks = gx * gy
+        start = np.concatenate([[0], np.cumsum(blocks)])
+        total = int(start[-1])
+        ell = np.array([int(np.ceil(np.log2(g))) if g > 1 else 0 for g in gx])
+        s = 31 + ell
+        m = np.array([(1 << int(si)) // int(g) + 1 for si, g in zip(s, gx)], dtype=object)
+        shift = 0
+        while (total >> shift) + 1 > 4 * (n + 1):
+            shift += 1
+        bucket, i = [], 0
+        for k in range((total >> shift) + 1):
+            while i + 1 < n and start[i + 1] <= (k << shift):
+                i += 1
+            bucket.append(i)
+        assert len(bucket) <= 4 * (n + 1)
+        for g in rng.integers(0, total, 2000):
+            i = bucket[int(g) >> shift]
+            while i + 1 < n and start[i + 1] <= g:
+                i += 1
+            assert start[i] <= g < start[i + 1]
+            local = int(g - start[i])
+            by = (local * m[i]) >> int(s[i])
+            bx = local - by * int(gx[i])
+            assert (by, bx) == divmod(local, int(gx[i]))
