@@ -234,6 +234,11 @@ int32_t lbm_kernel_count(void);
 const char *lbm_kernel_name(int32_t k);
 /* Kernel launches enqueued by this handle since creation. */
 int64_t lbm_launch_count(lbm_handle *h);
+/* Diagnostic, no counterpart in the paper: the GPU architecture of the
+ * device code the runtime loaded for this library on the current device
+ * (cudaFuncGetAttributes' binaryVersion of the stream-collide kernel,
+ * major * 10 + minor: 103 for sm_103a).  LBM_ECUDA without a usable device. */
+int lbm_binary_version(int32_t *version);
 
 /* ---- allocation-free link forces ---------------------------------------- */
 /* No counterpart in the paper: an entry point for callers that cannot
@@ -251,17 +256,21 @@ int64_t lbm_launch_count(lbm_handle *h);
  *                 plane_stride in elements), post-collision; its entries at
  *                 solid nodes are overwritten with the bounce-back values.
  *   d_owner       int32 [ny][nx]: particle id per node, -1 for fluid.
- *   d_particles   n particles (device); every radius must be <= r_max.
- *   d_forces      output, 3 doubles per particle (Fx, Fy, Tz); NaN for a
- *                 particle whose radius exceeds r_max or one of whose index
- *                 lines holds two links.
+ *   d_particles   n particles (device); every radius must be <= r_max, and
+ *                 the shapes follow lbm_init's rule (b >= 0; for an ellipse
+ *                 1 <= b <= r and |theta| <= 1.6e6).
+ *   d_forces      output, 3 doubles per particle (Fx, Fy, Tz); NaN for every
+ *                 particle when one of them breaks the radius or shape rule
+ *                 (checked on the device), NaN for a particle one of whose
+ *                 index lines holds two links.
  * Asynchronous on stream.  Returns LBM_ENOSPC when n or n * (12N(r_max) - 12)
  * exceeds the limits above or when r_max > 354.5 (the per-link results of one
  * zone, 24 bytes per slot, are held in 200 KB of shared memory), LBM_EINVAL
- * for bad arguments.  Every call shares
- * the static array and overwrites it, so calls whose GPU work overlaps race.
- * The first call on a device looks up the array's address and should come
- * before any stream capture. */
+ * for bad arguments (among them nx * ny > 2^31 - 1: node indices are int32).
+ * Every call shares the static array and overwrites it, so calls whose GPU
+ * work overlaps race.  Every call looks up the array's address on the current
+ * device; the first call on a device also loads the library's device code
+ * there and should come before any stream capture. */
 int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
                             const int32_t *d_owner, int32_t nx, int32_t ny,
                             const lbm_particle *d_particles, int32_t n, double r_max,
@@ -289,9 +298,12 @@ int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
  *   lbm_batch_step       enqueues nsteps steps of every instance on the
  *                        batch's stream; call lbm_batch_sync before using a
  *                        handle on its own again.
- *   lbm_batch_sync       waits for the batch's stream and returns the first
- *                        sticky device error of any instance (its index in
- *                        *which, may be NULL), else LBM_OK.
+ *   lbm_batch_sync       waits for the batch's stream, reads every
+ *                        instance's device error word (each failing handle
+ *                        then holds its error, sticky) and returns the first
+ *                        error (its instance's index in *which, may be NULL;
+ *                        -1 for an error of the batch's own launches), else
+ *                        LBM_OK.
  * Errors: LBM_EINVAL (mixed storage, a handle twice or with direct-addressed
  * links, n < 1 or n > 4096, or
  * from lbm_batch_step: a handle stepped on its own since), LBM_ENOSPC
@@ -327,7 +339,10 @@ int lbm_batch_destroy(lbm_batch *b);
  *                      workspace exceeds the whole pool.
  *   lbm_server_tick    one round; synchronises the stream; *stats (may be
  *                      NULL) receives its counts and the device time of its
- *                      steps.
+ *                      steps.  A request whose instance failed is retired
+ *                      as failed and the others go on; an error of the
+ *                      batch's own launches (no instance to blame) is
+ *                      returned, and no step of the round is counted.
  *   lbm_server_status  returns 0 queued, 1 active, 2 done, 3 failed (its
  *                      error code in *err, may be NULL), -1 unknown id.
  *   lbm_server_result  for a done request: rho - 1, ux, uy, T ([ny][nx] host

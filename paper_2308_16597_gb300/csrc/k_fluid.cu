@@ -826,6 +826,14 @@ cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, int
     }
 }
 
+cudaError_t stream_collide_binary_version(int *version)
+{
+    cudaFuncAttributes a{};
+    const cudaError_t e = cudaFuncGetAttributes(&a, k_stream_collide<float, 1, kSCAll>);
+    if (e == cudaSuccess) *version = a.binaryVersion;
+    return e;
+}
+
 cudaError_t launch_boundary(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
                             cudaStream_t s)
 {

@@ -14,10 +14,13 @@
 // the slot offsets of up to 32,768 particles: 16 MiB + 128 KiB held on every
 // GPU that loads the library, for the life of the process.  All calls share
 // it and it keeps the contents of the last call, so calls whose GPU work
-// overlaps (on two streams, or from two threads) race on it.  The first call
-// on a device looks up the array's device address (cudaGetSymbolAddress);
-// make that first call before any stream capture.
-#include <mutex>
+// overlaps (on two streams, or from two threads) race on it.  Every call
+// looks up the array's device address on the current device
+// (cudaGetSymbolAddress); the first call on a device also loads the
+// library's device code there, so make that first call before any stream
+// capture.
+#include <climits>
+#include <cmath>
 
 #include "lbm_internal.cuh"
 
@@ -27,7 +30,6 @@ namespace {
 constexpr long long kStaticSlots = 1ll << 21;   // 2,097,152 slots
 constexpr int kStaticParticles = 1 << 15;       // 32,768 particles
 constexpr int kThreads = 256;
-constexpr int kMaxDevices = 64;
 
 // [slot nodes: int32 x kStaticSlots][wall fractions: float x kStaticSlots]
 // [slot offsets: int32 x (kStaticParticles + 1)][reject flag: uint32]
@@ -66,7 +68,10 @@ struct View {
 
 // Slot offsets: running sum of 12N - 12 over the particles (one thread).
 // The reject flag is rewritten on every call: set when some radius exceeds
-// the r_max the host checked the capacity against.
+// the r_max the host checked the capacity against, or when a particle breaks
+// the shape rule of lbm_init (semi-minor axis b negative, or, for an
+// ellipse, b below 1 or above the semi-major axis r, or |theta| above 1.6e6),
+// since the zone and the slot capacity are sized from r.
 __global__ void k_static_bases(View v, unsigned char *scratch)
 {
     Scratch s = carve(scratch);
@@ -75,8 +80,10 @@ __global__ void k_static_bases(View v, unsigned char *scratch)
         unsigned bad = 0u;
         for (int a = 0; a < v.n; ++a) {
             s.base[a] = acc;
-            const double r = v.P[a].r;
-            if (!(r >= 1.0 && r <= v.r_max)) bad = 1u;
+            const double r = v.P[a].r, b = v.P[a].b;
+            const bool shape_ok = b >= 0.0 && (!is_ellipse(r, b) || (b >= 1.0 && b <= r &&
+                                                                     fabs(v.P[a].theta) <= 1.6e6));
+            if (!(r >= 1.0 && r <= v.r_max) || !shape_ok) bad = 1u;
             else acc += slot_capacity(r);
         }
         s.base[v.n] = acc;
@@ -236,21 +243,16 @@ __global__ void __launch_bounds__(kThreads) k_static_bbforce(View v, unsigned ch
     }
 }
 
-// Device address of the static array, looked up once per device.
-std::mutex g_mu;
-unsigned char *g_addr[kMaxDevices] = {};
-
+// Device address of the static array on the current device.  Looked up on
+// every call rather than cached: the query is cheap once the device code is
+// loaded, and a cached address would go stale when the context is reset
+// (cudaDeviceReset), which places the array anew.  In host code the array's
+// name is only a host-side stand-in, never a device address.
 int scratch_address(unsigned char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ECUDA;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_link_scratch) != cudaSuccess || !ptr) return LBM_ECUDA;
-        g_addr[dev] = static_cast<unsigned char *>(ptr);
-    }
-    *out = g_addr[dev];
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_link_scratch) != cudaSuccess || !ptr) return LBM_ECUDA;
+    *out = static_cast<unsigned char *>(ptr);
     return LBM_OK;
 }
 
@@ -264,6 +266,8 @@ extern "C" int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int3
 {
     using namespace lbm;
     if (n < 0 || nx < 1 || ny < 1 || pitch < nx || plane_stride < (int64_t)pitch * ny) return LBM_EINVAL;
+    // the index array stores j * nx + i as int32
+    if ((long long)nx * ny > INT_MAX) return LBM_EINVAL;
     if (n == 0) return LBM_OK;
     if (!d_dist || !d_owner || !d_particles || !d_forces || !(r_max >= 1.0) || r_max > 1e6)
         return LBM_EINVAL;

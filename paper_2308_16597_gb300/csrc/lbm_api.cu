@@ -797,4 +797,13 @@ const char *lbm_kernel_name(int32_t k)
 
 int64_t lbm_launch_count(lbm_handle *h) { return h ? h->launches : -1; }
 
+int lbm_binary_version(int32_t *version)
+{
+    if (!version) return LBM_EINVAL;
+    int v = 0;
+    if (stream_collide_binary_version(&v) != cudaSuccess) return LBM_ECUDA;
+    *version = v;
+    return LBM_OK;
+}
+
 } // extern "C"

@@ -323,14 +323,17 @@ int lbm_batch_sync(lbm_batch *b, int32_t *which)
     if (which) *which = -1;
     BCK(b, cudaStreamSynchronize(b->stream));
     if (b->sticky) return b->sticky;
+    // every handle reads its own device error word now (each failing one
+    // holds its error, sticky), and the first failure is reported
+    int first = LBM_OK;
     for (int i = 0; i < b->n; ++i) {
-        int rc = lbm_sync(b->hs[i]);
-        if (rc) {
+        const int rc = lbm_sync(b->hs[i]);
+        if (rc && first == LBM_OK) {
+            first = rc;
             if (which) *which = i;
-            return rc;
         }
     }
-    return LBM_OK;
+    return first;
 }
 
 int64_t lbm_batch_launch_count(lbm_batch *b) { return b ? b->launches : 0; }

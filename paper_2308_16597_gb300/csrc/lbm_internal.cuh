@@ -792,6 +792,9 @@ constexpr int kNearMargin = 2;
 
 // Planes are passed untyped: their element type is D.storage.
 cudaError_t launch_stream_collide(const Dev &D, const void *Ain, void *Aout, int mode, cudaStream_t s);
+// Binary (SASS) architecture of the loaded stream-collide kernel, as
+// cudaFuncGetAttributes reports it (major * 10 + minor).
+cudaError_t stream_collide_binary_version(int *version);
 // Near-tile bitmap of this step (clears it first).
 cudaError_t launch_near_mask(const Dev &D, cudaStream_t s);
 // Direct addressing (the paper's comparison for its index array): a per-

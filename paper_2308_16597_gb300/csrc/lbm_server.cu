@@ -231,6 +231,9 @@ int lbm_server_tick(lbm_server *s, int32_t max_steps, lbm_server_stats *st)
         if (cudaEventRecord(s->e1, s->stream) != cudaSuccess) return LBM_ECUDA;
         int32_t which = -1;
         rc = lbm_batch_sync(s->batch, &which);
+        // an error of the batch itself (not of one instance): no step can be
+        // counted as done
+        if (rc && which < 0) return rc;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, s->e0, s->e1);
         S.steps = (int32_t)steps;

@@ -80,6 +80,7 @@ _SIGS = [
     ("lbm_kernel_count", C.c_int32, []),
     ("lbm_kernel_name", C.c_char_p, [C.c_int32]),
     ("lbm_launch_count", C.c_int64, [_P]),
+    ("lbm_binary_version", C.c_int, [C.POINTER(C.c_int32)]),
     ("lbm_link_forces_noalloc", C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, _P,
                                           C.c_int32, C.c_double, _P, _P]),
     ("lbm_batch_footprint", C.c_int, [_P, C.c_int32, C.POINTER(C.c_size_t)]),
@@ -321,6 +322,13 @@ class Simulation:
 
     def launch_count(self) -> int:
         return int(library().lbm_launch_count(self.h))
+
+
+def lbm_binary_version() -> int:
+    """GPU architecture of the loaded device code (103 for sm_103a)."""
+    v = C.c_int32(0)
+    _check(library().lbm_binary_version(C.byref(v)), "lbm_binary_version")
+    return int(v.value)
 
 
 def lbm_link_forces_noalloc(dist_ptr, plane_stride, pitch, owner_ptr, nx, ny, particles_ptr, n,

@@ -39,10 +39,29 @@ def test_every_declared_entry_point_is_exported(lib):
     assert set(names) == set(lbm.exported_symbols())
 
 
-def test_library_is_built_for_sm_103a():
-    out = B.build()
-    data = open(out, "rb").read()
-    assert b"sm_103a" in data or b"sm_103" in data
+def test_build_targets_sm_103a_only():
+    """Every translation unit and the link step get exactly one -gencode,
+    arch=compute_103a,code=sm_103a (the GPU-side check of the loaded code is
+    test_gpu_parity::test_loaded_device_code_is_sm_103)."""
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert not any("gencode" in f or "arch" in f for f in B.FLAGS)
+
+
+def test_noalloc_rejects_sizes_beyond_its_static_array(lib):
+    """Host-side checks of lbm_link_forces_noalloc come before any device
+    call, so they run here without a GPU: 8000 disks of radius 20 need
+    8000 * (12 * 43 - 12) slots, more than its 2,097,152, and nx * ny beyond
+    2^31 - 1 would overflow its int32 node indices.  The pointers are never
+    dereferenced (stand-in addresses)."""
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_link_forces_noalloc(16, 1 << 20, 1024, 16, 1000, 1000, 16, 8000, 20.0, 16, 0)
+    assert e.value.code == lbm.LBM_ENOSPC
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_link_forces_noalloc(16, 50000 * 50000, 50000, 16, 50000, 50000, 16, 10, 10.0, 16, 0)
+    assert e.value.code == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:  # pitch below nx
+        lbm.lbm_link_forces_noalloc(16, 1 << 20, 999, 16, 1000, 1000, 16, 10, 10.0, 16, 0)
+    assert e.value.code == lbm.LBM_EINVAL
 
 
 def _setup(n_parts=3, nx=64, ny=48, r=5.0):

@@ -62,6 +62,12 @@ def base_f():
     return orc.feq(1.0, 0.0, 0.0), orc.geq(1.0, 0.0, 0.0)
 
 
+def test_loaded_device_code_is_sm_103():
+    """The runtime loaded the library's sm_103a code on this GPU (no PTX JIT
+    from another architecture): cudaFuncGetAttributes' binaryVersion."""
+    assert lbm.lbm_binary_version() == 103
+
+
 # --------------------------------------------------------------------------- lattice only
 def test_rest_state_stays_exactly_at_rest():
     dom = W.cavity(133, 70)
