@@ -1,7 +1,9 @@
 """Serving (lbm_server_*): requests of different sizes, particle counts and
 step budgets, arriving while others run, are admitted by device-memory
 footprint, advanced together (continuous batching) and retired; each
-result is exactly (bit for bit) what lbm_step gives the request alone."""
+result is exactly (bit for bit) what lbm_step gives the request alone, and
+matches the FP64 oracle's run of the request (fields rel-L2 <= 1e-5, centres
+within 1e-4 lattice units)."""
 import numpy as np
 import pytest
 
@@ -9,7 +11,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2308_16597_gb300 import lbm, workloads as W  # noqa: E402
-from test_gpu_batch import small_ensemble  # noqa: E402
+from test_gpu_batch import check_against_oracle, oracle_run, small_ensemble  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -74,6 +76,7 @@ def test_results_are_the_same_alone_and_in_the_mix():
     out, stats = run_until_done(srv, ids, 8, arrivals)
     for k in budgets:
         same_result(out[k], refs[k])
+        check_against_oracle(out[k][0], out[k][1], oracle_run(wls[k], budgets[k]), lbm.LBM_STORE_FP32)
     # requests overlapped on the device
     assert max(s["active"] + s["retired"] for s in stats) >= 3
     assert sum(s["admitted"] for s in stats) == 5
