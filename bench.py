@@ -124,6 +124,108 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (ctypes, read-only
+    queries) every `period` seconds by a background thread, so that samples
+    fall inside timed regions of a few milliseconds; `window()` marks the
+    host-side span of each timed region and `summary()` keeps only the
+    samples inside them.  The device is found by its PCI address."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, dev, period: float = 5e-4):
+        import ctypes
+        import threading
+        self.period, self.samples, self.windows = period, [], []
+        self.ok, self.max_mhz, self.err = False, None, None
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            import torch
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            pr = torch.cuda.get_device_properties(dev)
+            bus = getattr(pr, "pci_bus_id", None)
+            rc = -1
+            if bus is not None:
+                bid = "%08x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), bus, getattr(pr, "pci_device_id", 0))
+                rc = lib.nvmlDeviceGetHandleByPciBusId_v2(bid.encode(), ctypes.byref(h))
+            if rc != 0:
+                cnt = ctypes.c_uint(0)
+                lib.nvmlDeviceGetCount_v2(ctypes.byref(cnt))
+                if cnt.value != 1 or lib.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) != 0:
+                    raise OSError("no NVML handle for the device")
+            mx = ctypes.c_uint(0)
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+                self.max_mhz = float(mx.value)
+            self._reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.lib, self.h, self.ok = lib, h, True
+        except Exception as e:  # noqa: BLE001 - the line then says why there are no samples
+            self.err = str(e)
+
+    def _run(self):
+        import ctypes
+        mhz, rs = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz)) == 0 and \
+                    self._reasons(self.h, ctypes.byref(rs)) == 0:
+                self.samples.append((t, float(mhz.value), int(rs.value)))
+            time.sleep(self.period)
+
+    def start(self):
+        if self.ok:
+            import threading
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+
+    def stop(self):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join()
+
+    def window(self, t0: float, t1: float):
+        self.windows.append((t0, t1))
+
+    def summary(self) -> dict:
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["NVML unavailable: %s" % self.err],
+                    "samples": 0}
+        inside = [x for x in self.samples if any(a <= x[0] <= b for a, b in self.windows)]
+        reasons = sorted({name for _, _, r in inside for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median([m for _, m, _ in inside]) if inside else None,
+                "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples": len(inside),
+                "source": "NVML every %.1f ms inside the timed windows" % (self.period * 1e3)}
+
+
+def timed_windows(step, record, dev, steps: int, windows: int, sampler, world: int = 1):
+    """`windows` back-to-back timed regions of exactly `steps` steps each,
+    every one bracketed by a barrier (N > 1) and a device synchronisation on
+    both sides and timed with CUDA events on the launching stream (`record`
+    records an event there); returns the milliseconds of each region."""
+    import torch
+    out = []
+    for _ in range(windows):
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        record(e0)
+        step(steps)
+        record(e1)
+        torch.cuda.synchronize(dev)
+        sampler.window(t0, time.perf_counter())
+        if world > 1:
+            dist.barrier()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
 def measured_peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -227,6 +329,43 @@ def config_of(wl, args):
 
 
 # ------------------------------------------------------------------------------------ ours
+def kernel_pass(sim, steps: int) -> dict:
+    """Per-kernel times: `steps` steps launched directly, one kernel at a
+    time, each bracketed by CUDA events on the launching stream."""
+    sim.kernel_timing(True)
+    sim.step(3)
+    sim.sync()
+    sim.kernel_times()  # reset
+    sim.step(steps)
+    kt = sim.kernel_times()
+    sim.kernel_timing(False)
+    sim.sync()
+    return kt
+
+
+def storage_leg(wl, storage: str, args, dev, stream, sampler) -> dict:
+    """The same workload with the 14 planes stored as `storage`: MLUPS of the
+    graph-replayed step (median of the timed windows) and the stream-collide
+    kernel against the copy bandwidth on its algorithmic bytes per update."""
+    from paper_2308_16597_gb300 import lbm
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream, storage=STORAGE_CODES[storage])
+    sim.step(args.warmup)
+    sim.sync()
+    ms = timed_windows(sim.step, lambda e: e.record(stream), dev, args.steps, args.windows, sampler)
+    kt = kernel_pass(sim, args.steps)
+    sim.close()
+    med = statistics.median(ms) / args.steps
+    nodes = wl.nx * wl.ny
+    B_LU = metrics.bytes_per_update(STORAGE_BYTES[storage])
+    peak = measured_peaks()["hbm_gbs"]
+    sc_ms = kt["stream_collide"][0] / max(kt["stream_collide"][1], 1)
+    return {"value": nodes / (med / 1e3) / 1e6, "unit": UNIT, "ms_per_step": med,
+            "bytes_per_update": B_LU,
+            "whole_step_hbm_frac": B_LU * nodes / (med / 1e3) / 1e9 / peak,
+            "stream_collide": {"avg_launch_ms": sc_ms, "achieved_gbs": B_LU * nodes / (sc_ms / 1e3) / 1e9,
+                               "frac": B_LU * nodes / (sc_ms / 1e3) / 1e9 / peak}}
+
+
 def run_ours(args, wl):
     import torch
     from paper_2308_16597_gb300 import build as B, lbm
@@ -240,40 +379,25 @@ def run_ours(args, wl):
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.Stream(device=dev)
     nodes = wl.nx * wl.ny
+    storage = STORAGE_CODES[args.storage]
+    flags = lbm.LBM_FLAG_DIRECT_LINKS if args.links == "direct" else 0
+    sampler = NvmlSampler(dev)
     with torch.cuda.stream(stream):
-        storage = STORAGE_CODES[args.storage]
-        flags = lbm.LBM_FLAG_DIRECT_LINKS if args.links == "direct" else 0
         sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream, storage=storage, flags=flags)
         sim.step(args.warmup)
         sim.sync()
         clocks = ClockSampler(local)
         clocks.start()
+        sampler.start()
         time.sleep(0.4)
-        # headline: K steps replayed from the captured CUDA graphs
+        # headline: `windows` regions of exactly K steps each, replayed from
+        # the captured CUDA graphs; the value is the median region
         launches0 = sim.launch_count()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        sim.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
-        ms = ev0.elapsed_time(ev1)
-        launches = sim.launch_count() - launches0
-        # per-kernel times: K more steps launched directly, one kernel at a
-        # time, each bracketed by CUDA events on the launching stream
-        sim.kernel_timing(True)
-        sim.step(3)
-        sim.sync()
-        sim.kernel_times()  # reset
-        sim.step(args.steps)
-        ktimes = sim.kernel_times()
-        sim.kernel_timing(False)
-        sim.sync()
-        clk = clocks.stop()
+        win_ms = timed_windows(sim.step, lambda e: e.record(stream), dev, args.steps, args.windows, sampler, world)
+        launches = (sim.launch_count() - launches0) // args.windows
+        ktimes = kernel_pass(sim, args.steps)
+        smi = clocks.stop()
+    ms = statistics.median(win_ms)
     max_ms = max_over_ranks(ms, world, dev)
     value = aggregate_mlups(nodes, args.steps, world, max_ms / 1e3)
 
@@ -299,12 +423,15 @@ def run_ours(args, wl):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         h = lbm.lbm_init(dom, parts, params, ws.data_ptr(), ws_bytes, stream.cuda_stream)
+        lbm.lbm_sync(h)
+        t_init = time.perf_counter()
         for _ in range(e2e_steps):
             lbm.lbm_step(h, 1)
             # each step's particle states to page-locked host memory, the
             # copy overlapping the next step's kernels
             lbm.lbm_get_particles_async(h, pview)
         lbm.lbm_sync(h)
+        t_steps = time.perf_counter()
         lbm.lbm_get_fields(h, *[f.data_ptr() for f in fields], 0)
         t1 = time.perf_counter()
         lbm.lbm_destroy(h)
@@ -314,9 +441,12 @@ def run_ours(args, wl):
                "h2d_bytes_per_step": pbytes / e2e_steps,
                "d2h_bytes_per_step": pbytes + 4 * 4 * nodes / e2e_steps,
                "steps": e2e_steps,
-               "includes": "lbm_init from host particles, per step lbm_step(1) + "
-                           "lbm_get_particles_async to pinned host (the copy overlaps the next step), "
-                           "final lbm_sync and lbm_get_fields to host"}
+               "seconds": {"init": t_init - t0, "steps": t_steps - t_init, "fields_readback": t1 - t_steps},
+               "includes": "lbm_init from host particles (raster, initial collision, graph capture), per "
+                           "step lbm_step(1) + lbm_get_particles_async to pinned host (the copy overlaps the "
+                           "next step), final lbm_sync and lbm_get_fields of rho-1, ux, uy, T (%d MB) to "
+                           "host; at %d steps the init and the field read-back are a large share of the "
+                           "time (see seconds)" % (16 * nodes // 1000000, e2e_steps)}
 
     if rank != 0:
         if world > 1:
@@ -333,26 +463,43 @@ def run_ours(args, wl):
     achieved = B_LU * nodes / avg_s / 1e9
     traffic = profiled_traffic("stream_collide" if args.storage == "fp32" else "stream_collide_" + args.storage,
                                wl.name)
+    step_ms = max_ms / args.steps
+    direct_ms = sum(v[0] for v in ktimes.values()) / args.steps
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": "k_stream_collide" + (" (far-tile + near-tile passes of one step)"
                                                 if ktimes.get("stream_collide_near", (0.0, 0))[1] else ""),
                 "algorithmic_bytes_per_launch": B_LU * nodes,
                 "avg_launch_ms": avg_s * 1e3, "peak_source": peaks["source"] + " (hbm_gbs)",
-                "kernel_times_from": "a second pass of the same number of steps, launched "
-                                     "directly with CUDA events around every kernel"}
-    step_ms = max_ms / args.steps
+                "kernel_times_from": "a second pass of the same number of steps, launched directly with "
+                                     "CUDA events around every kernel: its kernels sum to %.4f ms per step "
+                                     "against %.4f ms per graph-replayed step (the boundary kernel runs "
+                                     "beside stream-collide in the graph, after it here)" % (direct_ms, step_ms)}
     per_kernel = {k: {"ms_per_step": v[0] / max(v[1], 1), "launches": v[1],
                       "share": v[0] / max(sum(x[0] for x in ktimes.values()), 1e-12)}
                   for k, v in ktimes.items() if v[1]}
+    clk = sampler.summary()
+    clk["nvidia_smi"] = smi
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_of(wl, args), "roofline": roofline, "e2e": e2e,
+            "config": dict(config_of(wl, args), timed_windows=args.windows),
+            "windows_ms_per_step": [w / args.steps for w in win_ms],
+            "roofline": roofline, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel,
             "particle_part_ms_per_step": sum(v["ms_per_step"] for k, v in per_kernel.items()
                                              if k in ("link_gather_bb_force", "particle_update", "node_flags")),
             "whole_step_hbm_frac": B_LU * nodes / (step_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    if world == 1 and not args.no_extra and args.workload == "cavity4000" and args.storage == "fp32":
+        with torch.cuda.stream(stream):
+            sampler.windows.clear()
+            line["reduced"] = {st: storage_leg(wl, st, args, dev, stream, sampler) for st in ("bf16", "fp16")}
+            line["reduced"]["clocks"] = sampler.summary()
+            sampler.stop()
+        line["ensemble"] = run_ensemble(args, summary=True)
+        line["served"] = run_served(args, summary=True)
+    else:
+        sampler.stop()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -362,9 +509,11 @@ def run_ours(args, wl):
 
 
 # ------------------------------------------------------------------------ batched ensemble
-def run_ensemble(args):
+def run_ensemble(args, summary: bool = False):
     """64 uneven cavities stepped as one batch (one graph per step, tile shape
-    from the autotuner): aggregate MLUPS over all instances."""
+    from the autotuner): aggregate MLUPS over all instances.  summary: called
+    from the headline run on one GPU (FP32, K steps in the headline's number
+    of windows); returns the key's dict instead of printing a line."""
     import torch
     from paper_2308_16597_gb300 import build as B, lbm
 
@@ -372,6 +521,8 @@ def run_ensemble(args):
     B.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if summary:
+        world, rank = 1, 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
@@ -379,6 +530,7 @@ def run_ensemble(args):
     storage = STORAGE_CODES[args.storage]
     nodes = sum(w.nx * w.ny for w in wls)
     stream = torch.cuda.Stream(device=dev)
+    sampler = NvmlSampler(dev)
     with torch.cuda.stream(stream):
         t_init0 = time.perf_counter()
         sims = [lbm.Simulation(w.domain, w.particles, w.params, stream=stream, storage=storage) for w in wls]
@@ -390,20 +542,12 @@ def run_ensemble(args):
         batch.sync()
         clocks = ClockSampler(local)
         clocks.start()
+        sampler.start()
         time.sleep(0.4)
         l0 = batch.launch_count()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        batch.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
-        ms = ev0.elapsed_time(ev1)
-        launches = batch.launch_count() - l0
+        win_ms = timed_windows(batch.step, lambda e: e.record(stream), dev, args.steps, args.windows, sampler, world)
+        ms = statistics.median(win_ms)
+        launches = (batch.launch_count() - l0) // args.windows
         # end to end: every instance's particles and fields read back to the host
         t0 = time.perf_counter()
         d2h = 0
@@ -412,7 +556,9 @@ def run_ensemble(args):
             f = s.fields()
             d2h += len(s._parts) * lbm.PARTICLE_DTYPE.itemsize + sum(a.nbytes for a in f)
         t_read = time.perf_counter() - t0
-        clk = clocks.stop()
+        smi = clocks.stop()
+        sampler.stop()
+        clk = dict(sampler.summary(), nvidia_smi=smi)
         batch.sync()
         sc_ms = batch.tuned_ms
         batch.close()
@@ -420,10 +566,21 @@ def run_ensemble(args):
             s.close()
     max_ms = max_over_ranks(ms, world, dev)
     value = aggregate_mlups(nodes, args.steps, world, max_ms / 1e3)
+    B_LU = metrics.bytes_per_update(STORAGE_BYTES[args.storage])
+    peaks = measured_peaks()
+    achieved = B_LU * nodes / (sc_ms / 1e3) / 1e9
+    if summary:
+        return {"workload": "ensemble64_seed4", "instances": len(wls), "nodes": nodes,
+                "particles": int(sum(len(w.particles) for w in wls)), "storage": args.storage,
+                "value": value, "unit": UNIT, "ms_per_step": max_ms / args.steps,
+                "windows_ms_per_step": [w / args.steps for w in win_ms],
+                "tile": ["128x1", "64x2", "32x4"][tile], "gpu_launches_per_window": int(launches),
+                "whole_step_hbm_frac": B_LU * nodes / (max_ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "stream_collide": {"kernel": "k_stream_collide_batch", "avg_launch_ms": sc_ms,
+                                   "achieved_gbs": achieved, "frac": achieved / peaks["hbm_gbs"],
+                                   "time_from": "the autotuner's timing of the chosen tile shape"},
+                "clocks": clk}
     if rank == 0:
-        B_LU = metrics.bytes_per_update(STORAGE_BYTES[args.storage])
-        peaks = measured_peaks()
-        achieved = B_LU * nodes / (sc_ms / 1e3) / 1e9
         e2e_s = (max_ms / 1e3) + t_init + t_read
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -463,11 +620,13 @@ def weighted_percentile(values, weights, q: float) -> float:
 
 
 # ------------------------------------------------------------------------------ served stream
-def run_served(args):
+def run_served(args, summary: bool = False):
     """Poisson stream of 40 sedimentation requests (512^2-2048^2, 2000-20000
     steps) through the request loop: aggregate MLUPS over the wall time from
     the first arrival to the last result, p50/p99 per-step and per-request
-    latency."""
+    latency.  summary: called from the headline run on one GPU, the first 10
+    requests of the same stream (FP32); returns the key's dict instead of
+    printing a line."""
     import torch
     from paper_2308_16597_gb300 import build as B, lbm
 
@@ -475,10 +634,14 @@ def run_served(args):
     B.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if summary:
+        world, rank = 1, 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     reqs = W.served_stream(40, seed=5)
+    if summary:
+        reqs = reqs[:10]
     storage = STORAGE_CODES[args.storage]
     free, _ = torch.cuda.mem_get_info(dev)
     pool = int(min(0.6 * free, 64 << 30))
@@ -519,6 +682,16 @@ def run_served(args):
         wall = time.perf_counter() - t0 - reqs[0][0]
         clk = clocks.stop()
         srv.close()
+    latency = {"step_ms_p50": weighted_percentile(step_ms, step_w, 0.5),
+               "step_ms_p99": weighted_percentile(step_ms, step_w, 0.99),
+               "request_s_p50": float(np.percentile(lat, 50)),
+               "request_s_p99": float(np.percentile(lat, 99))}
+    if summary:
+        return {"workload": "served_poisson20_%dreq_seed5" % len(reqs), "requests": len(reqs),
+                "storage": args.storage, "value": updates / wall / 1e6, "unit": UNIT,
+                "device_mlups": updates / (dev_ms / 1e3) / 1e6, "latency": latency,
+                "steps": int(sum(step_w)), "tick_steps": args.tick_steps, "peak_concurrent": max_active,
+                "wall_s": wall, "includes": "submission of host inputs, admission, all steps, results read back"}
     if rank == 0:
         line = {"metric": METRIC, "value": updates / wall / 1e6, "unit": UNIT, "n_gpus": world,
                 "steps": int(sum(step_w)), "warmup": 0, "ms_per_step": float(np.average(step_ms, weights=step_w)),
@@ -528,9 +701,7 @@ def run_served(args):
                            "storage": args.storage, "pool_gb": pool / 1e9, "max_active": 32,
                            "tick_steps": args.tick_steps, "peak_concurrent": max_active,
                            "parallelism": "replicas%d" % world},
-                "latency": {"step_ms_p50": weighted_percentile(step_ms, step_w, 0.5), "step_ms_p99": weighted_percentile(step_ms, step_w, 0.99),
-                            "request_s_p50": float(np.percentile(lat, 50)),
-                            "request_s_p99": float(np.percentile(lat, 99))},
+                "latency": latency,
                 "device_mlups": updates / (dev_ms / 1e3) / 1e6,
                 "e2e": {"value": updates / wall / 1e6, "unit": UNIT,
                         "includes": "submission of host inputs, admission, all steps, results read back"},
@@ -553,6 +724,10 @@ def main(argv=None):
     ap.add_argument("--tick-steps", type=int, default=100, help="served: steps per scheduling round")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline only: no reduced-storage, ensemble and served keys")
+    ap.add_argument("--windows", type=int, default=5,
+                    help="timed regions of exactly --steps steps each; the value is their median")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--links", choices=["index", "direct"], default="index",
                     help="links from the fixed index array (default) or by direct addressing (the paper's "
@@ -562,6 +737,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.windows < 1:
+        ap.error("--windows must be at least 1")
     if args.workload in ("ensemble64", "served"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the 4000^2 workload only"}))
