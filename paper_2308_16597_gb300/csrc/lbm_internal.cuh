@@ -378,20 +378,28 @@ __device__ __forceinline__ void df_offset(int i, float xh, float xl, float &h, f
     two_sum((float)i, -xh, h, e);
     l = e - xl;
 }
-// |d|^2 - r^2 for d = (i, j) - centre, with |error| < 1e-9 for |d| < 64.
-// Also returns d as double-float components.
-__device__ __forceinline__ float disk_gap2(int i, int j, const DiskDF &D, float &dxh, float &dxl,
-                                           float &dyh, float &dyl)
+// |d|^2 - r^2 for d = (i, j) - centre as an unevaluated sum t + low, with
+// |error| < 1e-9 for |d| < 64 and centre coordinates below 4096 (the error
+// grows with the coordinates' FP32 spacing).  Also returns d as double-float
+// components.
+__device__ __forceinline__ void disk_gap2_df(int i, int j, const DiskDF &D, float &t, float &low, float &dxh,
+                                             float &dxl, float &dyh, float &dyl)
 {
     df_offset(i, D.xh, D.xl, dxh, dxl);
     df_offset(j, D.yh, D.yl, dyh, dyl);
-    float p1, e1, p2, e2, s, es, t, et;
+    float p1, e1, p2, e2, s, es, et;
     two_prod(dxh, dxh, p1, e1);
     two_prod(dyh, dyh, p2, e2);
     two_sum(p1, p2, s, es);
     two_sum(s, -D.r2h, t, et);
-    const float low = ((e1 + e2) + (es + et)) - D.r2l + 2.f * (dxh * dxl + dyh * dyl) +
-                      (dxl * dxl + dyl * dyl);
+    low = ((e1 + e2) + (es + et)) - D.r2l + 2.f * (dxh * dxl + dyh * dyl) + (dxl * dxl + dyl * dyl);
+}
+// The same, rounded to FP32.
+__device__ __forceinline__ float disk_gap2(int i, int j, const DiskDF &D, float &dxh, float &dxl,
+                                           float &dyh, float &dyl)
+{
+    float t, low;
+    disk_gap2_df(i, j, D, t, low, dxh, dxl, dyh, dyl);
     return t + low;
 }
 // Exact disk predicate (the FP64 one above) decided in FP32 except inside a
@@ -407,21 +415,34 @@ __device__ __forceinline__ bool in_disk_df(int i, int j, const DiskDF &D, double
 }
 
 // Wall fraction q of the link from (i, j) along e_k to the circle: the
-// cancellation-free closed form, with |d|^2 - r^2 and d.e in double-float
-// and the rest in FP32; within 1e-6 relative of the FP64 value.  Also
-// returns d (FP32) for the wall velocity and torque.
+// cancellation-free closed form q = c / (-de + sqrt(de^2 - |e|^2 c)) with
+// c = |d|^2 - r^2 and de = d.e (de < 0 on a link).  c, de and the
+// discriminant are carried in double-float, so that near-tangent links,
+// whose small discriminant magnifies its absolute error by 1 / (2 sqrt(disc)),
+// see errors of about 1e-9 there instead of FP32 roundings of de^2 and c;
+// the square root, the sum and the division are FP32.  With u = 2^-24 (the
+// largest relative error of one FP32 rounding) and den = -de + sqrt(disc):
+//   |q - q_exact| <= 4.5 u q + (e_c + q e_de + q e_disc / (2 sqrt(disc))) / den,
+// e_c <= 2e-9, e_de <= 5e-11, e_disc <= 1e-8 for |d| < 32 and centre
+// coordinates below 4096 (the three scale with the coordinates' FP32 spacing
+// beyond).  Also returns d (FP32) for the wall velocity and torque.
 __device__ __forceinline__ float link_q_df(int i, int j, int k, const DiskDF &D, float &dxf,
                                            float &dyf)
 {
-    float dxh, dxl, dyh, dyl;
-    const float c = disk_gap2(i, j, D, dxh, dxl, dyh, dyl);
-    float sh, se;
+    float dxh, dxl, dyh, dyl, ch, cl;
+    disk_gap2_df(i, j, D, ch, cl, dxh, dxl, dyh, dyl);
+    float sh, se, deh, del;
     two_sum((float)ex(k) * dxh, (float)ey(k) * dyh, sh, se);
-    const float de = sh + (se + ((float)ex(k) * dxl + (float)ey(k) * dyl));
-    const float disc = fmaxf(de * de - (float)(ex(k) * ex(k) + ey(k) * ey(k)) * c, 0.f);
+    two_sum(sh, se + ((float)ex(k) * dxl + (float)ey(k) * dyl), deh, del);
+    // disc = de^2 - a c in double-float (a = |e_k|^2 is 1 or 2: a ch is exact)
+    const float a = (float)(ex(k) * ex(k) + ey(k) * ey(k));
+    float p, pe, s2, e2;
+    two_prod(deh, deh, p, pe);
+    two_sum(p, -a * ch, s2, e2);
+    const float disc = fmaxf(s2 + (e2 + ((pe + 2.f * deh * del) - a * cl)), 0.f);
     dxf = dxh + dxl;
     dyf = dyh + dyl;
-    return fminf(c / (sqrtf(disc) - de), 1.f);
+    return fminf((ch + cl) / (sqrtf(disc) - (deh + del)), 1.f);
 }
 
 // The ellipse predicate decided in FP32 (offsets from the double-float

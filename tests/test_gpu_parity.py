@@ -5,9 +5,10 @@ a common state agrees to rel-L2 <= 1e-6 per field; the coupled 256^2 run
 agrees to rel-L2 <= 1e-5 per field (rho - 1, ux, uy, T over the fluid nodes
 both runs share) after 100 steps, and the particle centres to 1e-4 lattice
 units.  Owner maps and the nodes of the fixed index array built from the
-same positions are bit-exact; the FP32 wall fractions q (FP64 |d|^2 - r^2,
-d.e in FP64, the rest of the closed form in FP32) agree with the oracle's
-FP64 q to 1e-6 relative.
+same positions are bit-exact; the FP32 wall fractions q of disks
+(double-float |d|^2 - r^2, d.e and discriminant, FP32 square root, sum and
+division) agree with the oracle's FP64 q within the per-link bound of
+q_bound, derived from those operations' rounding errors.
 """
 import numpy as np
 import pytest
@@ -52,10 +53,48 @@ def compare_fields(sim, ref, tol, min_norm=1e-12):
     return errs
 
 
-def same_q(q, oq):
-    q = q.astype(np.float64)
-    oq = oq.astype(np.float64)
-    return np.all(np.abs(q - oq) <= 1e-6 * np.abs(oq) + 1e-9)
+EX9 = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY9 = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+U32 = 2.0 ** -24  # largest relative error of one FP32 rounding
+
+
+def q_bound(node, oq, nx, parts):
+    """Per-slot bound on |q_gpu - q_oracle| for disks, derived from the
+    kernels' arithmetic (c = |d|^2 - r^2, d.e and the discriminant in
+    double-float; square root, sum and division in FP32; the oracle's FP64
+    root rounded to FP32): 5.5 u q + (e_c + q e_de + q e_disc / (2 sqrt(disc)))
+    / den with den = -d.e + sqrt(disc), e_c = 2e-9 s, e_de = 5e-11 s,
+    e_disc = 1e-8 s, s = max(1, largest centre coordinate / 4096).  Zero for
+    an ellipse, whose q both sides round from the same FP64 root."""
+    out = np.zeros(len(node))
+    base = 0
+    for P in parts:
+        N = orc.zone_size(P["r"])
+        cap = 12 * N - 12
+        sl = np.arange(cap)
+        n = node[base:base + cap]
+        ok = n >= 0
+        k = np.where(sl < 4 * N, 1 + sl // N, 5 + (sl - 4 * N) // (2 * N - 3))
+        if P["b"] > 0 and P["b"] != P["r"]:
+            base += cap
+            continue
+        i, j = (n % nx).astype(float), (n // nx).astype(float)
+        dx, dy = i - P["x"], j - P["y"]
+        de = EX9[k] * dx + EY9[k] * dy
+        c = dx * dx + dy * dy - P["r"] * P["r"]
+        disc = np.maximum(de * de - (EX9[k] ** 2 + EY9[k] ** 2) * c, 0.0)
+        sq = np.sqrt(disc)
+        den = np.where(ok, sq - de, 1.0)
+        q = oq[base:base + cap].astype(np.float64)
+        sc = max(1.0, abs(P["x"]) / 4096, abs(P["y"]) / 4096)
+        b = 5.5 * U32 * q + (2e-9 * sc + q * 5e-11 * sc + q * 1e-8 * sc / (2 * np.maximum(sq, 1e-300))) / den
+        out[base:base + cap] = np.where(ok, b, 0.0)
+        base += cap
+    return out
+
+
+def same_q(q, oq, node, nx, parts):
+    return np.all(np.abs(q.astype(np.float64) - oq.astype(np.float64)) <= q_bound(node, oq, nx, parts))
 
 
 def base_f():
@@ -140,7 +179,7 @@ def test_owner_map_and_fixed_slots_are_bit_exact():
     onode, oq, over = orc.build_slots(wl.nx, wl.ny, own0, wl.particles)
     assert over == 0
     assert np.array_equal(node, onode)
-    assert same_q(q, oq)
+    assert same_q(q, oq, node, wl.nx, wl.particles)
     # later steps: slots of the last step equal the oracle's slots built from
     # the positions the GPU had at the start of that step
     for _ in range(3):
@@ -151,7 +190,7 @@ def test_owner_map_and_fixed_slots_are_bit_exact():
         onode, oq, _ = orc.build_slots(wl.nx, wl.ny, own, p)
         node, q = sim.slots()
         assert np.array_equal(node, onode)
-        assert same_q(q, oq)
+        assert same_q(q, oq, node, wl.nx, p)
         assert np.array_equal(sim.owner(), orc.raster(wl.nx, wl.ny, sim.particles()))
 
 
@@ -169,7 +208,7 @@ def test_slots_match_brute_force_links_for_random_radii(seed):
     onode, oq, over = orc.build_slots(nx, ny, own, parts)
     node, q = sim.slots()
     assert over == 0 and np.array_equal(node, onode)
-    assert same_q(q, oq)
+    assert same_q(q, oq, node, nx, parts)
     bn, bd, bp, bq = orc.links_bruteforce(nx, ny, own, parts)
     assert (node >= 0).sum() == len(bn)
     assert sim.counters()[7] == len(bn)
@@ -178,8 +217,8 @@ def test_slots_match_brute_force_links_for_random_radii(seed):
 def test_largest_supported_disks_slots_and_forces():
     """Radii 28.0 and 28.4: link windows of 63 and 64 columns (zones of 59 and
     60 nodes plus the two-node margins), the limit of the 64-bit row masks, so
-    both 32-column ballot words of every row are in use.  Owner map, slots and
-    q bit-exact / within 1e-6, every brute-force link found, first-step
+    both 32-column ballot words of every row are in use.  Owner map and slots
+    bit-exact, q within its derived bound, every brute-force link found, first-step
     forces and fields as for the small disks."""
     nx, ny = 200, 160
     parts = np.zeros(2, W.PARTICLE_DTYPE)
@@ -201,7 +240,7 @@ def test_largest_supported_disks_slots_and_forces():
     node, q = sim.slots()
     onode, oq, over = orc.build_slots(nx, ny, own, parts)
     assert over == 0 and np.array_equal(node, onode)
-    assert same_q(q, oq)
+    assert same_q(q, oq, node, nx, parts)
     bn, bd, bp, bq = orc.links_bruteforce(nx, ny, own, parts)
     assert (node >= 0).sum() == len(bn) and sim.counters()[7] == len(bn)
     Fg, Fo = sim.forces(), ref.forces()
@@ -209,6 +248,67 @@ def test_largest_supported_disks_slots_and_forces():
     assert np.abs(Fg[:, 2] - Fo[:, 2]).max() <= 1e-5 * np.abs(Fo[:, 2]).max()
     compare_fields(sim, ref, 1e-6)
     sim.close()
+
+
+def worst_link_disks(seed=5):
+    """Disks (x, y, r) that put one link (i, j, k) at an extreme of the wall
+    fraction's conditioning, centres near x = 3960 (where the FP32 spacing
+    of the coordinates is 2^-12): the solid node B = A + e_k barely inside
+    (depth 1e-9..1e-6) on a line within 1e-4 rad of tangent to the circle
+    (q near 1, discriminant near 0), A barely outside (q near 0), or B
+    barely inside (q near 1), for each direction; r = 28.4 on the axis
+    directions' odd-numbered ones."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for kind in ("tangent", "q0", "q1"):
+        for k in range(1, 9):
+            r = 28.4 if k % 2 else float(rng.uniform(9.0, 28.4))
+            e = np.array([EX9[k], EY9[k]], float)
+            el = np.linalg.norm(e)
+            perp = np.array([-e[1], e[0]]) / el
+            for _ in range(1000):
+                A = np.array([float(rng.integers(3930, 3990)), float(rng.integers(70, 180))])
+                B = A + e
+                if kind == "tangent":
+                    delta, phi = float(rng.uniform(1e-9, 1e-6)), float(rng.uniform(-1e-4, 1e-4))
+                    c = B + (r - delta) * (perp * np.cos(phi) - e / el * np.sin(phi))
+                else:
+                    ang = float(rng.uniform(0, 2 * np.pi))
+                    n = np.array([np.cos(ang), np.sin(ang)])
+                    c = (A + (r + float(rng.uniform(1e-8, 1e-5))) * n if kind == "q0"
+                         else B + (r - float(rng.uniform(1e-8, 1e-5))) * n)
+                if np.hypot(*(A - c)) > r >= np.hypot(*(B - c)):
+                    out.append((float(c[0]), float(c[1]), r, int(A[0]), int(A[1]), k, kind))
+                    break
+    return out
+
+
+def test_wall_fraction_within_its_derived_bound_at_worst_geometries():
+    """The disk q of every link within the bound of q_bound, on disks built
+    so that one link each sits at a tangent line (discriminant ~1e-5, where
+    FP32 roundings of d.e^2 and c would give errors of ~1e-5), at q -> 0 and
+    at q -> 1, with centres near x = 3960; slot nodes bit-exact."""
+    nx, ny = 4064, 256
+    cases = worst_link_disks()
+    assert len(cases) == 24
+    prm = W.base_params(0.05, 0.71, 0.0, fixed_particles=1)
+    worst = 0.0
+    for x, y, r, i, j, k, kind in cases:
+        parts = np.zeros(1, W.PARTICLE_DTYPE)
+        parts["x"], parts["y"], parts["r"], parts["rho"] = x, y, r, 1.5
+        sim = lbm.Simulation(W.cavity(nx, ny), parts, prm)
+        sim.step(1)
+        node, q = sim.slots()
+        own = orc.raster(nx, ny, parts)
+        onode, oq, over = orc.build_slots(nx, ny, own, parts)
+        assert over == 0 and np.array_equal(node, onode)
+        assert j * nx + i in set(onode.tolist()), (kind, k)
+        err = np.abs(q.astype(np.float64) - oq.astype(np.float64))
+        b = q_bound(node, oq, nx, parts)
+        assert np.all(err <= b), (kind, k, (err / np.where(b > 0, b, 1)).max())
+        worst = max(worst, float((err / np.where(b > 0, b, 1)).max()))
+        sim.close()
+    print("largest error / bound: %.3f" % worst)
 
 
 # --------------------------------------------------------------------------- coupled
