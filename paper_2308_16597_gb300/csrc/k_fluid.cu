@@ -566,8 +566,9 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
 
 // General path, beside the stream-collide kernel (it reads only the previous
 // state and writes only nodes that kernel leaves alone): the fluid nodes of
-// the cavity frame (walls, periodic seams) and the newborn nodes listed by
-// k_flags, each pulled (or refilled, Sec. 2.5) by slow_node and collided.
+// the cavity frame (walls, periodic seams) and the newborn nodes off the
+// frame listed by k_flags, each pulled (or refilled, Sec. 2.5) by slow_node
+// and collided.
 // A fixed grid strides over the 2 nx + 2 (ny - 2) frame nodes and then the
 // list, whose length the device holds.
 template <typename T>
@@ -588,6 +589,7 @@ __device__ __forceinline__ void boundary_body(const Dev &D, const T *__restrict_
         else if (idx < nframe) { x = nx - 1; y = 1 + idx - 2 * nx - (ny - 2); }
         else {
             const int n = D.newborn[idx - nframe];
+            if (n < 0) continue; // a newborn node on the frame: visited above
             y = n / nx;
             x = n - y * nx;
         }

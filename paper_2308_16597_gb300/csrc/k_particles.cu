@@ -93,10 +93,24 @@ __device__ __forceinline__ void clear_cells_slice(const Dev &D, int parity, int 
         if (in_bounds(D, c, (long long)nc * (1 + kCellCap))) grid[c] = 0;
 }
 
+// The last step's newborn nodes (fluid now, listed by the flags kernel of
+// that step) go back to plain fluid: the flags kernel of this step rewrites
+// only the nodes whose class changes at the particles' edges.  Entries of
+// block p of np blocks of nthreads threads.
+__device__ __forceinline__ void revert_newborn(const Dev &D, int p, int tid, int nthreads)
+{
+    const int nb = min((int)D.status->nb, D.newborn_cap);
+    for (int e = p * nthreads + tid; e < nb; e += D.np * nthreads) {
+        const int v = D.newborn[e], n = v < 0 ? ~v : v;
+        const int y = n / D.nx, x = n - y * D.nx;
+        if (in_bounds(D, (long long)y * D.pitch + x, (long long)D.ny * D.pitch)) D.flags[(long long)y * D.pitch + x] = kFluid;
+    }
+}
+
 // One CTA per particle.  Phases:
 //  0. clear this CTA's share of the screening grid the update fills next,
 //     and the particle's zone one step back in the owner map that the
-//     raster fills next;
+//     raster fills next; return the last step's newborn nodes to fluid;
 //  1. the warps read the owner map over the particle's window (zone plus
 //     the two-node margin of the bounce-back stencil) and record per row a
 //     fluid mask and an owned-by-this-particle mask (one ballot per 32
@@ -154,6 +168,7 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
     // n + 1) still holds positions n - 1: clear this particle's zone of that
     // time
     clear_cells_slice(D, parity, p, tid, kLinkThreads);
+    revert_newborn(D, p, tid, kLinkThreads);
     {
         const GeomRec Gp = D.geo_prev[p];
         for (int r = warp; r < Gp.N; r += kLinkThreads / 32) {
@@ -597,9 +612,10 @@ __device__ __forceinline__ void disk_run(const Dev &D, const Box &B, const GeomR
 }
 
 // Raster of one particle by one warp: lane per zone row for the runs, then
-// coalesced writes.
+// coalesced writes.  runs (may be null): the particle's row runs (lo, hi),
+// empty when lo > hi, kept for the next step's flags.
 __device__ __forceinline__ void raster_one(const Dev &D, int *own, const GeomRec &G, double x, double y, double r,
-                                           double th, double pb, int p)
+                                           double th, double pb, int p, int2 *runs)
 {
     const int lane = threadIdx.x & 31;
     const Box B = box_of(G);
@@ -609,6 +625,8 @@ __device__ __forceinline__ void raster_one(const Dev &D, int *own, const GeomRec
         if (b0 + lane < B.N) {
             if (G.r < 0.f) ellipse_run(D, B, G, x, y, th, r, pb, j, lo, hi);
             else disk_run(D, B, G, x, y, r, j, lo, hi);
+            if (runs && in_bounds(D, (long long)p * D.zone_max + b0 + lane, (long long)D.np * D.zone_max))
+                runs[b0 + lane] = make_int2(lo, hi);
         }
         write_runs(D, own, B, b0, lo, hi, p);
     }
@@ -788,7 +806,7 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
         // the new position into the next step's screening grid (its atomic
         // round trip overlaps the raster)
         if (lane == 0) cell_insert(D, D.cells[parity ^ 1], a, R.G.xh, R.G.yh);
-        raster_one(D, own_nxt, R.G, R.x, R.y, R.r, R.th, R.b, a);
+        raster_one(D, own_nxt, R.G, R.x, R.y, R.r, R.th, R.b, a, D.runs[parity ^ 1] + (long long)a * D.zone_max);
     }
 }
 
@@ -804,41 +822,72 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
 // runs are then written row by row with coalesced atomicMax requests.
 
 __device__ __forceinline__ void raster_body(const Dev &D, int *own, const GeomRec *__restrict__ geo,
-                                            const PartSoA &pos, const int blk)
+                                            const PartSoA &pos, int2 *runs, const int blk)
 {
     const int p = blk * (kBoxThreads / 32) + (threadIdx.x >> 5);
     if (p >= D.np) return;
-    raster_one(D, own, geo[p], pos.x[p], pos.y[p], pos.r[p], pos.th[p], pos.b[p], p);
+    raster_one(D, own, geo[p], pos.x[p], pos.y[p], pos.r[p], pos.th[p], pos.b[p], p,
+               runs ? runs + (long long)p * D.zone_max : nullptr);
 }
 
-// Flags over the rectangle that holds the particle's zones one step back, now
-// and next (so every node whose flag may have changed since the last step):
-// solid at the new time, newborn (solid before, fluid now) or fluid, from
-// the two owner maps.  A team of TEAM warps per particle (one warp when the
-// particles alone fill the GPU, else 2 or 4): team warp w
-// takes rows w kU .. w kU + kU - 1 of every TEAM kU rows, eight at a time
-// (all loads issued first), lane l columns l and l + 32 of every 64.  During
-// a step team warp 0 also moves the particle's new state into the current
-// slot and keeps the old position for the next clear.
+// Class of a node from the two owner maps: solid at the new time, newborn
+// (solid before, fluid now) or fluid.
+__device__ __forceinline__ uint8_t node_class(int oc, int on) { return on >= 0 ? kSolid : oc >= 0 ? kNewborn : kFluid; }
+
+// A newborn node into this step's list (j * nx + i off the cavity frame,
+// ~(j * nx + i) on it, where the general path takes it anyway).
+__device__ __forceinline__ void list_newborn(const Dev &D, int i, int j)
+{
+    const unsigned at = atomicAdd(&D.status->nb, 1u);
+    const int n = j * D.nx + i;
+    const bool frame = i == 0 || i == D.nx - 1 || j == 0 || j == D.ny - 1;
+    if (at < (unsigned)D.newborn_cap) D.newborn[at] = frame ? ~n : n;
+    else atomicOr(&D.status->err, kErrOverflow);
+}
+
+// Nodes of run [lo, hi] of row j outside run [xlo, xhi] (one or two
+// intervals; all of it when [xlo, xhi] is empty), in order.
+template <typename F>
+__device__ __forceinline__ void run_minus(int lo, int hi, int xlo, int xhi, F &&f)
+{
+    if (xlo > xhi) {
+        for (int i = lo; i <= hi; ++i) f(i);
+        return;
+    }
+    for (int i = lo; i <= min(hi, xlo - 1); ++i) f(i);
+    for (int i = max(lo, xhi + 1); i <= hi; ++i) f(i);
+}
+
+// Node flags of a step.  Before it, every node holds its class for the
+// previous step (the link kernel has returned that step's newborn nodes to
+// fluid); a node's class can only change where it enters or leaves a
+// particle, so the team of particle p visits, row by row, the nodes of its
+// disk at the new position outside its disk at the current one (solid now:
+// every disk holding a node writes the same class) and the nodes of its
+// current disk outside the new one (solid if another particle now holds
+// them, else newborn, listed once, by the particle that owned the node),
+// from the row runs the rasters kept.  A team of TEAM warps per particle
+// (one warp when the particles alone fill the GPU, else 2 or 4), lane l on
+// rows l, l + 32 TEAM, ...  Team warp 0 also moves the particle's new state
+// into the current slot and keeps the old position for the next clear.
+// Initialisation (rotate == 0): every node of the zone rectangle from the
+// owner map (own_cur == own_nxt), nothing listed.
 template <int TEAM>
 __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__ own_cur,
-                                           const int *__restrict__ own_nxt, int rotate, const int p)
+                                           const int *__restrict__ own_nxt, int rotate, int parity, const int p)
 {
     const int lane = threadIdx.x & 31, tw = (threadIdx.x >> 5) % TEAM;
-    constexpr int kU = 8;
     // a team past the last particle still reaches the block barrier below
     const bool act = p < D.np; // uniform across the team
-    const bool list = rotate != 0; // a step (not the initial flags): list the newborn nodes
-    Box Ba{0, 0, 0}, Bb{0, 0, 0}, Bc{0, 0, 0};
+    Box Bb{0, 0, 0}, Bc{0, 0, 0};
     if (act) {
-        Ba = box_of(D.geo_prev[p]);
         Bb = box_of(D.geo_cur[p]);
         Bc = box_of(D.geo_nxt[p]);
     }
     if (rotate) {
         // the new state moves into the current slot (and the current position
         // into the previous one) while the other threads work on the flags;
-        // every thread of the team has read the three boxes before
+        // every thread of the team has read the boxes before
         if (TEAM == 1) __syncwarp();
         else __syncthreads();
         if (act && tw == 0) switch (lane) {
@@ -853,42 +902,44 @@ __device__ __forceinline__ void flags_body(const Dev &D, const int *__restrict__
         }
     }
     if (!act) return;
-    const int X0 = max(min(min(Ba.X0, Bb.X0), Bc.X0), 0);
-    const int Y0 = max(min(min(Ba.Y0, Bb.Y0), Bc.Y0), 0);
-    const int X1 = min(max(max(Ba.X0 + Ba.N, Bb.X0 + Bb.N), Bc.X0 + Bc.N), D.nx); // exclusive
-    const int Y1 = min(max(max(Ba.Y0 + Ba.N, Bb.Y0 + Bb.N), Bc.Y0 + Bc.N), D.ny);
-    for (int c0 = X0; c0 < X1; c0 += 64)
-        for (int r0 = Y0 + tw * kU; r0 < Y1; r0 += TEAM * kU) {
-            int oc[kU][2], on[kU][2];
-#pragma unroll
-            for (int t = 0; t < kU; ++t)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = r0 + t, i = c0 + lane + 32 * h;
-                    const bool v = j < Y1 && i < X1;
-                    const long long n = (long long)j * D.nx + i;
-                    oc[t][h] = v ? own_cur[n] : -3;
-                    on[t][h] = v ? own_nxt[n] : -3;
-                }
-#pragma unroll
-            for (int t = 0; t < kU; ++t)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (oc[t][h] == -3) continue;
-                    const int j = r0 + t, i = c0 + lane + 32 * h;
-                    const uint8_t f = on[t][h] >= 0 ? kSolid : oc[t][h] >= 0 ? kNewborn : kFluid;
-                    if (in_bounds(D, (long long)j * D.pitch + i, (long long)D.ny * D.pitch))
-                        D.flags[(long long)j * D.pitch + i] = f;
-                    // each newborn node once: by the particle that owned it;
-                    // frame nodes are always on the general path
-                    if (list && f == kNewborn && oc[t][h] == p && i > 0 && i < D.nx - 1 && j > 0 &&
-                        j < D.ny - 1) {
-                        const unsigned at = atomicAdd(&D.status->nb, 1u);
-                        if (at < (unsigned)D.newborn_cap) D.newborn[at] = j * D.nx + i;
-                        else atomicOr(&D.status->err, kErrOverflow);
-                    }
-                }
+    const long long nflags = (long long)D.ny * D.pitch;
+    if (!rotate) {
+        // every node of the zone (one position: own_cur == own_nxt)
+        for (int r = tw; r < Bb.N; r += TEAM) {
+            const int j = Bb.Y0 + r;
+            if (j < 0 || j >= D.ny) continue;
+            for (int c = lane; c < Bb.N; c += 32) {
+                const int i = Bb.X0 + c;
+                if (i < 0 || i >= D.nx) continue;
+                const int n = j * D.nx + i;
+                const long long o = (long long)j * D.pitch + i;
+                if (in_bounds(D, o, nflags)) D.flags[o] = node_class(own_cur[n], own_nxt[n]);
+            }
         }
+        return;
+    }
+    const int2 *Ro = D.runs[parity] + (long long)p * D.zone_max;     // current position
+    const int2 *Rn = D.runs[parity ^ 1] + (long long)p * D.zone_max; // new position
+    const int ylo = min(Bb.Y0, Bc.Y0), yhi = max(Bb.Y0 + Bb.N, Bc.Y0 + Bc.N);
+    for (int j = ylo + tw * 32 + lane; j < yhi; j += TEAM * 32) {
+        if (j < 0 || j >= D.ny) continue;
+        int2 o = make_int2(1, 0), w = make_int2(1, 0);
+        if (j - Bb.Y0 >= 0 && j - Bb.Y0 < Bb.N) o = Ro[j - Bb.Y0];
+        if (j - Bc.Y0 >= 0 && j - Bc.Y0 < Bc.N) w = Rn[j - Bc.Y0];
+        const long long row = (long long)j * D.pitch;
+        // entering the particle: solid at the new time
+        run_minus(w.x, w.y, o.x, o.y, [&](int i) {
+            if (in_bounds(D, row + i, nflags)) D.flags[row + i] = kSolid;
+        });
+        // leaving it: newborn unless another particle holds the node now
+        run_minus(o.x, o.y, w.x, w.y, [&](int i) {
+            const int n = j * D.nx + i;
+            const int oc = own_cur[n];
+            const uint8_t f = node_class(oc, own_nxt[n]);
+            if (in_bounds(D, row + i, nflags)) D.flags[row + i] = f;
+            if (f == kNewborn && oc == p) list_newborn(D, i, j);
+        });
+    }
 }
 
 // Near-tile bitmap: every warp tile (one row, 32 V nodes) that meets a
@@ -911,12 +962,14 @@ __global__ void __launch_bounds__(128) k_near_mask(const Dev D, int span)
 }
 
 // ---- direct addressing (comparison with the index array)
-// Per particle: clear its zone one step back in the next owner map, publish
-// its centre for the pair screening, zero its sums.
+// Per particle: clear its zone one step back in the next owner map, return
+// the last step's newborn nodes to fluid, publish its centre for the pair
+// screening, zero its sums.
 __global__ void __launch_bounds__(kBoxThreads) k_direct_prep(const Dev D, int *__restrict__ own_nxt, int parity)
 {
     const int p = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     clear_cells_slice(D, parity, p, threadIdx.x, kBoxThreads);
+    revert_newborn(D, p, threadIdx.x, kBoxThreads);
     const GeomRec Gp = D.geo_prev[p];
     for (int r = warp; r < Gp.N; r += kBoxThreads / 32) {
         const int j = Gp.Y0 + r;
@@ -1035,15 +1088,15 @@ __global__ void __launch_bounds__(kPartThreads, 4) k_particles(const Dev D, int 
     particles_body(D, parity, own_nxt, (int)blockIdx.x);
 }
 __global__ void __launch_bounds__(kBoxThreads)
-    k_raster(const Dev D, int *own, const GeomRec *__restrict__ geo, const PartSoA pos)
+    k_raster(const Dev D, int *own, const GeomRec *__restrict__ geo, const PartSoA pos, int2 *runs)
 {
-    raster_body(D, own, geo, pos, (int)blockIdx.x);
+    raster_body(D, own, geo, pos, runs, (int)blockIdx.x);
 }
 template <int TEAM>
 __global__ void __launch_bounds__(kBoxThreads, 9)
-    k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate)
+    k_flags(const Dev D, const int *__restrict__ own_cur, const int *__restrict__ own_nxt, int rotate, int parity)
 {
-    flags_body<TEAM>(D, own_cur, own_nxt, rotate,
+    flags_body<TEAM>(D, own_cur, own_nxt, rotate, parity,
                      (int)blockIdx.x * (kBoxThreads / 32 / TEAM) + (int)(threadIdx.x >> 5) / TEAM);
 }
 
@@ -1078,7 +1131,8 @@ __global__ void __launch_bounds__(kBoxThreads)
     const int i = batch_find(start, n, (int)blockIdx.x);
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
-    raster_body(sD, a.own[parity ^ a.poff ^ 1], sD.geo_nxt, sD.nxt, (int)blockIdx.x - __ldg(start + i));
+    raster_body(sD, a.own[parity ^ a.poff ^ 1], sD.geo_nxt, sD.nxt, sD.runs[parity ^ a.poff ^ 1],
+                (int)blockIdx.x - __ldg(start + i));
 }
 __global__ void __launch_bounds__(kBoxThreads)
     k_flags_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
@@ -1088,7 +1142,7 @@ __global__ void __launch_bounds__(kBoxThreads)
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
     const int par = parity ^ a.poff;
-    flags_body<1>(sD, a.own[par], a.own[par ^ 1], 1,
+    flags_body<1>(sD, a.own[par], a.own[par ^ 1], 1, par,
                   ((int)blockIdx.x - __ldg(start + i)) * (kBoxThreads / 32) + (int)(threadIdx.x >> 5));
 }
 
@@ -1298,11 +1352,11 @@ cudaError_t launch_particles(const Dev &D, int parity, int *own_nxt, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_raster(const Dev &D, int *own, const GeomRec *geo, const PartSoA &pos, cudaStream_t s)
+cudaError_t launch_raster(const Dev &D, int *own, const GeomRec *geo, const PartSoA &pos, int2 *runs, cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
     const int per = kBoxThreads / 32;
-    k_raster<<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own, geo, pos);
+    k_raster<<<(D.np + per - 1) / per, kBoxThreads, 0, s>>>(D, own, geo, pos, runs);
     return cudaGetLastError();
 }
 
@@ -1325,17 +1379,33 @@ cudaError_t launch_cells_init(const Dev &D, int parity, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate,
+cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate, int parity,
                          cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
     const int per = kBoxThreads / 32 / max(D.flag_team, 1); // particles per block
     const int grid = (D.np + per - 1) / per;
     switch (D.flag_team) {
-    case 4: k_flags<4><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate); break;
-    case 2: k_flags<2><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate); break;
-    default: k_flags<1><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate); break;
+    case 4: k_flags<4><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate, parity); break;
+    case 2: k_flags<2><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate, parity); break;
+    default: k_flags<1><<<grid, kBoxThreads, 0, s>>>(D, own_cur, own_nxt, rotate, parity); break;
     }
+    return cudaGetLastError();
+}
+
+// Newborn nodes of a restored state: every node whose flag says newborn
+// goes into the list (emptied first by the caller), which the next step's
+// link kernel returns to fluid.
+__global__ void k_collect_newborn(const Dev D)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= D.nx) return;
+    if (D.flags[(long long)j * D.pitch + i] == kNewborn) list_newborn(D, i, j);
+}
+
+cudaError_t launch_collect_newborn(const Dev &D, cudaStream_t s)
+{
+    k_collect_newborn<<<dim3((D.nx + 127) / 128, D.ny), 128, 0, s>>>(D);
     return cudaGetLastError();
 }
 

@@ -123,6 +123,8 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
     for (int a = 0; a < n; ++a) zmax = std::max(zmax, zone_size(p[a].r));
     L.newborn_cap = std::max(1024, 4 * n * zmax);
     L.newborn = take((size_t)L.newborn_cap * sizeof(int));
+    // each zone row's run of inside nodes, at the current and the next positions
+    for (int b = 0; b < 2; ++b) L.runs[b] = take((size_t)n * std::max(zmax, 1) * sizeof(int2));
     L.near = take(((size_t)d->ny * near_tiles_per_row(storage, L.pitch) + 31) / 32 * sizeof(unsigned));
     L.dsum = take((size_t)n * sizeof(DirectSums));
     // cell grid of the pair screening: side 2 r_max + s + 2 (every pair in
@@ -252,7 +254,7 @@ int enqueue_step(lbm_handle *h, int par, cudaStream_t st)
     // particle update and raster of the new positions (one kernel)
     if ((rc = timed(h, kKParticles, st, [&] { return launch_particles(D, par, on, st); }))) return rc;
     if (h->np > 0) {
-        if ((rc = timed(h, kKFlags, st, [&] { return launch_flags(D, oc, on, 1, st); }))) return rc;
+        if ((rc = timed(h, kKFlags, st, [&] { return launch_flags(D, oc, on, 1, par, st); }))) return rc;
     }
     if (overlap && !serial) CK(h, cudaStreamWaitEvent(st, h->join0, 0));
     const int kind = overlap ? kKStreamCollideNear : kKStreamCollide;
@@ -367,6 +369,7 @@ void fill_dev(lbm_handle *h)
     D.flags = reinterpret_cast<uint8_t *>(ws + L.flags);
     D.newborn = reinterpret_cast<int *>(ws + L.newborn);
     D.newborn_cap = L.newborn_cap;
+    for (int b = 0; b < 2; ++b) D.runs[b] = reinterpret_cast<int2 *>(ws + L.runs[b]);
     D.near = reinterpret_cast<unsigned *>(ws + L.near);
     D.dsum = reinterpret_cast<DirectSums *>(ws + L.dsum);
     D.direct = (P.flags & LBM_FLAG_DIRECT_LINKS) ? 1 : 0;
@@ -429,13 +432,15 @@ int rebuild_maps(lbm_handle *h)
     int *oc = h->own[h->parity];
     CK(h, launch_geom_init(h->D, h->stream));
     CK(h, launch_cells_init(h->D, h->parity, h->stream));
-    CK(h, launch_raster(h->D, oc, h->D.geo_cur, h->D.cur, h->stream));
-    CK(h, launch_flags(h->D, oc, oc, 0, h->stream));
+    CK(h, launch_raster(h->D, oc, h->D.geo_cur, h->D.cur, h->D.runs[h->parity], h->stream));
+    CK(h, launch_flags(h->D, oc, oc, 0, h->parity, h->stream));
+    // no newborn node yet
+    CK(h, cudaMemsetAsync(&h->D.status->nb, 0, sizeof(unsigned), h->stream));
     // the owner map one step back, which the first clear expects in the other buffer
     PartSoA prev = h->D.cur;
     prev.x = h->D.px;
     prev.y = h->D.py;
-    CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, h->stream));
+    CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, nullptr, h->stream));
     return LBM_OK;
 }
 
@@ -720,7 +725,13 @@ int lbm_set_state(lbm_handle *h, const void *buf, size_t bytes)
         prev.y = h->D.py;
         CK(h, launch_geom_init(h->D, h->stream));
         CK(h, launch_cells_init(h->D, h->parity, h->stream));
-        CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, h->stream));
+        CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, nullptr, h->stream));
+        // the row runs of the restored positions (their raster rewrites the
+        // restored owner map with the values it holds), and the newborn
+        // list of the restored flags, which the next step returns to fluid
+        CK(h, launch_raster(h->D, h->own[h->parity], h->D.geo_cur, h->D.cur, h->D.runs[h->parity], h->stream));
+        CK(h, cudaMemsetAsync(&h->D.status->nb, 0, sizeof(unsigned), h->stream));
+        CK(h, launch_collect_newborn(h->D, h->stream));
     }
     return sync_status(h);
 }

@@ -120,8 +120,9 @@ struct Dev {
     int flag_team;     // warps per particle in the flags kernel (1, 2 or 4)
     // device buffers
     uint8_t *flags;    // [ny][pitch]
-    int *newborn;      // [newborn_cap]: j * nx + i of this step's newborn nodes off the cavity frame
+    int *newborn;      // [newborn_cap]: this step's newborn nodes, j * nx + i off the cavity frame, ~(j * nx + i) on it
     int newborn_cap;
+    int2 *runs[2];     // [np][zone_max] by step parity: each zone row's run (lo, hi) of nodes inside the particle
     unsigned *near;    // bit per warp tile (row, 32 V nodes) within reach of a particle this step
     int near_tpr;      // warp tiles per row of that bitmap
     long long nslots;  // slots of the fixed index array
@@ -846,10 +847,16 @@ bool link_zone_supported(int N, int storage);
 cudaError_t prepare_links(Dev &D);
 // Particle update, then the raster of the new positions into own_nxt.
 cudaError_t launch_particles(const Dev &D, int parity, int *own_nxt, cudaStream_t s);
-cudaError_t launch_raster(const Dev &D, int *own, const struct GeomRec *geo, const PartSoA &pos,
+// runs (may be null): where each particle's zone-row runs go, for the flags
+// of the next step.
+cudaError_t launch_raster(const Dev &D, int *own, const struct GeomRec *geo, const PartSoA &pos, int2 *runs,
                           cudaStream_t s);
-cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate,
+// rotate == 0: the flags of one position from scratch; rotate == 1: a step's
+// flags from the row runs of parity (current) and parity ^ 1 (new).
+cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate, int parity,
                          cudaStream_t s);
+// The newborn list of a restored state, from its flags (the list is empty).
+cudaError_t launch_collect_newborn(const Dev &D, cudaStream_t s);
 cudaError_t launch_pack_particles(const Dev &D, lbm_particle *out, cudaStream_t s);
 // Geometry records of the current state (into cur, nxt and prev) and of the
 // previous positions (into prev), for init and restore.

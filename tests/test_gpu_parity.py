@@ -403,18 +403,22 @@ def test_node_flags_are_bit_exact():
     node after the step, newborn where one held it before and none does
     after, fluid elsewhere; both owner maps from the oracle's raster of the
     GPU's positions.  Two translating disks and a translating, spinning
-    ellipse uncover nodes every step."""
-    parts = np.zeros(3, W.PARTICLE_DTYPE)
-    parts["x"], parts["y"] = [40.3, 90.6, 140.2], [50.2, 47.7, 52.9]
-    parts["r"], parts["b"] = [8.5, 8.5, 11.0], [0.0, 0.0, 5.0]
-    parts["theta"] = [0.0, 0.0, 0.7]
+    ellipse uncover nodes every step, and two disks that start over the
+    first column and the first row of the cavity uncover nodes of its frame
+    (weak wall repulsion keeps them below a node per step)."""
+    parts = np.zeros(5, W.PARTICLE_DTYPE)
+    parts["x"], parts["y"] = [40.3, 90.6, 140.2, 8.2, 120.4], [50.2, 47.7, 52.9, 30.3, 8.15]
+    parts["r"], parts["b"] = [8.5, 8.5, 11.0, 8.5, 8.5], [0.0, 0.0, 5.0, 0.0, 0.0]
+    parts["theta"] = [0.0, 0.0, 0.7, 0.0, 0.0]
     parts["rho"], parts["T"] = 1.5, 1.0
-    parts["ux"], parts["uy"] = [0.04, -0.03, 0.02], [-0.02, 0.035, -0.03]
-    parts["omega"] = [0.0, 0.0, 0.02]
+    parts["ux"], parts["uy"] = [0.04, -0.03, 0.02, 0.12, 0.0], [-0.02, 0.035, -0.03, 0.0, 0.12]
+    parts["omega"] = [0.0, 0.0, 0.02, 0.0, 0.0]
     nx, ny = 180, 100
-    sim = lbm.Simulation(W.cavity(nx, ny), parts, W.base_params(0.05, 0.71, 1e-4))
+    own0 = orc.raster(nx, ny, parts)
+    assert (own0[:, 0] == 3).any() and (own0[0, :] == 4).any()  # frame nodes inside disks 3 and 4
+    sim = lbm.Simulation(W.cavity(nx, ny), parts, W.base_params(0.05, 0.71, 1e-4, eps_w=1e3))
     assert np.array_equal(state_flags(sim, nx, ny), (orc.raster(nx, ny, parts) >= 0).astype(np.uint8))
-    newborn = 0
+    newborn = frame_newborn = 0
     for _ in range(25):
         p0 = sim.particles()
         sim.step(1)
@@ -424,7 +428,8 @@ def test_node_flags_are_bit_exact():
         assert np.array_equal(state_flags(sim, nx, ny), exp)
         assert sim.counters()[6] == (exp == 2).sum()
         newborn += int((exp == 2).sum())
-    assert newborn > 0
+        frame_newborn += int((exp[:, 0] == 2).sum() + (exp[0, :] == 2).sum())
+    assert newborn > 0 and frame_newborn > 0
     sim.close()
 
 
@@ -449,6 +454,34 @@ def test_checkpoint_restore_is_bit_exact():
     b.step(30)
     assert np.array_equal(a.get_state(), b.get_state())
     assert np.array_equal(a.particles(), b.particles())
+
+
+def test_restore_with_newborn_nodes_keeps_the_flags_exact():
+    """A state saved right after a step that uncovered nodes (its flags hold
+    newborn nodes) and restored into a new handle: the next steps' flags are
+    the node classes of the oracle's rasters, as in a run that never
+    stopped, and the two runs stay bit-identical."""
+    parts = np.zeros(2, W.PARTICLE_DTYPE)
+    parts["x"], parts["y"] = [30.3, 70.6], [30.2, 28.7]
+    parts["r"] = 7.5
+    parts["rho"], parts["T"] = 1.5, 1.0
+    parts["ux"], parts["uy"] = [0.05, -0.04], [0.03, 0.05]
+    nx, ny = 100, 60
+    dom, prm = W.cavity(nx, ny), W.base_params(0.05, 0.71, 1e-4)
+    a = lbm.Simulation(dom, parts, prm)
+    a.step(7)
+    snap = a.get_state()
+    assert (state_flags(a, nx, ny) == 2).any()
+    b = lbm.Simulation(dom, parts, prm)
+    b.set_state(snap)
+    for _ in range(5):
+        p0 = b.particles()
+        a.step(1)
+        b.step(1)
+        o0, o1 = orc.raster(nx, ny, p0), orc.raster(nx, ny, b.particles())
+        exp = np.where(o1 >= 0, 1, np.where(o0 >= 0, 2, 0)).astype(np.uint8)
+        assert np.array_equal(state_flags(b, nx, ny), exp)
+    assert np.array_equal(a.get_state(), b.get_state())
 
 
 def test_async_particle_read_back_equals_the_synchronous_one():
