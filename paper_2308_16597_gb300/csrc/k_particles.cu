@@ -649,12 +649,15 @@ struct RasterIn {
 
 // FP64 tail of the particle update for particle b: total force, Newton-Euler
 // step, domain checks, new state and geometry record.  (pfx, pfy: the pair
-// repulsion; out: the new state for the raster and the next screening grid.)
-__device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, double pfx, double pfy, RasterIn &out)
+// repulsion; out: the new state for the raster and the next screening grid;
+// st, ls: the particle's state fields x, y, ux, uy, theta, omega, r, rho, T,
+// b and its link sums, staged in shared memory during the screening.)
+__device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, double pfx, double pfy, RasterIn &out,
+                                              const double *st, const LinkSums &ls)
 {
-    double x = D.cur.x[b], y = D.cur.y[b], ux = D.cur.ux[b], uy = D.cur.uy[b];
-    double th = D.cur.th[b], om = D.cur.om[b];
-    const double r = D.cur.r[b], rho = D.cur.rho[b], pb = D.cur.b[b];
+    double x = st[0], y = st[1], ux = st[2], uy = st[3];
+    double th = st[4], om = st[5];
+    const double r = st[6], rho = st[7], pb = st[9];
     // an ellipse: area pi r b, wall gaps to its support distances along the
     // wall normals, I = M (r^2 + b^2) / 4
     const bool ell = is_ellipse(r, pb);
@@ -670,7 +673,7 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, d
         S.dg_x = ds.c[3]; S.dg_y = ds.c[4]; S.dg_t = ds.c[5];
         assemble_force(S, x, y, Fx, Fy, Tz);
     } else {
-        assemble_force(D.lsum[b], x, y, Fx, Fy, Tz);
+        assemble_force(ls, x, y, Fx, Fy, Tz);
     }
     D.force[3 * b + 0] = Fx;
     D.force[3 * b + 1] = Fy;
@@ -703,14 +706,14 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, d
     // (beyond the reach of the near-tile bitmap), or whose state is no longer
     // finite raises the (sticky) domain error and stays where it was, so that
     // its zone stays inside the arrays every later kernel indexes
-    const double xo = D.cur.x[b], yo = D.cur.y[b];
+    const double xo = st[0], yo = st[1];
     if (!(x - r >= -0.5 && x + r <= (double)D.nx - 0.5 && y - r >= -0.5 && y + r <= (double)D.ny - 0.5 &&
           fabs(x - xo) < 1.0 && fabs(y - yo) < 1.0)) {
         atomicOr(&D.status->err, kErrDomain);
         x = xo;
         y = yo;
     }
-    const double T = D.cur.T[b];
+    const double T = st[8];
     D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
     D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T; D.nxt.b[b] = pb;
     const GeomRec Gn = make_geom(x, y, r, pb, th, ux, uy, om, T, rho, D.rho_f, D.g);
@@ -730,6 +733,22 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
     if (blk == 0 && threadIdx.x < kNumCounters) D.status->cnt[parity ^ 1][threadIdx.x] = 0ull;
     if (blk == 0 && threadIdx.x == 0) D.status->nb = 0u;
     const bool me = a < D.np;
+    // the last warp stages the tail's inputs (the block's particle states and
+    // link sums) while every warp screens, so that the FP64 tail starts
+    // without a global round trip
+    __shared__ double s_cur[kPartPerBlock][kPartFields];
+    __shared__ LinkSums s_ls[kPartPerBlock];
+    if (warp == kPartPerBlock - 1) {
+        for (int t = lane; t < kPartPerBlock * kPartFields; t += 32) {
+            const int q = t / kPartFields, f = t - q * kPartFields, bq = blk * kPartPerBlock + q;
+            if (bq < D.np) s_cur[q][f] = D.cur.x[(long long)f * D.np + bq];
+        }
+        if (!D.direct)
+            for (int t = lane; t < kPartPerBlock * 8; t += 32) {
+                const int q = t >> 3, w = t & 7, bq = blk * kPartPerBlock + q;
+                if (bq < D.np) reinterpret_cast<long long *>(&s_ls[q])[w] = reinterpret_cast<const long long *>(&D.lsum[bq])[w];
+            }
+    }
     float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 ca = make_float2(1.f, 0.f);
     if (me) {
@@ -797,7 +816,7 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
     __syncthreads();
     const int b = blk * kPartPerBlock + lane;
     if (warp == 0 && lane < kPartPerBlock && b < D.np)
-        particle_tail(D, b, parity, fix_value(sred[0][lane]), fix_value(sred[1][lane]), sras[lane]);
+        particle_tail(D, b, parity, fix_value(sred[0][lane]), fix_value(sred[1][lane]), sras[lane], s_cur[lane], s_ls[lane]);
     // then the owner map at the new positions: warp w rasters the block's
     // particle w (its own new state only, so no other block is waited for)
     __syncthreads();
