@@ -3,13 +3,14 @@
 //                fixed index array (Sec. 3), curved bounce-back of f and g on
 //                each link (Sec. 2.3) and the momentum-exchange force and
 //                torque (Sec. 2.4, Eq. force / Eq. torque) summed per
-//                particle in exact fixed point;
+//                particle in exact fixed point; entry of each particle in
+//                the pair-screening grid;
 //   k_particles  pair screening through the cell grid, Newton-Euler update
 //                with gravity, buoyancy and spring repulsion (Sec. 2.2,
 //                Sec. 2.4) in FP64, and the raster of the new positions into
 //                the next owner map (cleared over the old zones by k_links);
 //   k_flags      node flags at the new positions and the newborn list;
-// plus the initialisation kernels (k_raster, k_geom_init, k_cells_init), the
+// plus the initialisation kernels (k_raster, k_geom_init), the
 // direct-addressing comparison (k_direct_prep, k_links_direct), the near-tile
 // bitmap of the opt-in split stream-collide (k_near_mask) and the batched
 // forms of the step kernels.
@@ -81,7 +82,7 @@ __device__ __forceinline__ int slot_of(int k, int a, int b, int N)
 }
 
 // Counts (and overflow flag) of the screening grid of the next step, which
-// the particle update of this step fills: block p of the np blocks of a
+// the next step's link kernel fills: block p of the np blocks of a
 // per-particle kernel clears its share.  The grid was last read by the
 // previous step's update.
 __device__ __forceinline__ void clear_cells_slice(const Dev &D, int parity, int p, int tid, int nthreads)
@@ -91,6 +92,19 @@ __device__ __forceinline__ void clear_cells_slice(const Dev &D, int parity, int 
     const int c1 = min(nc, (p + 1) * per);
     for (int c = p * per + tid; c < c1; c += nthreads)
         if (in_bounds(D, c, (long long)nc * (1 + kCellCap))) grid[c] = 0;
+}
+
+// Entry of particle b at (xh, yh) in a screening grid (cleared beforehand);
+// a full cell flags the grid, whose next screening then scans all pairs.
+__device__ __forceinline__ void cell_insert(const Dev &D, int *grid, int b, float xh, float yh)
+{
+    const int ncell = D.cell_gx * D.cell_gy, c = cell_of(D, xh, yh);
+    const long long size = (long long)(ncell + 1) + (long long)ncell * kCellCap;
+    if (!in_bounds(D, c, ncell)) return;
+    const int k = atomicAdd(grid + c, 1);
+    if (k < kCellCap) {
+        if (in_bounds(D, ncell + 1 + (long long)c * kCellCap + k, size)) grid[ncell + 1 + c * kCellCap + k] = b;
+    } else grid[ncell] = 1;
 }
 
 // The last step's newborn nodes (fluid now, listed by the flags kernel of
@@ -108,9 +122,10 @@ __device__ __forceinline__ void revert_newborn(const Dev &D, int p, int tid, int
 }
 
 // One CTA per particle.  Phases:
-//  0. clear this CTA's share of the screening grid the update fills next,
-//     and the particle's zone one step back in the owner map that the
-//     raster fills next; return the last step's newborn nodes to fluid;
+//  0. clear this CTA's share of the screening grid the next step's link
+//     kernel fills, and the particle's zone one step back in the owner map
+//     that the raster fills next; return the last step's newborn nodes to
+//     fluid;
 //  1. the warps read the owner map over the particle's window (zone plus
 //     the two-node margin of the bounce-back stencil) and record per row a
 //     fluid mask and an owned-by-this-particle mask (one ballot per 32
@@ -136,7 +151,8 @@ __device__ __forceinline__ void revert_newborn(const Dev &D, int p, int tid, int
 //     and every read is of a fluid node, so the writes never race the reads),
 //     and the momentum-exchange bracket of Eq. force / Eq. torque, summed
 //     in exact fixed point per thread, per warp and over the warps (so the
-//     forces are bit-reproducible).
+//     forces are bit-reproducible);
+//  5. the particle enters the screening grid of this step's update.
 template <typename T>
 __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__restrict__ own,
                                            int *__restrict__ own_nxt, int parity, int ahead, const int p)
@@ -417,6 +433,10 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
             if (s_over) atomicOr(&D.status->err, kErrOverflow);
         }
     }
+    // the particle's position into the screening grid this step's update
+    // reads (its counts cleared by the previous step's link kernel): the
+    // atomic's round trip ends the CTA instead of lengthening the update
+    if (tid == 32) cell_insert(D, D.cells[parity], p, G.xh, G.yh);
 }
 
 // Spring repulsion magnitude of Sec. 2.4 for a gap (distance to the wall
@@ -434,14 +454,15 @@ __device__ __forceinline__ double repulsion(double gap, double s, double eps, do
 // with C_ab the mean of the two force scales C = pi r^2 (rho_p - rho_f) g).
 // Each block takes 8 particles: warp w screens particle w against the
 // particles listed in the 3 x 3 cells of the screening grid around its cell
-// (filled with the step's starting positions by the previous update; every
+// (filled with the step's starting positions by the link kernel; every
 // pair in reach is among them), or, when a cell of that grid overflowed,
 // against all particles in shared-memory tiles of 1600, and evaluates the
 // pairs in reach from double-float centre differences, summed in 64-bit
 // fixed point so that the result is the same whichever way the pairs were
 // found and in whatever order; lane l of warp 0 then sums, integrates and
-// stores particle l in FP64, and warp w enters particle w in the next step's
-// grid and rasters it.  Small
+// stores particle l in FP64 (its constants 1/M, 1/I, W and C, and its
+// geometry record, staged by the last warp while the others screen), and
+// warp w rasters particle w.  Small
 // blocks let four of them share an SM, so that the latency of one block's
 // loads and FP64 tail overlaps the others' work.  Integration:
 // U' = U + F/M, X' = X + (U + U')/2, Omega' = Omega + T/I,
@@ -449,19 +470,6 @@ __device__ __forceinline__ double repulsion(double gap, double s, double eps, do
 // (M = rho_p pi r b and I = M (r^2 + b^2) / 4 for an ellipse).
 constexpr int kPartTile = 1600;
 constexpr int kPartPerBlock = kPartThreads / 32;
-
-// Entry of particle b at (xh, yh) in a screening grid (cleared beforehand);
-// a full cell flags the grid, whose next screening then scans all pairs.
-__device__ __forceinline__ void cell_insert(const Dev &D, int *grid, int b, float xh, float yh)
-{
-    const int ncell = D.cell_gx * D.cell_gy, c = cell_of(D, xh, yh);
-    const long long size = (long long)(ncell + 1) + (long long)ncell * kCellCap;
-    if (!in_bounds(D, c, ncell)) return;
-    const int k = atomicAdd(grid + c, 1);
-    if (k < kCellCap) {
-        if (in_bounds(D, ncell + 1 + (long long)c * kCellCap + k, size)) grid[ncell + 1 + c * kCellCap + k] = b;
-    } else grid[ncell] = 1;
-}
 
 // Support distance of particle p along the unit vector (nx, ny): its radius
 // for a disk.
@@ -647,21 +655,35 @@ struct RasterIn {
     double x, y, r, th, b;
 };
 
+// Constants of the update of a particle (they depend only on its shape and
+// density): 1/M, 1/I, the buoyant weight W = (rho_p - rho_f) A g and the
+// repulsion force scale C = A (rho_p - rho_f) g, with the area A = pi r^2
+// (pi r b for an ellipse), M = rho_p A and I = M r^2 / 2 (M (r^2 + b^2) / 4
+// for an ellipse).  The update multiplies by 1/M and 1/I, which differs
+// from dividing by M and I by at most one rounding of the increment.
+__device__ __forceinline__ double4 part_consts(double r, double b, double rho, double rho_f, double g)
+{
+    const bool ell = is_ellipse(r, b);
+    const double rb = ell ? b : r;
+    const double M = rho * kPi * r * rb, I = ell ? 0.25 * M * (r * r + b * b) : 0.5 * M * r * r;
+    return make_double4(1.0 / M, 1.0 / I, (rho - rho_f) * kPi * r * rb * g, kPi * r * rb * (rho - rho_f) * g);
+}
+
 // FP64 tail of the particle update for particle b: total force, Newton-Euler
-// step, domain checks, new state and geometry record.  (pfx, pfy: the pair
-// repulsion; out: the new state for the raster and the next screening grid;
-// st, ls: the particle's state fields x, y, ux, uy, theta, omega, r, rho, T,
-// b and its link sums, staged in shared memory during the screening.)
-__device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, double pfx, double pfy, RasterIn &out,
-                                              const double *st, const LinkSums &ls)
+// step, domain checks, new state and geometry record.  (psx, psy: the pair
+// repulsion in fixed point; out: the new state for the raster; st, ls, Gc, pk: the
+// particle's state fields x, y, ux, uy, theta, omega, r, rho, T, b, its link
+// sums, its current geometry record and its constants, staged in shared
+// memory during the screening.)
+__device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, long long psx, long long psy, RasterIn &out,
+                                              const double *st, const LinkSums &ls, const GeomRec &Gc,
+                                              const double4 &pk)
 {
     double x = st[0], y = st[1], ux = st[2], uy = st[3];
     double th = st[4], om = st[5];
     const double r = st[6], rho = st[7], pb = st[9];
-    // an ellipse: area pi r b, wall gaps to its support distances along the
-    // wall normals, I = M (r^2 + b^2) / 4
+    // an ellipse: wall gaps to its support distances along the wall normals
     const bool ell = is_ellipse(r, pb);
-    const double rb = ell ? pb : r;
     double Fx, Fy, Tz;
     if (D.direct) {
         const DirectSums &ds = D.dsum[b];
@@ -678,23 +700,29 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, d
     D.force[3 * b + 0] = Fx;
     D.force[3 * b + 1] = Fy;
     D.force[3 * b + 2] = Tz;
-    const double Cb = kPi * r * rb * (rho - D.rho_f) * D.g;
-    Fy -= (rho - D.rho_f) * kPi * r * rb * D.g;
+    const double Cb = pk.w;
+    Fy -= pk.z;
     double hx = r, hy = r;
     if (ell) wall_supports(th, r, pb, hx, hy);
+    // A wall gap takes the FP64 repulsion only where the FP32 centre of the
+    // current geometry record puts it within the threshold plus a margin
+    // (mar) far above that centre's rounding error (half an FP32 spacing,
+    // 2.4e-4 at 4096): elsewhere the repulsion is zero either way, and GB300
+    // runs FP64 at a small fraction of its FP32 rate.
+    const float mar = 1e-3f + 2.4e-7f * (float)(D.nx + D.ny), near = (float)D.s_rep + mar;
+    const float hxf = (float)hx, hyf = (float)hy, nxf = (float)D.nx, nyf = (float)D.ny;
     if (!D.per_x) {
-        Fx += repulsion((x + 0.5) - hx, D.s_rep, D.eps_w, Cb);
-        Fx -= repulsion(((double)D.nx - 0.5 - x) - hx, D.s_rep, D.eps_w, Cb);
+        if ((Gc.xh + 0.5f) - hxf <= near) Fx += repulsion((x + 0.5) - hx, D.s_rep, D.eps_w, Cb);
+        if ((nxf - 0.5f - Gc.xh) - hxf <= near) Fx -= repulsion(((double)D.nx - 0.5 - x) - hx, D.s_rep, D.eps_w, Cb);
     }
     if (!D.per_y) {
-        Fy += repulsion((y + 0.5) - hy, D.s_rep, D.eps_w, Cb);
-        Fy -= repulsion(((double)D.ny - 0.5 - y) - hy, D.s_rep, D.eps_w, Cb);
+        if ((Gc.yh + 0.5f) - hyf <= near) Fy += repulsion((y + 0.5) - hy, D.s_rep, D.eps_w, Cb);
+        if ((nyf - 0.5f - Gc.yh) - hyf <= near) Fy -= repulsion(((double)D.ny - 0.5 - y) - hy, D.s_rep, D.eps_w, Cb);
     }
-    Fx += pfx;
-    Fy += pfy;
+    if (psx) Fx += fix_value(psx);
+    if (psy) Fy += fix_value(psy);
     if (!D.fixed) {
-        const double M = rho * kPi * r * rb, I = ell ? 0.25 * M * (r * r + pb * pb) : 0.5 * M * r * r;
-        const double ux1 = ux + Fx / M, uy1 = uy + Fy / M, om1 = om + Tz / I;
+        const double ux1 = ux + Fx * pk.x, uy1 = uy + Fy * pk.x, om1 = om + Tz * pk.y;
         x += 0.5 * (ux + ux1);
         y += 0.5 * (uy + uy1);
         th += 0.5 * (om + om1);
@@ -706,9 +734,15 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, d
     // (beyond the reach of the near-tile bitmap), or whose state is no longer
     // finite raises the (sticky) domain error and stays where it was, so that
     // its zone stays inside the arrays every later kernel indexes
+    // (decided in FP32 with the margin mar where that is certain, else in
+    // FP64; a non-finite state fails both)
     const double xo = st[0], yo = st[1];
-    if (!(x - r >= -0.5 && x + r <= (double)D.nx - 0.5 && y - r >= -0.5 && y + r <= (double)D.ny - 0.5 &&
-          fabs(x - xo) < 1.0 && fabs(y - yo) < 1.0)) {
+    const float xf = (float)x, yf = (float)y, rf = (float)r;
+    const bool surely_in = xf - rf >= mar - 0.5f && xf + rf <= nxf - 0.5f - mar && yf - rf >= mar - 0.5f &&
+                           yf + rf <= nyf - 0.5f - mar && fabsf(xf - Gc.xh) < 1.f - mar &&
+                           fabsf(yf - Gc.yh) < 1.f - mar;
+    if (!surely_in && !(x - r >= -0.5 && x + r <= (double)D.nx - 0.5 && y - r >= -0.5 && y + r <= (double)D.ny - 0.5 &&
+                        fabs(x - xo) < 1.0 && fabs(y - yo) < 1.0)) {
         atomicOr(&D.status->err, kErrDomain);
         x = xo;
         y = yo;
@@ -716,7 +750,7 @@ __device__ __forceinline__ void particle_tail(const Dev &D, int b, int parity, d
     const double T = st[8];
     D.nxt.x[b] = x; D.nxt.y[b] = y; D.nxt.ux[b] = ux; D.nxt.uy[b] = uy; D.nxt.th[b] = th;
     D.nxt.om[b] = om; D.nxt.r[b] = r; D.nxt.rho[b] = rho; D.nxt.T[b] = T; D.nxt.b[b] = pb;
-    const GeomRec Gn = make_geom(x, y, r, pb, th, ux, uy, om, T, rho, D.rho_f, D.g);
+    const GeomRec Gn = move_geom(Gc, x, y, r, pb, th, ux, uy, om);
     D.geo_nxt[b] = Gn;
     out.G = Gn;
     out.x = x; out.y = y; out.r = r; out.th = th; out.b = pb;
@@ -738,11 +772,19 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
     // without a global round trip
     __shared__ double s_cur[kPartPerBlock][kPartFields];
     __shared__ LinkSums s_ls[kPartPerBlock];
+    __shared__ GeomRec s_geo[kPartPerBlock];
+    __shared__ double4 s_pk[kPartPerBlock];
     if (warp == kPartPerBlock - 1) {
         for (int t = lane; t < kPartPerBlock * kPartFields; t += 32) {
             const int q = t / kPartFields, f = t - q * kPartFields, bq = blk * kPartPerBlock + q;
             if (bq < D.np) s_cur[q][f] = D.cur.x[(long long)f * D.np + bq];
         }
+        static_assert(sizeof(GeomRec) == 64, "a geometry record is 16 words");
+        for (int t = lane; t < kPartPerBlock * 16; t += 32) {
+            const int q = t >> 4, w = t & 15, bq = blk * kPartPerBlock + q;
+            if (bq < D.np) reinterpret_cast<int *>(&s_geo[q])[w] = reinterpret_cast<const int *>(&D.geo_cur[bq])[w];
+        }
+        if (lane < kPartPerBlock && blk * kPartPerBlock + lane < D.np) s_pk[lane] = D.pconst[blk * kPartPerBlock + lane];
         if (!D.direct)
             for (int t = lane; t < kPartPerBlock * 8; t += 32) {
                 const int q = t >> 3, w = t & 7, bq = blk * kPartPerBlock + q;
@@ -816,15 +858,13 @@ __device__ __forceinline__ void particles_body(const Dev &D, int parity, int *ow
     __syncthreads();
     const int b = blk * kPartPerBlock + lane;
     if (warp == 0 && lane < kPartPerBlock && b < D.np)
-        particle_tail(D, b, parity, fix_value(sred[0][lane]), fix_value(sred[1][lane]), sras[lane], s_cur[lane], s_ls[lane]);
+        particle_tail(D, b, parity, sred[0][lane], sred[1][lane], sras[lane], s_cur[lane], s_ls[lane],
+                      s_geo[lane], s_pk[lane]);
     // then the owner map at the new positions: warp w rasters the block's
     // particle w (its own new state only, so no other block is waited for)
     __syncthreads();
     if (a < D.np) {
         const RasterIn &R = sras[warp];
-        // the new position into the next step's screening grid (its atomic
-        // round trip overlaps the raster)
-        if (lane == 0) cell_insert(D, D.cells[parity ^ 1], a, R.G.xh, R.G.yh);
         raster_one(D, own_nxt, R.G, R.x, R.y, R.r, R.th, R.b, a, D.runs[parity ^ 1] + (long long)a * D.zone_max);
     }
 }
@@ -1003,6 +1043,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_direct_prep(const Dev D, int *_
         const DiskDF d0 = geom_df(G);
         D.pos4[p] = make_float4(d0.xh, d0.yh, d0.xl, d0.yl);
         D.prc[p] = make_float2(G.r, G.C);
+        cell_insert(D, D.cells[parity], p, G.xh, G.yh);
     }
     if (threadIdx.x < 3) D.dsum[p].f[threadIdx.x] = 0.0;
     if (threadIdx.x < 6) D.dsum[p].c[threadIdx.x] = 0;
@@ -1174,20 +1215,11 @@ __global__ void k_geom_init(const Dev D)
                                 D.cur.uy[a], D.cur.om[a], D.cur.T[a], D.cur.rho[a], D.rho_f, D.g);
     D.geo_cur[a] = G;
     D.geo_nxt[a] = G;
+    D.pconst[a] = part_consts(D.cur.r[a], D.cur.b[a], D.cur.rho[a], D.rho_f, D.g);
     // (the orientation one step back is not kept: the current one, which
     // only shapes the raster of that owner map inside the same zone)
     D.geo_prev[a] = make_geom(D.px[a], D.py[a], D.cur.r[a], D.cur.b[a], D.cur.th[a], 0.0, 0.0, 0.0, D.cur.T[a],
                               D.cur.rho[a], D.rho_f, D.g);
-}
-
-// The screening grid of the current positions (its counts cleared
-// beforehand), for the first update after init or restore.
-__global__ void k_cells_init(const Dev D, int *grid)
-{
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= D.np) return;
-    const GeomRec G = D.geo_cur[a];
-    cell_insert(D, grid, a, G.xh, G.yh);
 }
 
 __global__ void k_pack_particles(const Dev D, lbm_particle *out)
@@ -1386,16 +1418,14 @@ cudaError_t launch_geom_init(const Dev &D, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_cells_init(const Dev &D, int parity, cudaStream_t s)
+cudaError_t launch_cells_init(const Dev &D, cudaStream_t s)
 {
     const size_t counts = ((size_t)D.cell_gx * D.cell_gy + 1) * sizeof(int);
     for (int b = 0; b < 2; ++b) {
         const cudaError_t e = cudaMemsetAsync(D.cells[b], 0, counts, s);
         if (e != cudaSuccess) return e;
     }
-    if (D.np == 0) return cudaSuccess;
-    k_cells_init<<<(D.np + 127) / 128, 128, 0, s>>>(D, D.cells[parity]);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t launch_flags(const Dev &D, const int *own_cur, const int *own_nxt, int rotate, int parity,

@@ -18,6 +18,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t kDistTailPad = 256; // bytes after each distribution buffer
 constexpr size_t kStageBytes = size_t(4) << 20;
+constexpr int kGraphLevels = 4; // replayed graphs hold 1, 2, 4 or 8 steps
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -113,6 +114,7 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
     L.prc = take((size_t)n * sizeof(float2));
     L.lsum = take((size_t)n * sizeof(LinkSums));
     for (int b = 0; b < 3; ++b) L.geo[b] = take((size_t)n * sizeof(GeomRec));
+    L.pconst = take((size_t)n * sizeof(double4));
     L.status = take(sizeof(Status));
     L.pack = take((size_t)n * sizeof(lbm_particle));
     L.stage_rows = (int)std::max<size_t>(1, std::min<size_t>(d->ny, kStageBytes / (16 * (size_t)d->nx)));
@@ -281,13 +283,19 @@ int kernels_per_step(const lbm_handle *h)
     return ((h->prm.flags & LBM_FLAG_OVERLAP) ? 7 : 5) + ((h->prm.flags & LBM_FLAG_DIRECT_LINKS) ? 1 : 0);
 }
 
-int capture(lbm_handle *h, int par)
+// Graph of `steps` consecutive steps from parity par (an even count ends on
+// par again).  Consecutive graph launches on a stream cost about 4 us more
+// per step than kernel edges inside one graph (at 4000^2 / 4800 disks:
+// 0.3785 ms per step with one step per graph, 0.3751 with four, 0.3746 with
+// eight, 0.3745 with sixteen).
+int capture(lbm_handle *h, int par, int steps, cudaGraphExec_t *out)
 {
     if (!h->cap) CK(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     const long long before = h->launches;
-    int rc = enqueue_step(h, par, h->cap);
+    int rc = LBM_OK;
+    for (int k = 0; k < steps && !rc; ++k) rc = enqueue_step(h, par ^ (k & 1), h->cap);
     h->launches = before;
     cudaError_t e = cudaStreamEndCapture(h->cap, &g);
     if (rc) {
@@ -295,7 +303,7 @@ int capture(lbm_handle *h, int par)
         return rc;
     }
     CK(h, e);
-    e = cudaGraphInstantiate(&h->gexec[par], g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     CK(h, e);
     return LBM_OK;
@@ -391,6 +399,7 @@ void fill_dev(lbm_handle *h)
     D.geo_prev = reinterpret_cast<GeomRec *>(ws + L.geo[0]);
     D.geo_cur = reinterpret_cast<GeomRec *>(ws + L.geo[1]);
     D.geo_nxt = reinterpret_cast<GeomRec *>(ws + L.geo[2]);
+    D.pconst = reinterpret_cast<double4 *>(ws + L.pconst);
     D.status = reinterpret_cast<Status *>(ws + L.status);
     D.cell_gx = L.cell_gx;
     D.cell_gy = L.cell_gy;
@@ -431,7 +440,7 @@ int rebuild_maps(lbm_handle *h)
     CK(h, cudaMemsetAsync(h->D.flags, 0, (size_t)h->L.pitch * h->d.ny, h->stream));
     int *oc = h->own[h->parity];
     CK(h, launch_geom_init(h->D, h->stream));
-    CK(h, launch_cells_init(h->D, h->parity, h->stream));
+    CK(h, launch_cells_init(h->D, h->stream));
     CK(h, launch_raster(h->D, oc, h->D.geo_cur, h->D.cur, h->D.runs[h->parity], h->stream));
     CK(h, launch_flags(h->D, oc, oc, 0, h->parity, h->stream));
     // no newborn node yet
@@ -541,16 +550,24 @@ int lbm_step(lbm_handle *h, int32_t nsteps)
     if (!h || nsteps < 0) return LBM_EINVAL;
     if (h->sticky) return h->sticky;
     const bool graph = !(h->prm.flags & LBM_FLAG_NO_GRAPH) && !h->timing;
-    for (int32_t k = 0; k < nsteps; ++k) {
-        int rc;
+    int rc;
+    for (int32_t k = 0; k < nsteps;) {
         if (graph) {
-            if (!h->gexec[h->parity] && (rc = capture(h, h->parity))) return rc;
-            CK(h, cudaGraphLaunch(h->gexec[h->parity], h->stream));
-            h->launches += kernels_per_step(h);
-        } else if ((rc = enqueue_step(h, h->parity, h->stream))) {
-            return rc;
+            // the largest graph (8, 4, 2 or 1 steps) that fits what is left
+            int l = kGraphLevels - 1;
+            while ((1 << l) > nsteps - k) --l;
+            const int n = 1 << l;
+            cudaGraphExec_t &g = h->gexec[l][h->parity];
+            if (!g && (rc = capture(h, h->parity, n, &g))) return rc;
+            CK(h, cudaGraphLaunch(g, h->stream));
+            h->launches += (long long)n * kernels_per_step(h);
+            h->parity ^= n & 1;
+            k += n;
+        } else {
+            if ((rc = enqueue_step(h, h->parity, h->stream))) return rc;
+            h->parity ^= 1;
+            ++k;
         }
-        h->parity ^= 1;
     }
     return LBM_OK;
 }
@@ -625,8 +642,9 @@ int lbm_destroy(lbm_handle *h)
 {
     if (!h) return LBM_EINVAL;
     if (h->stream || h->cap) cudaStreamSynchronize(h->stream);
-    for (int b = 0; b < 2; ++b)
-        if (h->gexec[b]) cudaGraphExecDestroy(h->gexec[b]);
+    for (int l = 0; l < kGraphLevels; ++l)
+        for (int b = 0; b < 2; ++b)
+            if (h->gexec[l][b]) cudaGraphExecDestroy(h->gexec[l][b]);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->side) {
         cudaStreamSynchronize(h->side);
@@ -724,7 +742,7 @@ int lbm_set_state(lbm_handle *h, const void *buf, size_t bytes)
         prev.x = h->D.px;
         prev.y = h->D.py;
         CK(h, launch_geom_init(h->D, h->stream));
-        CK(h, launch_cells_init(h->D, h->parity, h->stream));
+        CK(h, launch_cells_init(h->D, h->stream));
         CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, nullptr, h->stream));
         // the row runs of the restored positions (their raster rewrites the
         // restored owner map with the values it holds), and the newborn

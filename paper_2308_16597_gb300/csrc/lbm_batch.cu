@@ -50,7 +50,7 @@ struct lbm_batch {
     int total[kBatchPhases] = {};
     int tile = 0, sc_resident = 1, links_ahead = 1;
     size_t links_smem = 0;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[4][2] = {}; // 2^l steps (l = 0..3) from each parity
     long long launches = 0;
     int sticky = LBM_OK;
 };
@@ -143,25 +143,29 @@ int enqueue_batch_step(lbm_batch *b, int par, cudaStream_t st)
 
 void drop_graphs(lbm_batch *b)
 {
-    for (int p = 0; p < 2; ++p)
-        if (b->gexec[p]) {
-            cudaGraphExecDestroy(b->gexec[p]);
-            b->gexec[p] = nullptr;
-        }
+    for (int l = 0; l < 4; ++l)
+        for (int p = 0; p < 2; ++p)
+            if (b->gexec[l][p]) {
+                cudaGraphExecDestroy(b->gexec[l][p]);
+                b->gexec[l][p] = nullptr;
+            }
 }
 
-int capture_batch(lbm_batch *b, int par)
+// Graph of `steps` consecutive batch steps from parity par (as lbm_step's:
+// an edge inside a graph costs less than a launch of the next graph).
+int capture_batch(lbm_batch *b, int par, int steps, cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
     BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_batch_step(b, par, b->cap);
+    int rc = LBM_OK;
+    for (int k = 0; k < steps && !rc; ++k) rc = enqueue_batch_step(b, par ^ (k & 1), b->cap);
     cudaError_t e = cudaStreamEndCapture(b->cap, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
     BCK(b, e);
-    e = cudaGraphInstantiate(&b->gexec[par], g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     BCK(b, e);
     return LBM_OK;
@@ -306,13 +310,21 @@ int lbm_batch_step(lbm_batch *b, int32_t nsteps)
     if (b->sticky) return b->sticky;
     for (int i = 0; i < b->n; ++i)
         if (b->hs[i]->parity != (b->parity ^ b->poff[i])) return LBM_EINVAL; // a handle was stepped on its own
-    for (int32_t k = 0; k < nsteps; ++k) {
+    int per_step = 0;
+    for (int ph = 0; ph < kBatchPhases; ++ph) per_step += ph != kBRaster && b->total[ph] > 0;
+    for (int32_t k = 0; k < nsteps;) {
+        // the largest graph (8, 4, 2 or 1 steps) that fits what is left
+        int l = 3;
+        while ((1 << l) > nsteps - k) --l;
+        const int m = 1 << l;
         int rc;
-        if (!b->gexec[b->parity] && (rc = capture_batch(b, b->parity))) return rc;
-        BCK(b, cudaGraphLaunch(b->gexec[b->parity], b->stream));
-        b->parity ^= 1;
-        for (int i = 0; i < b->n; ++i) b->hs[i]->parity ^= 1;
-        for (int ph = 0; ph < kBatchPhases; ++ph) b->launches += ph != kBRaster && b->total[ph] > 0;
+        cudaGraphExec_t &g = b->gexec[l][b->parity];
+        if (!g && (rc = capture_batch(b, b->parity, m, &g))) return rc;
+        BCK(b, cudaGraphLaunch(g, b->stream));
+        b->parity ^= m & 1;
+        for (int i = 0; i < b->n; ++i) b->hs[i]->parity ^= m & 1;
+        b->launches += (long long)m * per_step;
+        k += m;
     }
     return LBM_OK;
 }

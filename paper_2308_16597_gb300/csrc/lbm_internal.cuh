@@ -139,6 +139,7 @@ struct Dev {
     struct DirectSums *dsum; // [np]: the same sums accumulated by atomics (direct addressing)
     int direct;            // links found by the node-parallel scan instead of the index array
     struct GeomRec *geo_prev, *geo_cur, *geo_nxt; // [np] each: FP32/int geometry of the three positions
+    double4 *pconst;   // [np]: constants of the update (1/M, 1/I, weight W, repulsion scale C)
     // pair screening: a grid of square cells of side 1 / cell_inv >= 2 r_max
     // + s + 2, so that every pair in reach sits in the same or neighbouring
     // cells; per parity [cell_gx * cell_gy + 1] counts (the last one flags an
@@ -514,6 +515,29 @@ __device__ __forceinline__ GeomRec make_geom(double x, double y, double r, doubl
     G.ux = (float)ux; G.uy = (float)uy; G.om = (float)om; G.wT = (float)(0.2 * T);
     return G;
 }
+// make_geom at another position and motion of the same particle: the fields
+// that depend only on its shape, density and temperature (r, C, the zone
+// side, r^2 of a disk, 2 w_k T_w) are those of its record G at any other
+// position, so the result has the same bits as make_geom.
+__device__ __forceinline__ GeomRec move_geom(GeomRec G, double x, double y, double r, double b, double th, double ux,
+                                             double uy, double om)
+{
+    G.xh = (float)x;
+    G.xl = (float)(x - (double)G.xh);
+    G.yh = (float)y;
+    G.yl = (float)(y - (double)G.yh);
+    if (is_ellipse(r, b)) {
+        double c, s;
+        cos_sin_rn(th, c, s);
+        G.w0 = (float)c;
+        G.w1 = (float)s;
+    }
+    G.X0 = (int)floor(x - r) - 1;
+    G.Y0 = (int)floor(y - r) - 1;
+    G.ic = (int)floor(x + 0.5);
+    G.ux = (float)ux; G.uy = (float)uy; G.om = (float)om;
+    return G;
+}
 __device__ __forceinline__ DiskDF geom_df(const GeomRec &G)
 {
     DiskDF d;
@@ -861,9 +885,9 @@ cudaError_t launch_pack_particles(const Dev &D, lbm_particle *out, cudaStream_t 
 // Geometry records of the current state (into cur, nxt and prev) and of the
 // previous positions (into prev), for init and restore.
 cudaError_t launch_geom_init(const Dev &D, cudaStream_t s);
-// Screening grids: both cleared, the one of step parity `parity` filled with
-// the current positions (after launch_geom_init).
-cudaError_t launch_cells_init(const Dev &D, int parity, cudaStream_t s);
+// Screening grids: both cleared (the first step's link kernel enters the
+// current positions).
+cudaError_t launch_cells_init(const Dev &D, cudaStream_t s);
 
 // Batched step kernels over an InstArgs table (one grid over all instances;
 // `start` holds the n + 1 block offsets of the launch, `total` its blocks).

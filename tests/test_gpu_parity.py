@@ -435,12 +435,19 @@ def test_node_flags_are_bit_exact():
 
 # --------------------------------------------------------------------------- runtime
 def test_runs_are_deterministic_and_graphs_match_direct_launches():
+    """40 steps replayed as multi-step graphs, launched directly, and in
+    chunks that mix multi-step and single-step graphs from both parities."""
     wl = W.parity_256()
     a = lbm.Simulation(wl.domain, wl.particles, wl.params)
     b = lbm.Simulation(wl.domain, wl.particles, wl.params, flags=lbm.LBM_FLAG_NO_GRAPH)
+    c = lbm.Simulation(wl.domain, wl.particles, wl.params)
     a.step(40)
     b.step(40)
+    for n in (1, 3, 4, 5, 8, 9, 10):
+        c.step(n)
     assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(a.get_state(), c.get_state())
+    assert np.array_equal(a.particles(), c.particles())
 
 
 def test_checkpoint_restore_is_bit_exact():
