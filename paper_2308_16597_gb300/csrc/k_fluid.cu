@@ -63,6 +63,25 @@ __device__ float pull_general(const Dev &D, const T *__restrict__ A, int x, int 
 // g = g_eq(T_w, u_w).
 // Returns 0 for a general pull, else 1 + the refill class (1 quadratic,
 // 2 linear, 3 copy, 4 equilibrium).
+// The pull of plane p at the side node (x, y), x = 0 or nx - 1, of a row
+// between the first and the last, for a plane whose source lies across the
+// side wall or the periodic seam (pull_general restricted to that case).
+template <typename T>
+__device__ __forceinline__ float side_pull(const Dev &D, const T *__restrict__ A, int x, int y, int p)
+{
+    using E = Elem<T>;
+    const int d = pdir(p);
+    if (D.per_x) {
+        const int xs = x == 0 ? D.nx - 1 : 0;
+        const long long e = (long long)p * D.ps + (long long)(y - ey(d)) * D.pitch + xs;
+        return in_bounds(D, e, D.a_elems) ? E::ld(A[e]) : 0.f;
+    }
+    const long long e = (long long)(p < kQ9 ? opp(d) : kQ9 + opp(d)) * D.ps + (long long)y * D.pitch + x;
+    const float v = in_bounds(D, e, D.a_elems) ? E::ld(A[e]) : 0.f;
+    if (p < kQ9) return v;
+    return -v + 2.f * w5(d) * D.Twall[d == 1 ? 0 : 1];
+}
+
 template <typename T>
 __device__ __forceinline__ int slow_node(const Dev &D, const T *__restrict__ A,
                                       const int *__restrict__ own_cur, int x, int y, uint8_t fl,
@@ -418,8 +437,9 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
     // most 32 V + 1 elements, since a warp starts below the pitch) land in
     // the previous plane (every plane with e_x = 1 has index p >= 1), the
     // next row or the buffer's tail pad, so they stay inside the buffer; the
-    // values they bring feed only the frame nodes x = 0 and x = nx - 1,
-    // which k_boundary writes, and the padding past nx, which is zeroed.
+    // values they bring feed only the planes of the side nodes x = 0 and
+    // x = nx - 1 that pull across a wall or seam, which the general pull
+    // replaces below, and the padding past nx, which is zeroed.
     const bool interior = y >= 1 && y + 1 < D.ny;
     if (interior) {
         const T *b0 = Ain + (long long)y * D.pitch + x0;
@@ -489,6 +509,29 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
         }
     }
     if (!act) return;
+    // The nodes x = 0 and x = nx - 1 of the rows between the first and the
+    // last: the planes that pull across a side wall or the periodic seam
+    // take the wall rule or the far side's value (side_pull: the general
+    // pull that k_boundary applies to the first and last rows, restricted
+    // to that case, inlined: as a call it cost the 16-bit kernel 4 us of
+    // its 180 through register allocation); every other plane
+    // is the fast path's.  This warp thus writes whole sectors at the row's
+    // ends, and the side columns need no scattered pass of their own.
+    if (interior) {
+        if (x0 == 0) {
+#pragma unroll
+            for (int p = 0; p < kPop; ++p)
+                if (ex(pdir(p)) == 1) c[0][p] = side_pull(D, Ain, 0, y, p);
+        }
+        const int kl = D.nx - 1 - x0;
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (k == kl) {
+#pragma unroll
+                for (int p = 0; p < kPop; ++p)
+                    if (ex(pdir(p)) == -1) c[k][p] = side_pull(D, Ain, D.nx - 1, y, p);
+            }
+    }
     bool ok = true, gen[V], anygen = false;
     if constexpr (V == 2) {
         // both nodes collided at once on paired FP32 instructions; solid
@@ -501,8 +544,9 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
             const int x = x0 + k;
             const unsigned fl = (fl2 >> (8 * k)) & 0xffu;
             fluid[k] = x < D.nx && fl != kSolid;
-            // frame and newborn nodes belong to k_boundary, which writes them
-            gen[k] = fluid[k] && (fl == kNewborn || y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1);
+            // newborn nodes and the first and last rows belong to k_boundary,
+            // which writes them
+            gen[k] = fluid[k] && (fl == kNewborn || y == 0 || y == D.ny - 1);
             anygen |= gen[k];
         }
         float2 cc[kPop];
@@ -530,8 +574,9 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
             const uint8_t fl = D.flags[(long long)y * D.pitch + x];
             gen[k] = false;
             if (x < D.nx && fl != kSolid) {
-                // frame and newborn nodes belong to k_boundary, which writes them
-                gen[k] = fl == kNewborn || y == 0 || y == D.ny - 1 || x == 0 || x == D.nx - 1;
+                // newborn nodes and the first and last rows belong to
+                // k_boundary, which writes them
+                gen[k] = fl == kNewborn || y == 0 || y == D.ny - 1;
                 if (!gen[k]) ok &= collide(D, c[k]);
             } else {
 #pragma unroll
@@ -566,32 +611,32 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
 
 // General path, beside the stream-collide kernel (it reads only the previous
 // state and writes only nodes that kernel leaves alone): the fluid nodes of
-// the cavity frame (walls, periodic seams) and the newborn nodes off the
-// frame listed by k_flags, each pulled (or refilled, Sec. 2.5) by slow_node
-// and collided.
-// A fixed grid strides over the 2 nx + 2 (ny - 2) frame nodes and then the
-// list, whose length the device holds.
+// the first and last rows (walls, periodic seams) and the newborn nodes
+// listed by k_flags, each pulled (or refilled, Sec. 2.5) by slow_node and
+// collided.  (The side columns' fluid nodes between those rows are the
+// stream-collide kernel's.)
+// A fixed grid strides over the 2 nx nodes of the two rows and then the
+// list, whose length the device holds; a listed node on the frame (~n) is
+// taken from the list unless it lies in those rows.
 template <typename T>
 __device__ __forceinline__ void boundary_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
                                               const int *__restrict__ own_cur, int parity, const Blk blk)
 {
     using E = Elem<T>;
     const int nx = D.nx, ny = D.ny;
-    const int nframe = 2 * nx + 2 * (ny - 2);
+    const int nframe = 2 * nx;
     const int nlist = min((int)D.status->nb, D.newborn_cap);
     unsigned n4[4] = {0u, 0u, 0u, 0u};
     bool ok = true;
     for (int idx = blk.x * (int)blockDim.x + (int)threadIdx.x; idx < nframe + nlist; idx += blk.gx * (int)blockDim.x) {
         int x, y;
         if (idx < nx) { x = idx; y = 0; }
-        else if (idx < 2 * nx) { x = idx - nx; y = ny - 1; }
-        else if (idx < 2 * nx + (ny - 2)) { x = 0; y = 1 + idx - 2 * nx; }
-        else if (idx < nframe) { x = nx - 1; y = 1 + idx - 2 * nx - (ny - 2); }
+        else if (idx < nframe) { x = idx - nx; y = ny - 1; }
         else {
-            const int n = D.newborn[idx - nframe];
-            if (n < 0) continue; // a newborn node on the frame: visited above
+            const int v = D.newborn[idx - nframe], n = v < 0 ? ~v : v;
             y = n / nx;
             x = n - y * nx;
+            if (v < 0 && (y == 0 || y == ny - 1)) continue; // visited above
         }
         const long long o = (long long)y * D.pitch + x;
         const uint8_t fl = D.flags[o];

@@ -850,8 +850,8 @@ cudaError_t launch_links_direct(const Dev &D, void *A, const int *own_cur, int *
                                 cudaStream_t s);
 // Warp tiles per row of the near-tile bitmap for a storage and pitch.
 int near_tiles_per_row(int storage, int pitch);
-// Nodes the stream-collide kernel leaves to the general path: the cavity
-// frame (x = 0, nx - 1, y = 0, ny - 1) and the listed newborn nodes.
+// Nodes the stream-collide kernel leaves to the general path: the first and
+// last rows (y = 0, ny - 1) and the listed newborn nodes.
 cudaError_t launch_boundary(const Dev &D, const void *Ain, void *Aout, const int *own_cur, int parity,
                             cudaStream_t s);
 // mode 0: fluid at rest (unit density, T_init) then collide; mode 1: collide
