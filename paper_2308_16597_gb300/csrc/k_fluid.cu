@@ -659,11 +659,12 @@ __device__ __forceinline__ void boundary_body(const Dev &D, const T *__restrict_
 }
 
 // Blocks per SM that measured best on the 4000^2 benchmark: FP32 10 (48
-// registers; 268 us against 272 with 8 and 279 with 12), 16-bit storage 8
-// (at most 64 registers; before the paired collision, BF16 209 us against
-// 220 with 7 and 219 with 10 blocks).
+// registers; 268 us against 272 with 8 and 279 with 12), 16-bit storage 9
+// (at most 56 registers, a few spilled: BF16 180.8 us against 184.6 with 8
+// and 181.8 with 10; the kernel waits on L2 latency as much as on issue, so
+// the ninth block's warps outweigh the spills).
 template <typename T, int V, int mode>
-__global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 8)
+__global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 9)
     k_stream_collide(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ahead_y, int ahead_x)
 {
     const Blk blk = this_blk();
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(128)
 // block's own instance left most blocks of small instances without a
 // prefetch).
 template <typename T, int V>
-__global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 8)
+__global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 9) // as k_stream_collide (BF16 ensemble: 0.516 against 0.522 ms per step with 8)
     k_stream_collide_batch(const InstArgs *__restrict__ I, const ScInst *__restrict__ sc,
                            const int *__restrict__ bucket, int shift, int n, int total, int parity, int resident)
 {
