@@ -155,7 +155,7 @@ __device__ __forceinline__ void revert_newborn(const Dev &D, int p, int tid, int
 //  5. the particle enters the screening grid of this step's update.
 template <typename T>
 __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__restrict__ own,
-                                           int *__restrict__ own_nxt, int parity, int ahead, const int p)
+                                           int *__restrict__ own_nxt, int parity, const int p, const int pa)
 {
     using E = Elem<T>;
     extern __shared__ __align__(16) unsigned char lsm[];
@@ -235,9 +235,10 @@ __device__ __forceinline__ void links_body(const Dev &D, T *A, const int *__rest
             }
         }
     }
-    // L2 prefetch of the owner rows of the particle `ahead` places later
-    if (warp == 1 && p + ahead < D.np) {
-        const GeomRec Ga = D.geo_cur[p + ahead];
+    // L2 prefetch of the owner rows of particle pa, the one a residency wave
+    // later in launch order (none: pa < 0)
+    if (warp == 1 && pa >= 0) {
+        const GeomRec Ga = D.geo_cur[pa];
         const int xa = Ga.X0 - 2, ya = Ga.Y0 - 2;
         for (int r = lane; r < 2 * wy; r += 32) {
             const int j = ya + (r >> 1), i = min(max(xa + (r & 1) * (wx - 1), 0), D.nx - 1);
@@ -1141,7 +1142,10 @@ __global__ void __launch_bounds__(kLinkThreads, kLinkCtasPerSm)
     k_links(const Dev D, T *A, const int *__restrict__ own,
             int *__restrict__ own_nxt, int parity, int ahead)
 {
-    links_body<T>(D, A, own, own_nxt, parity, ahead, (int)blockIdx.x);
+    // CTAs in the link order (descending y, the rows stream-collide wrote
+    // last first)
+    const int b = (int)blockIdx.x;
+    links_body<T>(D, A, own, own_nxt, parity, __ldg(D.lorder + b), b + ahead < D.np ? __ldg(D.lorder + b + ahead) : -1);
 }
 __global__ void __launch_bounds__(kPartThreads, 4) k_particles(const Dev D, int parity, int *own_nxt)
 {
@@ -1172,8 +1176,8 @@ __global__ void __launch_bounds__(kLinkThreads, kLinkCtasPerSm)
     const InstArgs &a = I[i];
     copy_dev(sD, a.D);
     const int par = parity ^ a.poff;
-    links_body<T>(sD, static_cast<T *>(a.A[par]), a.own[par], a.own[par ^ 1], par, ahead,
-                  (int)blockIdx.x - __ldg(start + i));
+    const int b = (int)blockIdx.x - __ldg(start + i);
+    links_body<T>(sD, static_cast<T *>(a.A[par]), a.own[par], a.own[par ^ 1], par, b, b + ahead < sD.np ? b + ahead : -1);
 }
 __global__ void __launch_bounds__(kPartThreads, 4)
     k_particles_batch(const InstArgs *__restrict__ I, const int *__restrict__ start, int n, int parity)
@@ -1220,6 +1224,44 @@ __global__ void k_geom_init(const Dev D)
     // only shapes the raster of that owner map inside the same zone)
     D.geo_prev[a] = make_geom(D.px[a], D.py[a], D.cur.r[a], D.cur.b[a], D.cur.th[a], 0.0, 0.0, 0.0, D.cur.T[a],
                               D.cur.rho[a], D.rho_f, D.g);
+}
+
+// Link order: the particles by descending y in kOrderBands bands of rows,
+// counting-sorted by one block (inside a band, in the order of the block's
+// shared-memory atomics).  Stream-collide writes the rows in ascending y,
+// so the rows it wrote last are still in L2 when the next link kernel
+// gathers from them, and the CTAs of the particles there run first (at
+// 4000^2 / 4800 disks: link kernel 78.6 against 84.0 us, step 0.3697
+// against 0.3750 ms).  Only the order of the CTAs changes, not what any of
+// them computes.
+constexpr int kOrderBands = 1024;
+__global__ void __launch_bounds__(kOrderBands) k_link_order(const Dev D)
+{
+    __shared__ int cnt[kOrderBands], at[kOrderBands];
+    const int t = threadIdx.x;
+    auto band = [&](int p) {
+        const double y = D.cur.y[p];
+        const int b = (int)((double)kOrderBands * (((double)D.ny - 1.0) - y) / (double)D.ny);
+        return min(max(b, 0), kOrderBands - 1);
+    };
+    cnt[t] = 0;
+    __syncthreads();
+    for (int p = t; p < D.np; p += kOrderBands) atomicAdd(&cnt[band(p)], 1);
+    __syncthreads();
+    at[t] = cnt[t];
+    __syncthreads();
+    for (int o = 1; o < kOrderBands; o <<= 1) { // inclusive prefix sum
+        const int v = t >= o ? at[t - o] : 0;
+        __syncthreads();
+        at[t] += v;
+        __syncthreads();
+    }
+    at[t] -= cnt[t]; // first position of band t
+    __syncthreads();
+    for (int p = t; p < D.np; p += kOrderBands) {
+        const int pos = atomicAdd(&at[band(p)], 1);
+        if (in_bounds(D, pos, D.np)) D.lorder[pos] = p;
+    }
 }
 
 __global__ void k_pack_particles(const Dev D, lbm_particle *out)
@@ -1415,6 +1457,13 @@ cudaError_t launch_geom_init(const Dev &D, cudaStream_t s)
 {
     if (D.np == 0) return cudaSuccess;
     k_geom_init<<<(D.np + 127) / 128, 128, 0, s>>>(D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_link_order(const Dev &D, cudaStream_t s)
+{
+    if (D.np == 0) return cudaSuccess;
+    k_link_order<<<1, kOrderBands, 0, s>>>(D);
     return cudaGetLastError();
 }
 

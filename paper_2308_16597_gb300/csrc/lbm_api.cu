@@ -19,6 +19,7 @@ constexpr size_t kAlign = 256;
 constexpr size_t kDistTailPad = 256; // bytes after each distribution buffer
 constexpr size_t kStageBytes = size_t(4) << 20;
 constexpr int kGraphLevels = 4; // replayed graphs hold 1, 2, 4 or 8 steps
+constexpr int kOrderSteps = 256; // steps between recomputations of the link order
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -115,6 +116,7 @@ void layout(const lbm_domain *d, const lbm_particle *p, int32_t n, int storage, 
     L.lsum = take((size_t)n * sizeof(LinkSums));
     for (int b = 0; b < 3; ++b) L.geo[b] = take((size_t)n * sizeof(GeomRec));
     L.pconst = take((size_t)n * sizeof(double4));
+    L.lorder = take((size_t)n * sizeof(int));
     L.status = take(sizeof(Status));
     L.pack = take((size_t)n * sizeof(lbm_particle));
     L.stage_rows = (int)std::max<size_t>(1, std::min<size_t>(d->ny, kStageBytes / (16 * (size_t)d->nx)));
@@ -400,6 +402,7 @@ void fill_dev(lbm_handle *h)
     D.geo_cur = reinterpret_cast<GeomRec *>(ws + L.geo[1]);
     D.geo_nxt = reinterpret_cast<GeomRec *>(ws + L.geo[2]);
     D.pconst = reinterpret_cast<double4 *>(ws + L.pconst);
+    D.lorder = reinterpret_cast<int *>(ws + L.lorder);
     D.status = reinterpret_cast<Status *>(ws + L.status);
     D.cell_gx = L.cell_gx;
     D.cell_gy = L.cell_gy;
@@ -441,6 +444,8 @@ int rebuild_maps(lbm_handle *h)
     int *oc = h->own[h->parity];
     CK(h, launch_geom_init(h->D, h->stream));
     CK(h, launch_cells_init(h->D, h->stream));
+    CK(h, launch_link_order(h->D, h->stream));
+    h->since_order = 0;
     CK(h, launch_raster(h->D, oc, h->D.geo_cur, h->D.cur, h->D.runs[h->parity], h->stream));
     CK(h, launch_flags(h->D, oc, oc, 0, h->parity, h->stream));
     // no newborn node yet
@@ -552,6 +557,12 @@ int lbm_step(lbm_handle *h, int32_t nsteps)
     const bool graph = !(h->prm.flags & LBM_FLAG_NO_GRAPH) && !h->timing;
     int rc;
     for (int32_t k = 0; k < nsteps;) {
+        // the link order follows the particles every kOrderSteps steps
+        if (h->since_order >= kOrderSteps) {
+            CK(h, launch_link_order(h->D, h->stream));
+            ++h->launches;
+            h->since_order = 0;
+        }
         if (graph) {
             // the largest graph (8, 4, 2 or 1 steps) that fits what is left
             int l = kGraphLevels - 1;
@@ -562,10 +573,12 @@ int lbm_step(lbm_handle *h, int32_t nsteps)
             CK(h, cudaGraphLaunch(g, h->stream));
             h->launches += (long long)n * kernels_per_step(h);
             h->parity ^= n & 1;
+            h->since_order += n;
             k += n;
         } else {
             if ((rc = enqueue_step(h, h->parity, h->stream))) return rc;
             h->parity ^= 1;
+            ++h->since_order;
             ++k;
         }
     }
@@ -743,6 +756,8 @@ int lbm_set_state(lbm_handle *h, const void *buf, size_t bytes)
         prev.y = h->D.py;
         CK(h, launch_geom_init(h->D, h->stream));
         CK(h, launch_cells_init(h->D, h->stream));
+        CK(h, launch_link_order(h->D, h->stream));
+        h->since_order = 0;
         CK(h, launch_raster(h->D, h->own[h->parity ^ 1], h->D.geo_prev, prev, nullptr, h->stream));
         // the row runs of the restored positions (their raster rewrites the
         // restored owner map with the values it holds), and the newborn

@@ -14,7 +14,7 @@ struct Layout {
     long long ps = 0;
     size_t nslots = 0;
     size_t A[2], own[2], flags, slot_node, slot_q, slot_base, cur, nxt, prev, force, pos4, prc, lsum,
-        geo[3], pconst, status, pack, stage, newborn, near, dsum, cells[2], runs[2], total;
+        geo[3], pconst, lorder, status, pack, stage, newborn, near, dsum, cells[2], runs[2], total;
     int newborn_cap = 0;
     int cell_gx = 1, cell_gy = 1; // cell grid of the pair screening
     double cell_side = 1.0;
@@ -38,6 +38,7 @@ struct lbm_handle {
     void *A[2]; // planes of D.storage elements
     int *own[2];
     int parity = 0;
+    int since_order = 0; // steps since the link order was last computed
     cudaGraphExec_t gexec[4][2] = {};               // 2^l steps (l = 0..3) from each parity
     bool timing = false;
     struct Ev {

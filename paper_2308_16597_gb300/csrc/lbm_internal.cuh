@@ -140,6 +140,7 @@ struct Dev {
     int direct;            // links found by the node-parallel scan instead of the index array
     struct GeomRec *geo_prev, *geo_cur, *geo_nxt; // [np] each: FP32/int geometry of the three positions
     double4 *pconst;   // [np]: constants of the update (1/M, 1/I, weight W, repulsion scale C)
+    int *lorder;       // [np]: the link kernel's CTA order (particles by descending y)
     // pair screening: a grid of square cells of side 1 / cell_inv >= 2 r_max
     // + s + 2, so that every pair in reach sits in the same or neighbouring
     // cells; per parity [cell_gx * cell_gy + 1] counts (the last one flags an
@@ -888,6 +889,8 @@ cudaError_t launch_geom_init(const Dev &D, cudaStream_t s);
 // Screening grids: both cleared (the first step's link kernel enters the
 // current positions).
 cudaError_t launch_cells_init(const Dev &D, cudaStream_t s);
+// The link kernel's CTA order from the current positions (descending y).
+cudaError_t launch_link_order(const Dev &D, cudaStream_t s);
 
 // Batched step kernels over an InstArgs table (one grid over all instances;
 // `start` holds the n + 1 block offsets of the launch, `total` its blocks).

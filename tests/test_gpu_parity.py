@@ -386,6 +386,37 @@ def test_moving_disk_refills_like_the_oracle():
     assert np.abs(pg["x"] - po["x"]).max() < 1e-6
 
 
+def test_disks_leaving_the_side_columns_refill_like_the_oracle():
+    """Disks that start over the first and last columns and the first row
+    move off them: the uncovered side-column nodes are refilled by the
+    general path from the newborn list, the fluid side-column nodes are
+    pulled by the stream-collide kernel (wall rule across the side walls),
+    and every field, the newborn count and the centres follow the oracle."""
+    parts = np.zeros(4, W.PARTICLE_DTYPE)
+    parts["x"], parts["y"] = [8.2, 170.8, 90.3, 60.4], [30.3, 62.7, 8.15, 55.0]
+    parts["r"], parts["rho"], parts["T"] = 8.5, 1.5, 1.0
+    parts["ux"], parts["uy"] = [0.12, -0.12, 0.0, 0.03], [0.0, 0.01, 0.12, -0.02]
+    nx, ny = 180, 100
+    own0 = orc.raster(nx, ny, parts)
+    assert (own0[:, 0] == 0).any() and (own0[:, nx - 1] == 1).any() and (own0[0, :] == 2).any()
+    dom = W.cavity(nx, ny, T_wall=(0.3, 0.8, 1.0, 0.1))
+    prm = W.base_params(0.05, 0.71, 1e-4, eps_w=1e3)
+    sim = lbm.Simulation(dom, parts, prm)
+    ref = orc.Oracle(dom, parts, prm)
+    nb_g = nb_o = 0
+    for _ in range(25):
+        sim.step(1)
+        assert ref.step(1) == 0
+        nb_g += sim.counters()[6]
+        nb_o += ref.counters()[6]
+    assert nb_o > 0 and nb_g == nb_o
+    compare_fields(sim, ref, 1e-5)
+    own = orc.raster(nx, ny, sim.particles())
+    assert not (own[:, 0] == 0).any() and not (own[:, nx - 1] == 1).any()  # the side columns were uncovered
+    pg, po = sim.particles(), ref.particles()
+    assert np.abs(pg["x"] - po["x"]).max() < 1e-6 and np.abs(pg["y"] - po["y"]).max() < 1e-6
+
+
 def state_flags(sim, nx, ny):
     """Node flags (0 fluid, 1 solid, 2 newborn) from the raw state image, laid
     out as include/lbm.h states: 14 FP32 planes of plane_stride elements, the
