@@ -322,6 +322,7 @@ def config_of(wl, args):
             "radius": float(p["r"][0]) if len(p) else None,
             "minor_axis": float(p["b"][0]) if len(p) and p["b"][0] > 0 else None,
             "storage": getattr(args, "storage", "fp32"), "links": getattr(args, "links", "index"),
+            "stream_collide": getattr(args, "stream_collide", "staged"),
             "density_ratio": float(p["rho"][0]) if len(p) else None,
             "parallelism": "replicas%d" % args.gpus,
             "l2": "no flush: each step reads one distribution buffer and writes the other, %.2f GB "
@@ -381,6 +382,8 @@ def run_ours(args, wl):
     nodes = wl.nx * wl.ny
     storage = STORAGE_CODES[args.storage]
     flags = lbm.LBM_FLAG_DIRECT_LINKS if args.links == "direct" else 0
+    if args.stream_collide == "unstaged":
+        flags |= lbm.LBM_FLAG_SC_UNSTAGED
     sampler = NvmlSampler(dev)
     with torch.cuda.stream(stream):
         sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream, storage=storage, flags=flags)
@@ -732,6 +735,9 @@ def main(argv=None):
     ap.add_argument("--links", choices=["index", "direct"], default="index",
                     help="links from the fixed index array (default) or by direct addressing (the paper's "
                          "comparison, Table 1)")
+    ap.add_argument("--stream-collide", choices=["staged", "unstaged"], default="staged",
+                    help="whole-lattice stream-collide kernel: persistent blocks staging row tiles in shared "
+                         "memory (default), or one block per tile reading global memory (comparison)")
     ap.add_argument("--storage", choices=sorted(STORAGE_CODES), default="fp32",
                     help="plane storage: FP32 (the headline), or BF16 / scaled FP16 deviations")
     args = ap.parse_args(argv)

@@ -91,6 +91,18 @@ extern "C" {
  * back to all pairs for a step after one of its cells overflowed); for
  * tests. */
 #define LBM_FLAG_ALL_PAIRS 16u
+/* With BF16 or FP16 storage, stream-collide over the whole lattice with one
+ * block per row tile reading its pulled values straight from global memory,
+ * instead of the default staged kernel (persistent blocks, row tiles copied
+ * into shared memory by bulk asynchronous copies two tiles ahead).
+ * Bit-identical results; for comparisons.  FP32 storage always takes the
+ * one-block-per-tile kernel, which is the faster of the two there. */
+#define LBM_FLAG_SC_UNSTAGED 32u
+/* Tests only (BF16 or FP16 storage): the staged stream-collide kernel
+ * announces one byte more than its copies bring, so its bounded waits run
+ * out (after about a second) and the step reports LBM_ETIMEOUT; the
+ * distributions are then invalid. */
+#define LBM_FLAG_TEST_WAIT_TIMEOUT 64u
 
 typedef struct {
     int32_t nx, ny;    /* nodes per axis, >= 4 each */

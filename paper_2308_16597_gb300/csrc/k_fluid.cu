@@ -411,6 +411,10 @@ __device__ __forceinline__ void prefetch_block(const Dev &D, const T *__restrict
     }
 }
 
+template <typename T, int V>
+__device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
+                                        float (&c)[V][kPop], int x0, int y, const uint8_t *flp);
+
 // pf_x < 0: no look-ahead prefetch here (the caller issues its own).
 template <typename T, int V, int mode = kSCAll>
 __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout, int pf_x,
@@ -509,6 +513,20 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
         }
     }
     if (!act) return;
+    sc_tail<T, V>(D, Ain, Aout, c, x0, y, D.flags + (long long)y * D.pitch + x0);
+}
+
+// The part of a stream-collide update after the interior pulls, for the V
+// nodes x0 .. x0 + V - 1 of row y whose pulled values c holds: the side
+// nodes' wall or seam planes, the collision, the stores and the numeric
+// check.  flp points at the nodes' flags (global or shared memory).
+template <typename T, int V>
+__device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
+                                        float (&c)[V][kPop], int x0, int y, const uint8_t *flp)
+{
+    using E = Elem<T>;
+    using VW = typename Vec<T, V>::W;
+    const bool interior = y >= 1 && y + 1 < D.ny;
     // The nodes x = 0 and x = nx - 1 of the rows between the first and the
     // last: the planes that pull across a side wall or the periodic seam
     // take the wall rule or the far side's value (side_pull: the general
@@ -538,7 +556,7 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
         // nodes (and the padding past nx) are zeroed after
         bool fluid[2];
         // both nodes' flags in one 2-byte load (x0 is even)
-        const unsigned short fl2 = *reinterpret_cast<const unsigned short *>(D.flags + (long long)y * D.pitch + x0);
+        const unsigned short fl2 = *reinterpret_cast<const unsigned short *>(flp);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int x = x0 + k;
@@ -571,7 +589,7 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             const int x = x0 + k;
-            const uint8_t fl = D.flags[(long long)y * D.pitch + x];
+            const uint8_t fl = flp[k];
             gen[k] = false;
             if (x < D.nx && fl != kSolid) {
                 // newborn nodes and the first and last rows belong to
@@ -673,6 +691,275 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 9)
     sc_body<T, V, mode>(D, Ain, Aout, bx, by, blk);
 }
 
+
+// ---------------------------------------------------------------------------
+// Staged stream-collide (the default pass over the whole lattice).  The same
+// update as k_stream_collide, bit for bit, organised around shared memory:
+// a persistent grid of 128-thread blocks claims row tiles of 128 V nodes in
+// row order from a device counter, and each block keeps kStStages tiles in
+// flight.  For a tile, 14 lanes of warp 0 each issue one bulk asynchronous
+// copy (cp.async.bulk, completion counted in bytes on the stage's mbarrier)
+// of a plane's source row segment, with 16 bytes more on the side the plane
+// pulls from, and a fifteenth lane copies the tile's flags.  The block
+// collides one tile from shared memory while the copies of the next ones are
+// in flight: the memory latency overlaps the arithmetic without holding
+// registers, and every pulled value is a shared-memory load at a fixed
+// offset from one base (no shuffles, no edge loads, no per-plane address
+// arithmetic).  Rows stay in launch order, so the tiles in flight form a
+// compact band of rows, as in k_stream_collide.
+//
+// Shared memory per stage: 14 plane segments of 128 V + 2 H elements
+// (H = 16 bytes of elements; node x_s + i at element H + i), then the
+// tile's 128 V flag bytes.  The reads past a row's ends (x = -H .. -1 for a
+// plane pulling from x - 1, which has index p >= 1, so the previous plane or
+// row lies there; x = pitch .. pitch + H - 1 for one pulling from x + 1, the
+// next row, plane or the buffer's tail pad) feed only the side nodes' wall or
+// seam planes, which sc_tail replaces, and the zeroed padding.  The first and
+// last rows read clamped source rows: every fluid node there belongs to
+// k_boundary, and the others are stored as zeros.
+//
+// Every wait on an mbarrier is bounded (one second of the global timer);
+// one that runs out records kErrTimeout (LBM_ETIMEOUT), and the block waits,
+// again bounded, for its copies still in flight before it leaves.
+// ---------------------------------------------------------------------------
+#ifndef LBM_ST_STAGES
+#define LBM_ST_STAGES 3
+#endif
+constexpr int kStStages = LBM_ST_STAGES;
+#ifndef LBM_ST_MINB
+#define LBM_ST_MINB 9
+#endif
+constexpr unsigned long long kStWaitNs = 1000000000ull;
+
+template <typename T, int V>
+struct StGeo {
+    static constexpr int W = kSCThreads * V;                     // nodes of a tile
+    static constexpr int H = 16 / (int)sizeof(T);                // halo elements on a pulled side
+    static constexpr int SEG_B = (W + 2 * H) * (int)sizeof(T);   // bytes of a plane segment
+    static constexpr int FLAGS_OFF = kPop * SEG_B;               // the tile's flags
+    static constexpr int STAGE_B = (FLAGS_OFF + W + 127) / 128 * 128;
+    static constexpr int SMEM_B = kStStages * STAGE_B + 128;     // + barriers and tile slots
+};
+// Planes whose source lies one node to the side (e_x != 0): they copy H
+// elements more.
+__host__ __device__ constexpr int shifted_planes()
+{
+    int n = 0;
+    for (int p = 0; p < kPop; ++p) n += ex(pdir(p)) != 0;
+    return n;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned tx)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity to complete, for at most kStWaitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity))
+        if (global_ns() - t0 > kStWaitNs) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_to_smem(unsigned dst, const void *src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Shared memory after the stages: a `full` barrier per stage (complete when
+// the tile's copies have landed), the tile of each stage, and two slots that
+// pass the next claimed tile from thread 0 to the block.
+template <typename T, int V>
+struct StTail {
+    unsigned long long *full;
+    int *sitem, *snext;
+    __device__ explicit StTail(unsigned char *sm)
+    {
+        full = reinterpret_cast<unsigned long long *>(sm + kStStages * StGeo<T, V>::STAGE_B);
+        sitem = reinterpret_cast<int *>(full + kStStages);
+        snext = sitem + kStStages;
+    }
+};
+
+// The block loads tile `it` (row it / ntx, column tile it % ntx) into stage
+// s: copy c (planes 0..13, then the flags) is issued by lane c % 4 of warp
+// c / 4, so no warp carries the copies alone; thread 0 first records the
+// tile and announces the bytes (a copy that lands before the announcement
+// only makes the byte count negative for a while; the phase cannot complete
+// before thread 0's arrival).  it < 0: nothing to load, the stage's phase
+// completes at once and tells the block to stop.  Every thread passes the
+// same it.
+template <typename T, int V>
+__device__ __forceinline__ void st_issue(const Dev &D, const T *__restrict__ Ain, unsigned char *sm, int s, int it,
+                                         int ntx)
+{
+    using G = StGeo<T, V>;
+    const StTail<T, V> t(sm);
+    const int lane = threadIdx.x & 31, c = (threadIdx.x >> 5) * 4 + lane;
+    const unsigned b = smem_addr(t.full + s);
+    const int y = it < 0 ? 0 : it / ntx;
+    const int xs = (it - y * ntx) * G::W;
+    const int xe = min(xs + G::W, D.pitch);
+    if (threadIdx.x == 0) {
+        t.sitem[s] = it;
+        if (it < 0) mbar_arrive(b);
+        else
+            mbar_arrive_tx(b, (unsigned)((xe - xs) * (kPop * (int)sizeof(T) + 1) + shifted_planes() * 16 +
+                                         D.sc_extra_tx));
+    }
+    if (it < 0 || lane >= 4 || c > kPop) return;
+    unsigned char *st = sm + s * G::STAGE_B;
+    if (c == kPop) { // the tile's flags
+        bulk_to_smem(smem_addr(st + G::FLAGS_OFF), D.flags + (long long)y * D.pitch + xs, (unsigned)(xe - xs), b);
+        return;
+    }
+    const int p = c, d = pdir(p), dx = ex(d);
+    int ys = y - ey(d);
+    if (ys < 0 || ys >= D.ny) {
+        if (D.per_y) ys = ys < 0 ? ys + D.ny : ys - D.ny;
+        else ys = min(max(ys, 0), D.ny - 1); // the first or last row: values unused
+    }
+    const int lo = xs - (dx == 1 ? G::H : 0), hi = xe + (dx == -1 ? G::H : 0);
+    long long e = (long long)p * D.ps + (long long)ys * D.pitch + lo;
+    if (!(in_bounds(D, e, D.a_elems) && in_bounds(D, e + (hi - lo) - 1, D.a_elems))) e = 0; // checked builds
+    bulk_to_smem(smem_addr(st + p * G::SEG_B) + (unsigned)((lo - xs + G::H) * (int)sizeof(T)), Ain + e,
+                 (unsigned)((hi - lo) * (int)sizeof(T)), b);
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
+    k_stream_collide_staged(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ntx, int nitems)
+{
+    using G = StGeo<T, V>;
+    using E = Elem<T>;
+    using VW = typename Vec<T, V>::W;
+    extern __shared__ __align__(128) unsigned char sm[];
+    const StTail<T, V> t(sm);
+    const int tid = threadIdx.x;
+    unsigned *ctr = &D.status->sc_next;
+    auto claim = [&]() {
+        const int it = (int)atomicAdd(ctr, 1u);
+        return it < nitems ? it : -1;
+    };
+
+    // thread 0 claims the first kStStages tiles (after the first tile past
+    // the end, none): kStStages - 1 to load now, one for the first refill
+    if (tid == 0) {
+        for (int s = 0; s < kStStages; ++s) mbar_init(smem_addr(t.full + s), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        int it = 0;
+        for (int s = 0; s < kStStages; ++s) {
+            it = it < 0 ? -1 : claim();
+            if (s + 1 < kStStages) t.sitem[s] = it;
+            else t.snext[0] = it;
+        }
+    }
+    __syncthreads();
+    for (int s = 0; s + 1 < kStStages; ++s) {
+        const int it = t.sitem[s];
+        __syncthreads(); // every thread has read the slot st_issue rewrites
+        st_issue<T, V>(D, Ain, sm, s, it, ntx);
+    }
+    bool timeout = false;
+    int k = 0;
+    for (;; ++k) {
+        const int s = k % kStStages;
+        // refill the stage the block finished with in the last iteration
+        // with the tile claimed then; thread 0 claims the one after it
+        const int nit = t.snext[k & 1];
+        st_issue<T, V>(D, Ain, sm, (k + kStStages - 1) % kStStages, nit, ntx);
+        int claimed = -1;
+        if (tid == 0 && nit >= 0) claimed = claim();
+        const bool got = mbar_wait(smem_addr(t.full + s), (unsigned)(k / kStStages) & 1u);
+        const int it = got ? t.sitem[s] : -1;
+        if (got && it >= 0) {
+            const int y = it / ntx;
+            const int x0 = (it - y * ntx) * G::W + tid * V;
+            if (x0 < D.pitch) { // threads past the pitch have no node
+                const unsigned char *sb = sm + s * G::STAGE_B;
+                float c[V][kPop];
+#pragma unroll
+                for (int p = 0; p < kPop; ++p) {
+                    const int dx = ex(pdir(p));
+                    const T *seg = reinterpret_cast<const T *>(sb + p * G::SEG_B) + G::H + tid * V;
+                    if constexpr (V == 1) {
+                        c[0][p] = E::ld(seg[-dx]);
+                    } else {
+                        float a[2];
+                        Vec<T, V>::unpack(*reinterpret_cast<const VW *>(seg), a);
+                        if (dx == 0) {
+                            c[0][p] = a[0];
+                            c[1][p] = a[1];
+                        } else if (dx == 1) { // pull from x - 1
+                            float l[2];
+                            Vec<T, V>::unpack(*reinterpret_cast<const VW *>(seg - 2), l);
+                            c[0][p] = l[1];
+                            c[1][p] = a[0];
+                        } else { // pull from x + 1
+                            float r[2];
+                            Vec<T, V>::unpack(*reinterpret_cast<const VW *>(seg + 2), r);
+                            c[0][p] = a[1];
+                            c[1][p] = r[0];
+                        }
+                    }
+                }
+                sc_tail<T, V>(D, Ain, Aout, c, x0, y, sb + G::FLAGS_OFF + tid * V);
+            }
+        }
+        if (tid == 0) t.snext[(k + 1) & 1] = claimed;
+        // every thread is done with stage s and has read snext[k & 1]; stop
+        // together at the end of the work or after a wait ran out
+        if (__syncthreads_or((!got) | (it < 0))) {
+            timeout = __syncthreads_or(!got);
+            break;
+        }
+    }
+    if (timeout) {
+        if (tid == 0) atomicOr(&D.status->err, kErrTimeout);
+        // copies may still be in flight into the stages of iterations k ..
+        // k + kStStages - 1: wait for them (bounded) before leaving
+        for (int j = k; j < k + kStStages; ++j)
+            if (!mbar_wait(smem_addr(t.full + j % kStStages), (unsigned)(j / kStStages) & 1u)) break;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&D.status->sc_done, 1u) == gridDim.x - 1) { // the last block: reset for the next launch
+            D.status->sc_next = 0u;
+            D.status->sc_done = 0u;
+            __threadfence();
+        }
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(128)
@@ -812,13 +1099,42 @@ cudaError_t stream_collide_m(const Dev &D, const void *Ain, void *Aout, cudaStre
     return cudaGetLastError();
 }
 
+// The staged kernel's grid: as many blocks as the GPU holds at once (they
+// claim tiles from the work counter, so blocks that start late, behind the
+// boundary kernel's, take fewer).
+template <typename T, int V>
+cudaError_t stream_collide_staged(const Dev &D, const void *Ain, void *Aout, cudaStream_t s)
+{
+    using G = StGeo<T, V>;
+    static int resident = 0;
+    if (!resident) {
+        cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<T, V>,
+                                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_staged<T, V>, kSCThreads,
+                                                          G::SMEM_B);
+        if (e != cudaSuccess) return e;
+        resident = max(1, sms * per_sm);
+    }
+    const int ntx = (D.pitch + G::W - 1) / G::W;
+    const int nitems = ntx * D.ny;
+    k_stream_collide_staged<T, V><<<min(resident, nitems), kSCThreads, G::SMEM_B, s>>>(
+        D, static_cast<const T *>(Ain), static_cast<T *>(Aout), ntx, nitems);
+    return cudaGetLastError();
+}
+
 template <typename T, int V>
 cudaError_t stream_collide_t(const Dev &D, const void *Ain, void *Aout, int mode, cudaStream_t s)
 {
     switch (mode) {
     case kSCFar: return stream_collide_m<T, V, kSCFar>(D, Ain, Aout, s);
     case kSCNear: return stream_collide_m<T, V, kSCNear>(D, Ain, Aout, s);
-    default: return stream_collide_m<T, V, kSCAll>(D, Ain, Aout, s);
+    default:
+        return D.sc_staged ? stream_collide_staged<T, V>(D, Ain, Aout, s)
+                           : stream_collide_m<T, V, kSCAll>(D, Ain, Aout, s);
     }
 }
 

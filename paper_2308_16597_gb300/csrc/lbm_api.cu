@@ -383,6 +383,10 @@ void fill_dev(lbm_handle *h)
     D.near = reinterpret_cast<unsigned *>(ws + L.near);
     D.dsum = reinterpret_cast<DirectSums *>(ws + L.dsum);
     D.direct = (P.flags & LBM_FLAG_DIRECT_LINKS) ? 1 : 0;
+    // the staged stream-collide pays with 16-bit storage only (BF16 at
+    // 4000^2: 166.9 against 180.4 us; FP32: 292 or more against 272 us)
+    D.sc_staged = (P.storage != LBM_STORE_FP32 && !(P.flags & LBM_FLAG_SC_UNSTAGED)) ? 1 : 0;
+    D.sc_extra_tx = (P.flags & LBM_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0;
     D.all_pairs = (P.flags & LBM_FLAG_ALL_PAIRS) ? 1 : 0;
     D.near_tpr = near_tiles_per_row(P.storage, L.pitch);
     D.slot_node = reinterpret_cast<int *>(ws + L.slot_node);
@@ -541,8 +545,12 @@ int lbm_init(lbm_handle **out, const lbm_domain *d, const lbm_particle *p, int32
         if ((rc = upload_particles(h, p))) return fail(rc);
     }
     if ((rc = rebuild_maps(h))) return fail(rc);
-    const size_t abytes = (size_t)kPop * h->L.ps * storage_bytes(h->D.storage);
-    if (cudaMemsetAsync(h->A[1], 0, abytes, h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    // both buffers zeroed whole (the gaps between planes, where the plane
+    // stride exceeds ny x pitch, and the tail pad included), so that state
+    // images hold no leftover bytes of the workspace
+    const size_t abytes = (size_t)kPop * h->L.ps * storage_bytes(h->D.storage) + kDistTailPad;
+    for (int b = 0; b < 2; ++b)
+        if (cudaMemsetAsync(h->A[b], 0, abytes, h->stream) != cudaSuccess) return fail(LBM_ECUDA);
     if (launch_init_collide(h->D, h->A[1], h->A[0], (float)prm->T_init, 0, h->stream) != cudaSuccess)
         return fail(LBM_ECUDA);
     if ((rc = sync_status(h))) return fail(rc);

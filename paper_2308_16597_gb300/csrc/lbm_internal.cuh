@@ -93,6 +93,10 @@ struct Status {
     unsigned long long cnt[2][kNumCounters]; // double-buffered by step parity
     unsigned int nb;     // newborn nodes listed this step (reset by the particle update)
     unsigned int nb_pad;
+    // the staged stream-collide's work counter (next row tile to claim) and
+    // the count of its blocks done; the last block done resets both to 0
+    unsigned int sc_next;
+    unsigned int sc_done;
 };
 
 // Structure-of-arrays particle state on the device (FP64).
@@ -138,6 +142,8 @@ struct Dev {
     struct LinkSums *lsum; // [np]: link-kernel sums, assembled into force by the particle update
     struct DirectSums *dsum; // [np]: the same sums accumulated by atomics (direct addressing)
     int direct;            // links found by the node-parallel scan instead of the index array
+    int sc_staged;         // whole-lattice stream-collide through the staged kernel (else one block per tile)
+    int sc_extra_tx;       // bytes the staged kernel announces beyond its copies (tests of its bounded waits)
     struct GeomRec *geo_prev, *geo_cur, *geo_nxt; // [np] each: FP32/int geometry of the three positions
     double4 *pconst;   // [np]: constants of the update (1/M, 1/I, weight W, repulsion scale C)
     int *lorder;       // [np]: the link kernel's CTA order (particles by descending y)

@@ -28,6 +28,7 @@ LBM_BC_PERIODIC_X, LBM_BC_PERIODIC_Y = 1, 2
 LBM_STORE_FP32, LBM_STORE_BF16, LBM_STORE_FP16 = 0, 1, 2
 LBM_FLAG_FIXED_PARTICLES, LBM_FLAG_NO_GRAPH, LBM_FLAG_OVERLAP, LBM_FLAG_DIRECT_LINKS = 1, 2, 4, 8
 LBM_FLAG_ALL_PAIRS = 16
+LBM_FLAG_SC_UNSTAGED, LBM_FLAG_TEST_WAIT_TIMEOUT = 32, 64
 
 PARTICLE_DTYPE = np.dtype([(n, "f8") for n in
                            ("x", "y", "ux", "uy", "theta", "omega", "r", "rho", "T", "b")])

@@ -166,6 +166,53 @@ def test_stream_collide_overrun_fits_the_tail_pad():
     assert (448 + 32 * V + 1 - pitch) * 2 > pad_bytes
 
 
+def test_staged_stream_collide_copies_are_aligned_and_in_bounds():
+    """The staged stream-collide's bulk copies, restated: tile of W = 256
+    nodes of a row, halo H = 16 bytes of elements on the side a plane pulls
+    from (p with e_x = 1 reads from x_s - H, e_x = -1 up to x_e + H), source
+    row clamped on non-periodic first and last rows, plus the flags.  Every
+    copy must start on a 16-byte boundary in global and shared memory, move a
+    multiple of 16 bytes, stay inside its buffer (planes and tail pad, or the
+    flag map) and inside its shared-memory segment; and the announced byte
+    count must equal the bytes the copies bring."""
+    ex = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    ey = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    pdx = ex + ex[:5]
+    pdy = ey + ey[:5]
+    pad_bytes = 256
+    for es in (2, 4):
+        W, H = (256 if es == 2 else 128), 16 // es
+        seg_b = (W + 2 * H) * es
+        shifted = sum(1 for d in pdx if d != 0)
+        for nx in list(range(4, 700, 7)) + [4000, 4001, 2047]:
+            for ny in (4, 5, 9, 37):
+                pitch = (nx + 31) // 32 * 32
+                ps = (pitch * ny + 63) // 64 * 64
+                a_bytes = 14 * ps * es + pad_bytes
+                ntx = (pitch + W - 1) // W
+                for per_y in (0, 1):
+                    for it in range(ntx * ny):
+                        y, cx = divmod(it, ntx)
+                        xs, xe = cx * W, min(cx * W + W, pitch)
+                        got = xe - xs
+                        assert y * pitch + xs >= 0 and (y * pitch + xs) % 16 == 0 and (xe - xs) % 16 == 0
+                        assert y * pitch + xe <= pitch * ny
+                        for p in range(14):
+                            ys = y - pdy[p]
+                            if ys < 0 or ys >= ny:
+                                ys = (ys % ny) if per_y else min(max(ys, 0), ny - 1)
+                            lo = xs - (H if pdx[p] == 1 else 0)
+                            hi = xe + (H if pdx[p] == -1 else 0)
+                            start = (p * ps + ys * pitch + lo) * es
+                            size = (hi - lo) * es
+                            assert start >= 0 and start + size <= a_bytes, (es, nx, ny, it, p)
+                            assert start % 16 == 0 and size % 16 == 0
+                            dst = (lo - xs + H) * es
+                            assert dst % 16 == 0 and dst >= 0 and dst + size <= seg_b
+                            got += size
+                        assert got == (xe - xs) * (14 * es + 1) + shifted * 16
+
+
 def test_batched_block_lookup_finds_every_tile():
     """The batched stream-collide's block -> (instance, tile) mapping,
     restated: per-instance first block and tiles per row gx with the
