@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 9)
 #endif
 constexpr int kStStages = LBM_ST_STAGES;
 #ifndef LBM_ST_MINB
-#define LBM_ST_MINB 9
+#define LBM_ST_MINB 8
 #endif
 constexpr unsigned long long kStWaitNs = 1000000000ull;
 
@@ -796,63 +796,79 @@ __device__ __forceinline__ void bulk_to_smem(unsigned dst, const void *src, unsi
 }
 
 // Shared memory after the stages: a `full` barrier per stage (complete when
-// the tile's copies have landed), the tile of each stage, and two slots that
-// pass the next claimed tile from thread 0 to the block.
+// the tile's copies have landed), the tile of each stage (row y and first
+// column xs; y < 0: no tile), and two slots that pass the next claimed tile
+// from thread 0 to the block.
 template <typename T, int V>
 struct StTail {
     unsigned long long *full;
-    int *sitem, *snext;
+    int2 *stile, *snext;
     __device__ explicit StTail(unsigned char *sm)
     {
         full = reinterpret_cast<unsigned long long *>(sm + kStStages * StGeo<T, V>::STAGE_B);
-        sitem = reinterpret_cast<int *>(full + kStStages);
-        snext = sitem + kStStages;
+        stile = reinterpret_cast<int2 *>(full + kStStages);
+        snext = stile + kStStages;
     }
 };
 
-// The block loads tile `it` (row it / ntx, column tile it % ntx) into stage
-// s: copy c (planes 0..13, then the flags) is issued by lane c % 4 of warp
-// c / 4, so no warp carries the copies alone; thread 0 first records the
-// tile and announces the bytes (a copy that lands before the announcement
-// only makes the byte count negative for a while; the phase cannot complete
-// before thread 0's arrival).  it < 0: nothing to load, the stage's phase
-// completes at once and tells the block to stop.  Every thread passes the
-// same it.
+// The copy a thread issues for every tile, fixed for the launch: copy c
+// (planes 0..13, then the flags) belongs to lane c % 4 of warp c / 4, so no
+// warp carries the copies alone.  Three registers: the copy (-1 none, kPop
+// the flags), its shared-memory destination in stage 0, and for a plane its
+// row shift e_y + 1 (bits 0-1) and whether it pulls from x - 1 (bit 2) or
+// x + 1 (bit 3), i.e. takes H elements more on that side.
+struct StLane {
+    int c;
+    unsigned dst;
+    int meta;
+};
 template <typename T, int V>
-__device__ __forceinline__ void st_issue(const Dev &D, const T *__restrict__ Ain, unsigned char *sm, int s, int it,
-                                         int ntx)
+__device__ __forceinline__ StLane st_lane(unsigned char *sm)
+{
+    using G = StGeo<T, V>;
+    const int lane = threadIdx.x & 31, c = (threadIdx.x >> 5) * 4 + lane;
+    if (lane >= 4 || c > kPop) return StLane{-1, 0u, 0};
+    if (c == kPop) return StLane{c, smem_addr(sm + G::FLAGS_OFF), 0};
+    const int d = pdir(c), dx = ex(d);
+    return StLane{c, smem_addr(sm + c * G::SEG_B) + (unsigned)((dx == 1 ? 0 : G::H) * (int)sizeof(T)),
+                  (ey(d) + 1) | (dx == 1 ? 4 : 0) | (dx == -1 ? 8 : 0)};
+}
+
+// The block loads the tile of row y, columns xs .. xs + W - 1, into stage s,
+// each thread issuing its copy; thread 0 first records the tile and
+// announces the bytes (a copy that lands before the announcement only makes
+// the byte count negative for a while; the phase cannot complete before
+// thread 0's arrival).  y < 0: nothing to load, the stage's phase completes
+// at once and tells the block to stop.  Every thread passes the same tile.
+template <typename T, int V>
+__device__ __forceinline__ void st_issue(const Dev &D, const T *__restrict__ Ain, unsigned char *sm, int s, int2 tile,
+                                         const StLane &L)
 {
     using G = StGeo<T, V>;
     const StTail<T, V> t(sm);
-    const int lane = threadIdx.x & 31, c = (threadIdx.x >> 5) * 4 + lane;
     const unsigned b = smem_addr(t.full + s);
-    const int y = it < 0 ? 0 : it / ntx;
-    const int xs = (it - y * ntx) * G::W;
-    const int xe = min(xs + G::W, D.pitch);
+    const int y = tile.x, xs = tile.y;
+    const int n = min(G::W, D.pitch - xs); // nodes of the tile
     if (threadIdx.x == 0) {
-        t.sitem[s] = it;
-        if (it < 0) mbar_arrive(b);
-        else
-            mbar_arrive_tx(b, (unsigned)((xe - xs) * (kPop * (int)sizeof(T) + 1) + shifted_planes() * 16 +
-                                         D.sc_extra_tx));
+        t.stile[s] = tile;
+        if (y < 0) mbar_arrive(b);
+        else mbar_arrive_tx(b, (unsigned)(n * (kPop * (int)sizeof(T) + 1) + shifted_planes() * 16 + D.sc_extra_tx));
     }
-    if (it < 0 || lane >= 4 || c > kPop) return;
-    unsigned char *st = sm + s * G::STAGE_B;
-    if (c == kPop) { // the tile's flags
-        bulk_to_smem(smem_addr(st + G::FLAGS_OFF), D.flags + (long long)y * D.pitch + xs, (unsigned)(xe - xs), b);
+    if (y < 0 || L.c < 0) return;
+    const unsigned dst = L.dst + (unsigned)(s * G::STAGE_B);
+    if (L.c == kPop) { // the tile's flags
+        bulk_to_smem(dst, D.flags + (long long)y * D.pitch + xs, (unsigned)n, b);
         return;
     }
-    const int p = c, d = pdir(p), dx = ex(d);
-    int ys = y - ey(d);
-    if (ys < 0 || ys >= D.ny) {
+    int ys = y - ((L.meta & 3) - 1);
+    if ((unsigned)ys >= (unsigned)D.ny) {
         if (D.per_y) ys = ys < 0 ? ys + D.ny : ys - D.ny;
         else ys = min(max(ys, 0), D.ny - 1); // the first or last row: values unused
     }
-    const int lo = xs - (dx == 1 ? G::H : 0), hi = xe + (dx == -1 ? G::H : 0);
-    long long e = (long long)p * D.ps + (long long)ys * D.pitch + lo;
-    if (!(in_bounds(D, e, D.a_elems) && in_bounds(D, e + (hi - lo) - 1, D.a_elems))) e = 0; // checked builds
-    bulk_to_smem(smem_addr(st + p * G::SEG_B) + (unsigned)((lo - xs + G::H) * (int)sizeof(T)), Ain + e,
-                 (unsigned)((hi - lo) * (int)sizeof(T)), b);
+    const int halo = (L.meta & 12) ? G::H : 0;
+    long long e = (long long)L.c * D.ps + (long long)ys * D.pitch + xs - ((L.meta & 4) ? G::H : 0);
+    if (!(in_bounds(D, e, D.a_elems) && in_bounds(D, e + n + halo - 1, D.a_elems))) e = 0; // checked builds
+    bulk_to_smem(dst, Ain + e, (unsigned)((n + halo) * (int)sizeof(T)), b);
 }
 
 template <typename T, int V>
@@ -865,29 +881,34 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
     extern __shared__ __align__(128) unsigned char sm[];
     const StTail<T, V> t(sm);
     const int tid = threadIdx.x;
+    const StLane L = st_lane<T, V>(sm);
     unsigned *ctr = &D.status->sc_next;
+    // thread 0: the next tile from the work counter as (row, first column),
+    // row -1 past the end
     auto claim = [&]() {
         const int it = (int)atomicAdd(ctr, 1u);
-        return it < nitems ? it : -1;
+        if (it >= nitems) return make_int2(-1, 0);
+        const int y = it / ntx;
+        return make_int2(y, (it - y * ntx) * G::W);
     };
 
-    // thread 0 claims the first kStStages tiles (after the first tile past
+    // thread 0 claims the first kStStages tiles (after the first one past
     // the end, none): kStStages - 1 to load now, one for the first refill
     if (tid == 0) {
         for (int s = 0; s < kStStages; ++s) mbar_init(smem_addr(t.full + s), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        int it = 0;
+        int2 tile = make_int2(0, 0);
         for (int s = 0; s < kStStages; ++s) {
-            it = it < 0 ? -1 : claim();
-            if (s + 1 < kStStages) t.sitem[s] = it;
-            else t.snext[0] = it;
+            tile = tile.x < 0 ? tile : claim();
+            if (s + 1 < kStStages) t.stile[s] = tile;
+            else t.snext[0] = tile;
         }
     }
     __syncthreads();
     for (int s = 0; s + 1 < kStStages; ++s) {
-        const int it = t.sitem[s];
+        const int2 tile = t.stile[s];
         __syncthreads(); // every thread has read the slot st_issue rewrites
-        st_issue<T, V>(D, Ain, sm, s, it, ntx);
+        st_issue<T, V>(D, Ain, sm, s, tile, L);
     }
     bool timeout = false;
     int k = 0;
@@ -895,15 +916,15 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
         const int s = k % kStStages;
         // refill the stage the block finished with in the last iteration
         // with the tile claimed then; thread 0 claims the one after it
-        const int nit = t.snext[k & 1];
-        st_issue<T, V>(D, Ain, sm, (k + kStStages - 1) % kStStages, nit, ntx);
-        int claimed = -1;
-        if (tid == 0 && nit >= 0) claimed = claim();
+        const int2 nt = t.snext[k & 1];
+        st_issue<T, V>(D, Ain, sm, (k + kStStages - 1) % kStStages, nt, L);
+        int2 claimed = make_int2(-1, 0);
+        if (tid == 0 && nt.x >= 0) claimed = claim();
         const bool got = mbar_wait(smem_addr(t.full + s), (unsigned)(k / kStStages) & 1u);
-        const int it = got ? t.sitem[s] : -1;
-        if (got && it >= 0) {
-            const int y = it / ntx;
-            const int x0 = (it - y * ntx) * G::W + tid * V;
+        const int2 tile = got ? t.stile[s] : make_int2(-1, 0);
+        const int y = tile.x;
+        if (y >= 0) {
+            const int x0 = tile.y + tid * V;
             if (x0 < D.pitch) { // threads past the pitch have no node
                 const unsigned char *sb = sm + s * G::STAGE_B;
                 float c[V][kPop];
@@ -938,7 +959,7 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
         if (tid == 0) t.snext[(k + 1) & 1] = claimed;
         // every thread is done with stage s and has read snext[k & 1]; stop
         // together at the end of the work or after a wait ran out
-        if (__syncthreads_or((!got) | (it < 0))) {
+        if (__syncthreads_or(y < 0)) {
             timeout = __syncthreads_or(!got);
             break;
         }
