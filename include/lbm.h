@@ -303,10 +303,13 @@ int lbm_link_forces_noalloc(float *d_dist, int64_t plane_stride, int32_t pitch,
  *                        caller and must outlive the batch; while a batch
  *                        call runs, no other call may use them.
  *   lbm_batch_autotune   times the stream-collide tile shapes (128x1, 64x2,
- *                        32x4 threads) on the batch, `reps` launches each,
- *                        without changing any state, and keeps the fastest;
- *                        *choice receives its index and *best_ms its mean
- *                        time per launch (either may be NULL).
+ *                        32x4 threads: choices 0-2) and, with BF16 or FP16
+ *                        storage, the staged kernel (choice 3, the default
+ *                        there; choice 0 is the FP32 default) on the batch,
+ *                        `reps` launches each, without changing any state,
+ *                        and keeps the fastest; *choice receives its index
+ *                        and *best_ms its mean time per launch (either may
+ *                        be NULL).
  *   lbm_batch_step       enqueues nsteps steps of every instance on the
  *                        batch's stream; call lbm_batch_sync before using a
  *                        handle on its own again.

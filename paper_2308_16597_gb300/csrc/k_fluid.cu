@@ -411,9 +411,9 @@ __device__ __forceinline__ void prefetch_block(const Dev &D, const T *__restrict
     }
 }
 
-template <typename T, int V>
+template <typename T, int V, bool kSharedFlags>
 __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
-                                        float (&c)[V][kPop], int x0, int y, const uint8_t *flp);
+                                        float (&c)[V][kPop], int x0, int y, const uint8_t *sflags);
 
 // pf_x < 0: no look-ahead prefetch here (the caller issues its own).
 template <typename T, int V, int mode = kSCAll>
@@ -513,16 +513,18 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
         }
     }
     if (!act) return;
-    sc_tail<T, V>(D, Ain, Aout, c, x0, y, D.flags + (long long)y * D.pitch + x0);
+    sc_tail<T, V, false>(D, Ain, Aout, c, x0, y, nullptr);
 }
 
 // The part of a stream-collide update after the interior pulls, for the V
 // nodes x0 .. x0 + V - 1 of row y whose pulled values c holds: the side
 // nodes' wall or seam planes, the collision, the stores and the numeric
-// check.  flp points at the nodes' flags (global or shared memory).
-template <typename T, int V>
+// check.  The nodes' flags are read from sflags (shared memory) or, without
+// kSharedFlags, from the flag map where they are used (an address computed
+// earlier and held cost the one-block-per-tile kernels registers).
+template <typename T, int V, bool kSharedFlags>
 __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
-                                        float (&c)[V][kPop], int x0, int y, const uint8_t *flp)
+                                        float (&c)[V][kPop], int x0, int y, const uint8_t *sflags)
 {
     using E = Elem<T>;
     using VW = typename Vec<T, V>::W;
@@ -556,6 +558,7 @@ __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain,
         // nodes (and the padding past nx) are zeroed after
         bool fluid[2];
         // both nodes' flags in one 2-byte load (x0 is even)
+        const uint8_t *flp = kSharedFlags ? sflags : D.flags + (long long)y * D.pitch + x0;
         const unsigned short fl2 = *reinterpret_cast<const unsigned short *>(flp);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -589,7 +592,7 @@ __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain,
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             const int x = x0 + k;
-            const uint8_t fl = flp[k];
+            const uint8_t fl = kSharedFlags ? sflags[k] : D.flags[(long long)y * D.pitch + x];
             gen[k] = false;
             if (x < D.nx && fl != kSolid) {
                 // newborn nodes and the first and last rows belong to
@@ -796,20 +799,23 @@ __device__ __forceinline__ void bulk_to_smem(unsigned dst, const void *src, unsi
 }
 
 // Shared memory after the stages: a `full` barrier per stage (complete when
-// the tile's copies have landed), the tile of each stage (row y and first
-// column xs; y < 0: no tile), and two slots that pass the next claimed tile
-// from thread 0 to the block.
+// the tile's copies have landed), the tile of each stage (instance, row y,
+// first column xs; y < 0: no tile), and two slots that pass the next claimed
+// tile from thread 0 to the block.
 template <typename T, int V>
 struct StTail {
     unsigned long long *full;
-    int2 *stile, *snext;
+    int4 *stile, *snext;
+    int *chunk; // thread 0's claim state: the index of the last tile handed out, tiles left in its chunk
     __device__ explicit StTail(unsigned char *sm)
     {
         full = reinterpret_cast<unsigned long long *>(sm + kStStages * StGeo<T, V>::STAGE_B);
-        stile = reinterpret_cast<int2 *>(full + kStStages);
+        stile = reinterpret_cast<int4 *>(sm + kStStages * StGeo<T, V>::STAGE_B + 32);
         snext = stile + kStStages;
+        chunk = reinterpret_cast<int *>(snext + 2);
     }
 };
+static_assert(kStStages * 8 <= 32 && 32 + (kStStages + 2) * 16 + 8 <= 128, "staged stream-collide: tail layout");
 
 // The copy a thread issues for every tile, fixed for the launch: copy c
 // (planes 0..13, then the flags) belongs to lane c % 4 of warp c / 4, so no
@@ -834,20 +840,21 @@ __device__ __forceinline__ StLane st_lane(unsigned char *sm)
                   (ey(d) + 1) | (dx == 1 ? 4 : 0) | (dx == -1 ? 8 : 0)};
 }
 
-// The block loads the tile of row y, columns xs .. xs + W - 1, into stage s,
-// each thread issuing its copy; thread 0 first records the tile and
+// The block loads the tile of row y, columns xs .. xs + W - 1 (of the
+// instance whose state D and Ain hold), into stage s, each thread issuing its
+// copy; thread 0 first records the tile and
 // announces the bytes (a copy that lands before the announcement only makes
 // the byte count negative for a while; the phase cannot complete before
 // thread 0's arrival).  y < 0: nothing to load, the stage's phase completes
 // at once and tells the block to stop.  Every thread passes the same tile.
 template <typename T, int V>
-__device__ __forceinline__ void st_issue(const Dev &D, const T *__restrict__ Ain, unsigned char *sm, int s, int2 tile,
+__device__ __forceinline__ void st_issue(const Dev &D, const T *__restrict__ Ain, unsigned char *sm, int s, int4 tile,
                                          const StLane &L)
 {
     using G = StGeo<T, V>;
     const StTail<T, V> t(sm);
     const unsigned b = smem_addr(t.full + s);
-    const int y = tile.x, xs = tile.y;
+    const int y = tile.y, xs = tile.z;
     const int n = min(G::W, D.pitch - xs); // nodes of the tile
     if (threadIdx.x == 0) {
         t.stile[s] = tile;
@@ -871,9 +878,20 @@ __device__ __forceinline__ void st_issue(const Dev &D, const T *__restrict__ Ain
     bulk_to_smem(dst, Ain + e, (unsigned)((n + halo) * (int)sizeof(T)), b);
 }
 
-template <typename T, int V>
-__global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
-    k_stream_collide_staged(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ntx, int nitems)
+// Tiles claimed per step of the work counter: consecutive tiles, the first
+// looked up, the others found from it (next column, next row, or, at the
+// end of an instance, looked up), so the counter's round trip and the
+// lookup's dependent loads come once per kStChunk tiles.
+constexpr int kStChunk = 4;
+
+// The staged loop over the tiles a policy P hands out: P::decode(it) maps a
+// tile index to a tile (int4: instance, row, first column; row -1 past the
+// end), P::next(t, it) gives tile it from tile it - 1, P::dev / ain / aout
+// give an instance's state and buffers, P::ctr the work counter (in chunks
+// of kStChunk tiles) and the done count after it, P::err the error word a
+// timeout is recorded in.
+template <typename T, int V, typename P>
+__device__ __forceinline__ void staged_body(const P &pol)
 {
     using G = StGeo<T, V>;
     using E = Elem<T>;
@@ -882,14 +900,20 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
     const StTail<T, V> t(sm);
     const int tid = threadIdx.x;
     const StLane L = st_lane<T, V>(sm);
-    unsigned *ctr = &D.status->sc_next;
-    // thread 0: the next tile from the work counter as (row, first column),
-    // row -1 past the end
-    auto claim = [&]() {
-        const int it = (int)atomicAdd(ctr, 1u);
-        if (it >= nitems) return make_int2(-1, 0);
-        const int y = it / ntx;
-        return make_int2(y, (it - y * ntx) * G::W);
+    unsigned *ctr = pol.ctr();
+    // thread 0: the tile after `last`, the last one it handed out
+    auto claim = [&](int4 last) {
+        int it = t.chunk[0], left = t.chunk[1];
+        if (left == 0) {
+            it = (int)atomicAdd(ctr, 1u) * kStChunk;
+            left = kStChunk;
+            last = pol.decode(it);
+        } else {
+            last = pol.next(last, ++it);
+        }
+        t.chunk[0] = it;
+        t.chunk[1] = left - 1;
+        return last;
     };
 
     // thread 0 claims the first kStStages tiles (after the first one past
@@ -897,18 +921,19 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
     if (tid == 0) {
         for (int s = 0; s < kStStages; ++s) mbar_init(smem_addr(t.full + s), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        int2 tile = make_int2(0, 0);
+        t.chunk[1] = 0;
+        int4 tile = make_int4(0, 0, 0, 0);
         for (int s = 0; s < kStStages; ++s) {
-            tile = tile.x < 0 ? tile : claim();
+            tile = tile.y < 0 ? tile : claim(tile);
             if (s + 1 < kStStages) t.stile[s] = tile;
             else t.snext[0] = tile;
         }
     }
     __syncthreads();
     for (int s = 0; s + 1 < kStStages; ++s) {
-        const int2 tile = t.stile[s];
+        const int4 tile = t.stile[s];
         __syncthreads(); // every thread has read the slot st_issue rewrites
-        st_issue<T, V>(D, Ain, sm, s, tile, L);
+        st_issue<T, V>(pol.dev(tile.x), pol.ain(tile.x), sm, s, tile, L);
     }
     bool timeout = false;
     int k = 0;
@@ -916,15 +941,16 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
         const int s = k % kStStages;
         // refill the stage the block finished with in the last iteration
         // with the tile claimed then; thread 0 claims the one after it
-        const int2 nt = t.snext[k & 1];
-        st_issue<T, V>(D, Ain, sm, (k + kStStages - 1) % kStStages, nt, L);
-        int2 claimed = make_int2(-1, 0);
-        if (tid == 0 && nt.x >= 0) claimed = claim();
+        const int4 nt = t.snext[k & 1];
+        st_issue<T, V>(pol.dev(nt.x), pol.ain(nt.x), sm, (k + kStStages - 1) % kStStages, nt, L);
+        int4 claimed = make_int4(0, -1, 0, 0);
+        if (tid == 0 && nt.y >= 0) claimed = claim(nt);
         const bool got = mbar_wait(smem_addr(t.full + s), (unsigned)(k / kStStages) & 1u);
-        const int2 tile = got ? t.stile[s] : make_int2(-1, 0);
-        const int y = tile.x;
+        const int4 tile = got ? t.stile[s] : make_int4(0, -1, 0, 0);
+        const int y = tile.y;
         if (y >= 0) {
-            const int x0 = tile.y + tid * V;
+            const Dev &D = pol.dev(tile.x);
+            const int x0 = tile.z + tid * V;
             if (x0 < D.pitch) { // threads past the pitch have no node
                 const unsigned char *sb = sm + s * G::STAGE_B;
                 float c[V][kPop];
@@ -953,7 +979,7 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
                         }
                     }
                 }
-                sc_tail<T, V>(D, Ain, Aout, c, x0, y, sb + G::FLAGS_OFF + tid * V);
+                sc_tail<T, V, true>(D, pol.ain(tile.x), pol.aout(tile.x), c, x0, y, sb + G::FLAGS_OFF + tid * V);
             }
         }
         if (tid == 0) t.snext[(k + 1) & 1] = claimed;
@@ -965,7 +991,7 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
         }
     }
     if (timeout) {
-        if (tid == 0) atomicOr(&D.status->err, kErrTimeout);
+        if (tid == 0) atomicOr(pol.err(), kErrTimeout);
         // copies may still be in flight into the stages of iterations k ..
         // k + kStStages - 1: wait for them (bounded) before leaving
         for (int j = k; j < k + kStStages; ++j)
@@ -974,12 +1000,96 @@ __global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
     }
     if (tid == 0) {
         __threadfence();
-        if (atomicAdd(&D.status->sc_done, 1u) == gridDim.x - 1) { // the last block: reset for the next launch
-            D.status->sc_next = 0u;
-            D.status->sc_done = 0u;
+        if (atomicAdd(ctr + 1, 1u) == gridDim.x - 1) { // the last block: reset for the next launch
+            ctr[0] = 0u;
+            ctr[1] = 0u;
             __threadfence();
         }
     }
+}
+
+// One instance: tiles in row order, ntx per row.
+template <typename T, int V>
+struct StSingle {
+    const Dev &D;
+    const T *Ain;
+    T *Aout;
+    int ntx, nitems;
+    __device__ int4 decode(int it) const
+    {
+        if (it >= nitems) return make_int4(0, -1, 0, 0);
+        const int y = it / ntx;
+        return make_int4(0, y, (it - y * ntx) * StGeo<T, V>::W, 0);
+    }
+    __device__ int4 next(int4 t, int it) const
+    {
+        if (t.y < 0 || it >= nitems) return make_int4(0, -1, 0, 0);
+        t.z += StGeo<T, V>::W;
+        if (t.z >= D.pitch) {
+            t.z = 0;
+            ++t.y;
+        }
+        return t;
+    }
+    __device__ const Dev &dev(int) const { return D; }
+    __device__ const T *ain(int) const { return Ain; }
+    __device__ T *aout(int) const { return Aout; }
+    __device__ unsigned *ctr() const { return &D.status->sc_next; }
+    __device__ unsigned *err() const { return &D.status->err; }
+};
+static_assert(offsetof(Status, sc_done) == offsetof(Status, sc_next) + sizeof(unsigned), "work counter pair");
+
+// A batch: the tiles of all instances, instance by instance, found through
+// the batch's stream-collide records and buckets of the 128 x 1 tile shape
+// (one 128 V-node row tile per block); a timeout is recorded in instance 0's
+// error word (the batch's sync reads every instance's).
+template <typename T, int V>
+struct StBatch {
+    const InstArgs *__restrict__ I;
+    const ScInst *__restrict__ sc;
+    const int *__restrict__ bucket;
+    int shift, n, total, parity;
+    unsigned *counter;
+    __device__ int4 decode(int it) const
+    {
+        if (it >= total) return make_int4(0, -1, 0, 0);
+        const int i = sc_find(sc, bucket, shift, n, it);
+        int bx, by;
+        sc_tile(sc + i, it, bx, by);
+        return make_int4(i, by, bx * StGeo<T, V>::W, 0);
+    }
+    __device__ int4 next(int4 t, int it) const
+    {
+        if (t.y < 0 || it >= total) return make_int4(0, -1, 0, 0);
+        const Dev &D = I[t.x].D;
+        t.z += StGeo<T, V>::W;
+        if (t.z >= D.pitch) {
+            t.z = 0;
+            if (++t.y >= D.ny) return decode(it); // the next instance
+        }
+        return t;
+    }
+    __device__ const Dev &dev(int i) const { return I[i].D; }
+    __device__ const T *ain(int i) const { return static_cast<const T *>(I[i].A[parity ^ I[i].poff]); }
+    __device__ T *aout(int i) const { return static_cast<T *>(I[i].A[parity ^ I[i].poff ^ 1]); }
+    __device__ unsigned *ctr() const { return counter; }
+    __device__ unsigned *err() const { return &I[0].D.status->err; }
+};
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
+    k_stream_collide_staged(const Dev D, const T *__restrict__ Ain, T *__restrict__ Aout, int ntx, int nitems)
+{
+    staged_body<T, V>(StSingle<T, V>{D, Ain, Aout, ntx, nitems});
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kSCThreads, LBM_ST_MINB)
+    k_stream_collide_staged_batch(const InstArgs *__restrict__ I, const ScInst *__restrict__ sc,
+                                  const int *__restrict__ bucket, int shift, int n, int total, int parity,
+                                  unsigned *counter)
+{
+    staged_body<T, V>(StBatch<T, V>{I, sc, bucket, shift, n, total, parity, counter});
 }
 
 template <typename T>
@@ -1120,6 +1230,19 @@ cudaError_t stream_collide_m(const Dev &D, const void *Ain, void *Aout, cudaStre
     return cudaGetLastError();
 }
 
+// Blocks of a staged kernel the GPU holds at once (carveout set to the
+// largest shared-memory share first).
+template <typename K>
+int staged_resident(K kernel, int smem)
+{
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSCThreads, smem) != cudaSuccess) return 0;
+    return max(1, sms * per_sm);
+}
+
 // The staged kernel's grid: as many blocks as the GPU holds at once (they
 // claim tiles from the work counter, so blocks that start late, behind the
 // boundary kernel's, take fewer).
@@ -1128,22 +1251,25 @@ cudaError_t stream_collide_staged(const Dev &D, const void *Ain, void *Aout, cud
 {
     using G = StGeo<T, V>;
     static int resident = 0;
-    if (!resident) {
-        cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<T, V>,
-                                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_staged<T, V>, kSCThreads,
-                                                          G::SMEM_B);
-        if (e != cudaSuccess) return e;
-        resident = max(1, sms * per_sm);
-    }
+    if (!resident && !(resident = staged_resident(k_stream_collide_staged<T, V>, G::SMEM_B)))
+        return cudaErrorInvalidValue;
     const int ntx = (D.pitch + G::W - 1) / G::W;
     const int nitems = ntx * D.ny;
     k_stream_collide_staged<T, V><<<min(resident, nitems), kSCThreads, G::SMEM_B, s>>>(
         D, static_cast<const T *>(Ain), static_cast<T *>(Aout), ntx, nitems);
+    return cudaGetLastError();
+}
+
+template <typename T, int V>
+cudaError_t stream_collide_staged_batch(const InstArgs *I, const ScInst *sc, const int *bucket, int shift, int n,
+                                        int total, int parity, unsigned *counter, cudaStream_t s)
+{
+    using G = StGeo<T, V>;
+    static int resident = 0;
+    if (!resident && !(resident = staged_resident(k_stream_collide_staged_batch<T, V>, G::SMEM_B)))
+        return cudaErrorInvalidValue;
+    k_stream_collide_staged_batch<T, V><<<min(resident, total), kSCThreads, G::SMEM_B, s>>>(I, sc, bucket, shift, n,
+                                                                                          total, parity, counter);
     return cudaGetLastError();
 }
 
@@ -1262,6 +1388,19 @@ cudaError_t launch_boundary_batch(const InstArgs *I, const int *start, int n, in
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_stream_collide_staged_batch(const InstArgs *I, const ScInst *sc, const int *bucket, int shift,
+                                               int n, int total, int storage, int parity, unsigned *counter,
+                                               cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    switch (storage) {
+    case LBM_STORE_BF16:
+        return stream_collide_staged_batch<__nv_bfloat16, 2>(I, sc, bucket, shift, n, total, parity, counter, s);
+    case LBM_STORE_FP16: return stream_collide_staged_batch<__half, 2>(I, sc, bucket, shift, n, total, parity, counter, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 int stream_collide_batch_resident(int storage, dim3 block)

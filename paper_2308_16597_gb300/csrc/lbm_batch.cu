@@ -18,20 +18,27 @@ constexpr size_t kAlign = 256;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Stream-collide tile shapes (threads x rows of one block, 128 threads).
+// Stream-collide tile shapes (threads x rows of one block, 128 threads),
+// and with BF16 / FP16 storage a fourth candidate: the staged kernel
+// (persistent blocks, 128 x 1 row tiles copied into shared memory ahead).
 const dim3 kTiles[] = {dim3(128, 1), dim3(64, 2), dim3(32, 4)};
 constexpr int kNumTiles = 3;
+constexpr int kStagedTile = kNumTiles;
+int candidates(int storage) { return storage == LBM_STORE_FP32 ? kNumTiles : kNumTiles + 1; }
+// The block shape a candidate's block offsets and records are built for.
+dim3 tile_shape(int t) { return kTiles[t == kStagedTile ? 0 : t]; }
 
 // Stream-collide bucket table: at most 4 (n + 1) buckets.
 int bucket_cap(int n) { return 4 * (n + 1); }
 
 // Device tables: InstArgs [n], block offsets [phases][n + 1], stream-collide
-// records [n] and buckets [4 (n + 1)].
+// records [n] and buckets [4 (n + 1)], the staged kernel's work counter.
 size_t table_bytes(int n)
 {
     return round_up((size_t)n * sizeof(InstArgs), kAlign) +
            round_up((size_t)kBatchPhases * (n + 1) * sizeof(int), kAlign) +
-           round_up((size_t)n * sizeof(ScInst), kAlign) + round_up((size_t)bucket_cap(n) * sizeof(int), kAlign);
+           round_up((size_t)n * sizeof(ScInst), kAlign) + round_up((size_t)bucket_cap(n) * sizeof(int), kAlign) +
+           kAlign;
 }
 
 } // namespace
@@ -46,6 +53,7 @@ struct lbm_batch {
     int *d_start = nullptr; // [kBatchPhases][n + 1]
     ScInst *d_sc = nullptr; // [n] stream-collide records
     int *d_bucket = nullptr; // [4 (n + 1)] stream-collide buckets
+    unsigned *d_counter = nullptr; // [2] the staged kernel's work counter and done count
     int sc_shift = 0;
     int total[kBatchPhases] = {};
     int tile = 0, sc_resident = 1, links_ahead = 1;
@@ -78,7 +86,7 @@ int upload_starts(lbm_batch *b)
     for (int ph = 0; ph < kBatchPhases; ++ph) b->total[ph] = 0;
     for (int i = 0; i < b->n; ++i) {
         int blocks[kBatchPhases];
-        batch_blocks(b->hs[i]->D, kTiles[b->tile], blocks);
+        batch_blocks(b->hs[i]->D, tile_shape(b->tile), blocks);
         for (int ph = 0; ph < kBatchPhases; ++ph) {
             st[(size_t)ph * (b->n + 1) + i] = b->total[ph];
             b->total[ph] += blocks[ph];
@@ -89,7 +97,7 @@ int upload_starts(lbm_batch *b)
     // the exact reciprocal of the latter) and buckets of 2^shift blocks,
     // each holding the instance its first block belongs to
     const int V = b->storage == LBM_STORE_FP32 ? 1 : 2;
-    const int tx = (int)kTiles[b->tile].x;
+    const int tx = (int)tile_shape(b->tile).x;
     std::vector<ScInst> sc(b->n);
     for (int i = 0; i < b->n; ++i) {
         ScInst &e = sc[i];
@@ -115,11 +123,21 @@ int upload_starts(lbm_batch *b)
     BCK(b, cudaMemcpyAsync(b->d_sc, sc.data(), sc.size() * sizeof(ScInst), cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaMemcpyAsync(b->d_bucket, bk.data(), bk.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
-    b->sc_resident = stream_collide_batch_resident(b->storage, kTiles[b->tile]);
+    b->sc_resident = stream_collide_batch_resident(b->storage, tile_shape(b->tile));
     return LBM_OK;
 }
 
 const int *starts(const lbm_batch *b, int ph) { return b->d_start + (size_t)ph * (b->n + 1); }
+
+// Stream-collide of every instance with the current candidate.
+cudaError_t launch_sc(const lbm_batch *b, int par, cudaStream_t st)
+{
+    if (b->tile == kStagedTile)
+        return launch_stream_collide_staged_batch(b->d_inst, b->d_sc, b->d_bucket, b->sc_shift, b->n,
+                                                  b->total[kBStream], b->storage, par, b->d_counter, st);
+    return launch_stream_collide_batch(b->d_inst, b->d_sc, b->d_bucket, b->sc_shift, b->n, b->total[kBStream],
+                                       b->storage, par, kTiles[b->tile], b->sc_resident, st);
+}
 
 // One step of every instance, in the order of lbm_step: links -> particles
 // (and raster) -> flags -> stream-collide beside the general path.
@@ -135,8 +153,7 @@ int enqueue_batch_step(lbm_batch *b, int par, cudaStream_t st)
     BCK(b, cudaStreamWaitEvent(b->side, b->fork, 0));
     BCK(b, launch_boundary_batch(I, starts(b, kBBoundary), n, b->total[kBBoundary], b->storage, par, b->side));
     BCK(b, cudaEventRecord(b->join, b->side));
-    BCK(b, launch_stream_collide_batch(I, b->d_sc, b->d_bucket, b->sc_shift, n, b->total[kBStream], b->storage,
-                                       par, kTiles[b->tile], b->sc_resident, st));
+    BCK(b, launch_sc(b, par, st));
     BCK(b, cudaStreamWaitEvent(st, b->join, 0));
     return LBM_OK;
 }
@@ -211,6 +228,7 @@ int lbm_batch_create(lbm_batch **out, lbm_handle *const *hs, int32_t n, void *d_
     b->poff.assign(n, 0);
     b->n = n;
     b->storage = hs[0]->D.storage;
+    b->tile = b->storage == LBM_STORE_FP32 ? 0 : kStagedTile; // until lbm_batch_autotune picks
     b->parity = 0; // instance i runs at parity b->parity ^ poff[i]
     b->stream = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_workspace);
@@ -221,6 +239,8 @@ int lbm_batch_create(lbm_batch **out, lbm_handle *const *hs, int32_t n, void *d_
     b->d_sc = reinterpret_cast<ScInst *>(ws + at);
     at += round_up((size_t)n * sizeof(ScInst), kAlign);
     b->d_bucket = reinterpret_cast<int *>(ws + at);
+    at += round_up((size_t)bucket_cap(n) * sizeof(int), kAlign);
+    b->d_counter = reinterpret_cast<unsigned *>(ws + at);
     auto fail = [&](int code) {
         lbm_batch_destroy(b);
         return code;
@@ -246,7 +266,8 @@ int lbm_batch_create(lbm_batch **out, lbm_handle *const *hs, int32_t n, void *d_
         cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
         return fail(LBM_ECUDA);
     if (cudaMemcpyAsync(b->d_inst, inst.data(), n * sizeof(InstArgs), cudaMemcpyHostToDevice, b->stream) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(unsigned), b->stream) != cudaSuccess)
         return fail(LBM_ECUDA);
     if (prepare_links_batch(std::max(b->zone_max, 4), b->storage, &b->links_smem, &b->links_ahead) !=
         cudaSuccess)
@@ -268,20 +289,14 @@ int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *choice, double *best
     float best = 1e30f;
     int best_tile = b->tile;
     int rc = LBM_OK;
-    for (int t = 0; t < kNumTiles && !rc; ++t) {
+    for (int t = 0; t < candidates(b->storage) && !rc; ++t) {
         b->tile = t;
         if ((rc = upload_starts(b))) break;
         for (int w = 0; w < 2 && !rc; ++w)
-            if (launch_stream_collide_batch(b->d_inst, b->d_sc, b->d_bucket, b->sc_shift, b->n,
-                                            b->total[kBStream], b->storage, b->parity, kTiles[t],
-                                            b->sc_resident, b->stream) != cudaSuccess)
-                rc = fail_cuda(b, cudaErrorLaunchFailure);
+            if (launch_sc(b, b->parity, b->stream) != cudaSuccess) rc = fail_cuda(b, cudaErrorLaunchFailure);
         if (rc || cudaEventRecord(e0, b->stream) != cudaSuccess) break;
         for (int r = 0; r < reps && !rc; ++r)
-            if (launch_stream_collide_batch(b->d_inst, b->d_sc, b->d_bucket, b->sc_shift, b->n,
-                                            b->total[kBStream], b->storage, b->parity, kTiles[t],
-                                            b->sc_resident, b->stream) != cudaSuccess)
-                rc = fail_cuda(b, cudaErrorLaunchFailure);
+            if (launch_sc(b, b->parity, b->stream) != cudaSuccess) rc = fail_cuda(b, cudaErrorLaunchFailure);
         float ms = 0.f;
         if (rc || cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {

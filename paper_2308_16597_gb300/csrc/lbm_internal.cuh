@@ -916,5 +916,11 @@ cudaError_t launch_stream_collide_batch(const InstArgs *I, const ScInst *sc, con
 cudaError_t launch_boundary_batch(const InstArgs *I, const int *start, int n, int total, int storage, int parity,
                                   cudaStream_t s);
 int stream_collide_batch_resident(int storage, dim3 block);
+// The staged stream-collide over a batch (BF16 / FP16 storage): sc and
+// bucket built for the 128 x 1 tile shape; counter: two zeroed words of
+// device memory the launch leaves zeroed.
+cudaError_t launch_stream_collide_staged_batch(const InstArgs *I, const ScInst *sc, const int *bucket, int shift,
+                                               int n, int total, int storage, int parity, unsigned *counter,
+                                               cudaStream_t s);
 
 } // namespace lbm

@@ -105,7 +105,7 @@ def test_batch_equals_each_instance_alone(storage):
     b = lbm.Batch(sims)
     b.step(steps // 2)
     choice = b.autotune(2)
-    assert choice in (0, 1, 2)
+    assert choice in ((0, 1, 2) if storage == lbm.LBM_STORE_FP32 else (0, 1, 2, 3))
     b.step(steps - steps // 2)
     b.sync()
     assert b.launch_count() == 5 * steps  # links, particles (+ raster), flags, stream-collide, boundary
