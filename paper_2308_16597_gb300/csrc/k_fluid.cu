@@ -734,15 +734,19 @@ constexpr int kStStages = LBM_ST_STAGES;
 #endif
 constexpr unsigned long long kStWaitNs = 1000000000ull;
 
-template <typename T, int V>
+template <typename T, int V, bool kInst = false>
 struct StGeo {
     static constexpr int W = kSCThreads * V;                     // nodes of a tile
     static constexpr int H = 16 / (int)sizeof(T);                // halo elements on a pulled side
     static constexpr int SEG_B = (W + 2 * H) * (int)sizeof(T);   // bytes of a plane segment
     static constexpr int FLAGS_OFF = kPop * SEG_B;               // the tile's flags
-    static constexpr int STAGE_B = (FLAGS_OFF + W + 127) / 128 * 128;
+    // with kInst (a batch): the tile's instance record (state, buffers)
+    static constexpr int INST_OFF = (FLAGS_OFF + W + 15) / 16 * 16;
+    static constexpr int INST_B = kInst ? (int)sizeof(InstArgs) : 0;
+    static constexpr int STAGE_B = (INST_OFF + INST_B + 127) / 128 * 128;
     static constexpr int SMEM_B = kStStages * STAGE_B + 128;     // + barriers and tile slots
 };
+static_assert(sizeof(InstArgs) % 16 == 0, "an instance record is copied whole by a bulk copy");
 // Planes whose source lies one node to the side (e_x != 0): they copy H
 // elements more.
 __host__ __device__ constexpr int shifted_planes()
@@ -802,15 +806,15 @@ __device__ __forceinline__ void bulk_to_smem(unsigned dst, const void *src, unsi
 // the tile's copies have landed), the tile of each stage (instance, row y,
 // first column xs; y < 0: no tile), and two slots that pass the next claimed
 // tile from thread 0 to the block.
-template <typename T, int V>
+template <typename T, int V, bool kInst = false>
 struct StTail {
     unsigned long long *full;
     int4 *stile, *snext;
     int *chunk; // thread 0's claim state: the index of the last tile handed out, tiles left in its chunk
     __device__ explicit StTail(unsigned char *sm)
     {
-        full = reinterpret_cast<unsigned long long *>(sm + kStStages * StGeo<T, V>::STAGE_B);
-        stile = reinterpret_cast<int4 *>(sm + kStStages * StGeo<T, V>::STAGE_B + 32);
+        full = reinterpret_cast<unsigned long long *>(sm + kStStages * StGeo<T, V, kInst>::STAGE_B);
+        stile = reinterpret_cast<int4 *>(sm + kStStages * StGeo<T, V, kInst>::STAGE_B + 32);
         snext = stile + kStStages;
         chunk = reinterpret_cast<int *>(snext + 2);
     }
@@ -818,8 +822,8 @@ struct StTail {
 static_assert(kStStages * 8 <= 32 && 32 + (kStStages + 2) * 16 + 8 <= 128, "staged stream-collide: tail layout");
 
 // The copy a thread issues for every tile, fixed for the launch: copy c
-// (planes 0..13, then the flags) belongs to lane c % 4 of warp c / 4, so no
-// warp carries the copies alone.  Three registers: the copy (-1 none, kPop
+// (planes 0..13, then the flags, then in a batch the tile's instance record)
+// belongs to lane c % 4 of warp c / 4, so no warp carries the copies alone.  Three registers: the copy (-1 none, kPop
 // the flags), its shared-memory destination in stage 0, and for a plane its
 // row shift e_y + 1 (bits 0-1) and whether it pulls from x - 1 (bit 2) or
 // x + 1 (bit 3), i.e. takes H elements more on that side.
@@ -828,11 +832,12 @@ struct StLane {
     unsigned dst;
     int meta;
 };
-template <typename T, int V>
+template <typename T, int V, bool kInst = false>
 __device__ __forceinline__ StLane st_lane(unsigned char *sm)
 {
-    using G = StGeo<T, V>;
+    using G = StGeo<T, V, kInst>;
     const int lane = threadIdx.x & 31, c = (threadIdx.x >> 5) * 4 + lane;
+    if (kInst && lane < 4 && c == kPop + 1) return StLane{c, smem_addr(sm + G::INST_OFF), 0}; // the record
     if (lane >= 4 || c > kPop) return StLane{-1, 0u, 0};
     if (c == kPop) return StLane{c, smem_addr(sm + G::FLAGS_OFF), 0};
     const int d = pdir(c), dx = ex(d);
@@ -847,22 +852,28 @@ __device__ __forceinline__ StLane st_lane(unsigned char *sm)
 // the byte count negative for a while; the phase cannot complete before
 // thread 0's arrival).  y < 0: nothing to load, the stage's phase completes
 // at once and tells the block to stop.  Every thread passes the same tile.
-template <typename T, int V>
+template <typename T, int V, bool kInst = false>
 __device__ __forceinline__ void st_issue(const Dev &D, const T *__restrict__ Ain, unsigned char *sm, int s, int4 tile,
-                                         const StLane &L)
+                                         const StLane &L, const InstArgs *rec = nullptr)
 {
-    using G = StGeo<T, V>;
-    const StTail<T, V> t(sm);
+    using G = StGeo<T, V, kInst>;
+    const StTail<T, V, kInst> t(sm);
     const unsigned b = smem_addr(t.full + s);
     const int y = tile.y, xs = tile.z;
     const int n = min(G::W, D.pitch - xs); // nodes of the tile
     if (threadIdx.x == 0) {
         t.stile[s] = tile;
         if (y < 0) mbar_arrive(b);
-        else mbar_arrive_tx(b, (unsigned)(n * (kPop * (int)sizeof(T) + 1) + shifted_planes() * 16 + D.sc_extra_tx));
+        else
+            mbar_arrive_tx(b, (unsigned)(n * (kPop * (int)sizeof(T) + 1) + shifted_planes() * 16 + G::INST_B +
+                                         D.sc_extra_tx));
     }
     if (y < 0 || L.c < 0) return;
     const unsigned dst = L.dst + (unsigned)(s * G::STAGE_B);
+    if (kInst && L.c == kPop + 1) { // the tile's instance record
+        bulk_to_smem(dst, rec, (unsigned)G::INST_B, b);
+        return;
+    }
     if (L.c == kPop) { // the tile's flags
         bulk_to_smem(dst, D.flags + (long long)y * D.pitch + xs, (unsigned)n, b);
         return;
@@ -893,13 +904,14 @@ constexpr int kStChunk = 4;
 template <typename T, int V, typename P>
 __device__ __forceinline__ void staged_body(const P &pol)
 {
-    using G = StGeo<T, V>;
+    constexpr bool kInst = P::kInst;
+    using G = StGeo<T, V, kInst>;
     using E = Elem<T>;
     using VW = typename Vec<T, V>::W;
     extern __shared__ __align__(128) unsigned char sm[];
-    const StTail<T, V> t(sm);
+    const StTail<T, V, kInst> t(sm);
     const int tid = threadIdx.x;
-    const StLane L = st_lane<T, V>(sm);
+    const StLane L = st_lane<T, V, kInst>(sm);
     unsigned *ctr = pol.ctr();
     // thread 0: the tile after `last`, the last one it handed out
     auto claim = [&](int4 last) {
@@ -933,7 +945,7 @@ __device__ __forceinline__ void staged_body(const P &pol)
     for (int s = 0; s + 1 < kStStages; ++s) {
         const int4 tile = t.stile[s];
         __syncthreads(); // every thread has read the slot st_issue rewrites
-        st_issue<T, V>(pol.dev(tile.x), pol.ain(tile.x), sm, s, tile, L);
+        st_issue<T, V, kInst>(pol.dev(tile.x), pol.ain(tile.x), sm, s, tile, L, pol.rec(tile.x));
     }
     bool timeout = false;
     int k = 0;
@@ -942,17 +954,20 @@ __device__ __forceinline__ void staged_body(const P &pol)
         // refill the stage the block finished with in the last iteration
         // with the tile claimed then; thread 0 claims the one after it
         const int4 nt = t.snext[k & 1];
-        st_issue<T, V>(pol.dev(nt.x), pol.ain(nt.x), sm, (k + kStStages - 1) % kStStages, nt, L);
+        st_issue<T, V, kInst>(pol.dev(nt.x), pol.ain(nt.x), sm, (k + kStStages - 1) % kStStages, nt, L,
+                              pol.rec(nt.x));
         int4 claimed = make_int4(0, -1, 0, 0);
         if (tid == 0 && nt.y >= 0) claimed = claim(nt);
         const bool got = mbar_wait(smem_addr(t.full + s), (unsigned)(k / kStStages) & 1u);
         const int4 tile = got ? t.stile[s] : make_int4(0, -1, 0, 0);
         const int y = tile.y;
         if (y >= 0) {
-            const Dev &D = pol.dev(tile.x);
+            const unsigned char *sb = sm + s * G::STAGE_B;
+            // a batch's instance record came with the tile
+            const InstArgs *rec = reinterpret_cast<const InstArgs *>(sb + G::INST_OFF);
+            const Dev &D = kInst ? rec->D : pol.dev(tile.x);
             const int x0 = tile.z + tid * V;
             if (x0 < D.pitch) { // threads past the pitch have no node
-                const unsigned char *sb = sm + s * G::STAGE_B;
                 float c[V][kPop];
 #pragma unroll
                 for (int p = 0; p < kPop; ++p) {
@@ -979,7 +994,17 @@ __device__ __forceinline__ void staged_body(const P &pol)
                         }
                     }
                 }
-                sc_tail<T, V, true>(D, pol.ain(tile.x), pol.aout(tile.x), c, x0, y, sb + G::FLAGS_OFF + tid * V);
+                const T *ain;
+                T *aout;
+                if constexpr (kInst) {
+                    const int par = pol.parity ^ rec->poff;
+                    ain = static_cast<const T *>(rec->A[par]);
+                    aout = static_cast<T *>(rec->A[par ^ 1]);
+                } else {
+                    ain = pol.ain(tile.x);
+                    aout = pol.aout(tile.x);
+                }
+                sc_tail<T, V, true>(D, ain, aout, c, x0, y, sb + G::FLAGS_OFF + tid * V);
             }
         }
         if (tid == 0) t.snext[(k + 1) & 1] = claimed;
@@ -1011,6 +1036,7 @@ __device__ __forceinline__ void staged_body(const P &pol)
 // One instance: tiles in row order, ntx per row.
 template <typename T, int V>
 struct StSingle {
+    static constexpr bool kInst = false;
     const Dev &D;
     const T *Ain;
     T *Aout;
@@ -1032,6 +1058,7 @@ struct StSingle {
         return t;
     }
     __device__ const Dev &dev(int) const { return D; }
+    __device__ const InstArgs *rec(int) const { return nullptr; }
     __device__ const T *ain(int) const { return Ain; }
     __device__ T *aout(int) const { return Aout; }
     __device__ unsigned *ctr() const { return &D.status->sc_next; }
@@ -1045,6 +1072,7 @@ static_assert(offsetof(Status, sc_done) == offsetof(Status, sc_next) + sizeof(un
 // error word (the batch's sync reads every instance's).
 template <typename T, int V>
 struct StBatch {
+    static constexpr bool kInst = true;
     const InstArgs *__restrict__ I;
     const ScInst *__restrict__ sc;
     const int *__restrict__ bucket;
@@ -1056,13 +1084,13 @@ struct StBatch {
         const int i = sc_find(sc, bucket, shift, n, it);
         int bx, by;
         sc_tile(sc + i, it, bx, by);
-        return make_int4(i, by, bx * StGeo<T, V>::W, 0);
+        return make_int4(i, by, bx * StGeo<T, V, true>::W, 0);
     }
     __device__ int4 next(int4 t, int it) const
     {
         if (t.y < 0 || it >= total) return make_int4(0, -1, 0, 0);
         const Dev &D = I[t.x].D;
-        t.z += StGeo<T, V>::W;
+        t.z += StGeo<T, V, true>::W;
         if (t.z >= D.pitch) {
             t.z = 0;
             if (++t.y >= D.ny) return decode(it); // the next instance
@@ -1070,6 +1098,7 @@ struct StBatch {
         return t;
     }
     __device__ const Dev &dev(int i) const { return I[i].D; }
+    __device__ const InstArgs *rec(int i) const { return I + i; }
     __device__ const T *ain(int i) const { return static_cast<const T *>(I[i].A[parity ^ I[i].poff]); }
     __device__ T *aout(int i) const { return static_cast<T *>(I[i].A[parity ^ I[i].poff ^ 1]); }
     __device__ unsigned *ctr() const { return counter; }
@@ -1264,7 +1293,7 @@ template <typename T, int V>
 cudaError_t stream_collide_staged_batch(const InstArgs *I, const ScInst *sc, const int *bucket, int shift, int n,
                                         int total, int parity, unsigned *counter, cudaStream_t s)
 {
-    using G = StGeo<T, V>;
+    using G = StGeo<T, V, true>;
     static int resident = 0;
     if (!resident && !(resident = staged_resident(k_stream_collide_staged_batch<T, V>, G::SMEM_B)))
         return cudaErrorInvalidValue;
