@@ -53,8 +53,9 @@ extern "C" {
 #define LBM_ENUMERIC (-3)  /* non-finite density or temperature on the device */
 #define LBM_EDOMAIN (-4)   /* a particle crossed a cavity wall */
 #define LBM_EOVERFLOW (-5) /* a line of the fixed index array holds two links */
-#define LBM_ETIMEOUT (-6)  /* a bounded device wait gave up (reserved: no kernel of
-                              this library waits on another) */
+#define LBM_ETIMEOUT (-6)  /* a bounded device wait gave up: the staged
+                              stream-collide (BF16 / FP16 storage) waits at most
+                              about a second for each tile's copies */
 #define LBM_ECUDA (-7)     /* a CUDA runtime call failed */
 #define LBM_EBOUNDS (-8)   /* an index outside the buffer it addresses, skipped
                               (reported only by builds with -DLBM_CHECK) */

@@ -39,6 +39,23 @@ def test_every_declared_entry_point_is_exported(lib):
     assert set(names) == set(lbm.exported_symbols())
 
 
+def test_header_constants_match_the_binding():
+    """Every LBM_* integer constant the header defines (error codes, storage
+    formats, boundary and parameter flags) has the same value in the Python
+    binding, and every one the binding defines is in the header."""
+    import re
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    defs = {}
+    for name, val in re.findall(r"#define (LBM_[A-Z0-9_]+) \(?(-?[0-9]+)u?\)?", text):
+        defs[name] = int(val)
+    assert len(defs) >= 20
+    for name, val in defs.items():
+        assert getattr(lbm, name) == val, name
+    for name in dir(lbm):
+        if re.fullmatch(r"LBM_(E[A-Z]+|OK|STORE_[A-Z0-9]+|FLAG_[A-Z_]+|BC_[A-Z_]+)", name):
+            assert name in defs, name
+
+
 def test_build_targets_sm_103a_only():
     """Every translation unit and the link step get exactly one -gencode,
     arch=compute_103a,code=sm_103a (the GPU-side check of the loaded code is
