@@ -501,6 +501,9 @@ def run_ours(args, wl):
             sampler.stop()
         line["ensemble"] = run_ensemble(args, summary=True)
         line["served"] = run_served(args, summary=True)
+        bf16 = argparse.Namespace(**dict(vars(args), storage="bf16"))
+        line["ensemble_bf16"] = run_ensemble(bf16, summary=True)
+        line["served_bf16"] = run_served(bf16, summary=True)
     else:
         sampler.stop()
     if not args.no_cpu_baseline:
@@ -512,11 +515,18 @@ def run_ours(args, wl):
 
 
 # ------------------------------------------------------------------------ batched ensemble
+# lbm_batch_autotune's choices: three block shapes of the one-block-per-tile
+# kernel, and (BF16 / FP16 storage) the staged kernel over the batch
+TILE_NAMES = ["128x1", "64x2", "32x4", "staged"]
+TILE_KERNELS = ["k_stream_collide_batch"] * 3 + ["k_stream_collide_staged_batch"]
+
+
 def run_ensemble(args, summary: bool = False):
     """64 uneven cavities stepped as one batch (one graph per step, tile shape
     from the autotuner): aggregate MLUPS over all instances.  summary: called
-    from the headline run on one GPU (FP32, K steps in the headline's number
-    of windows); returns the key's dict instead of printing a line."""
+    from the headline run on one GPU (FP32 and BF16, K steps in the
+    headline's number of windows); returns the key's dict instead of
+    printing a line."""
     import torch
     from paper_2308_16597_gb300 import build as B, lbm
 
@@ -577,9 +587,9 @@ def run_ensemble(args, summary: bool = False):
                 "particles": int(sum(len(w.particles) for w in wls)), "storage": args.storage,
                 "value": value, "unit": UNIT, "ms_per_step": max_ms / args.steps,
                 "windows_ms_per_step": [w / args.steps for w in win_ms],
-                "tile": ["128x1", "64x2", "32x4"][tile], "gpu_launches_per_window": int(launches),
+                "tile": TILE_NAMES[tile], "gpu_launches_per_window": int(launches),
                 "whole_step_hbm_frac": B_LU * nodes / (max_ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"],
-                "stream_collide": {"kernel": "k_stream_collide_batch", "avg_launch_ms": sc_ms,
+                "stream_collide": {"kernel": TILE_KERNELS[tile], "avg_launch_ms": sc_ms,
                                    "achieved_gbs": achieved, "frac": achieved / peaks["hbm_gbs"],
                                    "time_from": "the autotuner's timing of the chosen tile shape"},
                 "clocks": clk}
@@ -590,13 +600,13 @@ def run_ensemble(args, summary: bool = False):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "ensemble64_seed4", "instances": len(wls), "nodes": nodes,
                            "particles": int(sum(len(w.particles) for w in wls)),
-                           "storage": args.storage, "tile": ["128x1", "64x2", "32x4"][tile],
+                           "storage": args.storage, "tile": TILE_NAMES[tile],
                            "parallelism": "replicas%d" % world,
                            "l2": "no flush: %.2f GB of distributions, %.0fx the 129 MB L2"
                                  % (nodes * B_LU / 1e9, nodes * B_LU / 129e6)},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                             "kernel": "k_stream_collide_batch",
+                             "kernel": TILE_KERNELS[tile],
                              "algorithmic_bytes_per_launch": B_LU * nodes, "avg_launch_ms": sc_ms,
                              "peak_source": peaks["source"] + " (hbm_gbs)",
                              "kernel_times_from": "the autotuner's timing of the chosen tile shape"},
@@ -628,8 +638,8 @@ def run_served(args, summary: bool = False):
     steps) through the request loop: aggregate MLUPS over the wall time from
     the first arrival to the last result, p50/p99 per-step and per-request
     latency.  summary: called from the headline run on one GPU, the first 10
-    requests of the same stream (FP32); returns the key's dict instead of
-    printing a line."""
+    requests of the same stream (FP32 and BF16); returns the key's dict
+    instead of printing a line."""
     import torch
     from paper_2308_16597_gb300 import build as B, lbm
 
