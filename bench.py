@@ -322,7 +322,9 @@ def config_of(wl, args):
             "radius": float(p["r"][0]) if len(p) else None,
             "minor_axis": float(p["b"][0]) if len(p) and p["b"][0] > 0 else None,
             "storage": getattr(args, "storage", "fp32"), "links": getattr(args, "links", "index"),
-            "stream_collide": getattr(args, "stream_collide", "staged"),
+            # the kernel that ran: FP32 storage always takes one block per row tile
+            "stream_collide": ("one_block_per_tile" if getattr(args, "storage", "fp32") == "fp32"
+                               or getattr(args, "stream_collide", "staged") == "unstaged" else "staged"),
             "density_ratio": float(p["rho"][0]) if len(p) else None,
             "parallelism": "replicas%d" % args.gpus,
             "l2": "no flush: each step reads one distribution buffer and writes the other, %.2f GB "
@@ -746,8 +748,9 @@ def main(argv=None):
                     help="links from the fixed index array (default) or by direct addressing (the paper's "
                          "comparison, Table 1)")
     ap.add_argument("--stream-collide", choices=["staged", "unstaged"], default="staged",
-                    help="whole-lattice stream-collide kernel: persistent blocks staging row tiles in shared "
-                         "memory (default), or one block per tile reading global memory (comparison)")
+                    help="whole-lattice stream-collide kernel with BF16 / FP16 storage: persistent blocks "
+                         "staging row tiles in shared memory (default), or one block per tile reading global "
+                         "memory (comparison; FP32 storage always runs the latter)")
     ap.add_argument("--storage", choices=sorted(STORAGE_CODES), default="fp32",
                     help="plane storage: FP32 (the headline), or BF16 / scaled FP16 deviations")
     args = ap.parse_args(argv)
