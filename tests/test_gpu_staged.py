@@ -138,3 +138,32 @@ def test_bounded_wait_reports_timeout_and_the_device_stays_usable():
     drho, ux, uy, T = ok.fields()
     assert np.all(drho == 0.0) and np.all(T == 0.0)
     ok.close()
+
+
+def test_batched_bounded_wait_reports_timeout():
+    """The staged kernel over a batch waits the same bounded way: with
+    LBM_FLAG_TEST_WAIT_TIMEOUT on its instances every wait runs out, the
+    timeout lands in instance 0's error word, and lbm_batch_sync reports
+    LBM_ETIMEOUT; a new batch on the same device then runs normally."""
+    dom = W.cavity(300, 40)
+    prm = W.base_params(0.05, 0.71, 1e-4)
+    sims = [lbm.Simulation(dom, None, prm, storage=lbm.LBM_STORE_BF16, flags=lbm.LBM_FLAG_TEST_WAIT_TIMEOUT)
+            for _ in range(2)]
+    b = lbm.Batch(sims)
+    b.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        b.sync()
+    assert e.value.code == lbm.LBM_ETIMEOUT
+    b.close()
+    for s in sims:
+        s.close()
+    sims = [lbm.Simulation(dom, None, prm, storage=lbm.LBM_STORE_BF16) for _ in range(2)]
+    b = lbm.Batch(sims)
+    b.step(3)
+    b.sync()
+    for s in sims:
+        drho, ux, uy, T = s.fields()
+        assert np.all(drho == 0.0) and np.all(T == 0.0)
+    b.close()
+    for s in sims:
+        s.close()
