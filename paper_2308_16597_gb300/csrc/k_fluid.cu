@@ -191,11 +191,16 @@ __device__ __forceinline__ bool phys_ok(float rho, float T)
 
 // MRT collision in deviation form (Eq. f with Guo forcing in moment space,
 // Eq. g), in place on c[14] (one node per lane of F).  ok: whether each
-// node's density and temperature are finite and physical.
-template <typename F>
+// node's density and temperature are finite and physical.  kS: c holds the
+// populations times 2^12 (FP16 storage's scale) and receives the results
+// times 2^12; every product of a scaled term takes the scale through a
+// scaled constant or one exact multiplication, so the results are those of
+// the unscaled collision times 2^12, bit for bit.
+template <typename F, bool kS = false>
 __device__ __forceinline__ void collide_t(const Dev &D, F *c, bool &ok0, bool &ok1)
 {
     using O = FOps<F>;
+    auto K = [&](float plain, int scaled) { return kS ? D.ksc[scaled] : plain; };
     const F f0 = c[0], f1 = c[1], f2 = c[2], f3 = c[3], f4 = c[4];
     const F f5 = c[5], f6 = c[6], f7 = c[7], f8 = c[8];
     // pair sums and differences shared by the moments
@@ -203,14 +208,16 @@ __device__ __forceinline__ void collide_t(const Dev &D, F *c, bool &ok0, bool &o
     const F s56 = O::add(f5, f6), d56 = O::sub(f5, f6), s78 = O::add(f7, f8), d87 = O::sub(f8, f7);
     const F sa = O::add(u13, u24), sd = O::add(s56, s78);
     const F drho = O::add(O::add(f0, sa), sd);
-    const F rho = O::add(O::bc(1.f), drho);
+    const F rho = kS ? O::fma(drho, O::bc(1.f / kHalfScale), O::bc(1.f)) : O::add(O::bc(1.f), drho);
     const F e = O::add(d56, d87), g = O::sub(s56, s78);
     const F jx = O::add(d13, e), jy = O::add(d24, g);
     const F T = O::add(O::add(O::add(c[9], c[10]), O::add(c[11], c[12])), c[13]);
+    const F Tu = kS ? O::mul(T, O::bc(1.f / kHalfScale)) : T; // the temperature itself
     const F Fx = O::bc(D.bfx);
-    const F Fy = O::fma(O::mul(rho, O::bc(D.gbeta)), O::sub(T, O::bc(D.T0)), O::bc(D.bfy));
-    const F inv = O::rcp(rho);
-    const F ux = O::mul(O::fma(O::bc(0.5f), Fx, jx), inv), uy = O::mul(O::fma(O::bc(0.5f), Fy, jy), inv);
+    const F Fy = O::fma(O::mul(rho, O::bc(D.gbeta)), O::sub(Tu, O::bc(D.T0)), O::bc(D.bfy));
+    const F FxS = kS ? O::bc(D.ksc[kScBfx]) : Fx, FyS = kS ? O::mul(Fy, O::bc(kHalfScale)) : Fy;
+    const F inv = O::rcp(rho), invS = kS ? O::mul(inv, O::bc(1.f / kHalfScale)) : inv;
+    const F ux = O::mul(O::fma(O::bc(0.5f), FxS, jx), invS), uy = O::mul(O::fma(O::bc(0.5f), FyS, jy), invS);
     const F m1 = O::fma(O::bc(2.f), sd, O::fma(O::bc(-4.f), f0, O::sub(O::bc(0.f), sa))); // -4 f0 - sa + 2 sd
     const F m2 = O::fma(O::bc(4.f), f0, O::fma(O::bc(-2.f), sa, sd));                     // 4 f0 - 2 sa + sd
     const F m4 = O::fma(O::bc(-2.f), d13, e); // 2 (f3 - f1) + (f5 - f6) + (f8 - f7)
@@ -219,22 +226,25 @@ __device__ __forceinline__ void collide_t(const Dev &D, F *c, bool &ok0, bool &o
     const F m8 = O::sub(O::add(f5, f7), O::add(f6, f8));
     const F uu = O::fma(ux, ux, O::mul(uy, uy));
     const F uF = O::fma(ux, Fx, O::mul(uy, Fy));
-    const F ru = O::mul(O::mul(O::bc(3.f), rho), uu);
+    const F ru = O::mul(O::mul(O::bc(K(3.f, kScThree)), rho), uu);
     // a_i = post-collision moment i / |M_i|^2, the rates and norms folded
     // into the coefficients k*: m_i - s_i (m_i - m_eq,i) + (1 - s_i / 2) F_i
     const F a0 = O::mul(drho, O::bc(1.f / 9.f));
     const F a1 = O::fma(O::bc(D.kA1), m1,
-                        O::fma(O::bc(D.kB1), O::fma(O::bc(-2.f), drho, ru), O::mul(O::bc(D.kC1), uF)));
-    const F a2 = O::fma(O::bc(D.kA2), m2, O::fma(O::bc(D.kB2), O::sub(drho, ru), O::mul(O::bc(-D.kC2), uF)));
-    const F a3 = O::mul(O::add(jx, Fx), O::bc(1.f / 6.f)), a5 = O::mul(O::add(jy, Fy), O::bc(1.f / 6.f));
+                        O::fma(O::bc(D.kB1), O::fma(O::bc(-2.f), drho, ru), O::mul(O::bc(K(D.kC1, kScC1)), uF)));
+    const F a2 =
+        O::fma(O::bc(D.kA2), m2, O::fma(O::bc(D.kB2), O::sub(drho, ru), O::mul(O::bc(-K(D.kC2, kScC2)), uF)));
+    const F a3 = O::mul(O::add(jx, FxS), O::bc(1.f / 6.f)), a5 = O::mul(O::add(jy, FyS), O::bc(1.f / 6.f));
     const F rux = O::mul(rho, ux), ruy = O::mul(rho, uy);
-    const F a4 = O::fma(O::bc(D.kA4), m4, O::fma(O::bc(-D.kB4), rux, O::mul(O::bc(-D.kC4), Fx)));
-    const F a6 = O::fma(O::bc(D.kA4), m6, O::fma(O::bc(-D.kB4), ruy, O::mul(O::bc(-D.kC4), Fy)));
+    const F a4 = O::fma(O::bc(D.kA4), m4, O::fma(O::bc(-K(D.kB4, kScB4)), rux, O::mul(O::bc(-D.kC4), FxS)));
+    const F a6 = O::fma(O::bc(D.kA4), m6, O::fma(O::bc(-K(D.kB4, kScB4)), ruy, O::mul(O::bc(-D.kC4), FyS)));
     const F pxx = O::fma(ux, ux, O::mul(O::sub(O::bc(0.f), uy), uy)); // ux^2 - uy^2
     const F fxx = O::fma(ux, Fx, O::mul(O::sub(O::bc(0.f), uy), Fy)); // ux Fx - uy Fy
     const F fxy = O::fma(ux, Fy, O::mul(uy, Fx));                     // ux Fy + uy Fx
-    const F a7 = O::fma(O::bc(D.kA7), m7, O::fma(O::bc(D.kB7), O::mul(rho, pxx), O::mul(O::bc(D.kC7), fxx)));
-    const F a8 = O::fma(O::bc(D.kA7), m8, O::fma(O::bc(D.kB7), O::mul(rux, uy), O::mul(O::bc(D.kC8), fxy)));
+    const F a7 = O::fma(O::bc(D.kA7), m7,
+                        O::fma(O::bc(K(D.kB7, kScB7)), O::mul(rho, pxx), O::mul(O::bc(K(D.kC7, kScC7)), fxx)));
+    const F a8 = O::fma(O::bc(D.kA7), m8,
+                        O::fma(O::bc(K(D.kB7, kScB7)), O::mul(rux, uy), O::mul(O::bc(K(D.kC8, kScC8)), fxy)));
     // f = M^T a
     const F base = O::fma(O::bc(-2.f), a2, O::sub(a0, a1)), dbase = O::fma(O::bc(2.f), a1, O::add(a0, a2));
     const F h34 = O::fma(O::bc(-2.f), a4, a3), h56 = O::fma(O::bc(-2.f), a6, a5);
@@ -255,8 +265,8 @@ __device__ __forceinline__ void collide_t(const Dev &D, F *c, bool &ok0, bool &o
     const F n3 = O::fma(O::bc(-4.f), g0, O::add(O::add(g1, g2), O::add(g3, g4)));
     const F n4 = O::sub(O::add(g1, g3), O::add(g2, g4));
     const F b0 = O::mul(T, O::bc(0.2f));
-    const F b1 = O::fma(O::bc(D.kG1), n1, O::mul(O::bc(D.kG2), O::mul(T, ux)));
-    const F b2 = O::fma(O::bc(D.kG1), n2, O::mul(O::bc(D.kG2), O::mul(T, uy)));
+    const F b1 = O::fma(O::bc(D.kG1), n1, O::mul(O::bc(K(D.kG2, kScG2)), O::mul(Tu, ux)));
+    const F b2 = O::fma(O::bc(D.kG1), n2, O::mul(O::bc(K(D.kG2, kScG2)), O::mul(Tu, uy)));
     const F b3 = O::fma(O::bc(D.kG3), n3, O::mul(O::bc(-D.kG4), T));
     const F b4 = O::mul(O::bc(D.kG5), n4);
     const F b03 = O::add(b0, b3);
@@ -266,10 +276,10 @@ __device__ __forceinline__ void collide_t(const Dev &D, F *c, bool &ok0, bool &o
     c[12] = O::add(O::sub(b03, b1), b4);
     c[13] = O::sub(O::sub(b03, b2), b4);
     if constexpr (sizeof(F) == sizeof(float)) {
-        ok0 = phys_ok(reinterpret_cast<const float &>(rho), reinterpret_cast<const float &>(T));
+        ok0 = phys_ok(reinterpret_cast<const float &>(rho), reinterpret_cast<const float &>(Tu));
         ok1 = ok0;
     } else {
-        const float2 r2 = reinterpret_cast<const float2 &>(rho), t2 = reinterpret_cast<const float2 &>(T);
+        const float2 r2 = reinterpret_cast<const float2 &>(rho), t2 = reinterpret_cast<const float2 &>(Tu);
         ok0 = phys_ok(r2.x, t2.x);
         ok1 = phys_ok(r2.y, t2.y);
     }
@@ -350,6 +360,37 @@ struct Vec<__half, 2> {
         v[1] = f.y * (1.f / kHalfScale);
     }
     __device__ static W pack(const float *v) { return __floats2half2_rn(v[0] * kHalfScale, v[1] * kHalfScale); }
+};
+
+// Loads and stores of the fused stream-collide kernels: FP16 values stay in
+// their stored scale (times 2^12) and the collision runs on the scaled
+// values (collide_t<F, true>, the same bits); every other storage as Elem
+// and Vec.
+template <typename T>
+struct Io {
+    static constexpr bool kScaled = false;
+    __device__ static float ld(T v) { return Elem<T>::ld(v); }
+    __device__ static T st(float v) { return Elem<T>::st(v); }
+};
+template <>
+struct Io<__half> {
+    static constexpr bool kScaled = true;
+    __device__ static float ld(__half v) { return __half2float(v); }
+    __device__ static __half st(float v) { return __float2half_rn(v); }
+};
+template <typename T, int V>
+struct VecIo : Vec<T, V> {
+};
+template <>
+struct VecIo<__half, 2> {
+    using W = __half2;
+    __device__ static void unpack(W w, float *v)
+    {
+        const float2 f = __half22float2(w);
+        v[0] = f.x;
+        v[1] = f.y;
+    }
+    __device__ static W pack(const float *v) { return __floats2half2_rn(v[0], v[1]); }
 };
 
 // Whether warp tile t of row y is within reach of a particle this step.
@@ -454,7 +495,7 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
             const T *src = b0 + (long long)p * D.ps - (long long)dy * D.pitch;
             const long long e = (long long)(src - Ain); // element index, for the bounds checks
             float v[V];
-            if (in_bounds(D, e, D.a_elems - V + 1)) Vec<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src)), v);
+            if (in_bounds(D, e, D.a_elems - V + 1)) VecIo<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src)), v);
             else {
 #pragma unroll
                 for (int k = 0; k < V; ++k) v[k] = 0.f;
@@ -464,13 +505,13 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
                 for (int k = 0; k < V; ++k) c[k][p] = v[k];
             } else if (dx == 1) { // pull from x - 1
                 float l = __shfl_up_sync(kFull, v[V - 1], 1);
-                if (lane == 0) l = in_bounds(D, e - 1, D.a_elems) ? E::ld(__ldg(src - 1)) : 0.f;
+                if (lane == 0) l = in_bounds(D, e - 1, D.a_elems) ? Io<T>::ld(__ldg(src - 1)) : 0.f;
                 c[0][p] = l;
 #pragma unroll
                 for (int k = 1; k < V; ++k) c[k][p] = v[k - 1];
             } else { // pull from x + 1
                 float r = __shfl_down_sync(kFull, v[0], 1);
-                if (lane == 31) r = in_bounds(D, e + V, D.a_elems) ? E::ld(__ldg(src + V)) : 0.f;
+                if (lane == 31) r = in_bounds(D, e + V, D.a_elems) ? Io<T>::ld(__ldg(src + V)) : 0.f;
 #pragma unroll
                 for (int k = 0; k + 1 < V; ++k) c[k][p] = v[k + 1];
                 c[V - 1][p] = r;
@@ -489,7 +530,7 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
             }
             const T *src = Ain + (long long)p * D.ps + (long long)(rowok ? ys : 0) * D.pitch;
             float v[V];
-            if (act && rowok) Vec<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src + x0)), v);
+            if (act && rowok) VecIo<T, V>::unpack(__ldg(reinterpret_cast<const VW *>(src + x0)), v);
             else {
 #pragma unroll
                 for (int k = 0; k < V; ++k) v[k] = 0.f;
@@ -499,13 +540,13 @@ __device__ __forceinline__ void sc_body(const Dev &D, const T *__restrict__ Ain,
                 for (int k = 0; k < V; ++k) c[k][p] = v[k];
             } else if (dx == 1) { // pull from x - 1
                 float l = __shfl_up_sync(kFull, v[V - 1], 1);
-                if (lane == 0) l = (act && rowok && x0 >= 1) ? E::ld(__ldg(src + x0 - 1)) : 0.f;
+                if (lane == 0) l = (act && rowok && x0 >= 1) ? Io<T>::ld(__ldg(src + x0 - 1)) : 0.f;
                 c[0][p] = l;
 #pragma unroll
                 for (int k = 1; k < V; ++k) c[k][p] = v[k - 1];
             } else { // pull from x + 1
                 float r = __shfl_down_sync(kFull, v[0], 1);
-                if (lane == 31) r = (act && rowok && x0 + V < D.pitch) ? E::ld(__ldg(src + x0 + V)) : 0.f;
+                if (lane == 31) r = (act && rowok && x0 + V < D.pitch) ? Io<T>::ld(__ldg(src + x0 + V)) : 0.f;
 #pragma unroll
                 for (int k = 0; k + 1 < V; ++k) c[k][p] = v[k + 1];
                 c[V - 1][p] = r;
@@ -526,8 +567,8 @@ template <typename T, int V, bool kSharedFlags>
 __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain, T *__restrict__ Aout,
                                         float (&c)[V][kPop], int x0, int y, const uint8_t *sflags)
 {
-    using E = Elem<T>;
     using VW = typename Vec<T, V>::W;
+    constexpr float kIo = Io<T>::kScaled ? kHalfScale : 1.f; // the side pulls' values in the kernel's scale
     const bool interior = y >= 1 && y + 1 < D.ny;
     // The nodes x = 0 and x = nx - 1 of the rows between the first and the
     // last: the planes that pull across a side wall or the periodic seam
@@ -541,7 +582,7 @@ __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain,
         if (x0 == 0) {
 #pragma unroll
             for (int p = 0; p < kPop; ++p)
-                if (ex(pdir(p)) == 1) c[0][p] = side_pull(D, Ain, 0, y, p);
+                if (ex(pdir(p)) == 1) c[0][p] = side_pull(D, Ain, 0, y, p) * kIo;
         }
         const int kl = D.nx - 1 - x0;
 #pragma unroll
@@ -549,7 +590,7 @@ __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain,
             if (k == kl) {
 #pragma unroll
                 for (int p = 0; p < kPop; ++p)
-                    if (ex(pdir(p)) == -1) c[k][p] = side_pull(D, Ain, D.nx - 1, y, p);
+                    if (ex(pdir(p)) == -1) c[k][p] = side_pull(D, Ain, D.nx - 1, y, p) * kIo;
             }
     }
     bool ok = true, gen[V], anygen = false;
@@ -574,7 +615,7 @@ __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain,
 #pragma unroll
         for (int p = 0; p < kPop; ++p) cc[p] = make_float2(c[0][p], c[1][p]);
         bool ok0, ok1;
-        collide_t<float2>(D, cc, ok0, ok1);
+        collide_t<float2, Io<T>::kScaled>(D, cc, ok0, ok1);
 #pragma unroll
         for (int p = 0; p < kPop; ++p) {
             c[0][p] = cc[p].x;
@@ -615,7 +656,7 @@ __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain,
 #pragma unroll
             for (int k = 0; k < V; ++k) v[k] = c[k][p];
             if (in_bounds(D, d0 + (long long)p * D.ps, D.a_elems - V + 1))
-                *reinterpret_cast<VW *>(dst + (long long)p * D.ps) = Vec<T, V>::pack(v);
+                *reinterpret_cast<VW *>(dst + (long long)p * D.ps) = VecIo<T, V>::pack(v);
         }
     } else {
 #pragma unroll
@@ -624,7 +665,7 @@ __device__ __forceinline__ void sc_tail(const Dev &D, const T *__restrict__ Ain,
 #pragma unroll
                 for (int p = 0; p < kPop; ++p)
                     if (in_bounds(D, d0 + (long long)p * D.ps + k, D.a_elems))
-                        dst[(long long)p * D.ps + k] = E::st(c[k][p]);
+                        dst[(long long)p * D.ps + k] = Io<T>::st(c[k][p]);
             }
     }
     if (!ok) atomicOr(&D.status->err, kErrNumeric);
@@ -977,18 +1018,18 @@ __device__ __forceinline__ void staged_body(const P &pol)
                         c[0][p] = E::ld(seg[-dx]);
                     } else {
                         float a[2];
-                        Vec<T, V>::unpack(*reinterpret_cast<const VW *>(seg), a);
+                        VecIo<T, V>::unpack(*reinterpret_cast<const VW *>(seg), a);
                         if (dx == 0) {
                             c[0][p] = a[0];
                             c[1][p] = a[1];
                         } else if (dx == 1) { // pull from x - 1
                             float l[2];
-                            Vec<T, V>::unpack(*reinterpret_cast<const VW *>(seg - 2), l);
+                            VecIo<T, V>::unpack(*reinterpret_cast<const VW *>(seg - 2), l);
                             c[0][p] = l[1];
                             c[1][p] = a[0];
                         } else { // pull from x + 1
                             float r[2];
-                            Vec<T, V>::unpack(*reinterpret_cast<const VW *>(seg + 2), r);
+                            VecIo<T, V>::unpack(*reinterpret_cast<const VW *>(seg + 2), r);
                             c[0][p] = a[1];
                             c[1][p] = r[0];
                         }

@@ -370,6 +370,15 @@ void fill_dev(lbm_handle *h)
     D.T0 = (float)P.T0;
     D.bfx = (float)P.body_fx;
     D.bfy = (float)P.body_fy;
+    {
+        // times a power of two: exact, so the collision on scaled values
+        // rounds exactly as the one on the values themselves
+        const float sc = kHalfScale;
+        for (int i = 0; i < 12; ++i) D.ksc[i] = 0.f;
+        D.ksc[kScC1] = sc * D.kC1; D.ksc[kScC2] = sc * D.kC2; D.ksc[kScB4] = sc * D.kB4;
+        D.ksc[kScB7] = sc * D.kB7; D.ksc[kScC7] = sc * D.kC7; D.ksc[kScC8] = sc * D.kC8;
+        D.ksc[kScG2] = sc * D.kG2; D.ksc[kScThree] = sc * 3.f; D.ksc[kScBfx] = sc * D.bfx;
+    }
     for (int i = 0; i < 4; ++i) D.Twall[i] = (float)h->d.T_wall[i];
     D.g = P.g;
     D.rho_f = P.rho_f;

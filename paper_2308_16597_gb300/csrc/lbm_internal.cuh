@@ -68,6 +68,8 @@ struct Elem<__half> {
     __host__ __device__ static float ld(__half v) { return __half2float(v) * (1.f / kHalfScale); }
     __host__ __device__ static __half st(float v) { return __float2half_rn(v * kHalfScale); }
 };
+// Indices of Dev::ksc.
+enum { kScC1 = 0, kScC2, kScB4, kScB7, kScC7, kScC8, kScG2, kScThree, kScBfx, kNumSc };
 // Bytes per stored population.
 __host__ __device__ constexpr int storage_bytes(int storage) { return storage == LBM_STORE_FP32 ? 4 : 2; }
 
@@ -116,6 +118,10 @@ struct Dev {
     // the relaxation rates folded with the moment norms (see collide())
     float kA1, kB1, kC1, kA2, kB2, kC2, kA4, kB4, kC4, kA7, kB7, kC7, kC8, kG1, kG2, kG3, kG4, kG5;
     float gbeta, T0, bfx, bfy;
+    // FP16 storage: constants of the collision times the storage scale 2^12,
+    // for the fused stream-collide kernels, which collide the scaled values
+    // (kScC1 ... below; the last three words pad the record)
+    float ksc[12];
     float Twall[4];
     double g, rho_f, eps_w, s_rep;
     int fixed;
