@@ -386,6 +386,8 @@ def run_ours(args, wl):
     flags = lbm.LBM_FLAG_DIRECT_LINKS if args.links == "direct" else 0
     if args.stream_collide == "unstaged":
         flags |= lbm.LBM_FLAG_SC_UNSTAGED
+    if getattr(args, "overlap", False):
+        flags |= lbm.LBM_FLAG_OVERLAP
     sampler = NvmlSampler(dev)
     with torch.cuda.stream(stream):
         sim = lbm.Simulation(wl.domain, wl.particles, wl.params, stream=stream, storage=storage, flags=flags)
@@ -751,6 +753,9 @@ def main(argv=None):
                     help="whole-lattice stream-collide kernel with BF16 / FP16 storage: persistent blocks "
                          "staging row tiles in shared memory (default), or one block per tile reading global "
                          "memory (comparison; FP32 storage always runs the latter)")
+    ap.add_argument("--overlap", action="store_true",
+                    help="stream-collide of the tiles away from every particle beside the particle kernels "
+                         "(LBM_FLAG_OVERLAP), the rest after them")
     ap.add_argument("--storage", choices=sorted(STORAGE_CODES), default="fp32",
                     help="plane storage: FP32 (the headline), or BF16 / scaled FP16 deviations")
     args = ap.parse_args(argv)

@@ -191,15 +191,17 @@ def test_escaping_disk_raises_domain_error_and_is_held():
     s.close()
 
 
+@pytest.mark.parametrize("storage", [lbm.LBM_STORE_FP32, lbm.LBM_STORE_BF16])
 @pytest.mark.parametrize("flags", [lbm.LBM_FLAG_OVERLAP, lbm.LBM_FLAG_OVERLAP | lbm.LBM_FLAG_NO_GRAPH,
                                    lbm.LBM_FLAG_NO_GRAPH])
-def test_step_schedules_are_bit_identical(flags):
+def test_step_schedules_are_bit_identical(flags, storage):
     """Stream-collide split into a far-tile pass beside the particle kernels
-    and a near-tile pass after them gives exactly the state of the default
-    single pass after them, with or without graphs."""
+    and a near-tile pass after them (with BF16 storage both through the
+    staged kernel) gives exactly the state of the default single pass after
+    them, with or without graphs."""
     wl = W.parity_256()
-    a = lbm.Simulation(wl.domain, wl.particles, wl.params)
-    b = lbm.Simulation(wl.domain, wl.particles, wl.params, flags=flags)
+    a = lbm.Simulation(wl.domain, wl.particles, wl.params, storage=storage)
+    b = lbm.Simulation(wl.domain, wl.particles, wl.params, storage=storage, flags=flags)
     a.step(60)
     b.step(60)
     same(snapshot(a), snapshot(b))
