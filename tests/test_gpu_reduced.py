@@ -183,3 +183,27 @@ def test_crop1024_against_oracle_after_1000_steps(storage):
         assert rl2 <= bound, (storage, k, rl2)
     assert dpos <= bpos
     sim.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+def test_full_size_4000_cavity_two_steps_in_reduced_storage(storage):
+    """The benchmark's 4000^2 / 4800-disk workload in 16-bit storage, in the
+    launch configuration the benchmark's reduced-storage leg times (the
+    staged stream-collide): owner map bit-exact at initialisation, every
+    field within 5 unit roundoffs (rel-L2) of the FP64 oracle after two
+    steps, centres within the FP32 bound."""
+    wl = W.sedimentation_4000()
+    sim = lbm.Simulation(wl.domain, wl.particles, wl.params, storage=STORAGE[storage])
+    ref = orc.Oracle(wl.domain, wl.particles, wl.params)
+    assert np.array_equal(sim.owner(), ref.owner())
+    sim.step(2)
+    assert ref.step(2) == 0
+    errs = field_errors(sim.fields(), ref.fields())
+    print("storage %s, 4000^2 x 4800 disks, 2 steps: %s"
+          % (storage, {k: "rel-L2 %.3e max-abs %.3e" % v for k, v in errs.items()}))
+    for k, (rl2, _) in errs.items():
+        assert rl2 <= TOL_FACTOR * UNIT_ROUNDOFF[storage], (storage, k, rl2)
+    pg, po = sim.particles(), ref.particles()
+    assert max(np.abs(pg["x"] - po["x"]).max(), np.abs(pg["y"] - po["y"]).max()) < 1e-4
+    sim.close()
