@@ -737,20 +737,22 @@ __global__ void __launch_bounds__(kSCThreads, V == 1 ? 10 : 9)
 
 
 // ---------------------------------------------------------------------------
-// Staged stream-collide (the default pass over the whole lattice).  The same
-// update as k_stream_collide, bit for bit, organised around shared memory:
-// a persistent grid of 128-thread blocks claims row tiles of 128 V nodes in
-// row order from a device counter, and each block keeps kStStages tiles in
-// flight.  For a tile, 14 lanes of warp 0 each issue one bulk asynchronous
-// copy (cp.async.bulk, completion counted in bytes on the stage's mbarrier)
-// of a plane's source row segment, with 16 bytes more on the side the plane
-// pulls from, and a fifteenth lane copies the tile's flags.  The block
-// collides one tile from shared memory while the copies of the next ones are
-// in flight: the memory latency overlaps the arithmetic without holding
-// registers, and every pulled value is a shared-memory load at a fixed
-// offset from one base (no shuffles, no edge loads, no per-plane address
-// arithmetic).  Rows stay in launch order, so the tiles in flight form a
-// compact band of rows, as in k_stream_collide.
+// Staged stream-collide (the whole-lattice pass with BF16 / FP16 storage).
+// The same update as k_stream_collide, bit for bit, organised around shared
+// memory: a persistent grid of 128-thread blocks takes row tiles of 128 V
+// nodes in row order from a device counter (kStChunk consecutive tiles per
+// claim, handed out one iteration ahead by thread 0), and each block keeps
+// kStStages tiles in flight.  For a tile, 15 bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on the stage's mbarrier) bring
+// the 14 planes' source row segments, each with 16 bytes more on the side
+// its plane pulls from, and the tile's flags (over a batch a sixteenth brings
+// the tile's instance record); lanes 0-3 of the four warps issue one each
+// (st_lane, st_issue).  The block collides one tile from shared memory while
+// the copies of the next ones are in flight: the memory latency overlaps the
+// arithmetic without holding registers, and every pulled value is a
+// shared-memory load at a fixed offset from one base (no shuffles, no edge
+// loads, no per-plane address arithmetic).  Rows stay in launch order, so
+// the tiles in flight form a compact band of rows, as in k_stream_collide.
 //
 // Shared memory per stage: 14 plane segments of 128 V + 2 H elements
 // (H = 16 bytes of elements; node x_s + i at element H + i), then the
